@@ -1,0 +1,246 @@
+/*
+ * catune — constraint-aware evolutionary auto-tuning hot path for B300 (sm_103a).
+ *
+ * C ABI of libcatune.so.  The calls follow the paper's statement of the problem
+ * ("Constraint-aware Optimization in Auto-Tuning"):
+ *   - a search space is a CSP P = (X, D, C): parameters X with finite value lists D
+ *     and constraints C, each a predicate over a subset of the parameters
+ *     (Section IV-A);
+ *   - the whole valid space is resolved before tuning (Section IV-A), giving a
+ *     sorted list of valid configurations that supports validity queries,
+ *     random valid samples and neighbour lookups;
+ *   - four optimizers (DE: Algorithm 1 and Section IV-B; PSO and Firefly:
+ *     Section IV-C; GA: Section IV-D, Algorithm 3) propose candidates, repair
+ *     invalid ones to a valid neighbour and evaluate only valid ones.
+ *
+ * Conventions
+ *   - A configuration is a tuple of value *indices* idx_k in [0, r_k).  Its key is
+ *     K = sum_k idx_k << off_k with field widths w_k = ceil(log2 r_k) (0 when
+ *     r_k == 1) and parameter n-1 in the lowest bits, so increasing key order is
+ *     Cartesian order with the last parameter varying fastest.  The total width
+ *     must be <= 64 bits.
+ *   - "d_" pointers are device pointers, owned by the caller unless stated.  Host
+ *     pointers are plain host memory.  Handles (ct_space, ct_opt) are owned by the
+ *     library; destroy them with the matching *_destroy call.
+ *   - Calls that take a stream are stream-ordered and asynchronous.  Calls that
+ *     return host values synchronise the stream and say so.
+ *   - Every call returns a ct_status; no C++ exception crosses the ABI.
+ *     ct_last_error() returns a thread-local message for the last failure.
+ *   - Errors found by kernels (a candidate outside the Cartesian domain) are
+ *     recorded in the space's device status word and returned by the next call
+ *     that synchronises (ct_space_status, ct_opt_best, ct_build_valid_space).
+ *   - Fitness is a cost (a runtime): lower is better, as in Algorithm 1
+ *     (a trial replaces x_i when f(u_i) <= f(x_i)).
+ */
+#ifndef CATUNE_H
+#define CATUNE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ct_space ct_space;
+typedef struct ct_opt ct_opt;
+typedef struct ct_batch ct_batch;
+typedef void *ct_stream; /* a cudaStream_t; NULL is the legacy default stream */
+
+typedef enum {
+    CT_OK = 0,
+    CT_ERR_INVALID_ARG = 1,  /* bad pointer/size/enum, or a candidate outside the domain */
+    CT_ERR_KEY_OVERFLOW = 2, /* sum of field widths > 64, or Cartesian size >= 2^63 */
+    CT_ERR_EMPTY_SPACE = 3,  /* no configuration satisfies the constraints */
+    CT_ERR_OOM = 4,          /* device or host allocation failed */
+    CT_ERR_CUDA = 5,         /* a CUDA runtime call failed (message in ct_last_error) */
+    CT_ERR_TIMEOUT = 6,      /* reserved: a bounded device wait expired */
+    CT_ERR_STATE = 7,        /* call out of order (e.g. repair before build) */
+    CT_ERR_LIMIT = 8         /* a documented size limit was exceeded */
+} ct_status;
+
+/* Size limits of one space. */
+#define CT_MAX_PARAMS 32
+#define CT_MAX_VALUES 4096      /* total entries over all value lists */
+#define CT_MAX_CONSTRAINTS 64
+#define CT_MAX_INSTR 4096       /* total instructions over all constraint programs */
+#define CT_MAX_STACK 16
+#define CT_MAX_POP 1024
+
+/* ------------------------------------------------------------------------- */
+/* constraint programs                                                       */
+/* ------------------------------------------------------------------------- */
+/* Each constraint c_j (Section IV-A) is a postfix program over 64-bit signed
+ * integers, terminated by CT_OP_END; the programs of all constraints are
+ * concatenated.  A constraint holds iff its final value is non-zero and not
+ * poisoned.  Arithmetic wraps (two's complement); DIV and MOD truncate toward
+ * zero; DIV or MOD by zero poisons the result; arithmetic on a poisoned operand
+ * stays poisoned; a comparison with a poisoned operand is 0; AND/OR/NOT treat a
+ * poisoned operand as false. */
+typedef enum {
+    CT_OP_END = 0,
+    CT_OP_PARAM = 1, /* push the *value* (not the index) of parameter `arg` */
+    CT_OP_CONST = 2, /* push `imm` */
+    CT_OP_ADD = 3, CT_OP_SUB = 4, CT_OP_MUL = 5, CT_OP_DIV = 6, CT_OP_MOD = 7,
+    CT_OP_NEG = 8, CT_OP_MIN = 9, CT_OP_MAX = 10,
+    CT_OP_LT = 11, CT_OP_LE = 12, CT_OP_GT = 13, CT_OP_GE = 14, CT_OP_EQ = 15, CT_OP_NE = 16,
+    CT_OP_AND = 17, CT_OP_OR = 18, CT_OP_NOT = 19
+} ct_opcode;
+
+typedef struct {
+    int32_t op;  /* ct_opcode */
+    int32_t arg; /* parameter index for CT_OP_PARAM */
+    int64_t imm; /* constant for CT_OP_CONST */
+} ct_instr;
+
+/* ------------------------------------------------------------------------- */
+/* search space (Section IV-A)                                               */
+/* ------------------------------------------------------------------------- */
+/* Defines P = (X, D, C).  n_values[k] (>= 1) is the length of parameter k's
+ * value list; values_flat holds all lists back to back (host memory, copied).
+ * program holds n_instr instructions (copied).  Host-only: lowers the
+ * constraints (scope, deepest parameter, block plan) and uploads the
+ * description to the current device.
+ * Errors: INVALID_ARG (malformed program, bad sizes), KEY_OVERFLOW, LIMIT, OOM, CUDA. */
+ct_status ct_define_space(int32_t n_params, const int32_t *n_values, const int64_t *values_flat,
+                          const ct_instr *program, int32_t n_instr, ct_space **out);
+void ct_space_destroy(ct_space *space);
+
+typedef struct {
+    int32_t n_params;
+    int32_t n_constraints;
+    int32_t key_bits;
+    int32_t n_blocks;          /* enumeration blocks chosen by the planner */
+    int32_t width[CT_MAX_PARAMS];
+    int32_t offset[CT_MAX_PARAMS];
+    int32_t n_values[CT_MAX_PARAMS];
+    uint64_t cartesian;        /* prod n_values */
+    uint64_t n_valid;          /* 0 until ct_build_valid_space */
+    int32_t built;
+} ct_space_info;
+ct_status ct_space_info_get(const ct_space *space, ct_space_info *info);
+
+/* Host helpers: value-index tuples (n rows of n_params int32) <-> keys.  Pack
+ * rejects indices outside [0, r_k) with INVALID_ARG. */
+ct_status ct_pack_keys(const ct_space *space, const int32_t *idx, int64_t n, uint64_t *keys);
+ct_status ct_unpack_keys(const ct_space *space, const uint64_t *keys, int64_t n, int32_t *idx);
+
+/* Resolves the whole valid space on the device (Section IV-A): decodes the
+ * Cartesian points, evaluates the constraints and compacts the valid keys in
+ * increasing key order into a library-owned device array.  Synchronises the
+ * stream; writes |V| to *n_valid_out.  Rebuilding replaces the previous keys.
+ * Errors: EMPTY_SPACE (|V| = 0; the space stays usable for queries), OOM, CUDA. */
+ct_status ct_build_valid_space(ct_space *space, ct_stream stream, uint64_t *n_valid_out);
+
+/* Borrowed pointer to the sorted valid keys (valid until rebuild/destroy). */
+ct_status ct_space_keys(const ct_space *space, const uint64_t **d_keys, uint64_t *n_valid);
+
+/* Registers the fitness table: d_table[rank] is the cost of the rank-th valid
+ * key (float32, caller-owned, borrowed until destroy or the next call). */
+ct_status ct_set_fitness(ct_space *space, const float *d_table, uint64_t n);
+
+/* Validity query (Section IV-A): d_rank[i] = position of d_cand[i] in the valid
+ * keys, or -1 if it is not a valid configuration (including keys outside the
+ * domain).  Binary search. */
+ct_status ct_lookup(const ct_space *space, const uint64_t *d_cand, int64_t n, int64_t *d_rank,
+                    ct_stream stream);
+
+/* Nearest-valid repair (Algorithm 1 Repair; Hamming neighbours of Section IV-A):
+ * d_out[i] = the valid key minimising (Hamming distance on value indices, key)
+ * lexicographically; a valid candidate maps to itself with distance 0.
+ * d_dist[i] = that distance (nullable).  A candidate outside the Cartesian domain
+ * is copied through with d_dist = 255 and records INVALID_ARG in the space status.
+ * Uses library-owned scratch sized for n (grown on demand).  Requires a built,
+ * non-empty space (else STATE / EMPTY_SPACE). */
+ct_status ct_repair(ct_space *space, const uint64_t *d_cand, int64_t n, uint64_t *d_out,
+                    uint8_t *d_dist, ct_stream stream);
+
+/* Repair strategy knob (tests and the autotuner): mode 0 = automatic (Hamming
+ * ball search up to a radius chosen from a cost model, then an exhaustive key
+ * scan), 1 = exhaustive scan only, 2 = ball search up to max_radius then scan. */
+ct_status ct_set_repair_mode(ct_space *space, int32_t mode, int32_t max_radius);
+
+/* Fitness lookup (memoised evaluation, Section IV-B): d_fit[i] = table[rank],
+ * +inf for an invalid key; d_rank (nullable) as in ct_lookup.  With a non-NULL
+ * opt, marks each rank in the run's memo bitmap and counts first visits as
+ * unique evaluations.  Requires ct_set_fitness. */
+ct_status ct_evaluate(ct_space *space, ct_opt *opt, const uint64_t *d_keys, int64_t n, float *d_fit,
+                      int64_t *d_rank, ct_stream stream);
+
+/* Reads and clears the space's device status word (synchronises). */
+ct_status ct_space_status(ct_space *space, ct_stream stream);
+
+/* ------------------------------------------------------------------------- */
+/* optimizers (Sections IV-B..IV-D, Table IV)                                */
+/* ------------------------------------------------------------------------- */
+typedef enum { CT_DE = 0, CT_PSO = 1, CT_FIREFLY = 2, CT_GA = 3 } ct_opt_kind;
+
+typedef struct {
+    float de_F, de_CR;               /* Table IV: 0.7, 0.6 (best1bin) */
+    float pso_w, pso_c1, pso_c2;     /* Table IV: 0.5, 3.0, 0.5 */
+    float fa_beta0, fa_gamma, fa_alpha; /* Table IV: 1.0, 1.0, 0.2 */
+    float ga_pmut;                   /* Table IV: mutation_chance 5 -> 0.2 */
+    float target;                    /* record unique evaluations when best <= target */
+} ct_opt_params;
+
+/* Fills *p with the Table IV values and target = -inf. */
+void ct_opt_params_default(ct_opt_params *p);
+
+/* Creates one run: population `pop` (3..CT_MAX_POP; DE needs >= 3), counter-based
+ * RNG seed `seed`.  Allocates the run's device state (population, positions,
+ * memo bitmap of |V| bits) on the space's device.  Requires a built space with a
+ * fitness table.  The space must outlive the run. */
+ct_status ct_opt_create(ct_space *space, ct_opt_kind kind, const ct_opt_params *params, int32_t pop,
+                        uint64_t seed, ct_opt **out);
+void ct_opt_destroy(ct_opt *opt);
+
+/* One generation is: propose -> repair -> post_repair -> evaluate -> select.
+ * Generation 0 proposes the initial valid sample (one rank per stratum of the
+ * valid list); later generations apply the optimizer's operators.  Generations
+ * must be issued in order 0, 1, 2, ...; `generation` is also the RNG counter.
+ *
+ * propose: writes pop candidate keys (unrepaired) to d_cand (caller-owned). */
+ct_status ct_propose_population(ct_opt *opt, uint32_t generation, uint64_t *d_cand, ct_stream stream);
+/* post_repair: GA mutation (replace a repaired child by a random valid Hamming
+ * neighbour with probability ga_pmut, Section IV-D); a no-op for the others. */
+ct_status ct_opt_post_repair(ct_opt *opt, uint32_t generation, uint64_t *d_keys, ct_stream stream);
+/* select: consumes the evaluated keys and their fitness (pop entries each):
+ * DE greedy selection with the u-not-in-X rule and stagnation re-draw, PSO
+ * personal/global best, Firefly brightness, GA generational replacement; updates
+ * the run's best (minimum (fitness, key) over everything evaluated). */
+ct_status ct_opt_select(ct_opt *opt, uint32_t generation, const uint64_t *d_keys, const float *d_fit,
+                        ct_stream stream);
+/* The whole generation with run-owned buffers. */
+ct_status ct_opt_step(ct_opt *opt, uint32_t generation, ct_stream stream);
+/* Runs generations [first, first + count) as one CUDA graph (captured on the
+ * first call for this count, replayed afterwards). */
+ct_status ct_opt_run_graph(ct_opt *opt, uint32_t first, uint32_t count, ct_stream stream);
+
+/* Run summary (synchronises): best key and fitness so far, unique evaluations,
+ * and the generation / unique-evaluation count at which best first reached
+ * params.target (-1 if never).  Any pointer may be NULL. */
+ct_status ct_opt_best(ct_opt *opt, uint64_t *best_key, float *best_fit, uint64_t *n_unique,
+                      int64_t *hit_generation, int64_t *hit_evals, ct_stream stream);
+
+/* Copies the run state to caller buffers (asynchronous; any pointer may be NULL):
+ * population keys [pop], population fitness [pop] (PSO: personal-best
+ * fitness), positions [pop x n_params] (PSO/Firefly). */
+ct_status ct_opt_state(const ct_opt *opt, uint64_t *d_keys, float *d_fit, float *d_pos, ct_stream stream);
+
+/* Checkpoint: serialises the whole run state (population, positions, bests,
+ * counters, memo bitmap) into a host buffer.  With buf == NULL, *len receives
+ * the size.  Load restores a run created with the same space, kind and pop.
+ * Both synchronise. */
+ct_status ct_opt_save(const ct_opt *opt, void *buf, size_t *len, ct_stream stream);
+ct_status ct_opt_load(ct_opt *opt, const void *buf, size_t len, ct_stream stream);
+
+/* ------------------------------------------------------------------------- */
+/* misc                                                                      */
+/* ------------------------------------------------------------------------- */
+const char *ct_last_error(void);
+const char *ct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CATUNE_H */

@@ -1,0 +1,347 @@
+"""Python binding of libcatune.so: the C-ABI calls under the same names, argument marshalling only.
+
+Device buffers are torch CUDA tensors (PyTorch supplies device memory and streams); every step
+of the hot path runs in the library's kernels.  There is no fallback: importing this module on a
+machine without the built library raises.
+"""
+from __future__ import annotations
+
+import ast
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcatune.so")
+
+CT_OK, CT_ERR_INVALID_ARG, CT_ERR_KEY_OVERFLOW, CT_ERR_EMPTY_SPACE = 0, 1, 2, 3
+CT_ERR_OOM, CT_ERR_CUDA, CT_ERR_TIMEOUT, CT_ERR_STATE, CT_ERR_LIMIT = 4, 5, 6, 7, 8
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "KEY_OVERFLOW", 3: "EMPTY_SPACE", 4: "OOM", 5: "CUDA",
+                6: "TIMEOUT", 7: "STATE", 8: "LIMIT"}
+KINDS = {"de": 0, "pso": 1, "firefly": 2, "ga": 3}
+
+OP = dict(END=0, PARAM=1, CONST=2, ADD=3, SUB=4, MUL=5, DIV=6, MOD=7, NEG=8, MIN=9, MAX=10, LT=11, LE=12,
+          GT=13, GE=14, EQ=15, NE=16, AND=17, OR=18, NOT=19)
+MAX_PARAMS = 32
+
+
+class CatuneError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ct_instr(C.Structure):
+    _fields_ = [("op", C.c_int32), ("arg", C.c_int32), ("imm", C.c_int64)]
+
+
+class ct_space_info(C.Structure):
+    _fields_ = [("n_params", C.c_int32), ("n_constraints", C.c_int32), ("key_bits", C.c_int32),
+                ("n_blocks", C.c_int32), ("width", C.c_int32 * MAX_PARAMS), ("offset", C.c_int32 * MAX_PARAMS),
+                ("n_values", C.c_int32 * MAX_PARAMS), ("cartesian", C.c_uint64), ("n_valid", C.c_uint64),
+                ("built", C.c_int32)]
+
+
+class ct_opt_params(C.Structure):
+    _fields_ = [(n, C.c_float) for n in ("de_F", "de_CR", "pso_w", "pso_c1", "pso_c2", "fa_beta0",
+                                         "fa_gamma", "fa_alpha", "ga_pmut", "target")]
+
+
+_lib = None
+_SIGS = {
+    "ct_define_space": [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)],
+    "ct_space_destroy": [C.c_void_p],
+    "ct_space_info_get": [C.c_void_p, C.POINTER(ct_space_info)],
+    "ct_pack_keys": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p],
+    "ct_unpack_keys": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p],
+    "ct_build_valid_space": [C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)],
+    "ct_space_keys": [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint64)],
+    "ct_set_fitness": [C.c_void_p, C.c_void_p, C.c_uint64],
+    "ct_lookup": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p],
+    "ct_repair": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
+    "ct_set_repair_mode": [C.c_void_p, C.c_int32, C.c_int32],
+    "ct_evaluate": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
+    "ct_space_status": [C.c_void_p, C.c_void_p],
+    "ct_opt_params_default": [C.POINTER(ct_opt_params)],
+    "ct_opt_create": [C.c_void_p, C.c_int32, C.POINTER(ct_opt_params), C.c_int32, C.c_uint64, C.POINTER(C.c_void_p)],
+    "ct_opt_destroy": [C.c_void_p],
+    "ct_propose_population": [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p],
+    "ct_opt_post_repair": [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p],
+    "ct_opt_select": [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p],
+    "ct_opt_step": [C.c_void_p, C.c_uint32, C.c_void_p],
+    "ct_opt_run_graph": [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p],
+    "ct_opt_best": [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_float), C.POINTER(C.c_uint64),
+                    C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_void_p],
+    "ct_opt_state": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "ct_opt_save": [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t), C.c_void_p],
+    "ct_opt_load": [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p],
+    "ct_last_error": [],
+    "ct_version": [],
+}
+
+
+def lib():
+    """The loaded C library.  Raises if it has not been built — there is no fallback path."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libcatune.so not built ({LIB_PATH}); run paper_2606_28372_b300/build.py")
+        L = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.ct_last_error.restype = C.c_char_p
+        L.ct_version.restype = C.c_char_p
+        L.ct_space_destroy.restype = None
+        L.ct_opt_destroy.restype = None
+        L.ct_opt_params_default.restype = None
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != CT_OK:
+        raise CatuneError(status, lib().ct_last_error().decode())
+    return status
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or None)."""
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+# ------------------------------------------------------------------------------------------
+# constraint strings -> postfix programs
+# ------------------------------------------------------------------------------------------
+class _Postfix:
+    BIN = {ast.Add: "ADD", ast.Sub: "SUB", ast.Mult: "MUL", ast.FloorDiv: "DIV", ast.Mod: "MOD"}
+    CMP = {ast.Lt: "LT", ast.LtE: "LE", ast.Gt: "GT", ast.GtE: "GE", ast.Eq: "EQ", ast.NotEq: "NE"}
+
+    def __init__(self, names):
+        self.idx = {n: i for i, n in enumerate(names)}
+        self.code = []
+
+    def emit(self, op, arg=0, imm=0):
+        self.code.append((OP[op], arg, imm))
+
+    def gen(self, e):
+        if isinstance(e, ast.Constant) and isinstance(e.value, (int, bool)):
+            return self.emit("CONST", imm=int(e.value))
+        if isinstance(e, ast.Name):
+            if e.id not in self.idx:
+                raise ValueError(f"unknown parameter {e.id!r}")
+            return self.emit("PARAM", arg=self.idx[e.id])
+        if isinstance(e, ast.UnaryOp):
+            self.gen(e.operand)
+            if isinstance(e.op, ast.USub):
+                return self.emit("NEG")
+            if isinstance(e.op, ast.Not):
+                return self.emit("NOT")
+            if isinstance(e.op, ast.UAdd):
+                return None
+        if isinstance(e, ast.BinOp) and type(e.op) in self.BIN:
+            self.gen(e.left)
+            self.gen(e.right)
+            return self.emit(self.BIN[type(e.op)])
+        if isinstance(e, ast.BoolOp):
+            op = "AND" if isinstance(e.op, ast.And) else "OR"
+            self.gen(e.values[0])
+            for v in e.values[1:]:
+                self.gen(v)
+                self.emit(op)
+            return None
+        if isinstance(e, ast.Compare):
+            operands = [e.left] + list(e.comparators)
+            for i, op in enumerate(e.ops):
+                self.gen(operands[i])
+                self.gen(operands[i + 1])
+                self.emit(self.CMP[type(op)])
+                if i:
+                    self.emit("AND")
+            return None
+        if isinstance(e, ast.Call) and isinstance(e.func, ast.Name) and e.func.id in ("min", "max"):
+            self.gen(e.args[0])
+            for a in e.args[1:]:
+                self.gen(a)
+                self.emit("MIN" if e.func.id == "min" else "MAX")
+            return None
+        raise ValueError(f"unsupported constraint syntax: {ast.dump(e)}")
+
+
+def compile_constraints(names, constraints):
+    """Constraint strings -> concatenated postfix program (ct_instr array)."""
+    pf = _Postfix(names)
+    for c in constraints:
+        pf.gen(ast.parse(c, mode="eval").body)
+        pf.emit("END")
+    arr = (ct_instr * max(1, len(pf.code)))()
+    for i, (op, arg, imm) in enumerate(pf.code):
+        arr[i].op, arr[i].arg, arr[i].imm = op, arg, imm
+    return arr, len(pf.code)
+
+
+# ------------------------------------------------------------------------------------------
+# handles
+# ------------------------------------------------------------------------------------------
+class Space:
+    """ct_space: a tuning space P = (X, D, C) and, once built, its sorted valid keys."""
+
+    def __init__(self, names, value_lists, constraints):
+        L = lib()
+        self.names = list(names)
+        nv = np.array([len(v) for v in value_lists], dtype=np.int32)
+        vals = np.array([int(x) for v in value_lists for x in v], dtype=np.int64)
+        prog, n_instr = compile_constraints(names, constraints)
+        h = C.c_void_p()
+        check(L.ct_define_space(len(nv), nv.ctypes.data_as(C.c_void_p), vals.ctypes.data_as(C.c_void_p),
+                                C.cast(prog, C.c_void_p), n_instr, C.byref(h)))
+        self.h = h
+        self._fit = None
+
+    @classmethod
+    def from_def(cls, sd):
+        return cls(sd.names, sd.values, sd.constraints)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ct_space_destroy(self.h)
+            self.h = None
+
+    def info(self):
+        inf = ct_space_info()
+        check(lib().ct_space_info_get(self.h, C.byref(inf)))
+        return inf
+
+    def pack(self, idx):
+        idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int32).reshape(-1, self.info().n_params))
+        out = np.zeros(len(idx), dtype=np.uint64)
+        check(lib().ct_pack_keys(self.h, idx.ctypes.data_as(C.c_void_p), len(idx), out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def unpack(self, keys):
+        keys = np.ascontiguousarray(np.asarray(keys, dtype=np.uint64))
+        out = np.zeros((len(keys), self.info().n_params), dtype=np.int32)
+        check(lib().ct_unpack_keys(self.h, keys.ctypes.data_as(C.c_void_p), len(keys), out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def build(self, stream=None, allow_empty=False):
+        n = C.c_uint64()
+        st = lib().ct_build_valid_space(self.h, _stream(stream), C.byref(n))
+        if st == CT_ERR_EMPTY_SPACE and allow_empty:
+            return 0
+        check(st)
+        return int(n.value)
+
+    def keys(self):
+        """Borrowed view of the device keys as an int64 torch tensor (bit pattern of uint64)."""
+        import torch
+        p, n = C.c_void_p(), C.c_uint64()
+        check(lib().ct_space_keys(self.h, C.byref(p), C.byref(n)))
+        n = int(n.value)
+        if n == 0:
+            return torch.zeros(0, dtype=torch.int64, device="cuda")
+        holder = _CudaArray(p.value, n)
+        return torch.as_tensor(holder, device="cuda")
+
+    def set_fitness(self, table):
+        check(lib().ct_set_fitness(self.h, _ptr(table), table.numel()))
+        self._fit = table
+
+    def lookup(self, cand, rank, stream=None):
+        check(lib().ct_lookup(self.h, _ptr(cand), cand.numel(), _ptr(rank), _stream(stream)))
+
+    def repair(self, cand, out, dist=None, stream=None):
+        check(lib().ct_repair(self.h, _ptr(cand), cand.numel(), _ptr(out), _ptr(dist), _stream(stream)))
+
+    def set_repair_mode(self, mode, max_radius=0):
+        check(lib().ct_set_repair_mode(self.h, mode, max_radius))
+
+    def evaluate(self, keys, fit, rank=None, opt=None, stream=None):
+        check(lib().ct_evaluate(self.h, opt.h if opt is not None else None, _ptr(keys), keys.numel(), _ptr(fit),
+                                _ptr(rank), _stream(stream)))
+
+    def status(self, stream=None):
+        return lib().ct_space_status(self.h, _stream(stream))
+
+
+class _CudaArray:
+    """Minimal __cuda_array_interface__ holder for a borrowed device pointer."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i8", "data": (ptr, False), "version": 3}
+
+
+def default_params(**over):
+    p = ct_opt_params()
+    lib().ct_opt_params_default(C.byref(p))
+    for k, v in over.items():
+        setattr(p, k, float(np.float32(v)))
+    return p
+
+
+class Opt:
+    """ct_opt: one constraint-aware optimizer run on a built space with a fitness table."""
+
+    def __init__(self, space, kind, pop, seed, **params):
+        self.space = space
+        self.pop = pop
+        self.kind = kind
+        self.params = default_params(**params)
+        h = C.c_void_p()
+        check(lib().ct_opt_create(space.h, KINDS[kind], C.byref(self.params), pop, seed, C.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ct_opt_destroy(self.h)
+            self.h = None
+
+    def propose(self, gen, cand, stream=None):
+        check(lib().ct_propose_population(self.h, gen, _ptr(cand), _stream(stream)))
+
+    def post_repair(self, gen, keys, stream=None):
+        check(lib().ct_opt_post_repair(self.h, gen, _ptr(keys), _stream(stream)))
+
+    def select(self, gen, keys, fit, stream=None):
+        check(lib().ct_opt_select(self.h, gen, _ptr(keys), _ptr(fit), _stream(stream)))
+
+    def step(self, gen, stream=None):
+        check(lib().ct_opt_step(self.h, gen, _stream(stream)))
+
+    def run_graph(self, first, count, stream=None):
+        check(lib().ct_opt_run_graph(self.h, first, count, _stream(stream)))
+
+    def best(self, stream=None):
+        k, f, u = C.c_uint64(), C.c_float(), C.c_uint64()
+        hg, he = C.c_int64(), C.c_int64()
+        check(lib().ct_opt_best(self.h, C.byref(k), C.byref(f), C.byref(u), C.byref(hg), C.byref(he), _stream(stream)))
+        return dict(best_key=int(k.value), best_fit=float(f.value), n_unique=int(u.value), hit_gen=int(hg.value),
+                    hit_evals=int(he.value))
+
+    def state(self, keys=None, fit=None, pos=None, stream=None):
+        check(lib().ct_opt_state(self.h, _ptr(keys), _ptr(fit), _ptr(pos), _stream(stream)))
+
+    def save(self, stream=None):
+        n = C.c_size_t()
+        check(lib().ct_opt_save(self.h, None, C.byref(n), _stream(stream)))
+        buf = (C.c_char * n.value)()
+        check(lib().ct_opt_save(self.h, C.cast(buf, C.c_void_p), C.byref(n), _stream(stream)))
+        return bytes(buf)
+
+    def load(self, blob, stream=None):
+        buf = C.create_string_buffer(blob, len(blob))
+        check(lib().ct_opt_load(self.h, C.cast(buf, C.c_void_p), len(blob), _stream(stream)))
+
+
+def u64(t):
+    """View an int64 torch tensor holding uint64 bit patterns as a numpy uint64 array (host copy)."""
+    return t.cpu().numpy().view(np.uint64)

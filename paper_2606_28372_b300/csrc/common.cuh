@@ -1,0 +1,235 @@
+// Device-side data layout and helpers shared by the catune kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/catune.h"
+
+namespace ct {
+
+constexpr int MAXP = CT_MAX_PARAMS;
+constexpr int MAXV = CT_MAX_VALUES;
+constexpr int MAXC = CT_MAX_CONSTRAINTS;
+constexpr int MAXI = CT_MAX_INSTR;
+constexpr int BLOCK_BITS_MAX = 4096;   // points of one enumeration block (mask bits)
+constexpr int MAX_RADIUS = 8;          // largest Hamming ball radius the ball search tables cover
+
+// One constraint after lowering.  Constraints are stored sorted by block.
+struct DevCons {
+    int32_t pc, len;          // program slice in DevSpace::prog (END excluded)
+    int32_t level;            // deepest parameter in the scope (-1: no parameter)
+    int32_t block;            // enumeration block holding `level`
+    int32_t tabled;           // 1: truth-mask table, 0: interpreted per point
+    int32_t n_outer;          // parameters of the scope that lie before the block
+    int32_t outer_k[MAXP];
+    int32_t outer_stride[MAXP];
+    uint64_t table_off;       // word offset of row 0 in the table arena
+    uint32_t rows;            // prod of outer value counts
+    uint32_t pad_;
+};
+
+// One enumeration block: consecutive parameters [s, e) whose Cartesian product
+// (B <= BLOCK_BITS_MAX points, W 32-bit words) is expanded per parent prefix.
+struct DevBlock {
+    int32_t s, e;
+    int32_t B, W;
+    int32_t pstride[MAXP];    // mixed-radix stride of parameter s + i inside the block
+    uint32_t innerkey_off;    // offset of the block's point -> key-bits table
+    int32_t key_shift;        // offset of the lowest field of the block (off[e-1])
+    int32_t cons_begin, cons_end;
+    int32_t has_vm;           // some constraint of the block is interpreted
+    int32_t pad_;
+};
+
+struct DevSpace {
+    int32_t n, key_bits, n_cons, n_blocks;
+    int32_t r[MAXP], w[MAXP], off[MAXP], vstart[MAXP];
+    uint64_t fmask[MAXP];     // field mask in place
+    uint64_t swar_low;        // every bit of every field except the field's top bit
+    uint64_t swar_high;       // the top bit of every field of width >= 1
+    uint64_t domain_bits;     // bits used by the key
+    int64_t values[MAXV];
+    DevCons cons[MAXC];
+    DevBlock blocks[MAXP];
+    ct_instr prog[MAXI];
+};
+
+// ------------------------------------------------------------------------------
+// Philox4x32-10 counter-based generator (Salmon et al., SC'11)
+// ------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+#ifdef __CUDA_ARCH__
+        uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+#else
+        uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+}
+
+enum Purpose : uint32_t {
+    PU_INIT = 1, PU_MUT_PICK = 2, PU_CROSS = 3, PU_PSO_R = 4, PU_FA_ALPHA = 5, PU_GA_SEL = 6,
+    PU_GA_CUT = 7, PU_GA_MUT = 8, PU_REINIT = 9, PU_POOL = 10, PU_MLP_INIT = 11, PU_MLP_BATCH = 12,
+    PU_PSO_VEL = 13
+};
+
+// Word t of the stream (individual, generation, purpose) for `seed`:
+// lane t % 4 of Philox(counter = (t / 4, individual, generation, purpose), key = seed).
+__host__ __device__ __forceinline__ uint32_t rng_word(uint64_t seed, uint32_t indiv, uint32_t gen,
+                                                      uint32_t purpose, uint32_t t) {
+    uint32_t c[4] = {t >> 2, indiv, gen, purpose};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return c[t & 3u];
+}
+
+// Block of 4 consecutive words starting at a multiple of 4.
+__host__ __device__ __forceinline__ void rng_block(uint64_t seed, uint32_t indiv, uint32_t gen,
+                                                   uint32_t purpose, uint32_t draw, uint32_t out[4]) {
+    out[0] = draw; out[1] = indiv; out[2] = gen; out[3] = purpose;
+    philox4x32_10(out, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+__host__ __device__ __forceinline__ float u01(uint32_t w) {
+    return (float)(w >> 8) * (1.0f / 16777216.0f);
+}
+__host__ __device__ __forceinline__ uint32_t uint_below(uint32_t w, uint32_t n) {
+    return (uint32_t)(((uint64_t)w * n) >> 32);
+}
+__device__ __forceinline__ uint64_t uint64_below(uint32_t whi, uint32_t wlo, uint64_t n) {
+    return __umul64hi(((uint64_t)whi << 32) | wlo, n);
+}
+
+// ------------------------------------------------------------------------------
+// key fields
+// ------------------------------------------------------------------------------
+__device__ __forceinline__ int32_t field(const DevSpace* sp, uint64_t key, int k) {
+    return (int32_t)((key & sp->fmask[k]) >> sp->off[k]);
+}
+
+// 1 when every field is < r_k and no bit above the key is set.
+__device__ __forceinline__ bool in_domain(const DevSpace* sp, uint64_t key) {
+    if (key & ~sp->domain_bits) return false;
+    for (int k = 0; k < sp->n; ++k)
+        if (field(sp, key, k) >= sp->r[k]) return false;
+    return true;
+}
+
+// Number of fields in which a and b differ: per-field non-zero test on a^b by
+// carrying every field's low bits into its top bit, then a population count.
+__device__ __forceinline__ int hamming_keys(uint64_t a, uint64_t b, uint64_t lowm, uint64_t highm) {
+    uint64_t x = a ^ b;
+    uint64_t t = ((x & lowm) + lowm) | x;
+    return __popcll(t & highm);
+}
+
+// ------------------------------------------------------------------------------
+// constraint program interpreter (postfix, 64-bit, poison on division by zero)
+// ------------------------------------------------------------------------------
+__device__ __forceinline__ bool vm_eval(const ct_instr* __restrict__ prog, int pc, int len,
+                                        const int64_t* pv) {
+    int64_t st[CT_MAX_STACK];
+    uint32_t poison = 0;  // bit i: slot i poisoned
+    int sp = 0;
+    for (int i = 0; i < len; ++i) {
+        const ct_instr in = prog[pc + i];
+        const int op = in.op;
+        if (op == CT_OP_PARAM) { st[sp] = pv[in.arg]; poison &= ~(1u << sp); ++sp; continue; }
+        if (op == CT_OP_CONST) { st[sp] = in.imm; poison &= ~(1u << sp); ++sp; continue; }
+        if (op == CT_OP_NEG) {
+            st[sp - 1] = (int64_t)(0ull - (uint64_t)st[sp - 1]);
+            continue;
+        }
+        if (op == CT_OP_NOT) {
+            bool t = !((poison >> (sp - 1)) & 1u) && st[sp - 1] != 0;
+            st[sp - 1] = t ? 0 : 1;
+            poison &= ~(1u << (sp - 1));
+            continue;
+        }
+        const int64_t a = st[sp - 2], b = st[sp - 1];
+        const bool pa = (poison >> (sp - 2)) & 1u, pb = (poison >> (sp - 1)) & 1u;
+        const bool p = pa || pb;
+        const bool at = !pa && a != 0, bt = !pb && b != 0;
+        int64_t r = 0;
+        bool rp = false;
+        switch (op) {
+            case CT_OP_ADD: r = (int64_t)((uint64_t)a + (uint64_t)b); rp = p; break;
+            case CT_OP_SUB: r = (int64_t)((uint64_t)a - (uint64_t)b); rp = p; break;
+            case CT_OP_MUL: r = (int64_t)((uint64_t)a * (uint64_t)b); rp = p; break;
+            case CT_OP_DIV:
+            case CT_OP_MOD:
+                if (p || b == 0) { rp = true; break; }
+                if (a == INT64_MIN && b == -1) { r = (op == CT_OP_DIV) ? INT64_MIN : 0; break; }
+                r = (op == CT_OP_DIV) ? a / b : a % b;
+                break;
+            case CT_OP_MIN: r = a < b ? a : b; rp = p; break;
+            case CT_OP_MAX: r = a > b ? a : b; rp = p; break;
+            case CT_OP_LT: r = !p && a < b; break;
+            case CT_OP_LE: r = !p && a <= b; break;
+            case CT_OP_GT: r = !p && a > b; break;
+            case CT_OP_GE: r = !p && a >= b; break;
+            case CT_OP_EQ: r = !p && a == b; break;
+            case CT_OP_NE: r = !p && a != b; break;
+            case CT_OP_AND: r = at && bt; break;
+            case CT_OP_OR: r = at || bt; break;
+            default: rp = true; break;
+        }
+        --sp;
+        st[sp - 1] = r;
+        if (rp) poison |= 1u << (sp - 1); else poison &= ~(1u << (sp - 1));
+    }
+    return sp == 1 && !(poison & 1u) && st[0] != 0;
+}
+
+// Full-tuple constraint test of an in-domain key: AND over every constraint,
+// tabled ones by one bit of their truth-mask table, the rest interpreted.
+__device__ __forceinline__ bool valid_key(const DevSpace* __restrict__ sp,
+                                          const uint32_t* __restrict__ tables, uint64_t key) {
+    const int nb = sp->n_blocks;
+    for (int j = 0; j < nb; ++j) {
+        const DevBlock& bl = sp->blocks[j];
+        int32_t p = 0;
+        for (int k = bl.s; k < bl.e; ++k) p += field(sp, key, k) * bl.pstride[k - bl.s];
+        for (int c = bl.cons_begin; c < bl.cons_end; ++c) {
+            const DevCons& cs = sp->cons[c];
+            if (cs.tabled) {
+                uint32_t o = 0;
+                for (int q = 0; q < cs.n_outer; ++q) o += (uint32_t)field(sp, key, cs.outer_k[q]) * cs.outer_stride[q];
+                uint32_t wv = __ldg(tables + cs.table_off + (uint64_t)o * bl.W + (p >> 5));
+                if (!((wv >> (p & 31)) & 1u)) return false;
+            } else {
+                int64_t pv[MAXP];
+                for (int k = 0; k < sp->n; ++k) pv[k] = sp->values[sp->vstart[k] + field(sp, key, k)];
+                if (!vm_eval(sp->prog, cs.pc, cs.len, pv)) return false;
+            }
+        }
+    }
+    return true;
+}
+
+// lower_bound over the sorted keys: first position with keys[pos] >= x.
+__device__ __forceinline__ int64_t lower_bound_keys(const uint64_t* __restrict__ keys, int64_t n, uint64_t x) {
+    int64_t base = 0, len = n;
+    while (len > 0) {
+        int64_t half = len >> 1;
+        uint64_t v = __ldg(keys + base + half);
+        if (v < x) { base += half + 1; len -= half + 1; } else { len = half; }
+    }
+    return base;
+}
+
+__device__ __forceinline__ int64_t rank_of(const uint64_t* __restrict__ keys, int64_t n, uint64_t x) {
+    int64_t p = lower_bound_keys(keys, n, x);
+    return (p < n && __ldg(keys + p) == x) ? p : -1;
+}
+
+// Status bits recorded by kernels into the space's device status word.
+constexpr uint32_t ST_BAD_CANDIDATE = 1u;
+
+}  // namespace ct

@@ -1,0 +1,119 @@
+// Host-side internals of libcatune: handle layouts, error plumbing, shared launch helpers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ct {
+
+void set_error(const char* fmt, ...);
+
+#define CT_TRY_CUDA(call)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            ::ct::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                            __LINE__);                                                      \
+            return CT_ERR_CUDA;                                                             \
+        }                                                                                   \
+    } while (0)
+
+#define CT_TRY(st)                     \
+    do {                               \
+        ct_status s_ = (st);           \
+        if (s_ != CT_OK) return s_;    \
+    } while (0)
+
+// Device buffer with grow-only capacity.
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t cap = 0;
+    ct_status ensure(size_t n) {
+        if (n <= cap && p) return CT_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = n ? n : 1;
+        cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc(%zu bytes) failed: %s", want * sizeof(T), cudaGetErrorString(e));
+            p = nullptr;
+            return e == cudaErrorMemoryAllocation ? CT_ERR_OOM : CT_ERR_CUDA;
+        }
+        cap = want;
+        return CT_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+// Hamming-ball enumeration tables for one radius: the d-subsets of parameters (as
+// bit masks over parameters with r_k > 1) and the prefix sums of their sizes
+// prod_{k in S} (r_k - 1).
+struct BallRadius {
+    int d = 0;
+    uint64_t total = 0;                // points at exactly distance d
+    std::vector<uint32_t> masks;
+    std::vector<uint64_t> prefix;      // size masks.size() + 1
+    DevBuf<uint32_t> d_masks;
+    DevBuf<uint64_t> d_prefix;
+};
+
+struct RepairScratch {
+    DevBuf<int32_t> pend_a, pend_b;    // pending candidate indices
+    DevBuf<uint32_t> counts;           // [0]: pending a, [1]: pending b
+    DevBuf<unsigned long long> best;   // per pending slot: best key / packed (dist, rank)
+};
+
+}  // namespace ct
+
+struct ct_space {
+    int device = 0;
+    ct::DevSpace h{};                      // host copy of the descriptor
+    ct::DevSpace* d = nullptr;             // device copy
+    std::vector<int> tab_cons;             // tabled constraints (indices into h.cons)
+    std::vector<uint64_t> tab_prefix;      // cumulative table words, size tab_cons.size() + 1
+    ct::DevBuf<uint32_t> tables;           // truth-mask arena
+    ct::DevBuf<int32_t> d_tab_cons;
+    ct::DevBuf<uint64_t> d_tab_prefix;
+    ct::DevBuf<uint32_t> innerkey;         // per block: point -> key bits (shifted)
+    bool tables_ready = false;
+    std::vector<uint32_t> ik_host;         // innerkey tables before upload
+
+    // build
+    ct::DevBuf<uint64_t> keys;
+    uint64_t n_valid = 0;
+    bool built = false;
+    std::vector<ct::DevBuf<uint64_t>> frontier;
+    ct::DevBuf<uint32_t> tile_counts;
+    ct::DevBuf<unsigned long long> tile_base;
+    ct::DevBuf<unsigned long long> d_total;
+    unsigned long long* h_total = nullptr; // pinned
+
+    // repair
+    std::vector<ct::BallRadius> balls;     // radius 1..max_ball
+    int repair_mode = 0, repair_max_radius = 0;
+    ct::RepairScratch rs;
+
+    // evaluate
+    const float* fit = nullptr;
+    uint64_t n_fit = 0;
+
+    ct::DevBuf<uint32_t> status;           // device status word
+    ~ct_space();
+};
+
+namespace ct {
+ct_status ensure_device(ct_space* s);
+ct_status repair_impl(ct_space* s, const uint64_t* d_cand, int64_t n, uint64_t* d_out, uint8_t* d_dist,
+                      cudaStream_t st);
+int auto_radius(const ct_space* s);
+}  // namespace ct

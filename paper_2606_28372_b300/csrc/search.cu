@@ -1,0 +1,290 @@
+// Validity lookup, nearest-valid repair and fitness lookup over the resolved space.
+//
+// Repair returns, for an invalid candidate u, the valid key v minimising
+// (Hamming distance on value indices, key) — the exact nearest neighbour of
+// Algorithm 1's Repair under the Hamming neighbour rule of Section IV-A.  Two
+// exact strategies are combined:
+//   ball search: for radius d = 1, 2, ... every point at distance exactly d is
+//     generated (subsets of d parameters x alternative values) and tested with
+//     the constraint truth masks; if any is valid, the smallest such key is the
+//     answer because every point outside the ball is farther away;
+//   streaming scan: for the candidates still pending, every valid key is read
+//     once per chunk of 32 candidates; per (key, candidate) the distance is a
+//     SWAR per-field non-zero test plus a population count, reduced as the packed
+//     minimum of (distance << 57 | rank) by warp shuffles, shared memory and one
+//     64-bit atomicMin per candidate and CTA.
+#include <cuda_runtime.h>
+
+#include <climits>
+
+#include "internal.hpp"
+
+namespace ct {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_CHUNK = 32;        // candidates per CTA of the scan
+constexpr unsigned long long NONE = ~0ull;
+
+__global__ void k_lookup(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, int64_t nv,
+                         const uint64_t* __restrict__ cand, int64_t n, int64_t* __restrict__ rank) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t c = cand[i];
+        rank[i] = in_domain(sp, c) ? rank_of(keys, nv, c) : -1;
+    }
+}
+
+__global__ void k_evaluate(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, int64_t nv,
+                           const float* __restrict__ table, const uint64_t* __restrict__ cand, int64_t n,
+                           float* __restrict__ fit, int64_t* __restrict__ rank_out, uint32_t* __restrict__ memo,
+                           unsigned long long* __restrict__ unique) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t c = cand[i];
+        const int64_t r = in_domain(sp, c) ? rank_of(keys, nv, c) : -1;
+        if (fit) fit[i] = r >= 0 ? __ldg(table + r) : __int_as_float(0x7f800000);
+        if (rank_out) rank_out[i] = r;
+        if (memo && r >= 0) {
+            const uint32_t bit = 1u << (r & 31);
+            const uint32_t old = atomicOr(memo + (r >> 5), bit);
+            if (!(old & bit)) atomicAdd(unique, 1ull);
+        }
+    }
+}
+
+// valid candidates map to themselves; the others are queued for the search
+__global__ void k_repair_init(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
+                              const uint64_t* __restrict__ cand, int64_t n, uint64_t* __restrict__ out,
+                              uint8_t* __restrict__ dist, int32_t* __restrict__ pend, uint32_t* __restrict__ count,
+                              unsigned long long* __restrict__ best, uint32_t* __restrict__ status) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t c = cand[i];
+        if (!in_domain(sp, c)) {
+            out[i] = c;
+            if (dist) dist[i] = 255;
+            atomicOr(status, ST_BAD_CANDIDATE);
+            continue;
+        }
+        if (valid_key(sp, tables, c)) {
+            out[i] = c;
+            if (dist) dist[i] = 0;
+            continue;
+        }
+        const uint32_t slot = atomicAdd(count, 1u);
+        pend[slot] = (int32_t)i;
+        best[slot] = NONE;
+    }
+}
+
+// every point at Hamming distance exactly d of each pending candidate
+__global__ void __launch_bounds__(256)
+k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, const uint32_t* __restrict__ masks,
+       const uint64_t* __restrict__ prefix, int n_subsets, uint64_t points, const uint64_t* __restrict__ cand,
+       const int32_t* __restrict__ pend, const uint32_t* __restrict__ count, unsigned long long* __restrict__ best) {
+    const uint64_t total = (uint64_t)(*count) * points;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t q = g / points, j = g - q * points;
+        const uint64_t u = __ldg(cand + pend[q]);
+        int lo = 0, hi = n_subsets - 1;   // last subset with prefix <= j
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(prefix + mid) <= j) lo = mid; else hi = mid - 1;
+        }
+        uint32_t local = (uint32_t)(j - __ldg(prefix + lo));
+        uint32_t m = __ldg(masks + lo);
+        uint64_t key = u;
+        while (m) {
+            const int k = 31 - __clz(m);
+            m &= ~(1u << k);
+            const uint32_t alt = (uint32_t)sp->r[k] - 1u;
+            const uint32_t a = local % alt;
+            local /= alt;
+            const uint32_t uk = (uint32_t)field(sp, u, k);
+            const uint32_t v = a < uk ? a : a + 1u;
+            key = (key & ~sp->fmask[k]) | ((uint64_t)v << sp->off[k]);
+        }
+        if (valid_key(sp, tables, key)) atomicMin(best + q, (unsigned long long)key);
+    }
+}
+
+// settle candidates whose ball held a valid point; requeue the rest
+__global__ void k_ball_resolve(int d, const int32_t* __restrict__ pend_in, const uint32_t* __restrict__ count_in,
+                               const unsigned long long* __restrict__ best_in, uint64_t* __restrict__ out,
+                               uint8_t* __restrict__ dist, int32_t* __restrict__ pend_out, uint32_t* __restrict__ count_out,
+                               unsigned long long* __restrict__ best_out) {
+    const uint32_t cnt = *count_in;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
+        const unsigned long long b = best_in[q];
+        const int32_t i = pend_in[q];
+        if (b != NONE) {
+            out[i] = b;
+            if (dist) dist[i] = (uint8_t)d;
+        } else {
+            const uint32_t slot = atomicAdd(count_out, 1u);
+            pend_out[slot] = i;
+            best_out[slot] = NONE;
+        }
+    }
+}
+
+// exhaustive streaming argmin of (distance, rank) for up to 32 candidates per CTA
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_scan(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_t highm,
+       const uint64_t* __restrict__ cand, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
+       unsigned long long* __restrict__ best) {
+    __shared__ uint64_t cq[SCAN_CHUNK];
+    __shared__ unsigned long long red[SCAN_THREADS / 32][SCAN_CHUNK];
+    const uint32_t cnt = *count;
+    const uint32_t q0 = blockIdx.y * SCAN_CHUNK;
+    if (q0 >= cnt) return;
+    const int nq = min((uint32_t)SCAN_CHUNK, cnt - q0);
+    if (threadIdx.x < SCAN_CHUNK) cq[threadIdx.x] = threadIdx.x < nq ? cand[pend[q0 + threadIdx.x]] : 0ull;
+    __syncthreads();
+    unsigned long long b[SCAN_CHUNK];
+#pragma unroll
+    for (int q = 0; q < SCAN_CHUNK; ++q) b[q] = NONE;
+    for (int64_t i = (int64_t)blockIdx.x * SCAN_THREADS + threadIdx.x; i < nv; i += (int64_t)gridDim.x * SCAN_THREADS) {
+        const uint64_t k = __ldg(keys + i);
+#pragma unroll
+        for (int q = 0; q < SCAN_CHUNK; ++q) {
+            const unsigned long long p = ((unsigned long long)hamming_keys(k, cq[q], lowm, highm) << 57) | (unsigned long long)i;
+            b[q] = p < b[q] ? p : b[q];
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < SCAN_CHUNK; ++q) {
+        unsigned long long v = b[q];
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = w < v ? w : v;
+        }
+        if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nq) {
+        unsigned long long v = NONE;
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) v = red[w][threadIdx.x] < v ? red[w][threadIdx.x] : v;
+        atomicMin(best + q0 + threadIdx.x, v);
+    }
+}
+
+__global__ void k_scan_resolve(const uint64_t* __restrict__ keys, const int32_t* __restrict__ pend,
+                               const uint32_t* __restrict__ count, const unsigned long long* __restrict__ best,
+                               uint64_t* __restrict__ out, uint8_t* __restrict__ dist) {
+    const uint32_t cnt = *count;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
+        const unsigned long long b = best[q];
+        const int32_t i = pend[q];
+        out[i] = keys[b & ((1ull << 57) - 1)];
+        if (dist) dist[i] = (uint8_t)(b >> 57);
+    }
+}
+
+static int g_sm_count = 0;
+static int sm_count() {
+    if (!g_sm_count) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sm_count <= 0) g_sm_count = 148;
+    }
+    return g_sm_count;
+}
+
+// Largest radius whose cumulative ball is cheaper than one scan pass per candidate:
+// a ball point costs a table test (~8x a scanned key's SWAR distance).
+int auto_radius(const ct_space* s) {
+    const double budget = (double)s->n_valid / 8.0;
+    double cum = 0;
+    int d = 0;
+    for (const auto& br : s->balls) {
+        cum += (double)br.total;
+        if (cum > budget) break;
+        d = br.d;
+    }
+    return d;
+}
+
+ct_status repair_impl(ct_space* s, const uint64_t* d_cand, int64_t n, uint64_t* d_out, uint8_t* d_dist,
+                      cudaStream_t st) {
+    if (n == 0) return CT_OK;
+    if (n > 0x7fffffffLL) { set_error("n too large"); return CT_ERR_LIMIT; }
+    RepairScratch& rs = s->rs;
+    CT_TRY(rs.pend_a.ensure(n));
+    CT_TRY(rs.pend_b.ensure(n));
+    CT_TRY(rs.counts.ensure(2));
+    CT_TRY(rs.best.ensure(2 * (size_t)n));
+    unsigned long long* best[2] = {rs.best.p, rs.best.p + n};
+    int32_t* pend[2] = {rs.pend_a.p, rs.pend_b.p};
+    uint32_t* cnt[2] = {rs.counts.p, rs.counts.p + 1};
+    const int sms = sm_count();
+    const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+    CT_TRY_CUDA(cudaMemsetAsync(rs.counts.p, 0, 8, st));
+    k_repair_init<<<g1, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, pend[0], cnt[0], best[0], s->status.p);
+    int dmax;
+    if (s->repair_mode == 1) dmax = 0;
+    else if (s->repair_mode == 2) dmax = std::min<int>(s->repair_max_radius, (int)s->balls.size());
+    else dmax = auto_radius(s);
+    int cur = 0;
+    for (int d = 1; d <= dmax; ++d) {
+        const BallRadius& br = s->balls[d - 1];
+        const uint64_t work = (uint64_t)n * br.total;
+        const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 16);
+        k_ball<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
+                                   d_cand, pend[cur], cnt[cur], best[cur]);
+        CT_TRY_CUDA(cudaMemsetAsync(cnt[cur ^ 1], 0, 4, st));
+        k_ball_resolve<<<g1, 256, 0, st>>>(d, pend[cur], cnt[cur], best[cur], d_out, d_dist, pend[cur ^ 1],
+                                           cnt[cur ^ 1], best[cur ^ 1]);
+        cur ^= 1;
+    }
+    // whatever is left: exhaustive scan (a full ball search always ends here as well)
+    const unsigned chunks = (unsigned)((n + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)s->n_valid + SCAN_THREADS * 8 - 1) / (SCAN_THREADS * 8), (int64_t)sms * 4));
+    k_scan<<<dim3(gx, chunks), SCAN_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, s->h.swar_low, s->h.swar_high,
+                                                     d_cand, pend[cur], cnt[cur], best[cur]);
+    k_scan_resolve<<<g1, 256, 0, st>>>(s->keys.p, pend[cur], cnt[cur], best[cur], d_out, d_dist);
+    CT_TRY_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+}  // namespace ct
+
+using namespace ct;
+
+extern "C" {
+
+ct_status ct_lookup(const ct_space* s, const uint64_t* d_cand, int64_t n, int64_t* d_rank, ct_stream stream) {
+    if (!s || n < 0 || (n > 0 && (!d_cand || !d_rank))) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
+    if (!s->built) { set_error("space not built"); return CT_ERR_STATE; }
+    if (n == 0) return CT_OK;
+    const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+    k_lookup<<<g, 256, 0, (cudaStream_t)stream>>>(s->d, s->keys.p, (int64_t)s->n_valid, d_cand, n, d_rank);
+    CT_TRY_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+ct_status ct_repair(ct_space* s, const uint64_t* d_cand, int64_t n, uint64_t* d_out, uint8_t* d_dist, ct_stream stream) {
+    if (!s || n < 0 || (n > 0 && (!d_cand || !d_out))) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
+    if (!s->built) { set_error("space not built"); return CT_ERR_STATE; }
+    if (s->n_valid == 0) { set_error("empty valid space"); return CT_ERR_EMPTY_SPACE; }
+    return repair_impl(s, d_cand, n, d_out, d_dist, (cudaStream_t)stream);
+}
+
+ct_status ct_set_repair_mode(ct_space* s, int32_t mode, int32_t max_radius) {
+    if (!s || mode < 0 || mode > 2 || max_radius < 0) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
+    s->repair_mode = mode;
+    s->repair_max_radius = max_radius;
+    return CT_OK;
+}
+
+}  // extern "C"
+
+namespace ct {
+ct_status evaluate_impl(ct_space* s, uint32_t* memo, unsigned long long* unique, const uint64_t* d_keys, int64_t n,
+                        float* d_fit, int64_t* d_rank, cudaStream_t st) {
+    if (n == 0) return CT_OK;
+    const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+    k_evaluate<<<g, 256, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, s->fit, d_keys, n, d_fit, d_rank, memo, unique);
+    CT_TRY_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+}  // namespace ct

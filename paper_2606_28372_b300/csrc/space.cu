@@ -1,0 +1,621 @@
+// Search-space definition and full resolution of the valid space (Section IV-A).
+//
+// Lowering (host): field layout of the packed keys, the scope and deepest
+// parameter of every constraint, and a plan of enumeration blocks: consecutive
+// parameters [s, e) whose Cartesian product has at most 4096 points.  Every
+// constraint is attached to the block holding its deepest parameter; if its
+// truth table over (its parameters before the block) x (the block's points) is
+// small it becomes a bit-mask table, built on the GPU by interpreting the
+// constraint over that sub-domain.
+//
+// Build (device): a prefix of the first blocks is expanded into the next one.
+// For each parent prefix and each 32-point word of the next block the valid
+// points are the AND of the constraint masks selected by the parent's fields;
+// pass one counts per tile, a scan gives tile offsets, pass two recomputes the
+// masks and writes the children, in increasing key order, through shared
+// memory with coalesced stores.  The last block writes the final sorted keys.
+// Work is proportional to the valid prefixes of every level, not to the
+// Cartesian size; nothing spins on another block.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.hpp"
+
+namespace ct {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+const char* last_error() { return g_err.c_str(); }
+
+constexpr int EXP_THREADS = 256;
+constexpr int EXP_ROUNDS = 8;
+constexpr int EXP_TILE = EXP_THREADS * EXP_ROUNDS;   // items (parent, word) per tile
+constexpr uint64_t TABLE_WORDS_PER_CONS = 1ull << 22;   // 16 MB
+constexpr uint64_t TABLE_WORDS_TOTAL = 1ull << 24;      // 64 MB
+
+// ---------------------------------------------------------------------------
+// table construction: one thread per (tabled constraint, row, point)
+// ---------------------------------------------------------------------------
+__global__ void k_build_tables(const DevSpace* __restrict__ sp, const int32_t* __restrict__ tab_cons,
+                               const uint64_t* __restrict__ tab_prefix, int n_tab, uint64_t total_words,
+                               uint32_t* __restrict__ tables) {
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t gw = gid >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= total_words) return;   // whole warps share gw
+    int lo = 0, hi = n_tab - 1;      // last i with tab_prefix[i] <= gw
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tab_prefix[mid] <= gw) lo = mid; else hi = mid - 1;
+    }
+    const DevCons& cs = sp->cons[tab_cons[lo]];
+    const DevBlock& bl = sp->blocks[cs.block];
+    const uint64_t lw = gw - tab_prefix[lo];
+    const uint32_t row = (uint32_t)(lw / bl.W), wd = (uint32_t)(lw % bl.W);
+    const int p = wd * 32 + lane;
+    bool bit = false;
+    if (p < bl.B) {
+        int64_t pv[MAXP];
+        for (int k = 0; k < sp->n; ++k) pv[k] = 0;
+        uint32_t o = row;
+        for (int q = cs.n_outer - 1; q >= 0; --q) {
+            const int k = cs.outer_k[q];
+            const int32_t ik = (int32_t)(o % sp->r[k]);
+            o /= sp->r[k];
+            pv[k] = sp->values[sp->vstart[k] + ik];
+        }
+        int t = p;
+        for (int k = bl.e - 1; k >= bl.s; --k) {
+            const int32_t ik = t % sp->r[k];
+            t /= sp->r[k];
+            pv[k] = sp->values[sp->vstart[k] + ik];
+        }
+        bit = vm_eval(sp->prog, cs.pc, cs.len, pv);
+    }
+    const uint32_t word = __ballot_sync(0xffffffffu, bit);
+    if (lane == 0) tables[cs.table_off + lw] = word;
+}
+
+// ---------------------------------------------------------------------------
+// expand: valid children of (parent, word)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t block_word(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
+                                               const DevBlock& bl, const uint32_t* __restrict__ ik,
+                                               uint64_t parent, uint32_t wd) {
+    uint32_t m = 0xffffffffu;
+    const int rem = bl.B - (int)wd * 32;
+    if (rem < 32) m = (1u << rem) - 1u;
+    for (int c = bl.cons_begin; c < bl.cons_end && m; ++c) {
+        const DevCons& cs = sp->cons[c];
+        if (!cs.tabled) continue;
+        uint32_t o = 0;
+        for (int q = 0; q < cs.n_outer; ++q) o += (uint32_t)field(sp, parent, cs.outer_k[q]) * cs.outer_stride[q];
+        m &= __ldg(tables + cs.table_off + (uint64_t)o * bl.W + wd);
+    }
+    if (m && bl.has_vm) {   // interpreted constraints, one point at a time
+        uint32_t keep = m;
+        for (uint32_t mm = m; mm; mm &= mm - 1) {
+            const int b = __ffs(mm) - 1;
+            const uint64_t key = parent | ((uint64_t)ik[wd * 32 + b] << bl.key_shift);
+            int64_t pv[MAXP];
+            for (int k = 0; k < bl.e; ++k) pv[k] = sp->values[sp->vstart[k] + field(sp, key, k)];
+            for (int c = bl.cons_begin; c < bl.cons_end; ++c) {
+                const DevCons& cs = sp->cons[c];
+                if (!cs.tabled && !vm_eval(sp->prog, cs.pc, cs.len, pv)) { keep &= ~(1u << b); break; }
+            }
+        }
+        m = keep;
+    }
+    return m;
+}
+
+__global__ void __launch_bounds__(EXP_THREADS)
+k_expand_count(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
+               const uint32_t* __restrict__ innerkey, int j, const uint64_t* __restrict__ parents,
+               uint64_t n_items, uint32_t* __restrict__ tile_counts) {
+    const DevBlock& bl = sp->blocks[j];
+    const uint32_t* ik = innerkey + bl.innerkey_off;
+    const uint64_t t0 = (uint64_t)blockIdx.x * EXP_TILE;
+    uint32_t cnt = 0;
+    for (int r = 0; r < EXP_ROUNDS; ++r) {
+        const uint64_t it = t0 + (uint64_t)r * EXP_THREADS + threadIdx.x;
+        if (it >= n_items) break;
+        const uint64_t pi = it / (uint32_t)bl.W;
+        const uint32_t wd = (uint32_t)(it - pi * (uint32_t)bl.W);
+        const uint64_t parent = parents ? __ldg(parents + pi) : 0ull;
+        cnt += __popc(block_word(sp, tables, bl, ik, parent, wd));
+    }
+    __shared__ uint32_t ws[EXP_THREADS / 32];
+    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int w = 0; w < EXP_THREADS / 32; ++w) s += ws[w];
+        tile_counts[blockIdx.x] = s;
+    }
+}
+
+// exclusive scan of n tile counts into bases (one CTA; contiguous segments per thread)
+__global__ void __launch_bounds__(1024)
+k_scan_tiles(const uint32_t* __restrict__ counts, uint64_t n, unsigned long long* __restrict__ base,
+             unsigned long long* __restrict__ total) {
+    __shared__ unsigned long long part[1024];
+    const uint64_t seg = (n + 1023) / 1024;
+    const uint64_t b = threadIdx.x * seg, e = min(n, b + seg);
+    unsigned long long s = 0;
+    for (uint64_t i = b; i < e; ++i) s += counts[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {   // Hillis-Steele inclusive scan of the 1024 sums
+        unsigned long long v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned long long run = part[threadIdx.x] - s;
+    for (uint64_t i = b; i < e; ++i) {
+        base[i] = run;
+        run += counts[i];
+    }
+    if (threadIdx.x == 1023) *total = part[1023];
+}
+
+__global__ void __launch_bounds__(EXP_THREADS)
+k_expand_emit(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
+              const uint32_t* __restrict__ innerkey, int j, const uint64_t* __restrict__ parents,
+              uint64_t n_items, const unsigned long long* __restrict__ tile_base, uint64_t* __restrict__ out) {
+    extern __shared__ uint64_t stage[];                // EXP_THREADS * 32 keys
+    __shared__ uint32_t wsum[EXP_THREADS / 32];
+    const DevBlock& bl = sp->blocks[j];
+    const uint32_t* ik = innerkey + bl.innerkey_off;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t base = tile_base[blockIdx.x];
+    const uint64_t t0 = (uint64_t)blockIdx.x * EXP_TILE;
+    for (int r = 0; r < EXP_ROUNDS; ++r) {
+        const uint64_t r0 = t0 + (uint64_t)r * EXP_THREADS;
+        if (r0 >= n_items) break;                      // uniform across the CTA
+        const uint64_t it = r0 + threadIdx.x;
+        uint32_t m = 0;
+        uint64_t parent = 0;
+        uint32_t wd = 0;
+        if (it < n_items) {
+            const uint64_t pi = it / (uint32_t)bl.W;
+            wd = (uint32_t)(it - pi * (uint32_t)bl.W);
+            parent = parents ? __ldg(parents + pi) : 0ull;
+            m = block_word(sp, tables, bl, ik, parent, wd);
+        }
+        // CTA exclusive scan of the popcounts
+        const uint32_t c = __popc(m);
+        uint32_t inc = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        uint32_t wbase = 0, tot = 0;
+        for (int w = 0; w < EXP_THREADS / 32; ++w) {
+            const uint32_t v = wsum[w];
+            wbase += (w < warp) ? v : 0u;
+            tot += v;
+        }
+        uint32_t pos = wbase + inc - c;
+        for (uint32_t mm = m; mm; mm &= mm - 1) {
+            const int b = __ffs(mm) - 1;
+            stage[pos++] = parent | ((uint64_t)__ldg(ik + wd * 32 + b) << bl.key_shift);
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < tot; i += EXP_THREADS) out[base + i] = stage[i];
+        base += tot;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host: lowering
+// ---------------------------------------------------------------------------
+static int ceil_log2(int64_t r) {
+    int w = 0;
+    while (((int64_t)1 << w) < r) ++w;
+    return w;
+}
+
+static ct_status lower(ct_space* s, int32_t n, const int32_t* nv, const int64_t* vals, const ct_instr* prog,
+                       int32_t n_instr) {
+    DevSpace& h = s->h;
+    if (n < 1 || n > MAXP) { set_error("n_params must be in [1, %d]", MAXP); return CT_ERR_LIMIT; }
+    if (!nv || !vals || (n_instr > 0 && !prog) || n_instr < 0) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    h.n = n;
+    int64_t total_vals = 0;
+    for (int k = 0; k < n; ++k) {
+        if (nv[k] < 1) { set_error("parameter %d has no values", k); return CT_ERR_INVALID_ARG; }
+        if (nv[k] > BLOCK_BITS_MAX) { set_error("parameter %d has %d values (> %d)", k, nv[k], BLOCK_BITS_MAX); return CT_ERR_LIMIT; }
+        h.r[k] = nv[k];
+        h.vstart[k] = (int32_t)total_vals;
+        total_vals += nv[k];
+    }
+    if (total_vals > MAXV) { set_error("%lld values in total (> %d)", (long long)total_vals, MAXV); return CT_ERR_LIMIT; }
+    for (int64_t i = 0; i < total_vals; ++i) h.values[i] = vals[i];
+    // key layout: param n-1 lowest
+    int bits = 0;
+    double cart_log2 = 0;
+    for (int k = n - 1; k >= 0; --k) {
+        h.w[k] = ceil_log2(h.r[k]);
+        h.off[k] = bits;
+        bits += h.w[k];
+        cart_log2 += std::log2((double)h.r[k]);
+    }
+    if (bits > 64 || cart_log2 >= 62.99) { set_error("key needs %d bits (> 64) or Cartesian size >= 2^63", bits); return CT_ERR_KEY_OVERFLOW; }
+    h.key_bits = bits;
+    h.domain_bits = bits == 64 ? ~0ull : ((1ull << bits) - 1);
+    h.swar_low = h.swar_high = 0;
+    for (int k = 0; k < n; ++k) {
+        h.fmask[k] = h.w[k] ? (((h.w[k] == 64) ? ~0ull : ((1ull << h.w[k]) - 1)) << h.off[k]) : 0ull;
+        if (h.w[k]) {
+            h.swar_high |= 1ull << (h.off[k] + h.w[k] - 1);
+            h.swar_low |= h.fmask[k] & ~(1ull << (h.off[k] + h.w[k] - 1));
+        }
+    }
+    // constraints: split at END, validate stack discipline, collect scope
+    if (n_instr > MAXI) { set_error("%d instructions (> %d)", n_instr, MAXI); return CT_ERR_LIMIT; }
+    struct Raw { int pc, len; uint64_t scope; int level; };
+    std::vector<Raw> raw;
+    int start = 0, depth = 0;
+    uint64_t scope = 0;
+    for (int i = 0; i < n_instr; ++i) {
+        const ct_instr& in = prog[i];
+        switch (in.op) {
+            case CT_OP_END:
+                if (depth != 1) { set_error("constraint %zu leaves %d values on the stack", raw.size(), depth); return CT_ERR_INVALID_ARG; }
+                {
+                    int level = -1;
+                    for (int k = 0; k < n; ++k) if (scope >> k & 1) level = k;
+                    raw.push_back({start, i - start, scope, level});
+                }
+                start = i + 1; depth = 0; scope = 0;
+                continue;
+            case CT_OP_PARAM:
+                if (in.arg < 0 || in.arg >= n) { set_error("instruction %d: parameter %d out of range", i, in.arg); return CT_ERR_INVALID_ARG; }
+                scope |= 1ull << in.arg;
+                ++depth; break;
+            case CT_OP_CONST: ++depth; break;
+            case CT_OP_NEG: case CT_OP_NOT:
+                if (depth < 1) { set_error("instruction %d: stack underflow", i); return CT_ERR_INVALID_ARG; }
+                break;
+            default:
+                if (in.op < CT_OP_ADD || in.op > CT_OP_OR) { set_error("instruction %d: bad opcode %d", i, in.op); return CT_ERR_INVALID_ARG; }
+                if (depth < 2) { set_error("instruction %d: stack underflow", i); return CT_ERR_INVALID_ARG; }
+                --depth; break;
+        }
+        if (depth > CT_MAX_STACK) { set_error("instruction %d: stack deeper than %d", i, CT_MAX_STACK); return CT_ERR_LIMIT; }
+    }
+    if (start != n_instr) { set_error("program does not end with CT_OP_END"); return CT_ERR_INVALID_ARG; }
+    if ((int)raw.size() > MAXC) { set_error("%zu constraints (> %d)", raw.size(), MAXC); return CT_ERR_LIMIT; }
+    for (int i = 0; i < n_instr; ++i) h.prog[i] = prog[i];
+
+    // block plan: from the last parameter backwards, grow while the product fits
+    std::vector<std::pair<int, int>> blocks;
+    int e = n;
+    while (e > 0) {
+        int s0 = e - 1;
+        int64_t prod = h.r[s0];
+        while (s0 > 0 && prod * h.r[s0 - 1] <= BLOCK_BITS_MAX) { prod *= h.r[s0 - 1]; --s0; }
+        blocks.push_back({s0, e});
+        e = s0;
+    }
+    std::reverse(blocks.begin(), blocks.end());
+    h.n_blocks = (int)blocks.size();
+    std::vector<uint32_t> ik_all;
+    for (int j = 0; j < h.n_blocks; ++j) {
+        DevBlock& bl = h.blocks[j];
+        bl.s = blocks[j].first;
+        bl.e = blocks[j].second;
+        int64_t B = 1;
+        for (int k = bl.e - 1; k >= bl.s; --k) { bl.pstride[k - bl.s] = (int32_t)B; B *= h.r[k]; }
+        bl.B = (int32_t)B;
+        bl.W = (int32_t)((B + 31) / 32);
+        bl.key_shift = h.off[bl.e - 1];
+        bl.innerkey_off = (uint32_t)ik_all.size();
+        for (int64_t p = 0; p < B; ++p) {
+            uint64_t key = 0;
+            int64_t t = p;
+            for (int k = bl.e - 1; k >= bl.s; --k) { key |= (uint64_t)(t % h.r[k]) << h.off[k]; t /= h.r[k]; }
+            ik_all.push_back((uint32_t)(key >> bl.key_shift));
+        }
+    }
+    // attach constraints to blocks, sorted by block (stable)
+    std::vector<int> order(raw.size());
+    for (size_t i = 0; i < raw.size(); ++i) order[i] = (int)i;
+    auto block_of = [&](int level) {
+        if (level < 0) return 0;
+        for (int j = 0; j < h.n_blocks; ++j) if (level >= h.blocks[j].s && level < h.blocks[j].e) return j;
+        return 0;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return block_of(raw[a].level) < block_of(raw[b].level); });
+    h.n_cons = (int)raw.size();
+    uint64_t words = 0;
+    // table memory budget; CATUNE_TABLE_WORDS overrides it (0 interprets every constraint)
+    uint64_t per_cons = TABLE_WORDS_PER_CONS, total_cap = TABLE_WORDS_TOTAL;
+    if (const char* env = getenv("CATUNE_TABLE_WORDS")) per_cons = total_cap = strtoull(env, nullptr, 10);
+    s->tab_cons.clear();
+    s->tab_prefix.assign(1, 0);
+    for (int j = 0; j < h.n_blocks; ++j) { h.blocks[j].cons_begin = h.blocks[j].cons_end = 0; h.blocks[j].has_vm = 0; }
+    for (int ci = 0; ci < h.n_cons; ++ci) {
+        const Raw& rc = raw[order[ci]];
+        DevCons& cs = h.cons[ci];
+        memset(&cs, 0, sizeof cs);
+        cs.pc = rc.pc; cs.len = rc.len; cs.level = rc.level; cs.block = block_of(rc.level);
+        const DevBlock& bl = h.blocks[cs.block];
+        uint64_t rows = 1;
+        cs.n_outer = 0;
+        for (int k = 0; k < bl.s; ++k)
+            if (rc.scope >> k & 1) { cs.outer_k[cs.n_outer++] = k; rows *= (uint64_t)h.r[k]; }
+        uint64_t stride = 1;
+        for (int q = cs.n_outer - 1; q >= 0; --q) { cs.outer_stride[q] = (int32_t)stride; stride *= h.r[cs.outer_k[q]]; }
+        const uint64_t tw = rows * (uint64_t)bl.W;
+        if (rows < (1ull << 31) && tw <= per_cons && words + tw <= total_cap) {
+            cs.tabled = 1;
+            cs.rows = (uint32_t)rows;
+            cs.table_off = words;
+            words += tw;
+            s->tab_cons.push_back(ci);
+            s->tab_prefix.push_back(words);
+        } else {
+            cs.tabled = 0;
+        }
+    }
+    for (int ci = 0; ci < h.n_cons; ++ci) {
+        DevBlock& bl = h.blocks[h.cons[ci].block];
+        if (bl.cons_end == 0 && bl.cons_begin == 0) bl.cons_begin = ci;
+        bl.cons_end = ci + 1;
+        if (!h.cons[ci].tabled) bl.has_vm = 1;
+    }
+    for (int j = 0; j < h.n_blocks; ++j) if (h.blocks[j].cons_end == 0) h.blocks[j].cons_begin = 0;
+
+    s->frontier.resize(h.n_blocks);
+    s->ik_host = std::move(ik_all);
+    return CT_OK;
+}
+
+// first device use: descriptor, tables, ball plan and status word go to the current device
+ct_status ensure_device(ct_space* s) {
+    if (s->d) return CT_OK;
+    const DevSpace& h = s->h;
+    cudaGetDevice(&s->device);
+    CT_TRY_CUDA(cudaMalloc(&s->d, sizeof(DevSpace)));
+    CT_TRY_CUDA(cudaMemcpy(s->d, &h, sizeof(DevSpace), cudaMemcpyHostToDevice));
+    CT_TRY(s->innerkey.ensure(s->ik_host.size()));
+    CT_TRY_CUDA(cudaMemcpy(s->innerkey.p, s->ik_host.data(), s->ik_host.size() * 4, cudaMemcpyHostToDevice));
+    CT_TRY(s->tables.ensure(s->tab_prefix.back()));
+    if (!s->tab_cons.empty()) {
+        CT_TRY(s->d_tab_cons.ensure(s->tab_cons.size()));
+        CT_TRY(s->d_tab_prefix.ensure(s->tab_prefix.size()));
+        CT_TRY_CUDA(cudaMemcpy(s->d_tab_cons.p, s->tab_cons.data(), s->tab_cons.size() * 4, cudaMemcpyHostToDevice));
+        CT_TRY_CUDA(cudaMemcpy(s->d_tab_prefix.p, s->tab_prefix.data(), s->tab_prefix.size() * 8, cudaMemcpyHostToDevice));
+    }
+    CT_TRY(s->status.ensure(1));
+    CT_TRY_CUDA(cudaMemset(s->status.p, 0, 4));
+    CT_TRY_CUDA(cudaMallocHost(&s->h_total, sizeof(unsigned long long)));
+    for (auto& br : s->balls) {
+        CT_TRY(br.d_masks.ensure(br.masks.size()));
+        CT_TRY(br.d_prefix.ensure(br.prefix.size()));
+        CT_TRY_CUDA(cudaMemcpy(br.d_masks.p, br.masks.data(), br.masks.size() * 4, cudaMemcpyHostToDevice));
+        CT_TRY_CUDA(cudaMemcpy(br.d_prefix.p, br.prefix.data(), br.prefix.size() * 8, cudaMemcpyHostToDevice));
+    }
+    CT_TRY_CUDA(cudaFuncSetAttribute(k_expand_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     EXP_THREADS * 32 * (int)sizeof(uint64_t)));
+    return CT_OK;
+}
+
+// Hamming-ball tables (radius 1..): subsets of the parameters with r_k > 1.
+static void plan_balls(ct_space* s) {
+    const DevSpace& h = s->h;
+    std::vector<int> free_k;
+    for (int k = 0; k < h.n; ++k) if (h.r[k] > 1) free_k.push_back(k);
+    const int m = (int)free_k.size();
+    s->balls.clear();
+    const uint64_t SUBSET_CAP = 1u << 20, POINT_CAP = 1ull << 40;
+    for (int d = 1; d <= std::min(m, MAX_RADIUS); ++d) {
+        BallRadius br;
+        br.d = d;
+        br.prefix.push_back(0);
+        std::vector<int> idx(d);
+        for (int i = 0; i < d; ++i) idx[i] = i;
+        bool ok = true;
+        while (true) {
+            uint32_t mask = 0;
+            uint64_t sz = 1;
+            for (int i = 0; i < d; ++i) { mask |= 1u << free_k[idx[i]]; sz *= (uint64_t)(h.r[free_k[idx[i]]] - 1); }
+            br.masks.push_back(mask);
+            br.total += sz;
+            br.prefix.push_back(br.total);
+            if (br.masks.size() > SUBSET_CAP || br.total > POINT_CAP || sz >= (1ull << 32)) { ok = false; break; }
+            int i = d - 1;
+            while (i >= 0 && idx[i] == m - d + i) --i;
+            if (i < 0) break;
+            ++idx[i];
+            for (int t = i + 1; t < d; ++t) idx[t] = idx[t - 1] + 1;
+        }
+        if (!ok) break;
+        s->balls.push_back(std::move(br));
+    }
+}
+
+static ct_status ensure_tables(ct_space* s, cudaStream_t st) {
+    if (s->tables_ready) return CT_OK;
+    const uint64_t words = s->tab_prefix.back();
+    if (words) {
+        const uint64_t threads = words * 32;
+        const unsigned grid = (unsigned)((threads + 255) / 256);
+        k_build_tables<<<grid, 256, 0, st>>>(s->d, s->d_tab_cons.p, s->d_tab_prefix.p, (int)s->tab_cons.size(),
+                                             words, s->tables.p);
+        CT_TRY_CUDA(cudaGetLastError());
+    }
+    s->tables_ready = true;
+    return CT_OK;
+}
+
+}  // namespace ct
+
+using namespace ct;
+
+ct_space::~ct_space() {
+    if (d) cudaFree(d);
+    if (h_total) cudaFreeHost(h_total);
+    tables.release(); d_tab_cons.release(); d_tab_prefix.release(); innerkey.release();
+    keys.release(); tile_counts.release(); tile_base.release(); d_total.release(); status.release();
+    for (auto& f : frontier) f.release();
+    for (auto& b : balls) { b.d_masks.release(); b.d_prefix.release(); }
+    rs.pend_a.release(); rs.pend_b.release(); rs.counts.release(); rs.best.release();
+}
+
+extern "C" {
+
+const char* ct_last_error(void) { return ct::last_error(); }
+const char* ct_version(void) { return "catune 0.1 (sm_103a)"; }
+
+ct_status ct_define_space(int32_t n_params, const int32_t* n_values, const int64_t* values_flat,
+                          const ct_instr* program, int32_t n_instr, ct_space** out) {
+    if (!out) { set_error("out is NULL"); return CT_ERR_INVALID_ARG; }
+    *out = nullptr;
+    ct_space* s = new (std::nothrow) ct_space();
+    if (!s) { set_error("host allocation failed"); return CT_ERR_OOM; }
+    ct_status st = lower(s, n_params, n_values, values_flat, program, n_instr);
+    if (st == CT_OK) plan_balls(s);
+    if (st != CT_OK) { delete s; return st; }
+    *out = s;
+    return CT_OK;
+}
+
+void ct_space_destroy(ct_space* s) { delete s; }
+
+ct_status ct_space_info_get(const ct_space* s, ct_space_info* info) {
+    if (!s || !info) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    memset(info, 0, sizeof *info);
+    info->n_params = s->h.n;
+    info->n_constraints = s->h.n_cons;
+    info->key_bits = s->h.key_bits;
+    info->n_blocks = s->h.n_blocks;
+    uint64_t cart = 1;
+    for (int k = 0; k < s->h.n; ++k) {
+        info->width[k] = s->h.w[k];
+        info->offset[k] = s->h.off[k];
+        info->n_values[k] = s->h.r[k];
+        cart *= (uint64_t)s->h.r[k];
+    }
+    info->cartesian = cart;
+    info->n_valid = s->n_valid;
+    info->built = s->built;
+    return CT_OK;
+}
+
+ct_status ct_pack_keys(const ct_space* s, const int32_t* idx, int64_t n, uint64_t* keys) {
+    if (!s || (n > 0 && (!idx || !keys)) || n < 0) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    const int np = s->h.n;
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t k = 0;
+        for (int p = 0; p < np; ++p) {
+            const int32_t v = idx[i * np + p];
+            if (v < 0 || v >= s->h.r[p]) { set_error("row %lld: index %d of parameter %d out of range", (long long)i, v, p); return CT_ERR_INVALID_ARG; }
+            k |= (uint64_t)v << s->h.off[p];
+        }
+        keys[i] = k;
+    }
+    return CT_OK;
+}
+
+ct_status ct_unpack_keys(const ct_space* s, const uint64_t* keys, int64_t n, int32_t* idx) {
+    if (!s || (n > 0 && (!idx || !keys)) || n < 0) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    const int np = s->h.n;
+    for (int64_t i = 0; i < n; ++i)
+        for (int p = 0; p < np; ++p) idx[i * np + p] = (int32_t)((keys[i] & s->h.fmask[p]) >> s->h.off[p]);
+    return CT_OK;
+}
+
+ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_out) {
+    if (!s) { set_error("space is NULL"); return CT_ERR_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    CT_TRY(ensure_device(s));
+    CT_TRY(ensure_tables(s, st));
+    const DevSpace& h = s->h;
+    const uint64_t* parents = nullptr;
+    uint64_t F = 1;
+    s->built = false;
+    for (int j = 0; j < h.n_blocks; ++j) {
+        const uint64_t items = F * (uint64_t)h.blocks[j].W;
+        const uint64_t tiles = (items + EXP_TILE - 1) / EXP_TILE;
+        if (tiles > 0x7fffffffull) { set_error("level %d needs %llu tiles", j, (unsigned long long)tiles); return CT_ERR_LIMIT; }
+        CT_TRY(s->tile_counts.ensure(tiles));
+        CT_TRY(s->tile_base.ensure(tiles));
+        CT_TRY(s->d_total.ensure(1));
+        k_expand_count<<<(unsigned)tiles, EXP_THREADS, 0, st>>>(s->d, s->tables.p, s->innerkey.p, j, parents, items,
+                                                               s->tile_counts.p);
+        k_scan_tiles<<<1, 1024, 0, st>>>(s->tile_counts.p, tiles, s->tile_base.p, s->d_total.p);
+        CT_TRY_CUDA(cudaMemcpyAsync(s->h_total, s->d_total.p, 8, cudaMemcpyDeviceToHost, st));
+        CT_TRY_CUDA(cudaStreamSynchronize(st));
+        const uint64_t Fn = *s->h_total;
+        DevBuf<uint64_t>& dst = (j == h.n_blocks - 1) ? s->keys : s->frontier[j];
+        CT_TRY(dst.ensure(Fn));
+        if (Fn) {
+            k_expand_emit<<<(unsigned)tiles, EXP_THREADS, EXP_THREADS * 32 * sizeof(uint64_t), st>>>(
+                s->d, s->tables.p, s->innerkey.p, j, parents, items, s->tile_base.p, dst.p);
+            CT_TRY_CUDA(cudaGetLastError());
+        }
+        parents = dst.p;
+        F = Fn;
+        if (F == 0) break;
+    }
+    CT_TRY_CUDA(cudaStreamSynchronize(st));
+    s->n_valid = F;
+    s->built = true;
+    if (n_valid_out) *n_valid_out = F;
+    if (F == 0) { set_error("no configuration satisfies the constraints"); return CT_ERR_EMPTY_SPACE; }
+    return CT_OK;
+}
+
+ct_status ct_space_keys(const ct_space* s, const uint64_t** d_keys, uint64_t* n) {
+    if (!s || !d_keys) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    if (!s->built) { set_error("space not built"); return CT_ERR_STATE; }
+    *d_keys = s->keys.p;
+    if (n) *n = s->n_valid;
+    return CT_OK;
+}
+
+ct_status ct_set_fitness(ct_space* s, const float* d_table, uint64_t n) {
+    if (!s || !d_table) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    if (!s->built) { set_error("space not built"); return CT_ERR_STATE; }
+    if (n != s->n_valid) { set_error("table has %llu entries, space has %llu valid", (unsigned long long)n, (unsigned long long)s->n_valid); return CT_ERR_INVALID_ARG; }
+    s->fit = d_table;
+    s->n_fit = n;
+    return CT_OK;
+}
+
+ct_status ct_space_status(ct_space* s, ct_stream stream) {
+    if (!s) { set_error("space is NULL"); return CT_ERR_INVALID_ARG; }
+    uint32_t v = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!s->d) return CT_OK;
+    CT_TRY_CUDA(cudaMemcpyAsync(&v, s->status.p, 4, cudaMemcpyDeviceToHost, st));
+    CT_TRY_CUDA(cudaMemsetAsync(s->status.p, 0, 4, st));
+    CT_TRY_CUDA(cudaStreamSynchronize(st));
+    if (v & ST_BAD_CANDIDATE) { set_error("a candidate key was outside the Cartesian domain"); return CT_ERR_INVALID_ARG; }
+    return CT_OK;
+}
+
+}  // extern "C"

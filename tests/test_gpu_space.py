@@ -1,0 +1,88 @@
+"""GPU parity: the valid space built by the CUDA path equals the oracle's, key for key."""
+import numpy as np
+import pytest
+
+from paper_2606_28372_b300 import workloads as W
+from tests.helpers import Pair, from_dev_u64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("name", ["tiny", "medium", "large_a", "large_b"])
+def test_build_equals_oracle(oracle_mod, name):
+    p = Pair(W.SPACES[name](), oracle_mod, table=None)
+    assert p.nv == len(p.okeys)
+    assert np.array_equal(p.gkeys(), p.okeys)
+
+
+@pytest.mark.parametrize("s", [0, 7, 13, 22, 31])
+def test_batched_spaces_equal_oracle(oracle_mod, s):
+    p = Pair(W.batched_space(s), oracle_mod, table=None)
+    assert np.array_equal(p.gkeys(), p.okeys)
+
+
+def test_large_full_size(oracle_mod):
+    """51.6e9 Cartesian points: count = |V(A)|*|V(B)|, keys strictly increasing, and sampled
+    Cartesian windows equal the oracle's brute force of the same windows."""
+    import torch
+    from paper_2606_28372_b300 import catune as ct
+    sd = W.large_space()
+    sp = ct.Space.from_def(sd)
+    nv = sp.build()
+    assert nv == 695_228_960
+    keys = sp.keys()
+    # strictly increasing over the whole array (as unsigned: keys < 2^40, so signed compare is fine)
+    assert bool((keys[1:] > keys[:-1]).all())
+    osp = oracle_mod.from_def(sd)
+    cart = sd.cartesian_size
+    for c0 in [0, 7_777_777_777, 25_000_000_000, cart - 500_000]:
+        c1 = min(cart, c0 + 500_000)
+        exp = oracle_mod.enumerate_range(osp, c0, c1)
+        idx0 = np.zeros(16, np.int64)
+        t = c0
+        r = sd.n_values
+        for k in range(15, -1, -1):
+            idx0[k] = t % r[k]
+            t //= r[k]
+        lo_key = int(oracle_mod.pack(osp, idx0[None])[0])
+        lo = int(torch.searchsorted(keys, torch.tensor([lo_key], device="cuda")).item())
+        got = from_dev_u64(keys[lo: lo + len(exp)])
+        assert np.array_equal(got, exp)
+        if lo + len(exp) < nv and c1 < cart:   # the next key lies beyond the window
+            idx1 = np.zeros(16, np.int64)
+            t = c1
+            for k in range(15, -1, -1):
+                idx1[k] = t % r[k]
+                t //= r[k]
+            hi_key = int(oracle_mod.pack(osp, idx1[None])[0])
+            assert int(keys[lo + len(exp)].item()) >= hi_key
+    del keys
+
+
+def test_edge_spaces(oracle_mod):
+    from paper_2606_28372_b300 import catune as ct
+    cases = [
+        (["a", "b", "c"], [[1, 2, 3], [5, 6], [7, 8, 9, 10, 11]], []),                      # no constraints
+        (["a", "b"], [[4], [1, 2, 3]], ["a % b == 0"]),                                      # single-value param
+        (["a", "b"], [[-7, -1, 0, 3, 7], [-2, 0, 2, 3]], ["b == 0 or a // b >= 1", "not (a % b == 1)"]),
+        (["x"], list([list(range(4096))]), ["x % 7 == 3"]),                                  # one full block
+        ([f"p{i}" for i in range(12)], [[0, 1, 2]] * 12, ["p0 + p1 + p2 + p3 + p4 + p5 + p6 + p7 + p8 + p9 + p10 + p11 == 12"]),
+        (["a", "b", "c"], [[1, 2], [3, 4, 5], [6]], ["1 == 1", "a < b"]),                     # constant constraint
+    ]
+    for names, vals, cons in cases:
+        osp = oracle_mod.make_space(names, vals, cons)
+        exp = oracle_mod.valid_keys(osp)
+        sp = ct.Space(names, vals, cons)
+        nv = sp.build(allow_empty=True)
+        assert nv == len(exp), cons
+        if nv:
+            assert np.array_equal(from_dev_u64(sp.keys()), exp), cons
+
+
+def test_empty_space_status(oracle_mod):
+    from paper_2606_28372_b300 import catune as ct
+    sp = ct.Space(["a", "b"], [[1, 2], [3, 4]], ["a > b"])
+    with pytest.raises(ct.CatuneError) as e:
+        sp.build()
+    assert e.value.status == ct.CT_ERR_EMPTY_SPACE
+    assert sp.info().n_valid == 0 and sp.info().built
