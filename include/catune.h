@@ -235,6 +235,26 @@ ct_status ct_opt_save(const ct_opt *opt, void *buf, size_t *len, ct_stream strea
 ct_status ct_opt_load(ct_opt *opt, const void *buf, size_t len, ct_stream stream);
 
 /* ------------------------------------------------------------------------- */
+/* measurement                                                               */
+/* ------------------------------------------------------------------------- */
+/* Per-level statistics of the last ct_build_valid_space: parents expanded,
+ * children written, and (when timing is enabled) the device time of the count
+ * and emit kernels, measured with CUDA events recorded on the build's stream. */
+typedef struct {
+    int32_t n_levels;
+    int32_t timed;
+    uint64_t parents[CT_MAX_PARAMS];
+    uint64_t children[CT_MAX_PARAMS];
+    float count_ms[CT_MAX_PARAMS];
+    float emit_ms[CT_MAX_PARAMS];
+} ct_build_stats;
+ct_status ct_space_set_timing(ct_space *space, int32_t enable);
+ct_status ct_space_build_stats(const ct_space *space, ct_build_stats *stats);
+
+/* Number of kernels this library has launched in this process (all devices). */
+uint64_t ct_launch_count(void);
+
+/* ------------------------------------------------------------------------- */
 /* misc                                                                      */
 /* ------------------------------------------------------------------------- */
 const char *ct_last_error(void);

@@ -43,6 +43,12 @@ class ct_space_info(C.Structure):
                 ("built", C.c_int32)]
 
 
+class ct_build_stats(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("timed", C.c_int32), ("parents", C.c_uint64 * MAX_PARAMS),
+                ("children", C.c_uint64 * MAX_PARAMS), ("count_ms", C.c_float * MAX_PARAMS),
+                ("emit_ms", C.c_float * MAX_PARAMS)]
+
+
 class ct_opt_params(C.Structure):
     _fields_ = [(n, C.c_float) for n in ("de_F", "de_CR", "pso_w", "pso_c1", "pso_c2", "fa_beta0",
                                          "fa_gamma", "fa_alpha", "ga_pmut", "target")]
@@ -76,6 +82,9 @@ _SIGS = {
     "ct_opt_state": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_opt_save": [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t), C.c_void_p],
     "ct_opt_load": [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p],
+    "ct_space_set_timing": [C.c_void_p, C.c_int32],
+    "ct_space_build_stats": [C.c_void_p, C.c_void_p],
+    "ct_launch_count": [],
     "ct_last_error": [],
     "ct_version": [],
 }
@@ -97,6 +106,7 @@ def lib():
         L.ct_space_destroy.restype = None
         L.ct_opt_destroy.restype = None
         L.ct_opt_params_default.restype = None
+        L.ct_launch_count.restype = C.c_uint64
         _lib = L
     return _lib
 
@@ -271,6 +281,20 @@ class Space:
 
     def status(self, stream=None):
         return lib().ct_space_status(self.h, _stream(stream))
+
+    def set_timing(self, enable=True):
+        check(lib().ct_space_set_timing(self.h, 1 if enable else 0))
+
+    def build_stats(self):
+        st = ct_build_stats()
+        check(lib().ct_space_build_stats(self.h, C.byref(st)))
+        n = st.n_levels
+        return dict(levels=n, timed=bool(st.timed), parents=list(st.parents[:n]), children=list(st.children[:n]),
+                    count_ms=list(st.count_ms[:n]), emit_ms=list(st.emit_ms[:n]))
+
+
+def launch_count():
+    return int(lib().ct_launch_count())
 
 
 class _CudaArray:

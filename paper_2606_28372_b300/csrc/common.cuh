@@ -38,7 +38,17 @@ struct DevBlock {
     int32_t key_shift;        // offset of the lowest field of the block (off[e-1])
     int32_t cons_begin, cons_end;
     int32_t has_vm;           // some constraint of the block is interpreted
-    int32_t pad_;
+    // pattern mode: the block's valid-point mask depends only on the parent's fields of the
+    // parameters U (before the block) read by its constraints; one compacted inner-key list per
+    // signature sig = mixed radix over U
+    int32_t pattern;
+    int32_t n_u;
+    int32_t u_k[MAXP];
+    int32_t u_stride[MAXP];
+    uint32_t n_sig;
+    uint32_t Bpad;            // list capacity per signature (B rounded up to 4)
+    uint64_t pat_cnt_off;     // offset into the pattern count arena
+    uint64_t pat_list_off;    // offset into the pattern list arena
 };
 
 struct DevSpace {

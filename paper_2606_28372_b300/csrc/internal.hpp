@@ -10,6 +10,7 @@
 namespace ct {
 
 void set_error(const char* fmt, ...);
+void count_launch(uint64_t n = 1);
 
 #define CT_TRY_CUDA(call)                                                                   \
     do {                                                                                    \
@@ -87,6 +88,8 @@ struct ct_space {
     ct::DevBuf<uint32_t> innerkey;         // per block: point -> key bits (shifted)
     bool tables_ready = false;
     std::vector<uint32_t> ik_host;         // innerkey tables before upload
+    ct::DevBuf<uint32_t> pat_cnt, pat_list;  // pattern-mode arenas
+    uint64_t pat_cnt_words = 0, pat_list_words = 0;
 
     // build
     ct::DevBuf<uint64_t> keys;
@@ -108,12 +111,18 @@ struct ct_space {
     uint64_t n_fit = 0;
 
     ct::DevBuf<uint32_t> status;           // device status word
+
+    // measurement
+    bool timing = false;
+    ct_build_stats stats{};
+    std::vector<cudaEvent_t> events;
     ~ct_space();
 };
 
 namespace ct {
 ct_status ensure_device(ct_space* s);
-ct_status repair_impl(ct_space* s, const uint64_t* d_cand, int64_t n, uint64_t* d_out, uint8_t* d_dist,
-                      cudaStream_t st);
+ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, int64_t n, uint64_t* d_out,
+                      uint8_t* d_dist, cudaStream_t st);
 int auto_radius(const ct_space* s);
+ct_status repair_reserve(RepairScratch& rs, int64_t n);
 }  // namespace ct

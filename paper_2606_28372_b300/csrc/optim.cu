@@ -419,10 +419,14 @@ struct ct_opt {
     DevBuf<uint32_t> memo;
     size_t memo_words = 0;
     std::map<uint32_t, cudaGraphExec_t> graphs;
+    std::map<uint32_t, uint64_t> graph_kernels;   // kernels per replay of each graph
+    const void* graph_keys = nullptr;             // space key buffer the graphs were captured with
+    RepairScratch rs;                             // run-owned repair scratch (fixed size: pop)
     ~ct_opt() {
         for (auto& g : graphs) cudaGraphExecDestroy(g.second);
         st.release(); X.release(); cand.release(); rep.release(); FX.release(); pos.release(); vel.release();
         pb.release(); fpb.release(); gb.release(); ynew.release(); fit.release(); memo.release();
+        rs.pend_a.release(); rs.pend_b.release(); rs.counts.release(); rs.best.release();
     }
     OptArgs args() const {
         OptArgs a;
@@ -438,10 +442,13 @@ namespace ct {
 static ct_status step_impl(ct_opt* o, uint32_t gen, int use_dev, cudaStream_t st) {
     const OptArgs a = o->args();
     k_propose<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->cand.p);
-    CT_TRY(repair_impl(o->s, o->cand.p, o->P, o->rep.p, nullptr, st));
+    count_launch();
+    CT_TRY(repair_impl(o->s, o->rs, o->cand.p, o->P, o->rep.p, nullptr, st));
     k_post_repair<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->rep.p);
+    count_launch();
     CT_TRY(evaluate_impl(o->s, o->memo.p, &o->st.p->n_unique, o->rep.p, o->P, o->fit.p, nullptr, st));
     k_select<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->rep.p, o->fit.p);
+    count_launch();
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -480,6 +487,7 @@ ct_status ct_opt_create(ct_space* s, ct_opt_kind kind, const ct_opt_params* para
     ALLOC(pos, PN); ALLOC(vel, PN); ALLOC(pb, PN); ALLOC(fpb, pop); ALLOC(gb, o->N); ALLOC(ynew, PN);
     ALLOC(memo, o->memo_words);
 #undef ALLOC
+    if (e == CT_OK) e = repair_reserve(o->rs, pop);
     if (e != CT_OK) { delete o; return e; }
     OptDev init{};
     init.de_fbest = __builtin_inff();
@@ -506,6 +514,7 @@ void ct_opt_destroy(ct_opt* o) { delete o; }
 ct_status ct_propose_population(ct_opt* o, uint32_t gen, uint64_t* d_cand, ct_stream stream) {
     if (!o || !d_cand) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
     k_propose<<<1, OPT_THREADS, 0, (cudaStream_t)stream>>>(o->args(), gen, 0, d_cand);
+    count_launch();
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -513,6 +522,7 @@ ct_status ct_propose_population(ct_opt* o, uint32_t gen, uint64_t* d_cand, ct_st
 ct_status ct_opt_post_repair(ct_opt* o, uint32_t gen, uint64_t* d_keys, ct_stream stream) {
     if (!o || !d_keys) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
     k_post_repair<<<1, OPT_THREADS, 0, (cudaStream_t)stream>>>(o->args(), gen, 0, d_keys);
+    count_launch();
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -520,6 +530,7 @@ ct_status ct_opt_post_repair(ct_opt* o, uint32_t gen, uint64_t* d_keys, ct_strea
 ct_status ct_opt_select(ct_opt* o, uint32_t gen, const uint64_t* d_keys, const float* d_fit, ct_stream stream) {
     if (!o || !d_keys || !d_fit) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
     k_select<<<1, OPT_THREADS, 0, (cudaStream_t)stream>>>(o->args(), gen, 0, d_keys, d_fit);
+    count_launch();
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -542,6 +553,12 @@ ct_status ct_opt_step(ct_opt* o, uint32_t gen, ct_stream stream) {
 ct_status ct_opt_run_graph(ct_opt* o, uint32_t first, uint32_t count, ct_stream stream) {
     if (!o || count == 0) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
+    if (o->graph_keys != (const void*)o->s->keys.p) {   // the space was rebuilt into a new buffer
+        for (auto& gx : o->graphs) cudaGraphExecDestroy(gx.second);
+        o->graphs.clear();
+        o->graph_kernels.clear();
+        o->graph_keys = o->s->keys.p;
+    }
     auto it = o->graphs.find(count);
     if (it == o->graphs.end()) {
         cudaStream_t cap;
@@ -553,7 +570,11 @@ ct_status ct_opt_run_graph(ct_opt* o, uint32_t first, uint32_t count, ct_stream 
             set_error("stream capture failed to start");
             return CT_ERR_CUDA;
         }
+        const uint64_t c0 = ct_launch_count();
         for (uint32_t i = 0; i < count && e == CT_OK; ++i) e = step_impl(o, 0, 1, cap);
+        const uint64_t captured = ct_launch_count() - c0;
+        count_launch(0 - captured);   // captured launches have not run yet
+        o->graph_kernels[count] = captured;
         cudaError_t ce = cudaStreamEndCapture(cap, &g);
         cudaStreamDestroy(cap);
         if (e != CT_OK) return e;
@@ -565,7 +586,9 @@ ct_status ct_opt_run_graph(ct_opt* o, uint32_t first, uint32_t count, ct_stream 
         it = o->graphs.emplace(count, ex).first;
     }
     k_set_gen<<<1, 1, 0, st>>>(o->st.p, first);
+    count_launch();
     CT_TRY_CUDA(cudaGraphLaunch(it->second, st));
+    count_launch(o->graph_kernels[count]);
     return CT_OK;
 }
 

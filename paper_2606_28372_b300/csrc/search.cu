@@ -204,15 +204,19 @@ int auto_radius(const ct_space* s) {
     return d;
 }
 
-ct_status repair_impl(ct_space* s, const uint64_t* d_cand, int64_t n, uint64_t* d_out, uint8_t* d_dist,
-                      cudaStream_t st) {
-    if (n == 0) return CT_OK;
-    if (n > 0x7fffffffLL) { set_error("n too large"); return CT_ERR_LIMIT; }
-    RepairScratch& rs = s->rs;
+ct_status repair_reserve(RepairScratch& rs, int64_t n) {
     CT_TRY(rs.pend_a.ensure(n));
     CT_TRY(rs.pend_b.ensure(n));
     CT_TRY(rs.counts.ensure(2));
     CT_TRY(rs.best.ensure(2 * (size_t)n));
+    return CT_OK;
+}
+
+ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, int64_t n, uint64_t* d_out,
+                      uint8_t* d_dist, cudaStream_t st) {
+    if (n == 0) return CT_OK;
+    if (n > 0x7fffffffLL) { set_error("n too large"); return CT_ERR_LIMIT; }
+    CT_TRY(repair_reserve(rs, n));
     unsigned long long* best[2] = {rs.best.p, rs.best.p + n};
     int32_t* pend[2] = {rs.pend_a.p, rs.pend_b.p};
     uint32_t* cnt[2] = {rs.counts.p, rs.counts.p + 1};
@@ -220,6 +224,7 @@ ct_status repair_impl(ct_space* s, const uint64_t* d_cand, int64_t n, uint64_t* 
     const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
     CT_TRY_CUDA(cudaMemsetAsync(rs.counts.p, 0, 8, st));
     k_repair_init<<<g1, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, pend[0], cnt[0], best[0], s->status.p);
+    count_launch();
     int dmax;
     if (s->repair_mode == 1) dmax = 0;
     else if (s->repair_mode == 2) dmax = std::min<int>(s->repair_max_radius, (int)s->balls.size());
@@ -231,9 +236,11 @@ ct_status repair_impl(ct_space* s, const uint64_t* d_cand, int64_t n, uint64_t* 
         const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 16);
         k_ball<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
                                    d_cand, pend[cur], cnt[cur], best[cur]);
+        count_launch();
         CT_TRY_CUDA(cudaMemsetAsync(cnt[cur ^ 1], 0, 4, st));
         k_ball_resolve<<<g1, 256, 0, st>>>(d, pend[cur], cnt[cur], best[cur], d_out, d_dist, pend[cur ^ 1],
                                            cnt[cur ^ 1], best[cur ^ 1]);
+        count_launch();
         cur ^= 1;
     }
     // whatever is left: exhaustive scan (a full ball search always ends here as well)
@@ -241,7 +248,9 @@ ct_status repair_impl(ct_space* s, const uint64_t* d_cand, int64_t n, uint64_t* 
     const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)s->n_valid + SCAN_THREADS * 8 - 1) / (SCAN_THREADS * 8), (int64_t)sms * 4));
     k_scan<<<dim3(gx, chunks), SCAN_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, s->h.swar_low, s->h.swar_high,
                                                      d_cand, pend[cur], cnt[cur], best[cur]);
+    count_launch();
     k_scan_resolve<<<g1, 256, 0, st>>>(s->keys.p, pend[cur], cnt[cur], best[cur], d_out, d_dist);
+    count_launch();
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -258,6 +267,7 @@ ct_status ct_lookup(const ct_space* s, const uint64_t* d_cand, int64_t n, int64_
     if (n == 0) return CT_OK;
     const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
     k_lookup<<<g, 256, 0, (cudaStream_t)stream>>>(s->d, s->keys.p, (int64_t)s->n_valid, d_cand, n, d_rank);
+    count_launch();
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -266,7 +276,7 @@ ct_status ct_repair(ct_space* s, const uint64_t* d_cand, int64_t n, uint64_t* d_
     if (!s || n < 0 || (n > 0 && (!d_cand || !d_out))) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
     if (!s->built) { set_error("space not built"); return CT_ERR_STATE; }
     if (s->n_valid == 0) { set_error("empty valid space"); return CT_ERR_EMPTY_SPACE; }
-    return repair_impl(s, d_cand, n, d_out, d_dist, (cudaStream_t)stream);
+    return repair_impl(s, s->rs, d_cand, n, d_out, d_dist, (cudaStream_t)stream);
 }
 
 ct_status ct_set_repair_mode(ct_space* s, int32_t mode, int32_t max_radius) {
@@ -284,6 +294,7 @@ ct_status evaluate_impl(ct_space* s, uint32_t* memo, unsigned long long* unique,
     if (n == 0) return CT_OK;
     const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
     k_evaluate<<<g, 256, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, s->fit, d_keys, n, d_fit, d_rank, memo, unique);
+    count_launch();
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
 }

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -41,6 +42,9 @@ void set_error(const char* fmt, ...) {
     g_err = buf;
 }
 const char* last_error() { return g_err.c_str(); }
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 constexpr int EXP_THREADS = 256;
 constexpr int EXP_ROUNDS = 8;
@@ -228,6 +232,145 @@ k_expand_emit(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tabl
 }
 
 // ---------------------------------------------------------------------------
+// pattern mode: per-signature compacted inner-key lists, then broadcast-OR emission
+// ---------------------------------------------------------------------------
+constexpr int PAT_THREADS = 128;   // >= max words per block (4096 / 32)
+constexpr int PE_THREADS = 256;    // parents per tile of the pattern count/emit kernels
+
+__global__ void __launch_bounds__(PAT_THREADS)
+k_build_patterns(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
+                 const uint32_t* __restrict__ innerkey, int j, uint32_t* __restrict__ pat_cnt,
+                 uint32_t* __restrict__ pat_list) {
+    const DevBlock& bl = sp->blocks[j];
+    const uint32_t sig = blockIdx.x;
+    __shared__ int32_t fidx[MAXP];
+    __shared__ uint32_t wsum[PAT_THREADS / 32];
+    if (threadIdx.x == 0) {
+        uint32_t t = sig;
+        for (int q = bl.n_u - 1; q >= 0; --q) {
+            const int k = bl.u_k[q];
+            fidx[k] = (int32_t)(t % (uint32_t)sp->r[k]);
+            t /= (uint32_t)sp->r[k];
+        }
+    }
+    __syncthreads();
+    const uint32_t* ik = innerkey + bl.innerkey_off;
+    const int t = threadIdx.x;
+    uint32_t m = 0;
+    if (t < bl.W) {
+        m = 0xffffffffu;
+        const int rem = bl.B - t * 32;
+        if (rem < 32) m = (1u << rem) - 1u;
+        for (int c = bl.cons_begin; c < bl.cons_end; ++c) {
+            const DevCons& cs = sp->cons[c];
+            uint32_t o = 0;
+            for (int q = 0; q < cs.n_outer; ++q) o += (uint32_t)fidx[cs.outer_k[q]] * cs.outer_stride[q];
+            m &= tables[cs.table_off + (uint64_t)o * bl.W + t];
+        }
+    }
+    const int lane = t & 31, warp = t >> 5;
+    const uint32_t c = __popc(m);
+    uint32_t inc = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t base = 0, tot = 0;
+    for (int w = 0; w < PAT_THREADS / 32; ++w) { base += (w < warp) ? wsum[w] : 0u; tot += wsum[w]; }
+    uint32_t pos = base + inc - c;
+    uint32_t* list = pat_list + bl.pat_list_off + (uint64_t)sig * bl.Bpad;
+    for (uint32_t mm = m; mm; mm &= mm - 1) list[pos++] = ik[t * 32 + __ffs(mm) - 1];
+    if (t == 0) pat_cnt[bl.pat_cnt_off + sig] = tot;
+}
+
+struct PatArgs {
+    int32_t n_u;
+    int32_t key_shift;
+    uint32_t Bpad;
+    int32_t pad_;
+    uint64_t u_mask[MAXP];
+    int32_t u_off[MAXP];
+    int32_t u_stride[MAXP];
+    const uint32_t* cnt;
+    const uint32_t* list;
+};
+
+__device__ __forceinline__ uint32_t sig_of(const PatArgs& pa, uint64_t parent) {
+    uint32_t sg = 0;
+    for (int q = 0; q < pa.n_u; ++q) sg += (uint32_t)((parent & pa.u_mask[q]) >> pa.u_off[q]) * (uint32_t)pa.u_stride[q];
+    return sg;
+}
+
+__global__ void __launch_bounds__(PE_THREADS)
+k_pcount(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents, uint64_t F,
+         uint32_t* __restrict__ tile_counts) {
+    const uint64_t i = (uint64_t)blockIdx.x * PE_THREADS + threadIdx.x;
+    uint32_t c = 0;
+    if (i < F) c = __ldg(pa.cnt + sig_of(pa, parents ? __ldg(parents + i) : 0ull));
+    __shared__ uint32_t ws[PE_THREADS / 32];
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int w = 0; w < PE_THREADS / 32; ++w) s += ws[w];
+        tile_counts[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(PE_THREADS)
+k_pemit(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents, uint64_t F,
+        const unsigned long long* __restrict__ tile_base, uint64_t* __restrict__ out) {
+    __shared__ uint32_t off_s[PE_THREADS], cnt_s[PE_THREADS], sig_s[PE_THREADS];
+    __shared__ uint64_t par_s[PE_THREADS];
+    __shared__ uint32_t wsum[PE_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint64_t i0 = (uint64_t)blockIdx.x * PE_THREADS;
+    const uint64_t i = i0 + t;
+    uint32_t c = 0, sg = 0;
+    uint64_t parent = 0;
+    if (i < F) {
+        parent = parents ? __ldg(parents + i) : 0ull;
+        sg = sig_of(pa, parent);
+        c = __ldg(pa.cnt + sg);
+    }
+    uint32_t inc = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t base = 0;
+    for (int w = 0; w < warp; ++w) base += wsum[w];
+    off_s[t] = base + inc - c;
+    cnt_s[t] = c;
+    sig_s[t] = sg;
+    par_s[t] = parent;
+    __syncthreads();
+    const uint64_t tb = tile_base[blockIdx.x];
+    const int np = (int)min((uint64_t)PE_THREADS, F - i0);
+    for (int p = warp; p < np; p += PE_THREADS / 32) {
+        const uint32_t cp = cnt_s[p];
+        const uint64_t par = par_s[p];
+        const uint32_t* __restrict__ lst = pa.list + (uint64_t)sig_s[p] * pa.Bpad;
+        uint64_t* __restrict__ o = out + tb + off_s[p];
+        uint32_t jj = lane;
+        for (; jj + 96 < cp; jj += 128) {   // four independent 32-key rows per iteration
+            const uint32_t a0 = __ldg(lst + jj), a1 = __ldg(lst + jj + 32), a2 = __ldg(lst + jj + 64),
+                           a3 = __ldg(lst + jj + 96);
+            o[jj] = par | ((uint64_t)a0 << pa.key_shift);
+            o[jj + 32] = par | ((uint64_t)a1 << pa.key_shift);
+            o[jj + 64] = par | ((uint64_t)a2 << pa.key_shift);
+            o[jj + 96] = par | ((uint64_t)a3 << pa.key_shift);
+        }
+        for (; jj < cp; jj += 32) o[jj] = par | ((uint64_t)__ldg(lst + jj) << pa.key_shift);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host: lowering
 // ---------------------------------------------------------------------------
 static int ceil_log2(int64_t r) {
@@ -388,6 +531,34 @@ static ct_status lower(ct_space* s, int32_t n, const int32_t* nv, const int64_t*
     }
     for (int j = 0; j < h.n_blocks; ++j) if (h.blocks[j].cons_end == 0) h.blocks[j].cons_begin = 0;
 
+    // pattern plan: U = parameters before the block read by its constraints
+    const uint64_t PAT_SIG_MAX = 1ull << 22, PAT_LIST_WORDS_MAX = 1ull << 26;   // 256 MB of lists
+    s->pat_cnt_words = s->pat_list_words = 0;
+    const bool no_patterns = getenv("CATUNE_NO_PATTERNS") != nullptr;   // forces the per-word path
+    for (int j = 0; j < h.n_blocks; ++j) {
+        DevBlock& bl = h.blocks[j];
+        bl.pattern = 0;
+        bl.n_u = 0;
+        if (bl.has_vm || no_patterns) continue;
+        uint64_t used = 0;
+        for (int c = bl.cons_begin; c < bl.cons_end; ++c)
+            for (int q = 0; q < h.cons[c].n_outer; ++q) used |= 1ull << h.cons[c].outer_k[q];
+        uint64_t nsig = 1;
+        for (int k = 0; k < bl.s; ++k)
+            if (used >> k & 1) { bl.u_k[bl.n_u++] = k; nsig *= (uint64_t)h.r[k]; }
+        const uint64_t bpad = ((uint64_t)bl.B + 3) / 4 * 4;
+        if (nsig > PAT_SIG_MAX || s->pat_list_words + nsig * bpad > PAT_LIST_WORDS_MAX) continue;
+        uint64_t st = 1;
+        for (int q = bl.n_u - 1; q >= 0; --q) { bl.u_stride[q] = (int32_t)st; st *= (uint64_t)h.r[bl.u_k[q]]; }
+        bl.pattern = 1;
+        bl.n_sig = (uint32_t)nsig;
+        bl.Bpad = (uint32_t)bpad;
+        bl.pat_cnt_off = s->pat_cnt_words;
+        bl.pat_list_off = s->pat_list_words;
+        s->pat_cnt_words += nsig;
+        s->pat_list_words += nsig * bpad;
+    }
+
     s->frontier.resize(h.n_blocks);
     s->ik_host = std::move(ik_all);
     return CT_OK;
@@ -418,6 +589,8 @@ ct_status ensure_device(ct_space* s) {
         CT_TRY_CUDA(cudaMemcpy(br.d_masks.p, br.masks.data(), br.masks.size() * 4, cudaMemcpyHostToDevice));
         CT_TRY_CUDA(cudaMemcpy(br.d_prefix.p, br.prefix.data(), br.prefix.size() * 8, cudaMemcpyHostToDevice));
     }
+    CT_TRY(s->pat_cnt.ensure(s->pat_cnt_words));
+    CT_TRY(s->pat_list.ensure(s->pat_list_words));
     CT_TRY_CUDA(cudaFuncSetAttribute(k_expand_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      EXP_THREADS * 32 * (int)sizeof(uint64_t)));
     return CT_OK;
@@ -465,10 +638,37 @@ static ct_status ensure_tables(ct_space* s, cudaStream_t st) {
         const unsigned grid = (unsigned)((threads + 255) / 256);
         k_build_tables<<<grid, 256, 0, st>>>(s->d, s->d_tab_cons.p, s->d_tab_prefix.p, (int)s->tab_cons.size(),
                                              words, s->tables.p);
+        count_launch();
         CT_TRY_CUDA(cudaGetLastError());
     }
+    for (int j = 0; j < s->h.n_blocks; ++j) {
+        const DevBlock& bl = s->h.blocks[j];
+        if (!bl.pattern) continue;
+        k_build_patterns<<<bl.n_sig, PAT_THREADS, 0, st>>>(s->d, s->tables.p, s->innerkey.p, j, s->pat_cnt.p,
+                                                           s->pat_list.p);
+        count_launch();
+    }
+    CT_TRY_CUDA(cudaGetLastError());
     s->tables_ready = true;
     return CT_OK;
+}
+
+static PatArgs pat_args(const ct_space* s, int j) {
+    const DevSpace& h = s->h;
+    const DevBlock& bl = h.blocks[j];
+    PatArgs pa;
+    memset(&pa, 0, sizeof pa);
+    pa.n_u = bl.n_u;
+    pa.key_shift = bl.key_shift;
+    pa.Bpad = bl.Bpad;
+    for (int q = 0; q < bl.n_u; ++q) {
+        pa.u_mask[q] = h.fmask[bl.u_k[q]];
+        pa.u_off[q] = h.off[bl.u_k[q]];
+        pa.u_stride[q] = bl.u_stride[q];
+    }
+    pa.cnt = s->pat_cnt.p + bl.pat_cnt_off;
+    pa.list = s->pat_list.p + bl.pat_list_off;
+    return pa;
 }
 
 }  // namespace ct
@@ -476,8 +676,10 @@ static ct_status ensure_tables(ct_space* s, cudaStream_t st) {
 using namespace ct;
 
 ct_space::~ct_space() {
+    for (auto& e : events) cudaEventDestroy(e);
     if (d) cudaFree(d);
     if (h_total) cudaFreeHost(h_total);
+    pat_cnt.release(); pat_list.release();
     tables.release(); d_tab_cons.release(); d_tab_prefix.release(); innerkey.release();
     keys.release(); tile_counts.release(); tile_base.release(); d_total.release(); status.release();
     for (auto& f : frontier) f.release();
@@ -557,37 +759,82 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
     const uint64_t* parents = nullptr;
     uint64_t F = 1;
     s->built = false;
+    memset(&s->stats, 0, sizeof s->stats);
+    s->stats.timed = s->timing;
+    if (s->timing && s->events.empty()) {
+        s->events.resize(4 * (size_t)h.n_blocks);
+        for (auto& e : s->events) CT_TRY_CUDA(cudaEventCreate(&e));
+    }
     for (int j = 0; j < h.n_blocks; ++j) {
-        const uint64_t items = F * (uint64_t)h.blocks[j].W;
-        const uint64_t tiles = (items + EXP_TILE - 1) / EXP_TILE;
+        const DevBlock& bl = h.blocks[j];
+        const uint64_t items = bl.pattern ? F : F * (uint64_t)bl.W;
+        const uint64_t per_tile = bl.pattern ? PE_THREADS : EXP_TILE;
+        const uint64_t tiles = (items + per_tile - 1) / per_tile;
         if (tiles > 0x7fffffffull) { set_error("level %d needs %llu tiles", j, (unsigned long long)tiles); return CT_ERR_LIMIT; }
         CT_TRY(s->tile_counts.ensure(tiles));
         CT_TRY(s->tile_base.ensure(tiles));
         CT_TRY(s->d_total.ensure(1));
-        k_expand_count<<<(unsigned)tiles, EXP_THREADS, 0, st>>>(s->d, s->tables.p, s->innerkey.p, j, parents, items,
-                                                               s->tile_counts.p);
+        PatArgs pa;
+        if (bl.pattern) pa = pat_args(s, j);
+        if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j], st));
+        if (bl.pattern)
+            k_pcount<<<(unsigned)tiles, PE_THREADS, 0, st>>>(pa, parents, F, s->tile_counts.p);
+        else
+            k_expand_count<<<(unsigned)tiles, EXP_THREADS, 0, st>>>(s->d, s->tables.p, s->innerkey.p, j, parents,
+                                                                   items, s->tile_counts.p);
+        if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j + 1], st));
         k_scan_tiles<<<1, 1024, 0, st>>>(s->tile_counts.p, tiles, s->tile_base.p, s->d_total.p);
+        count_launch(2);
         CT_TRY_CUDA(cudaMemcpyAsync(s->h_total, s->d_total.p, 8, cudaMemcpyDeviceToHost, st));
         CT_TRY_CUDA(cudaStreamSynchronize(st));
         const uint64_t Fn = *s->h_total;
         DevBuf<uint64_t>& dst = (j == h.n_blocks - 1) ? s->keys : s->frontier[j];
         CT_TRY(dst.ensure(Fn));
         if (Fn) {
-            k_expand_emit<<<(unsigned)tiles, EXP_THREADS, EXP_THREADS * 32 * sizeof(uint64_t), st>>>(
-                s->d, s->tables.p, s->innerkey.p, j, parents, items, s->tile_base.p, dst.p);
+            if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j + 2], st));
+            if (bl.pattern)
+                k_pemit<<<(unsigned)tiles, PE_THREADS, 0, st>>>(pa, parents, F, s->tile_base.p, dst.p);
+            else
+                k_expand_emit<<<(unsigned)tiles, EXP_THREADS, EXP_THREADS * 32 * sizeof(uint64_t), st>>>(
+                    s->d, s->tables.p, s->innerkey.p, j, parents, items, s->tile_base.p, dst.p);
+            if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j + 3], st));
+            count_launch();
             CT_TRY_CUDA(cudaGetLastError());
         }
+        s->stats.n_levels = j + 1;
+        s->stats.parents[j] = F;
+        s->stats.children[j] = Fn;
         parents = dst.p;
         F = Fn;
         if (F == 0) break;
     }
     CT_TRY_CUDA(cudaStreamSynchronize(st));
+    if (s->timing)
+        for (int j = 0; j < s->stats.n_levels; ++j) {
+            CT_TRY_CUDA(cudaEventElapsedTime(&s->stats.count_ms[j], s->events[4 * j], s->events[4 * j + 1]));
+            if (s->stats.children[j])
+                CT_TRY_CUDA(cudaEventElapsedTime(&s->stats.emit_ms[j], s->events[4 * j + 2], s->events[4 * j + 3]));
+        }
     s->n_valid = F;
     s->built = true;
     if (n_valid_out) *n_valid_out = F;
     if (F == 0) { set_error("no configuration satisfies the constraints"); return CT_ERR_EMPTY_SPACE; }
     return CT_OK;
 }
+
+ct_status ct_space_set_timing(ct_space* s, int32_t enable) {
+    if (!s) { set_error("space is NULL"); return CT_ERR_INVALID_ARG; }
+    s->timing = enable != 0;
+    return CT_OK;
+}
+
+ct_status ct_space_build_stats(const ct_space* s, ct_build_stats* out) {
+    if (!s || !out) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    *out = s->stats;
+    return CT_OK;
+}
+
+uint64_t ct_launch_count(void) { return g_launches.load(); }
 
 ct_status ct_space_keys(const ct_space* s, const uint64_t** d_keys, uint64_t* n) {
     if (!s || !d_keys) { set_error("null argument"); return CT_ERR_INVALID_ARG; }

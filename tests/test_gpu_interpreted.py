@@ -27,9 +27,13 @@ print("OK")
 '''
 
 
-def test_interpreted_constraints(oracle_mod):
+@pytest.mark.parametrize("knob", [("CATUNE_TABLE_WORDS", "0"), ("CATUNE_NO_PATTERNS", "1")])
+def test_interpreted_constraints(oracle_mod, knob):
+    """Both fallback build paths: every constraint interpreted per point, and truth-mask tables
+    expanded per (parent, word) without per-signature patterns."""
     import os
-    env = dict(os.environ, CATUNE_TABLE_WORDS="0")
+    env = dict(os.environ)
+    env[knob[0]] = knob[1]
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", SCRIPT], env=env, cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and "OK" in r.stdout, r.stdout + r.stderr
