@@ -155,6 +155,22 @@ ct_status ct_lookup(const ct_space *space, const uint64_t *d_cand, int64_t n, in
 ct_status ct_repair(ct_space *space, const uint64_t *d_cand, int64_t n, uint64_t *d_out,
                     uint8_t *d_dist, ct_stream stream);
 
+/* Repair that allocates nothing (the paper has no counterpart to this call).
+ * Same arguments and result as ct_repair, for callers that must not allocate
+ * device memory: host applications that reserve device memory through their own
+ * allocator and forbid allocations from libraries, and latency-sensitive loops in
+ * which cudaFree's implicit device-wide synchronisation would stall other streams.
+ * Scratch comes from a fixed array compiled into the library (one ~384 KB copy on
+ * every device that loads it, held until the process exits), so n may not exceed
+ * CT_REPAIR_NOALLOC_MAX (larger n returns CT_ERR_LIMIT; split the batch).  The
+ * first call on each device looks up the array's device address once; make that
+ * call before capturing any stream.  All calls share the array: calls whose
+ * execution overlaps on the GPU race on it, so the caller must order them (one
+ * stream, or explicit synchronisation).  The space must already be built. */
+#define CT_REPAIR_NOALLOC_MAX 16384
+ct_status ct_repair_noalloc(ct_space *space, const uint64_t *d_cand, int64_t n, uint64_t *d_out,
+                            uint8_t *d_dist, ct_stream stream);
+
 /* Repair strategy knob (tests and the autotuner): mode 0 = automatic (Hamming
  * ball search up to a radius chosen from a cost model, then an exhaustive key
  * scan), 1 = exhaustive scan only, 2 = ball search up to max_radius then scan. */

@@ -24,6 +24,7 @@ KINDS = {"de": 0, "pso": 1, "firefly": 2, "ga": 3}
 OP = dict(END=0, PARAM=1, CONST=2, ADD=3, SUB=4, MUL=5, DIV=6, MOD=7, NEG=8, MIN=9, MAX=10, LT=11, LE=12,
           GT=13, GE=14, EQ=15, NE=16, AND=17, OR=18, NOT=19)
 MAX_PARAMS = 32
+REPAIR_NOALLOC_MAX = 16384
 
 
 class CatuneError(RuntimeError):
@@ -67,6 +68,7 @@ _SIGS = {
     "ct_lookup": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p],
     "ct_repair": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_set_repair_mode": [C.c_void_p, C.c_int32, C.c_int32],
+    "ct_repair_noalloc": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_evaluate": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_space_status": [C.c_void_p, C.c_void_p],
     "ct_opt_params_default": [C.POINTER(ct_opt_params)],
@@ -271,6 +273,11 @@ class Space:
 
     def repair(self, cand, out, dist=None, stream=None):
         check(lib().ct_repair(self.h, _ptr(cand), cand.numel(), _ptr(out), _ptr(dist), _stream(stream)))
+
+    def repair_noalloc(self, cand, out, dist=None, stream=None):
+        """ct_repair without device allocations (fixed in-library scratch; at most
+        REPAIR_NOALLOC_MAX candidates per call; calls must not overlap on the GPU)."""
+        check(lib().ct_repair_noalloc(self.h, _ptr(cand), cand.numel(), _ptr(out), _ptr(dist), _stream(stream)))
 
     def set_repair_mode(self, mode, max_radius=0):
         check(lib().ct_set_repair_mode(self.h, mode, max_radius))
