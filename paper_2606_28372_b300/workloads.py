@@ -115,6 +115,15 @@ def large_space() -> SpaceDef:
                   "|V| = |V(large_a)| * |V(large_b)|")
 
 
+def large_slice_space() -> SpaceDef:
+    """The large space with wgx restricted to {64, 128}: 146,321,600 valid keys (1.17 GB), the
+    same constraint structure and key layout widths; a smaller case of the same kernels for
+    hardware-counter captures."""
+    params = list(_LARGE_A[0] + _LARGE_B[0])
+    params[0] = ("wgx", [64, 128])
+    return _space("large_slice", params, _LARGE_A[1] + _LARGE_B[1])
+
+
 def batched_space(s: int) -> SpaceDef:
     """Space ``s`` (0..31) of the batched workload: the medium template with resized value lists.
 
@@ -159,7 +168,7 @@ def batched_space(s: int) -> SpaceDef:
 
 
 SPACES = {"tiny": tiny_space, "medium": medium_space, "large": large_space,
-          "large_a": large_group_a, "large_b": large_group_b}
+          "large_a": large_group_a, "large_b": large_group_b, "large_slice": large_slice_space}
 
 
 # ---------------------------------------------------------------------------------------
