@@ -324,6 +324,7 @@ def run_ours(args):
     sub = {"valid_configs_per_s": value, "cartesian_points_covered_per_s": world * sd.cartesian_size * args.steps / (ms / 1000.0)}
     sub.update(repair_rates(sp, sd, torch, ct, dev))
     sub.update(plain_runs(torch, ct, W, dev))
+    sub.update(batched_runs(torch, ct, W, dev))
     del opt, table
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -408,6 +409,64 @@ def plain_runs(torch, ct, W, dev, gens=500, chunk=50):
         del o
     res["plain_runs_per_s_medium"] = 4 / total
     return res
+
+
+def batched_runs(torch, ct, W, dev, n_runs=4096, gens=100, plain_sample=48):
+    """Batched form: 4096 runs over the 32 batched spaces (mixed DE/PSO/GA, pop 32..128, seed r),
+    `gens` generations as one CUDA graph of persistent launches, launch shape autotuned; against
+    the same run definitions done one at a time through the single-run path (a sample of them)."""
+    import tempfile
+    spaces, mins = [], []
+    for si in range(32):
+        sd = W.batched_space(si)
+        sp = ct.Space.from_def(sd)
+        sp.build()
+        keys = sp.keys().cpu().numpy().view(np.uint64)
+        table = torch.from_numpy(W.smooth_table(sd, sp.unpack(keys), seed=si)).to(dev)
+        sp.set_fitness(table)
+        sp._table_ref = table
+        spaces.append(sp)
+        mins.append(float(table.min()))
+    kinds = ["de", "pso", "ga"]
+    runs = [(r % 32, kinds[r % 3], 32 * (1 + (r // 3) % 4), r, float(np.float32(1.01 * mins[r % 32])))
+            for r in range(n_runs)]
+    b = ct.Batch(spaces, runs)
+    cache = os.path.join(tempfile.gettempdir(), "catune_batch_autotune.jsonl")
+    th, cps, tune_ms = b.autotune(cache, gens=3)
+    b.run_graph(gens)                                  # capture + first replay (warm-up)
+    torch.cuda.synchronize()
+    b.reset()
+    l0 = ct.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.run_graph(gens)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    batched_launches = ct.launch_count() - l0
+    res = b.results()
+    hits = res["hit_evals"][res["hit_evals"] >= 0]
+    # the same runs, one at a time (plain path: per-generation kernels, graph replay per run)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in range(plain_sample):
+        si, kind, pop, seed, tgt = runs[r]
+        o = ct.Opt(spaces[si], kind, pop, seed, target=tgt)
+        o.run_graph(0, 1)
+        o.run_graph(1, gens - 1)
+        del o
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    del b
+    batched = n_runs / (ms / 1000.0)
+    plain = plain_sample / plain_s
+    return {"batched_runs_per_s": batched, "batched_ms_for_all_runs": ms, "batched_generations": gens,
+            "batched_runs": n_runs, "batched_launch": {"threads": th, "ctas_per_sm": cps},
+            "batched_kernel_launches": batched_launches,
+            "plain_runs_per_s_same_runs": plain, "plain_sample_runs": plain_sample,
+            "batched_vs_plain": batched / plain,
+            "batched_runs_within_1pct": int(len(hits)),
+            "batched_median_evals_to_1pct": float(np.median(hits)) if len(hits) else None}
 
 
 if __name__ == "__main__":

@@ -251,6 +251,53 @@ ct_status ct_opt_save(const ct_opt *opt, void *buf, size_t *len, ct_stream strea
 ct_status ct_opt_load(ct_opt *opt, const void *buf, size_t len, ct_stream stream);
 
 /* ------------------------------------------------------------------------- */
+/* batched runs                                                              */
+/* ------------------------------------------------------------------------- */
+/* Many independent runs of the optimizers above (Sections IV-B..IV-D) over
+ * several built spaces, advanced together: one persistent kernel launch per
+ * generation in which each CTA takes whole runs from a work list and performs
+ * propose, repair, GA mutation, memoised evaluation and selection on chip.
+ * Every run gives exactly the trajectory ct_opt gives for the same space, kind,
+ * population, seed and parameters.  Population per run: 3..256. */
+typedef struct {
+    int32_t space;  /* index into the spaces array given to ct_batch_create */
+    int32_t kind;   /* ct_opt_kind */
+    int32_t pop;
+    int32_t pad;
+    uint64_t seed;
+    float target;   /* record unique evaluations when the run's best <= target */
+    int32_t pad2;
+} ct_batch_run;
+
+/* spaces: n_spaces built spaces with fitness tables (borrowed; must outlive the
+ * batch).  params: shared hyper-parameters (NULL = Table IV); each run's target
+ * replaces params->target.  Allocates all run state on the device. */
+ct_status ct_batch_create(ct_space *const *spaces, int32_t n_spaces, const ct_batch_run *runs, int32_t n_runs,
+                          const ct_opt_params *params, ct_batch **out);
+void ct_batch_destroy(ct_batch *batch);
+/* One generation for every run (generation 0 first). Asynchronous. */
+ct_status ct_batch_step(ct_batch *batch, ct_stream stream);
+/* `count` generations as one CUDA graph (captured once per count, replayed). */
+ct_status ct_batch_run_graph(ct_batch *batch, uint32_t count, ct_stream stream);
+/* Per-run summaries into host arrays of n_runs entries (each may be NULL). Synchronises. */
+ct_status ct_batch_results(ct_batch *batch, uint64_t *best_key, float *best_fit, uint64_t *n_unique,
+                           int64_t *hit_generation, int64_t *hit_evals, ct_stream stream);
+/* Copies run `run`'s population keys, fitness and positions to caller device buffers. */
+ct_status ct_batch_run_state(const ct_batch *batch, int32_t run, uint64_t *d_keys, float *d_fit, float *d_pos,
+                             ct_stream stream);
+/* Returns every run to its state before generation 0 (synchronises the device). */
+ct_status ct_batch_reset(ct_batch *batch);
+/* Launch shape of the persistent kernel: threads per CTA (64, 128 or 256) and
+ * CTAs per SM (0 = 4). Results do not depend on it. */
+ct_status ct_batch_set_launch(ct_batch *batch, int32_t threads, int32_t ctas_per_sm);
+/* Autotuner: times `gens` generations for each launch shape from the reset state,
+ * requires every shape to end in the same state, keeps the fastest and resets the
+ * batch.  cache_path (nullable): a JSON-lines file; a stored result for the same
+ * batch signature is reused, a new one appended.  Synchronises. */
+ct_status ct_batch_autotune(ct_batch *batch, const char *cache_path, int32_t gens, int32_t *threads_out,
+                            int32_t *ctas_per_sm_out, float *ms_out, ct_stream stream);
+
+/* ------------------------------------------------------------------------- */
 /* measurement                                                               */
 /* ------------------------------------------------------------------------- */
 /* Per-level statistics of the last ct_build_valid_space: parents expanded,

@@ -84,6 +84,16 @@ _SIGS = {
     "ct_opt_state": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_opt_save": [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t), C.c_void_p],
     "ct_opt_load": [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p],
+    "ct_batch_create": [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.POINTER(ct_opt_params), C.POINTER(C.c_void_p)],
+    "ct_batch_destroy": [C.c_void_p],
+    "ct_batch_step": [C.c_void_p, C.c_void_p],
+    "ct_batch_run_graph": [C.c_void_p, C.c_uint32, C.c_void_p],
+    "ct_batch_results": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "ct_batch_run_state": [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "ct_batch_reset": [C.c_void_p],
+    "ct_batch_set_launch": [C.c_void_p, C.c_int32, C.c_int32],
+    "ct_batch_autotune": [C.c_void_p, C.c_char_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                          C.POINTER(C.c_float), C.c_void_p],
     "ct_space_set_timing": [C.c_void_p, C.c_int32],
     "ct_space_build_stats": [C.c_void_p, C.c_void_p],
     "ct_launch_count": [],
@@ -107,6 +117,7 @@ def lib():
         L.ct_version.restype = C.c_char_p
         L.ct_space_destroy.restype = None
         L.ct_opt_destroy.restype = None
+        L.ct_batch_destroy.restype = None
         L.ct_opt_params_default.restype = None
         L.ct_launch_count.restype = C.c_uint64
         _lib = L
@@ -371,6 +382,68 @@ class Opt:
     def load(self, blob, stream=None):
         buf = C.create_string_buffer(blob, len(blob))
         check(lib().ct_opt_load(self.h, C.cast(buf, C.c_void_p), len(blob), _stream(stream)))
+
+
+class ct_batch_run(C.Structure):
+    _fields_ = [("space", C.c_int32), ("kind", C.c_int32), ("pop", C.c_int32), ("pad", C.c_int32),
+                ("seed", C.c_uint64), ("target", C.c_float), ("pad2", C.c_int32)]
+
+
+class Batch:
+    """ct_batch: many independent runs over several spaces, one persistent launch per generation.
+
+    runs: list of (space_index, kind, pop, seed, target)."""
+
+    def __init__(self, spaces, runs, **params):
+        self.spaces = list(spaces)
+        self.n = len(runs)
+        arr = (ct_batch_run * self.n)()
+        for i, (si, kind, pop, seed, target) in enumerate(runs):
+            arr[i].space, arr[i].kind, arr[i].pop, arr[i].seed = si, KINDS[kind], pop, seed
+            arr[i].target = float(np.float32(target))
+        hs = (C.c_void_p * len(self.spaces))(*[s.h.value for s in self.spaces])
+        self.params = default_params(**params)
+        h = C.c_void_p()
+        check(lib().ct_batch_create(C.cast(hs, C.c_void_p), len(self.spaces), C.cast(arr, C.c_void_p), self.n,
+                                    C.byref(self.params), C.byref(h)))
+        self.h = h
+        self.runs = runs
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ct_batch_destroy(self.h)
+            self.h = None
+
+    def step(self, stream=None):
+        check(lib().ct_batch_step(self.h, _stream(stream)))
+
+    def run_graph(self, count, stream=None):
+        check(lib().ct_batch_run_graph(self.h, count, _stream(stream)))
+
+    def reset(self):
+        check(lib().ct_batch_reset(self.h))
+
+    def set_launch(self, threads, ctas_per_sm):
+        check(lib().ct_batch_set_launch(self.h, threads, ctas_per_sm))
+
+    def autotune(self, cache_path=None, gens=5, stream=None):
+        t, c, ms = C.c_int32(), C.c_int32(), C.c_float()
+        check(lib().ct_batch_autotune(self.h, cache_path.encode() if cache_path else None, gens, C.byref(t),
+                                      C.byref(c), C.byref(ms), _stream(stream)))
+        return int(t.value), int(c.value), float(ms.value)
+
+    def results(self, stream=None):
+        bk = np.zeros(self.n, np.uint64)
+        bf = np.zeros(self.n, np.float32)
+        nu = np.zeros(self.n, np.uint64)
+        hg = np.zeros(self.n, np.int64)
+        he = np.zeros(self.n, np.int64)
+        check(lib().ct_batch_results(self.h, *[a.ctypes.data_as(C.c_void_p) for a in (bk, bf, nu, hg, he)],
+                                     _stream(stream)))
+        return dict(best_key=bk, best_fit=bf, n_unique=nu, hit_gen=hg, hit_evals=he)
+
+    def run_state(self, run, keys=None, fit=None, pos=None, stream=None):
+        check(lib().ct_batch_run_state(self.h, run, _ptr(keys), _ptr(fit), _ptr(pos), _stream(stream)))
 
 
 def u64(t):

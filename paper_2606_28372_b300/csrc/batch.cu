@@ -1,0 +1,520 @@
+// Batched form: thousands of independent constraint-aware runs over many spaces of
+// uneven size, one persistent kernel launch per generation.
+//
+// Each CTA takes runs from a work list (largest first) and performs the whole
+// generation of a run on chip: propose (Sections IV-B..IV-D), repair (exact
+// Hamming nearest valid key: table test, then Hamming balls of growing radius,
+// then a scan of the space's keys for what is left), GA mutation, memoised
+// evaluation and selection.  The per-run arithmetic is the same device code as
+// the single-run kernels, so every batched run equals the same run done alone.
+// A generation is two launches (the persistent kernel and a one-thread advance
+// of the generation counter), so G generations replay as one CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <new>
+#include <sstream>
+#include <vector>
+
+#include "internal.hpp"
+#include "optim_dev.cuh"
+
+namespace ct {
+
+constexpr int BATCH_MAX_POP = 256;
+
+struct BatchSpace {
+    const DevSpace* sp;
+    const uint32_t* tables;
+    const uint64_t* keys;
+    int64_t nv;
+    const float* fit;
+    int32_t dmax;
+    int32_t pad_;
+    const uint32_t* masks[MAX_RADIUS];
+    const uint64_t* prefix[MAX_RADIUS];
+    int32_t n_subsets[MAX_RADIUS];
+    uint64_t total[MAX_RADIUS];
+    uint64_t swar_low, swar_high;
+    float eps;
+    int32_t N;
+};
+
+struct BatchRun {
+    int32_t space, kind, P, pad_;
+    uint64_t seed;
+    float target;
+    int32_t pad2_;
+    uint64_t off_pop, off_pn, off_n, off_memo;
+};
+
+struct BatchArgs {
+    const BatchSpace* spaces;
+    const BatchRun* runs;
+    const int32_t* order;
+    int32_t n_runs;
+    ct_opt_params prm;
+    OptDev* st;
+    uint64_t* X;
+    float* FX;
+    float* pos;
+    float* vel;
+    float* pb;
+    float* fpb;
+    float* gb;
+    float* ynew;
+    uint32_t* memo;
+    uint32_t* work;
+    const uint32_t* gen;
+};
+
+struct RepairSmem {
+    int32_t pend[BATCH_MAX_POP];
+    unsigned long long best[BATCH_MAX_POP];
+    int npend;
+};
+
+// exact nearest valid key (Hamming on value indices, ties to the smallest key) for P candidates
+__device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t* rep, int P, RepairSmem& rs) {
+    const DevSpace* sp = bs.sp;
+    const int t = threadIdx.x, nt = blockDim.x;
+    if (t == 0) rs.npend = 0;
+    __syncthreads();
+    for (int i = t; i < P; i += nt) {
+        const uint64_t c = cand[i];
+        if (valid_key(sp, bs.tables, c)) rep[i] = c;
+        else rs.pend[atomicAdd(&rs.npend, 1)] = i;
+    }
+    __syncthreads();
+    for (int d = 1; d <= bs.dmax; ++d) {
+        const int np = rs.npend;
+        if (np == 0) break;
+        for (int q = t; q < np; q += nt) rs.best[q] = ~0ull;
+        __syncthreads();
+        const uint64_t pts = bs.total[d - 1];
+        const uint32_t* masks = bs.masks[d - 1];
+        const uint64_t* prefix = bs.prefix[d - 1];
+        const int nsub = bs.n_subsets[d - 1];
+        const uint64_t total = (uint64_t)np * pts;
+        for (uint64_t g = t; g < total; g += nt) {
+            const uint64_t q = g / pts, j = g - q * pts;
+            const uint64_t u = cand[rs.pend[q]];
+            int lo = 0, hi = nsub - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(prefix + mid) <= j) lo = mid; else hi = mid - 1;
+            }
+            uint32_t local = (uint32_t)(j - __ldg(prefix + lo));
+            uint32_t m = __ldg(masks + lo);
+            uint64_t key = u;
+            while (m) {
+                const int k = 31 - __clz(m);
+                m &= ~(1u << k);
+                const uint32_t alt = (uint32_t)sp->r[k] - 1u;
+                const uint32_t a = local % alt;
+                local /= alt;
+                const uint32_t uk = (uint32_t)field(sp, u, k);
+                key = (key & ~sp->fmask[k]) | ((uint64_t)(a < uk ? a : a + 1u) << sp->off[k]);
+            }
+            if (valid_key(sp, bs.tables, key)) atomicMin(&rs.best[q], (unsigned long long)key);
+        }
+        __syncthreads();
+        if (t == 0) {
+            int n2 = 0;
+            for (int q = 0; q < np; ++q) {
+                if (rs.best[q] != ~0ull) rep[rs.pend[q]] = rs.best[q];
+                else rs.pend[n2++] = rs.pend[q];
+            }
+            rs.npend = n2;
+        }
+        __syncthreads();
+    }
+    // exhaustive scan for the rest, eight candidates per pass over the keys
+    const int np = rs.npend;
+    for (int q0 = 0; q0 < np; q0 += 8) {
+        const int nq = min(8, np - q0);
+        for (int q = t; q < nq; q += nt) rs.best[q0 + q] = ~0ull;
+        __syncthreads();
+        uint64_t cu[8];
+        unsigned long long b[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { cu[q] = q < nq ? cand[rs.pend[q0 + q]] : 0ull; b[q] = ~0ull; }
+        for (int64_t i = t; i < bs.nv; i += nt) {
+            const uint64_t k = __ldg(bs.keys + i);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const unsigned long long p = ((unsigned long long)hamming_keys(k, cu[q], bs.swar_low, bs.swar_high) << 57) |
+                                             (unsigned long long)i;
+                b[q] = p < b[q] ? p : b[q];
+            }
+        }
+        for (int q = 0; q < nq; ++q) atomicMin(&rs.best[q0 + q], b[q]);
+        __syncthreads();
+        for (int q = t; q < nq; q += nt) rep[rs.pend[q0 + q]] = __ldg(bs.keys + (rs.best[q0 + q] & ((1ull << 57) - 1)));
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256, 1) k_batch_gen(const __grid_constant__ BatchArgs ba) {
+    __shared__ uint64_t cand[BATCH_MAX_POP], rep[BATCH_MAX_POP];
+    __shared__ float fit[BATCH_MAX_POP];
+    __shared__ int order[BATCH_MAX_POP];
+    __shared__ SelectSmem sel;
+    __shared__ RepairSmem rsm;
+    __shared__ int slot_s;
+    const uint32_t gen = *ba.gen;
+    while (true) {
+        if (threadIdx.x == 0) slot_s = (int)atomicAdd(ba.work, 1u);
+        __syncthreads();
+        const int slot = slot_s;
+        __syncthreads();
+        if (slot >= ba.n_runs) break;
+        const int r = ba.order[slot];
+        const BatchRun run = ba.runs[r];
+        const BatchSpace& bs = ba.spaces[run.space];
+        OptArgs a;
+        a.kind = run.kind; a.P = run.P; a.N = bs.N; a.seed = run.seed; a.prm = ba.prm; a.prm.target = run.target;
+        a.eps = bs.eps; a.sp = bs.sp; a.tables = bs.tables; a.keys = bs.keys; a.nv = bs.nv;
+        a.st = ba.st + r; a.X = ba.X + run.off_pop; a.FX = ba.FX + run.off_pop;
+        a.pos = ba.pos + run.off_pn; a.vel = ba.vel + run.off_pn; a.pb = ba.pb + run.off_pn;
+        a.fpb = ba.fpb + run.off_pop; a.gb = ba.gb + run.off_n; a.ynew = ba.ynew + run.off_pn;
+        const int P = run.P;
+        propose_dev(a, gen, cand, order);
+        __syncthreads();
+        cta_repair(bs, cand, rep, P, rsm);
+        post_repair_dev(a, gen, rep);
+        __syncthreads();
+        uint32_t* memo = ba.memo + run.off_memo;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const int64_t rk = rank_of(bs.keys, bs.nv, rep[i]);
+            fit[i] = __ldg(bs.fit + rk);
+            const uint32_t bit = 1u << (rk & 31);
+            const uint32_t old = atomicOr(memo + (rk >> 5), bit);
+            if (!(old & bit)) atomicAdd(&a.st->n_unique, 1ull);
+        }
+        __syncthreads();
+        select_dev(a, gen, rep, fit, sel);
+    }
+}
+
+__global__ void k_batch_advance(uint32_t* gen, uint32_t* work) {
+    *gen += 1;
+    *work = 0;
+}
+
+}  // namespace ct
+
+using namespace ct;
+
+struct ct_batch {
+    std::vector<ct_space*> spaces;
+    std::vector<ct_batch_run> runs_h;
+    ct_opt_params prm{};
+    DevBuf<BatchSpace> d_spaces;
+    DevBuf<BatchRun> d_runs;
+    DevBuf<int32_t> d_order;
+    DevBuf<OptDev> st;
+    DevBuf<uint64_t> X;
+    DevBuf<float> FX, pos, vel, pb, fpb, gb, ynew;
+    DevBuf<uint32_t> memo, ctr;   // ctr[0] = generation, ctr[1] = work counter
+    std::vector<BatchRun> brun;
+    uint64_t n_pop = 0, n_pn = 0, n_n = 0, n_memo = 0;
+    int threads = 256, ctas_per_sm = 0, sms = 148;
+    std::map<uint32_t, cudaGraphExec_t> graphs;
+    uint32_t generation = 0;      // host mirror (generations launched)
+    ~ct_batch() {
+        for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+        d_spaces.release(); d_runs.release(); d_order.release(); st.release(); X.release(); FX.release();
+        pos.release(); vel.release(); pb.release(); fpb.release(); gb.release(); ynew.release(); memo.release();
+        ctr.release();
+    }
+    BatchArgs args() const {
+        BatchArgs a;
+        a.spaces = d_spaces.p; a.runs = d_runs.p; a.order = d_order.p; a.n_runs = (int)runs_h.size(); a.prm = prm;
+        a.st = st.p; a.X = X.p; a.FX = FX.p; a.pos = pos.p; a.vel = vel.p; a.pb = pb.p; a.fpb = fpb.p; a.gb = gb.p;
+        a.ynew = ynew.p; a.memo = memo.p; a.work = ctr.p + 1; a.gen = ctr.p;
+        return a;
+    }
+    int grid() const {
+        int per = ctas_per_sm > 0 ? ctas_per_sm : 4;
+        return std::max(1, std::min((int)runs_h.size(), sms * per));
+    }
+};
+
+namespace ct {
+static ct_status batch_launch(ct_batch* b, cudaStream_t st) {
+    k_batch_gen<<<b->grid(), b->threads, 0, st>>>(b->args());
+    k_batch_advance<<<1, 1, 0, st>>>(b->ctr.p, b->ctr.p + 1);
+    count_launch(2);
+    CT_TRY_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+static ct_status batch_reset(ct_batch* b) {
+    const size_t R = b->runs_h.size();
+    std::vector<OptDev> init(R);
+    for (size_t i = 0; i < R; ++i) {
+        OptDev& o = init[i];
+        memset(&o, 0, sizeof o);
+        o.de_fbest = __builtin_inff();
+        o.fgb = __builtin_inff();
+        o.best_key = ~0ull;
+        o.best_fit = __builtin_inff();
+        o.hit_gen = -1;
+        o.hit_evals = -1;
+    }
+    CT_TRY_CUDA(cudaMemcpy(b->st.p, init.data(), R * sizeof(OptDev), cudaMemcpyHostToDevice));
+    CT_TRY_CUDA(cudaMemset(b->memo.p, 0, b->n_memo * 4));
+    CT_TRY_CUDA(cudaMemset(b->pos.p, 0, b->n_pn * 4));
+    CT_TRY_CUDA(cudaMemset(b->vel.p, 0, b->n_pn * 4));
+    CT_TRY_CUDA(cudaMemset(b->pb.p, 0, b->n_pn * 4));
+    CT_TRY_CUDA(cudaMemset(b->ynew.p, 0, b->n_pn * 4));
+    CT_TRY_CUDA(cudaMemset(b->gb.p, 0, b->n_n * 4));
+    CT_TRY_CUDA(cudaMemset(b->ctr.p, 0, 8));
+    b->generation = 0;
+    return CT_OK;
+}
+}  // namespace ct
+
+extern "C" {
+
+ct_status ct_batch_create(ct_space* const* spaces, int32_t n_spaces, const ct_batch_run* runs, int32_t n_runs,
+                          const ct_opt_params* params, ct_batch** out) {
+    if (!spaces || n_spaces < 1 || !runs || n_runs < 1 || !out) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
+    *out = nullptr;
+    std::vector<BatchSpace> bsp(n_spaces);
+    for (int s = 0; s < n_spaces; ++s) {
+        ct_space* sp = spaces[s];
+        if (!sp || !sp->built || sp->n_valid == 0 || !sp->fit) { set_error("space %d is not built or has no fitness table", s); return CT_ERR_STATE; }
+        BatchSpace& b = bsp[s];
+        memset(&b, 0, sizeof b);
+        b.sp = sp->d; b.tables = sp->tables.p; b.keys = sp->keys.p; b.nv = (int64_t)sp->n_valid; b.fit = sp->fit;
+        b.dmax = std::min<int>(auto_radius(sp), MAX_RADIUS);
+        for (int d = 0; d < b.dmax; ++d) {
+            b.masks[d] = sp->balls[d].d_masks.p;
+            b.prefix[d] = sp->balls[d].d_prefix.p;
+            b.n_subsets[d] = (int)sp->balls[d].masks.size();
+            b.total[d] = sp->balls[d].total;
+        }
+        b.swar_low = sp->h.swar_low; b.swar_high = sp->h.swar_high;
+        int rmax = 1;
+        for (int k = 0; k < sp->h.n; ++k) rmax = std::max(rmax, (int)sp->h.r[k]);
+        b.eps = rmax > 1 ? 1.0f / (float)(rmax - 1) : 1.0f;
+        b.N = sp->h.n;
+    }
+    ct_batch* bt = new (std::nothrow) ct_batch();
+    if (!bt) { set_error("host allocation failed"); return CT_ERR_OOM; }
+    bt->spaces.assign(spaces, spaces + n_spaces);
+    bt->runs_h.assign(runs, runs + n_runs);
+    if (params) bt->prm = *params; else ct_opt_params_default(&bt->prm);
+    bt->brun.resize(n_runs);
+    std::vector<std::pair<double, int>> cost(n_runs);
+    for (int r = 0; r < n_runs; ++r) {
+        const ct_batch_run& u = runs[r];
+        if (u.space < 0 || u.space >= n_spaces || u.kind < CT_DE || u.kind > CT_GA || u.pop < 3 || u.pop > BATCH_MAX_POP) {
+            delete bt;
+            set_error("run %d: bad space/kind/pop (pop must be in [3, %d])", r, BATCH_MAX_POP);
+            return CT_ERR_INVALID_ARG;
+        }
+        const ct_space* sp = spaces[u.space];
+        BatchRun& br = bt->brun[r];
+        memset(&br, 0, sizeof br);
+        br.space = u.space; br.kind = u.kind; br.P = u.pop; br.seed = u.seed; br.target = u.target;
+        br.off_pop = bt->n_pop; bt->n_pop += u.pop;
+        br.off_pn = bt->n_pn; bt->n_pn += (uint64_t)u.pop * sp->h.n;
+        br.off_n = bt->n_n; bt->n_n += sp->h.n;
+        br.off_memo = bt->n_memo; bt->n_memo += (sp->n_valid + 31) / 32;
+        // cost: population times (neighbourhood work ~ log |V|), Firefly quadratic in P
+        const double P = u.pop;
+        cost[r] = {-(u.kind == CT_FIREFLY ? P * P : P * 8.0) * (1.0 + std::log2((double)sp->n_valid)), r};
+    }
+    std::stable_sort(cost.begin(), cost.end());
+    std::vector<int32_t> order(n_runs);
+    for (int i = 0; i < n_runs; ++i) order[i] = cost[i].second;
+    ct_status e = CT_OK;
+#define ALLOC(b, n) if (e == CT_OK) e = bt->b.ensure(n)
+    ALLOC(d_spaces, n_spaces); ALLOC(d_runs, n_runs); ALLOC(d_order, n_runs); ALLOC(st, n_runs);
+    ALLOC(X, bt->n_pop); ALLOC(FX, bt->n_pop); ALLOC(fpb, bt->n_pop); ALLOC(pos, bt->n_pn); ALLOC(vel, bt->n_pn);
+    ALLOC(pb, bt->n_pn); ALLOC(ynew, bt->n_pn); ALLOC(gb, bt->n_n); ALLOC(memo, bt->n_memo); ALLOC(ctr, 2);
+#undef ALLOC
+    if (e == CT_OK && (cudaMemcpy(bt->d_spaces.p, bsp.data(), n_spaces * sizeof(BatchSpace), cudaMemcpyHostToDevice) != cudaSuccess ||
+                       cudaMemcpy(bt->d_runs.p, bt->brun.data(), n_runs * sizeof(BatchRun), cudaMemcpyHostToDevice) != cudaSuccess ||
+                       cudaMemcpy(bt->d_order.p, order.data(), n_runs * 4, cudaMemcpyHostToDevice) != cudaSuccess)) {
+        set_error("uploading the batch failed");
+        e = CT_ERR_CUDA;
+    }
+    if (e == CT_OK) e = batch_reset(bt);
+    if (e != CT_OK) { delete bt; return e; }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&bt->sms, cudaDevAttrMultiProcessorCount, dev);
+    *out = bt;
+    return CT_OK;
+}
+
+void ct_batch_destroy(ct_batch* b) { delete b; }
+
+ct_status ct_batch_set_launch(ct_batch* b, int32_t threads, int32_t ctas_per_sm) {
+    if (!b || (threads != 64 && threads != 128 && threads != 256) || ctas_per_sm < 0 || ctas_per_sm > 16) {
+        set_error("threads must be 64, 128 or 256; ctas_per_sm in [0, 16]");
+        return CT_ERR_INVALID_ARG;
+    }
+    b->threads = threads;
+    b->ctas_per_sm = ctas_per_sm;
+    for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
+    b->graphs.clear();
+    return CT_OK;
+}
+
+ct_status ct_batch_step(ct_batch* b, ct_stream stream) {
+    if (!b) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    CT_TRY(batch_launch(b, (cudaStream_t)stream));
+    b->generation++;
+    return CT_OK;
+}
+
+ct_status ct_batch_run_graph(ct_batch* b, uint32_t count, ct_stream stream) {
+    if (!b || count == 0) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    auto it = b->graphs.find(count);
+    if (it == b->graphs.end()) {
+        cudaStream_t cap;
+        CT_TRY_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            set_error("stream capture failed to start");
+            return CT_ERR_CUDA;
+        }
+        ct_status e = CT_OK;
+        const uint64_t c0 = ct_launch_count();
+        for (uint32_t i = 0; i < count && e == CT_OK; ++i) e = batch_launch(b, cap);
+        count_launch(0 - (ct_launch_count() - c0));
+        cudaGraph_t g;
+        cudaError_t ce = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (e != CT_OK) return e;
+        if (ce != cudaSuccess) { set_error("capture failed: %s", cudaGetErrorString(ce)); return CT_ERR_CUDA; }
+        cudaGraphExec_t ex;
+        ce = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) { set_error("instantiate failed: %s", cudaGetErrorString(ce)); return CT_ERR_CUDA; }
+        it = b->graphs.emplace(count, ex).first;
+    }
+    CT_TRY_CUDA(cudaGraphLaunch(it->second, st));
+    count_launch(2ull * count);
+    b->generation += count;
+    return CT_OK;
+}
+
+ct_status ct_batch_results(ct_batch* b, uint64_t* best_key, float* best_fit, uint64_t* n_unique, int64_t* hit_gen,
+                           int64_t* hit_evals, ct_stream stream) {
+    if (!b) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    const size_t R = b->runs_h.size();
+    std::vector<OptDev> h(R);
+    cudaStream_t st = (cudaStream_t)stream;
+    CT_TRY_CUDA(cudaMemcpyAsync(h.data(), b->st.p, R * sizeof(OptDev), cudaMemcpyDeviceToHost, st));
+    CT_TRY_CUDA(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < R; ++i) {
+        if (best_key) best_key[i] = h[i].best_key;
+        if (best_fit) best_fit[i] = h[i].best_fit;
+        if (n_unique) n_unique[i] = h[i].n_unique;
+        if (hit_gen) hit_gen[i] = h[i].hit_gen;
+        if (hit_evals) hit_evals[i] = h[i].hit_evals;
+    }
+    return CT_OK;
+}
+
+ct_status ct_batch_run_state(const ct_batch* b, int32_t run, uint64_t* d_keys, float* d_fit, float* d_pos, ct_stream stream) {
+    if (!b || run < 0 || run >= (int)b->runs_h.size()) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
+    const BatchRun& br = b->brun[run];
+    const int N = b->spaces[br.space]->h.n;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (d_keys) CT_TRY_CUDA(cudaMemcpyAsync(d_keys, b->X.p + br.off_pop, br.P * 8, cudaMemcpyDeviceToDevice, st));
+    if (d_fit) CT_TRY_CUDA(cudaMemcpyAsync(d_fit, b->FX.p + br.off_pop, br.P * 4, cudaMemcpyDeviceToDevice, st));
+    if (d_pos) CT_TRY_CUDA(cudaMemcpyAsync(d_pos, b->pos.p + br.off_pn, (size_t)br.P * N * 4, cudaMemcpyDeviceToDevice, st));
+    return CT_OK;
+}
+
+ct_status ct_batch_reset(ct_batch* b) {
+    if (!b) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    CT_TRY_CUDA(cudaDeviceSynchronize());
+    return batch_reset(b);
+}
+
+// Autotuner: times `gens` generations for every (threads, CTAs per SM) variant from a reset
+// state, checks that every variant ends in the same state as the first, keeps the fastest,
+// and leaves the batch reset.  With a cache path, a previous result for the same batch
+// signature is reused, and a new one is appended.
+ct_status ct_batch_autotune(ct_batch* b, const char* cache_path, int32_t gens, int32_t* threads_out,
+                            int32_t* ctas_out, float* ms_out, ct_stream stream) {
+    if (!b || gens < 1) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    std::ostringstream sig;
+    sig << "runs=" << b->runs_h.size() << ";pop=" << b->n_pop << ";pn=" << b->n_pn << ";memo=" << b->n_memo << ";sms=" << b->sms;
+    const std::string key = sig.str();
+    if (cache_path && *cache_path) {
+        std::ifstream f(cache_path);
+        std::string line;
+        while (std::getline(f, line)) {
+            if (line.find("\"" + key + "\"") == std::string::npos) continue;
+            int th = 0, cps = 0;
+            float ms = 0;
+            if (sscanf(line.c_str() + line.find("threads"), "threads\": %d, \"ctas_per_sm\": %d, \"ms\": %f", &th, &cps, &ms) == 3) {
+                CT_TRY(ct_batch_set_launch(b, th, cps));
+                if (threads_out) *threads_out = th;
+                if (ctas_out) *ctas_out = cps;
+                if (ms_out) *ms_out = ms;
+                return CT_OK;
+            }
+        }
+    }
+    const int variants[][2] = {{64, 8}, {64, 16}, {128, 4}, {128, 8}, {256, 2}, {256, 4}};
+    std::vector<uint64_t> ref_keys;
+    float best_ms = 1e30f;
+    int best_t = 256, best_c = 4;
+    cudaEvent_t e0, e1;
+    CT_TRY_CUDA(cudaEventCreate(&e0));
+    CT_TRY_CUDA(cudaEventCreate(&e1));
+    for (auto& v : variants) {
+        CT_TRY(batch_reset(b));
+        b->threads = v[0];
+        b->ctas_per_sm = v[1];
+        CT_TRY_CUDA(cudaEventRecord(e0, st));
+        for (int g = 0; g < gens; ++g) CT_TRY(batch_launch(b, st));
+        CT_TRY_CUDA(cudaEventRecord(e1, st));
+        CT_TRY_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        CT_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        std::vector<uint64_t> keys(b->n_pop);
+        CT_TRY_CUDA(cudaMemcpy(keys.data(), b->X.p, b->n_pop * 8, cudaMemcpyDeviceToHost));
+        if (ref_keys.empty()) ref_keys = keys;
+        else if (keys != ref_keys) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            set_error("autotune variant threads=%d ctas_per_sm=%d changed the result", v[0], v[1]);
+            return CT_ERR_STATE;
+        }
+        if (ms < best_ms) { best_ms = ms; best_t = v[0]; best_c = v[1]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CT_TRY(batch_reset(b));
+    CT_TRY(ct_batch_set_launch(b, best_t, best_c));
+    if (cache_path && *cache_path) {
+        std::ofstream f(cache_path, std::ios::app);
+        f << "{\"batch\": \"" << key << "\", \"threads\": " << best_t << ", \"ctas_per_sm\": " << best_c
+          << ", \"ms\": " << best_ms << "}\n";
+    }
+    if (threads_out) *threads_out = best_t;
+    if (ctas_out) *ctas_out = best_c;
+    if (ms_out) *ms_out = best_ms;
+    return CT_OK;
+}
+
+}  // extern "C"

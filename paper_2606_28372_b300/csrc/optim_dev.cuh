@@ -1,0 +1,398 @@
+// Per-run optimizer logic as CTA-level device functions (Sections IV-B..IV-D, Table IV),
+// shared by the single-run kernels and the batched persistent kernel.
+#pragma once
+#include "internal.hpp"
+
+namespace ct {
+
+struct OptDev {
+    uint64_t de_best;
+    float de_fbest;
+    int32_t stag;
+    int32_t reinit_pending;
+    float fgb;
+    uint64_t best_key;
+    float best_fit;
+    uint32_t gen;              // next generation (advanced by select)
+    unsigned long long n_unique;
+    long long hit_gen, hit_evals;
+};
+
+struct OptArgs {
+    int kind, P, N;
+    uint64_t seed;
+    ct_opt_params prm;
+    float eps;
+    const DevSpace* sp;
+    const uint32_t* tables;
+    const uint64_t* keys;
+    int64_t nv;
+    OptDev* st;
+    uint64_t* X;
+    float* FX;
+    float* pos;
+    float* vel;
+    float* pb;
+    float* fpb;
+    float* gb;
+    float* ynew;
+};
+
+constexpr int OPT_THREADS = 256;
+
+__device__ __forceinline__ float clip01(float v) { return v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v); }
+
+__device__ __forceinline__ uint64_t stratified_key(const OptArgs& a, uint32_t k, uint32_t gen, uint32_t purpose) {
+    const uint64_t nv = (uint64_t)a.nv;
+    const uint64_t lo = (uint64_t)(((unsigned __int128)k * nv) / (uint32_t)a.P);
+    const uint64_t hi = (uint64_t)(((unsigned __int128)(k + 1) * nv) / (uint32_t)a.P);
+    uint64_t off = 0;
+    if (hi > lo) {
+        uint32_t w[4];
+        rng_block(a.seed, k, gen, purpose, 0, w);
+        off = uint64_below(w[1], w[0], hi - lo);
+    }
+    return __ldg(a.keys + lo + off);
+}
+
+__device__ __forceinline__ uint64_t snap_key(const OptArgs& a, const float* x) {
+    uint64_t key = 0;
+    for (int k = 0; k < a.N; ++k) {
+        const float q = rintf(__fdiv_rn(x[k], a.eps));
+        int v = (int)q;
+        if (q < 0.0f) v = 0;
+        if (v > a.sp->r[k] - 1) v = a.sp->r[k] - 1;
+        key |= (uint64_t)v << a.sp->off[k];
+    }
+    return key;
+}
+
+// Cody-Waite reduction + degree-7 Taylor polynomial, binary32 ops rounded one by
+// one; x <= 0, x < -80 gives 0.
+__device__ __forceinline__ float exp_ct(float x) {
+    if (!(x >= -80.0f)) return 0.0f;
+    if (x > 0.0f) x = 0.0f;
+    const float LOG2E = 1.44269504088896340736f;
+    const float LN2_HI = 0.693145751953125f;
+    const float LN2_LO = 1.42860682030941723212e-6f;
+    const float nf = rintf(__fmul_rn(x, LOG2E));
+    const float r = __fsub_rn(__fsub_rn(x, __fmul_rn(nf, LN2_HI)), __fmul_rn(nf, LN2_LO));
+    float p = 1.0f / 5040.0f;
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 720.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 120.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 24.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f / 6.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 0.5f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    const int n = (int)nf;
+    return __fmul_rn(p, __int_as_float((n + 127) << 23));
+}
+
+// Beta(1,3)-shaped rank selection: smallest k with w*P^3 < 2^32*(P^3 - (P-k-1)^3).
+__device__ __forceinline__ uint32_t beta_pick(uint32_t w, uint32_t P) {
+    const uint64_t P3 = (uint64_t)P * P * P;
+    const unsigned __int128 lhs = (unsigned __int128)w * P3;
+    uint32_t lo = 0, hi = P - 1;   // predicate is monotone in k
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint64_t q = (uint64_t)(P - mid - 1);
+        const unsigned __int128 rhs = ((unsigned __int128)(P3 - q * q * q)) << 32;
+        if (lhs < rhs) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t gen_of(const OptArgs& a, uint32_t gen_arg, int use_dev) {
+    return use_dev ? a.st->gen : gen_arg;
+}
+
+// Proposals of one generation for one run; every thread of the CTA takes part.
+// `order` is shared scratch of at least P ints.
+static __device__ void propose_dev(const OptArgs& a, uint32_t gen, uint64_t* __restrict__ cand, int* order) {
+    const int P = a.P, N = a.N;
+    const bool init = gen == 0 || (a.kind == CT_DE && a.st->reinit_pending);
+    if (init) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x)
+            cand[i] = stratified_key(a, (uint32_t)i, gen, gen == 0 ? PU_INIT : PU_REINIT);
+        return;
+    }
+    const DevSpace* sp = a.sp;
+    if (a.kind == CT_DE) {
+        const uint64_t best = a.st->de_best;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            uint32_t w[4];
+            rng_block(a.seed, i, gen, PU_MUT_PICK, 0, w);
+            uint32_t r2 = uint_below(w[0], (uint32_t)P - 1);
+            if (r2 >= (uint32_t)i) ++r2;
+            uint32_t r3 = uint_below(w[1], (uint32_t)P - 2);
+            const uint32_t lo = min((uint32_t)i, r2), hi = max((uint32_t)i, r2);
+            if (r3 >= lo) ++r3;
+            if (r3 >= hi) ++r3;
+            const uint64_t x2 = a.X[r2], x3 = a.X[r3], xi = a.X[i];
+            uint32_t cw[4];
+            rng_block(a.seed, i, gen, PU_CROSS, 0, cw);
+            const uint32_t jrand = uint_below(cw[0], (uint32_t)N);
+            uint64_t key = 0;
+            for (int j = 0; j < N; ++j) {
+                const int ib = field(sp, best, j), i2 = field(sp, x2, j), i3 = field(sp, x3, j);
+                const float m = __fadd_rn((float)ib, __fmul_rn(a.prm.de_F, (float)(i2 - i3)));
+                const float q = rintf(m);
+                int v = (int)q;
+                if (q < 0.0f) v = 0;
+                if (v > sp->r[j] - 1) v = sp->r[j] - 1;
+                const uint32_t t = 1u + (uint32_t)j;
+                if ((t & 3u) == 0) rng_block(a.seed, i, gen, PU_CROSS, t >> 2, cw);
+                const float rr = u01(cw[t & 3u]);
+                const int pick = (rr < a.prm.de_CR || (uint32_t)j == jrand) ? v : field(sp, xi, j);
+                key |= (uint64_t)pick << sp->off[j];
+            }
+            cand[i] = key;
+        }
+    } else if (a.kind == CT_PSO) {
+        const ct_opt_params& pr = a.prm;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            float* x = a.pos + (size_t)i * N;
+            float* v = a.vel + (size_t)i * N;
+            const float* p = a.pb + (size_t)i * N;
+            uint32_t w[4];
+            for (int j = 0; j < N; ++j) {
+                const uint32_t t = 2u * j;
+                if ((t & 3u) == 0) rng_block(a.seed, i, gen, PU_PSO_R, t >> 2, w);
+                const float r1 = u01(w[t & 3u]), r2 = u01(w[(t + 1) & 3u]);
+                const float t1 = __fmul_rn(pr.pso_w, v[j]);
+                const float t2 = __fmul_rn(__fmul_rn(pr.pso_c1, r1), __fsub_rn(p[j], x[j]));
+                const float t3 = __fmul_rn(__fmul_rn(pr.pso_c2, r2), __fsub_rn(a.gb[j], x[j]));
+                const float nv = __fadd_rn(__fadd_rn(t1, t2), t3);
+                v[j] = nv;
+                x[j] = clip01(__fadd_rn(x[j], nv));
+            }
+            cand[i] = snap_key(a, x);
+        }
+    } else if (a.kind == CT_FIREFLY) {
+        const ct_opt_params& pr = a.prm;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            float y[MAXP];
+            for (int d = 0; d < N; ++d) y[d] = a.pos[(size_t)i * N + d];
+            const float fi = a.FX[i];
+            for (int j = 0; j < P; ++j) {
+                if (!(a.FX[j] < fi)) continue;
+                const float* xj = a.pos + (size_t)j * N;
+                float s = 0.0f;
+                for (int d = 0; d < N; ++d) {
+                    const float t = __fsub_rn(y[d], xj[d]);
+                    s = __fadd_rn(s, __fmul_rn(t, t));
+                }
+                const float beta = __fmul_rn(pr.fa_beta0, exp_ct(__fmul_rn(-pr.fa_gamma, s)));
+                uint32_t w[4];
+                for (int d = 0; d < N; ++d) {
+                    const uint32_t t = (uint32_t)(j * N + d);
+                    if (d == 0 || (t & 3u) == 0) rng_block(a.seed, i, gen, PU_FA_ALPHA, t >> 2, w);
+                    const float u = u01(w[t & 3u]);
+                    const float nv = __fadd_rn(__fadd_rn(y[d], __fmul_rn(beta, __fsub_rn(xj[d], y[d]))),
+                                               __fmul_rn(pr.fa_alpha, __fsub_rn(u, 0.5f)));
+                    y[d] = clip01(nv);
+                }
+            }
+            for (int d = 0; d < N; ++d) a.ynew[(size_t)i * N + d] = y[d];
+            cand[i] = snap_key(a, y);
+        }
+    } else {  // GA
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const float fi = a.FX[i];
+            const uint64_t ki = a.X[i];
+            int rk = 0;
+            for (int j = 0; j < P; ++j) {
+                const float fj = a.FX[j];
+                const uint64_t kj = a.X[j];
+                rk += (fj < fi) || (fj == fi && (kj < ki || (kj == ki && j < i)));
+            }
+            order[rk] = i;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; 2 * c < P; c += blockDim.x) {
+            uint32_t w[4];
+            rng_block(a.seed, c, gen, PU_GA_SEL, 0, w);
+            const uint32_t pa = beta_pick(w[0], (uint32_t)P), pbk = beta_pick(w[1], (uint32_t)P);
+            uint32_t cut = 1;
+            if (N >= 2) {
+                uint32_t cw[4];
+                rng_block(a.seed, c, gen, PU_GA_CUT, 0, cw);
+                cut = 1u + uint_below(cw[0], (uint32_t)N - 1);
+            }
+            const uint64_t A = a.X[order[pa]], B = a.X[order[pbk]];
+            uint64_t hmask = 0;   // fields of params [0, cut)
+            for (int j = 0; j < (int)cut && j < N; ++j) hmask |= sp->fmask[j];
+            cand[2 * c] = (A & hmask) | (B & ~hmask);
+            if (2 * c + 1 < P) cand[2 * c + 1] = (B & hmask) | (A & ~hmask);
+        }
+    }
+}
+
+// GA mutation: with probability p_mut, a random valid Hamming neighbour
+static __device__ void post_repair_dev(const OptArgs& a, uint32_t gen, uint64_t* __restrict__ keys) {
+    if (a.kind != CT_GA || gen == 0) return;
+    const DevSpace* sp = a.sp;
+    for (int i = threadIdx.x; i < a.P; i += blockDim.x) {
+        uint32_t w[4];
+        rng_block(a.seed, i, gen, PU_GA_MUT, 0, w);
+        if (!(u01(w[0]) < a.prm.ga_pmut)) continue;
+        const uint64_t u = keys[i];
+        uint32_t cnt = 0;
+        for (int k = 0; k < a.N; ++k) {
+            const int uk = field(sp, u, k);
+            for (int v = 0; v < sp->r[k]; ++v) {
+                if (v == uk) continue;
+                const uint64_t kk = (u & ~sp->fmask[k]) | ((uint64_t)v << sp->off[k]);
+                cnt += valid_key(sp, a.tables, kk);
+            }
+        }
+        if (!cnt) continue;
+        const uint32_t pick = uint_below(w[1], cnt);
+        uint32_t seen = 0;
+        uint64_t res = u;
+        for (int k = 0; k < a.N && res == u; ++k) {
+            const int uk = field(sp, u, k);
+            for (int v = 0; v < sp->r[k]; ++v) {
+                if (v == uk) continue;
+                const uint64_t kk = (u & ~sp->fmask[k]) | ((uint64_t)v << sp->off[k]);
+                if (valid_key(sp, a.tables, kk)) {
+                    if (seen == pick) { res = kk; break; }
+                    ++seen;
+                }
+            }
+        }
+        keys[i] = res;
+    }
+}
+
+__device__ __forceinline__ bool lex_less(float fa, uint64_t ka, float fb, uint64_t kb) {
+    return fa < fb || (fa == fb && ka < kb);
+}
+
+// Shared scratch of select_dev (block size <= SEL_MAX_THREADS, pop <= CT_MAX_POP).
+constexpr int SEL_MAX_THREADS = 512;
+struct SelectSmem {
+    float sf[SEL_MAX_THREADS];
+    uint64_t sk[SEL_MAX_THREADS];
+    uint8_t pass[CT_MAX_POP];
+    uint8_t acc[CT_MAX_POP];
+    int init_s;
+};
+
+// Selection / update after evaluation; every thread of the CTA takes part.
+static __device__ void select_dev(const OptArgs& a, uint32_t gen, const uint64_t* __restrict__ keys,
+                           const float* __restrict__ fit, SelectSmem& sm) {
+    const int P = a.P, N = a.N;
+    OptDev* st = a.st;
+    float* sf = sm.sf;
+    uint64_t* sk = sm.sk;
+    uint8_t* pass = sm.pass;
+    uint8_t* acc = sm.acc;
+    int& init_s = sm.init_s;
+    // run best = min (fitness, key) over everything evaluated
+    float bf = __int_as_float(0x7f800000);
+    uint64_t bk = ~0ull;
+    for (int i = threadIdx.x; i < P; i += blockDim.x)
+        if (lex_less(fit[i], keys[i], bf, bk)) { bf = fit[i]; bk = keys[i]; }
+    sf[threadIdx.x] = bf;
+    sk[threadIdx.x] = bk;
+    if (threadIdx.x == 0) init_s = gen == 0 || (a.kind == CT_DE && st->reinit_pending);
+    __syncthreads();
+    const bool init = init_s;
+    if (threadIdx.x == 0) {
+        for (int t = 1; t < blockDim.x; ++t)
+            if (lex_less(sf[t], sk[t], bf, bk)) { bf = sf[t]; bk = sk[t]; }
+        if (lex_less(bf, bk, st->best_fit, st->best_key)) { st->best_fit = bf; st->best_key = bk; }
+        if (st->hit_gen < 0 && st->best_fit <= a.prm.target) { st->hit_gen = gen; st->hit_evals = (long long)st->n_unique; }
+    }
+    if (a.kind == CT_DE) {
+        if (init) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) { a.X[i] = keys[i]; a.FX[i] = fit[i]; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int i0 = 0;
+                if (gen == 0) { st->de_best = a.X[0]; st->de_fbest = a.FX[0]; i0 = 1; }
+                for (int i = i0; i < P; ++i)
+                    if (a.FX[i] <= st->de_fbest) { st->de_best = a.X[i]; st->de_fbest = a.FX[i]; }
+                st->reinit_pending = 0;
+                st->stag = 0;
+            }
+        } else {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const uint64_t u = keys[i];
+                bool in_x = false;
+                for (int k = 0; k < P && !in_x; ++k) in_x = a.X[k] == u;
+                pass[i] = fit[i] <= a.FX[i] && !in_x;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                bool ok = pass[i];
+                const uint64_t u = keys[i];
+                for (int k = 0; k < i && ok; ++k) ok = !(pass[k] && keys[k] == u);
+                acc[i] = ok;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < P; i += blockDim.x)
+                if (acc[i]) { a.X[i] = keys[i]; a.FX[i] = fit[i]; }
+            if (threadIdx.x == 0) {
+                int n_acc = 0;
+                for (int i = 0; i < P; ++i) {
+                    if (!acc[i]) continue;
+                    ++n_acc;
+                    if (fit[i] <= st->de_fbest) { st->de_best = keys[i]; st->de_fbest = fit[i]; }
+                }
+                st->stag = n_acc ? 0 : st->stag + 1;
+                if (st->stag >= 2) { st->reinit_pending = 1; st->stag = 0; }
+            }
+        }
+    } else if (a.kind == CT_PSO || a.kind == CT_FIREFLY) {
+        if (gen == 0) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                uint32_t w[4];
+                for (int j = 0; j < N; ++j) {
+                    const float x0 = __fmul_rn((float)field(a.sp, keys[i], j), a.eps);
+                    a.pos[(size_t)i * N + j] = x0;
+                    a.pb[(size_t)i * N + j] = x0;
+                    if (a.kind == CT_PSO) {
+                        if ((j & 3) == 0) rng_block(a.seed, i, 0, PU_PSO_VEL, (uint32_t)j >> 2, w);
+                        a.vel[(size_t)i * N + j] = __fmul_rn(__fsub_rn(__fmul_rn(2.0f, u01(w[j & 3])), 1.0f), a.eps);
+                    }
+                }
+                a.fpb[i] = fit[i];
+                a.FX[i] = fit[i];
+            }
+        } else if (a.kind == CT_PSO) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x)
+                if (fit[i] < a.fpb[i]) {
+                    a.fpb[i] = fit[i];
+                    for (int j = 0; j < N; ++j) a.pb[(size_t)i * N + j] = a.pos[(size_t)i * N + j];
+                }
+        } else {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                for (int j = 0; j < N; ++j) a.pos[(size_t)i * N + j] = a.ynew[(size_t)i * N + j];
+                a.FX[i] = fit[i];
+            }
+        }
+        __syncthreads();
+        if (a.kind == CT_PSO && threadIdx.x == 0) {
+            for (int i = 0; i < P; ++i)
+                if (a.fpb[i] < st->fgb) {
+                    st->fgb = a.fpb[i];
+                    for (int j = 0; j < N; ++j) a.gb[j] = a.pb[(size_t)i * N + j];
+                }
+        }
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            a.X[i] = keys[i];
+            if (a.kind == CT_PSO) a.FX[i] = a.fpb[i];
+        }
+    } else {  // GA: generational replacement
+        for (int i = threadIdx.x; i < P; i += blockDim.x) { a.X[i] = keys[i]; a.FX[i] = fit[i]; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st->gen = gen + 1;
+    __syncthreads();
+}
+
+
+}  // namespace ct
