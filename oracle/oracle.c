@@ -486,9 +486,136 @@ static uint64_t snap_key(const layout_t *L, const float *x, float eps)
 
 static float clip01(float v) { return v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v); }
 
+
+void or_mlp_forward(const float *params, int D, int H, int N, const int32_t *feats, int B, float *pred, float *acts);
+void or_mlp_grad(const float *params, int D, int H, int N, const int32_t *feats, const float *y, int B, float *grad);
+void or_mlp_sgd(float *params, float *mom, const float *grad, int64_t n, float lr, float mu);
+void or_mlp_init(int D, int H, uint64_t seed, float *params);
+int64_t or_mlp_param_count(int D, int H);
+
+/* DE best1bin trial for target i, drawing from the RNG streams of individual si
+ * (si = i for the plain method; i + s*P for proposal s of a surrogate pool). */
+static uint64_t de_trial(ctx_t *C, const uint64_t *X, uint64_t de_best, int P, int i, uint32_t si, int g,
+                         uint64_t seed, const or_params *prm)
+{
+    const int N = C->L.n;
+    int32_t ia[OR_MAXP], ib[OR_MAXP], ic[OR_MAXP], id[OR_MAXP], t[OR_MAXP];
+    unpack(&C->L, de_best, ia);
+    uint32_t w0 = rng_word(seed, si, g, P_MUT_PICK, 0), w1 = rng_word(seed, si, g, P_MUT_PICK, 1);
+    uint32_t r2 = uint_below(w0, (uint32_t)P - 1);
+    if (r2 >= (uint32_t)i) r2++;
+    uint32_t r3 = uint_below(w1, (uint32_t)P - 2);
+    uint32_t lo = (uint32_t)i < r2 ? (uint32_t)i : r2, hi = (uint32_t)i < r2 ? r2 : (uint32_t)i;
+    if (r3 >= lo) r3++;
+    if (r3 >= hi) r3++;
+    unpack(&C->L, X[r2], ib);
+    unpack(&C->L, X[r3], ic);
+    unpack(&C->L, X[i], id);
+    uint32_t jrand = uint_below(rng_word(seed, si, g, P_CROSS, 0), (uint32_t)N);
+    for (int j = 0; j < N; j++) {
+        /* Algorithm 1, Mutate: m = i_r1 + F*(i_r2 - i_r3), round and clip */
+        float diff = (float)(ib[j] - ic[j]);
+        float m = (float)ia[j] + prm->de_F * diff;
+        float q = rintf(m);
+        int v = (int)q;
+        if (q < 0.0f) v = 0;
+        if (v > C->L.r[j] - 1) v = C->L.r[j] - 1;
+        /* Algorithm 1, Crossover (binomial) */
+        float rr = u01(rng_word(seed, si, g, P_CROSS, 1 + (uint32_t)j));
+        t[j] = (rr < prm->de_CR || (uint32_t)j == jrand) ? v : id[j];
+    }
+    return pack(&C->L, t);
+}
+
+/* GA pair c: two beta-selected parents of the ranked population, single-point
+ * crossover; streams of pair sc. */
+static void ga_pair(ctx_t *C, const uint64_t *X, const int *order, int P, uint32_t sc, int g, uint64_t seed,
+                    uint64_t *child0, uint64_t *child1)
+{
+    const int N = C->L.n;
+    int32_t ia[OR_MAXP], ib[OR_MAXP], ic[OR_MAXP], id[OR_MAXP];
+    uint32_t pa = beta_pick(rng_word(seed, sc, g, P_GA_SEL, 0), (uint32_t)P);
+    uint32_t pbi = beta_pick(rng_word(seed, sc, g, P_GA_SEL, 1), (uint32_t)P);
+    uint32_t cut = N >= 2 ? 1 + uint_below(rng_word(seed, sc, g, P_GA_CUT, 0), (uint32_t)N - 1) : 1;
+    unpack(&C->L, X[order[pa]], ia);
+    unpack(&C->L, X[order[pbi]], ib);
+    for (int j = 0; j < N; j++) {
+        ic[j] = (uint32_t)j < cut ? ia[j] : ib[j];
+        id[j] = (uint32_t)j < cut ? ib[j] : ia[j];
+    }
+    *child0 = pack(&C->L, ic);
+    *child1 = pack(&C->L, id);
+}
+
+/* GA mutation of a repaired child: with probability p_mut, a random valid Hamming
+ * neighbour enumerated by (parameter, value index); streams of individual si. */
+static uint64_t ga_mutate(ctx_t *C, uint64_t key, uint32_t si, int g, uint64_t seed, const or_params *prm)
+{
+    const int N = C->L.n;
+    if (!(u01(rng_word(seed, si, g, P_GA_MUT, 0)) < prm->ga_pmut)) return key;
+    int32_t ia[OR_MAXP];
+    unpack(&C->L, key, ia);
+    int64_t cnt = 0;
+    for (int k = 0; k < N; k++)
+        for (int v = 0; v < C->L.r[k]; v++) {
+            if (v == ia[k]) continue;
+            int32_t save = ia[k];
+            ia[k] = v;
+            if (rank_of(C->keys, C->nv, pack(&C->L, ia)) >= 0) cnt++;
+            ia[k] = save;
+        }
+    if (cnt == 0) return key;
+    uint32_t pick = uint_below(rng_word(seed, si, g, P_GA_MUT, 1), (uint32_t)cnt);
+    int64_t seen = 0;
+    for (int k = 0; k < N; k++)
+        for (int v = 0; v < C->L.r[k]; v++) {
+            if (v == ia[k]) continue;
+            int32_t save = ia[k];
+            ia[k] = v;
+            uint64_t kk = pack(&C->L, ia);
+            ia[k] = save;
+            if (rank_of(C->keys, C->nv, kk) >= 0) {
+                if (seen == (int64_t)pick) return kk;
+                seen++;
+            }
+        }
+    return key;
+}
+
+/* surrogate configuration and per-generation trace */
+typedef struct {
+    int pool, H, batch, steps, warm_mult;
+    float lr, mu, mae_ratio;
+    const float *logt;   /* log-fitness per valid rank */
+} or_surr;
+
+typedef struct {
+    int8_t *used;        /* (G+1): proposals were screened this generation */
+    float *mae, *tau;    /* (G+1): judge of this generation */
+    int64_t *n_e;        /* (G+1): evaluated-set size after appending */
+    float *params;       /* final fp32 master parameters */
+} or_strace;
+
+static void feats_of(const ctx_t *C, uint64_t key, int32_t *f)
+{
+    int32_t idx[OR_MAXP];
+    unpack(&C->L, key, idx);
+    int base = 0;
+    for (int k = 0; k < C->L.n; k++) { f[k] = base + idx[k]; base += C->L.r[k]; }
+}
+
+static float predict1(const ctx_t *C, const float *params, int D, int H, uint64_t key)
+{
+    int32_t f[OR_MAXP];
+    float y;
+    feats_of(C, key, f);
+    or_mlp_forward(params, D, H, C->L.n, f, 1, &y, NULL);
+    return y;
+}
+
 /* Runs G generations after the initial one; writes the trace.  Returns 0. */
 int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, const float *table,
-           int P, int G, uint64_t seed, const or_params *prm, or_trace *T)
+           int P, int G, uint64_t seed, const or_params *prm, or_trace *T, const or_surr *sg, or_strace *ST)
 {
     ctx_t C;
     make_layout(&C.L, n, r);
@@ -527,6 +654,23 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
     float de_fbest = INFINITY;
     int stag = 0, reinit_pending = 0;
 
+    /* surrogate state: network, momentum, evaluated set (keys and log-fitness) */
+    int D = 0;
+    for (int k = 0; k < N; k++) D += C.L.r[k];
+    int64_t n_par = sg ? or_mlp_param_count(D, sg->H) : 0;
+    float *mlp = sg ? (float *)malloc(sizeof(float) * (size_t)n_par) : NULL;
+    float *mom = sg ? (float *)calloc((size_t)n_par, sizeof(float)) : NULL;
+    float *grad = sg ? (float *)malloc(sizeof(float) * (size_t)n_par) : NULL;
+    uint64_t *EK = sg ? (uint64_t *)malloc(sizeof(uint64_t) * (size_t)P * (G + 1)) : NULL;
+    float *EY = sg ? (float *)malloc(sizeof(float) * (size_t)P * (G + 1)) : NULL;
+    int32_t *bf = sg ? (int32_t *)malloc(sizeof(int32_t) * (size_t)sg->batch * N) : NULL;
+    float *by = sg ? (float *)malloc(sizeof(float) * (size_t)sg->batch) : NULL;
+    float *spred = (float *)malloc(sizeof(float) * P);
+    int *newi = (int *)malloc(sizeof(int) * P);
+    int64_t n_e = 0;
+    int use_surr = 0;
+    if (sg) or_mlp_init(D, sg->H, seed, mlp);
+
     for (int g = 0; g <= G; g++) {
         int init_mode = (g == 0) || (kind == K_DE && reinit_pending);
         /* ---------------- propose ---------------- */
@@ -534,34 +678,7 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
             uint32_t purpose = g == 0 ? P_INIT : P_REINIT;
             for (int i = 0; i < P; i++) U[i] = stratified_key(&C, seed, (uint32_t)i, (uint32_t)P, (uint32_t)g, purpose);
         } else if (kind == K_DE) {
-            unpack(&C.L, de_best, ia);
-            for (int i = 0; i < P; i++) {
-                uint32_t w0 = rng_word(seed, i, g, P_MUT_PICK, 0), w1 = rng_word(seed, i, g, P_MUT_PICK, 1);
-                uint32_t r2 = uint_below(w0, (uint32_t)P - 1);
-                if (r2 >= (uint32_t)i) r2++;
-                uint32_t r3 = uint_below(w1, (uint32_t)P - 2);
-                uint32_t lo = (uint32_t)i < r2 ? (uint32_t)i : r2, hi = (uint32_t)i < r2 ? r2 : (uint32_t)i;
-                if (r3 >= lo) r3++;
-                if (r3 >= hi) r3++;
-                unpack(&C.L, X[r2], ib);
-                unpack(&C.L, X[r3], ic);
-                unpack(&C.L, X[i], id);
-                uint32_t jrand = uint_below(rng_word(seed, i, g, P_CROSS, 0), (uint32_t)N);
-                int32_t t[OR_MAXP];
-                for (int j = 0; j < N; j++) {
-                    /* Algorithm 1, Mutate: m = i_r1 + F*(i_r2 - i_r3), round and clip */
-                    float diff = (float)(ib[j] - ic[j]);
-                    float m = (float)ia[j] + prm->de_F * diff;
-                    float q = rintf(m);
-                    int v = (int)q;
-                    if (q < 0.0f) v = 0;
-                    if (v > C.L.r[j] - 1) v = C.L.r[j] - 1;
-                    /* Algorithm 1, Crossover (binomial) */
-                    float rr = u01(rng_word(seed, i, g, P_CROSS, 1 + (uint32_t)j));
-                    t[j] = (rr < prm->de_CR || (uint32_t)j == jrand) ? v : id[j];
-                }
-                U[i] = pack(&C.L, t);
-            }
+            for (int i = 0; i < P; i++) U[i] = de_trial(&C, X, de_best, P, i, (uint32_t)i, g, seed, prm);
         } else if (kind == K_PSO) {
             for (int i = 0; i < P; i++) {
                 float *x = pos + (size_t)i * N, *v = vel + (size_t)i * N, *p = pb + (size_t)i * N;
@@ -605,57 +722,84 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
                 order[b + 1] = v;
             }
             for (int c = 0; 2 * c < P; c++) {
-                uint32_t pa = beta_pick(rng_word(seed, c, g, P_GA_SEL, 0), (uint32_t)P);
-                uint32_t pbi = beta_pick(rng_word(seed, c, g, P_GA_SEL, 1), (uint32_t)P);
-                uint32_t cut = N >= 2 ? 1 + uint_below(rng_word(seed, c, g, P_GA_CUT, 0), (uint32_t)N - 1) : 1;
-                unpack(&C.L, X[order[pa]], ia);
-                unpack(&C.L, X[order[pbi]], ib);
-                for (int j = 0; j < N; j++) {
-                    ic[j] = (uint32_t)j < cut ? ia[j] : ib[j];
-                    id[j] = (uint32_t)j < cut ? ib[j] : ia[j];
-                }
-                U[2 * c] = pack(&C.L, ic);
-                if (2 * c + 1 < P) U[2 * c + 1] = pack(&C.L, id);
+                uint64_t k0, k1;
+                ga_pair(&C, X, order, P, (uint32_t)c, g, seed, &k0, &k1);
+                U[2 * c] = k0;
+                if (2 * c + 1 < P) U[2 * c + 1] = k1;
             }
         }
         /* ---------------- repair (+ GA mutation), evaluate ---------------- */
         for (int i = 0; i < P; i++) {
             UR[i] = init_mode ? U[i] : repair_key(&C, U[i]);
-            UE[i] = UR[i];
-            if (kind == K_GA && !init_mode) {
-                if (u01(rng_word(seed, i, g, P_GA_MUT, 0)) < prm->ga_pmut) {
-                    /* random valid Hamming neighbour, enumerated by (param, value index) */
-                    unpack(&C.L, UR[i], ia);
-                    int64_t cnt = 0;
-                    for (int k = 0; k < N; k++)
-                        for (int v = 0; v < C.L.r[k]; v++) {
-                            if (v == ia[k]) continue;
-                            int32_t save = ia[k];
-                            ia[k] = v;
-                            if (rank_of(C.keys, C.nv, pack(&C.L, ia)) >= 0) cnt++;
-                            ia[k] = save;
-                        }
-                    if (cnt > 0) {
-                        uint32_t pick = uint_below(rng_word(seed, i, g, P_GA_MUT, 1), (uint32_t)cnt);
-                        int64_t seen = 0;
-                        int done = 0;
-                        for (int k = 0; k < N && !done; k++)
-                            for (int v = 0; v < C.L.r[k] && !done; v++) {
-                                if (v == ia[k]) continue;
-                                int32_t save = ia[k];
-                                ia[k] = v;
-                                uint64_t kk = pack(&C.L, ia);
-                                if (rank_of(C.keys, C.nv, kk) >= 0) {
-                                    if (seen == (int64_t)pick) { UE[i] = kk; done = 1; }
-                                    seen++;
-                                }
-                                ia[k] = save;
-                            }
+            UE[i] = (kind == K_GA && !init_mode) ? ga_mutate(&C, UR[i], (uint32_t)i, g, seed, prm) : UR[i];
+        }
+        /* surrogate screening: proposals s = 1..pool-1 from streams offset by s, all
+         * repaired (and mutated), the lowest prediction wins each slot */
+        int screened = sg && use_surr && !init_mode && (kind == K_DE || kind == K_GA);
+        if (screened) {
+            const int npairs = (P + 1) / 2;
+            for (int i = 0; i < P; i++) spred[i] = predict1(&C, mlp, D, sg->H, UE[i]);
+            for (int s = 1; s < sg->pool; s++) {
+                for (int i = 0; i < P; i++) {
+                    uint64_t c0 = 0, c1 = 0;
+                    if (kind == K_DE) c0 = de_trial(&C, X, de_best, P, i, (uint32_t)(i + s * P), g, seed, prm);
+                    else {
+                        ga_pair(&C, X, order, P, (uint32_t)(i / 2 + s * npairs), g, seed, &c0, &c1);
+                        if (i & 1) c0 = c1;
+                    }
+                    uint64_t cr = repair_key(&C, c0);
+                    uint64_t ce = (kind == K_GA) ? ga_mutate(&C, cr, (uint32_t)(i + s * P), g, seed, prm) : cr;
+                    float pr = predict1(&C, mlp, D, sg->H, ce);
+                    if (pr < spred[i] || (pr == spred[i] && ce < UE[i])) {
+                        spred[i] = pr;
+                        U[i] = c0;
+                        UR[i] = cr;
+                        UE[i] = ce;
                     }
                 }
             }
         }
-        for (int i = 0; i < P; i++) FU[i] = evaluate(&C, UE[i]);
+        int64_t n_new = 0;
+        for (int i = 0; i < P; i++) {
+            int64_t rk = rank_of(C.keys, C.nv, UE[i]);
+            if (sg && rk >= 0 && !C.memo[rk]) newi[n_new++] = i;
+            FU[i] = evaluate(&C, UE[i]);
+        }
+        if (sg) {   /* judge on this generation's evaluations, then learn from them */
+            float sa = 0.0f, sy = 0.0f, sd = 0.0f;
+            for (int i = 0; i < P; i++) {
+                float pr = predict1(&C, mlp, D, sg->H, UE[i]);
+                float y = sg->logt[rank_of(C.keys, C.nv, UE[i])];
+                sa = sa + fabsf(pr - y);
+                sy = sy + y;
+                spred[i] = y;
+            }
+            float mae = sa / (float)P, ybar = sy / (float)P;
+            for (int i = 0; i < P; i++) sd = sd + fabsf(spred[i] - ybar);
+            float tau = sg->mae_ratio * (sd / (float)P);
+            for (int64_t q = 0; q < n_new; q++) {
+                EK[n_e] = UE[newi[q]];
+                EY[n_e] = sg->logt[rank_of(C.keys, C.nv, UE[newi[q]])];
+                n_e++;
+            }
+            for (int t = 0; t < sg->steps && n_e > 0; t++) {
+                for (int b = 0; b < sg->batch; b++) {
+                    uint32_t pick = uint_below(rng_word(seed, (uint32_t)b, (uint32_t)g, P_MLP_BATCH, (uint32_t)t), (uint32_t)n_e);
+                    feats_of(&C, EK[pick], bf + (size_t)b * N);
+                    by[b] = EY[pick];
+                }
+                or_mlp_grad(mlp, D, sg->H, N, bf, by, sg->batch, grad);
+                or_mlp_sgd(mlp, mom, grad, n_par, sg->lr, sg->mu);
+            }
+            if (ST) {
+                ST->used[g] = (int8_t)screened;
+                ST->mae[g] = mae;
+                ST->tau[g] = tau;
+                ST->n_e[g] = n_e;
+            }
+            use_surr = n_e >= (int64_t)sg->warm_mult * P && mae <= tau;
+        }
+
 
         /* ---------------- select / update ---------------- */
         if (kind == K_DE) {
@@ -734,9 +878,238 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
     }
     free(X); free(FX); free(U); free(UR); free(UE); free(FU); free(pos); free(vel); free(pb);
     free(fpb); free(gb); free(ynew); free(tmp); free(pass); free(order); free(C.vt); free(C.memo);
+    if (sg && ST && ST->params) memcpy(ST->params, mlp, sizeof(float) * (size_t)n_par);
+    free(mlp); free(mom); free(grad); free(EK); free(EY); free(bf); free(by); free(spred); free(newi);
     return 0;
 }
 
 /* exported helpers for the pins */
 uint32_t or_beta_pick(uint32_t w, uint32_t P) { return beta_pick(w, P); }
 float or_u01(uint32_t w) { return u01(w); }
+
+/* ------------------------------------------------------------------------- */
+/* MLP surrogate (a learned screen over proposals; not part of the paper)     */
+/* ------------------------------------------------------------------------- */
+/* Network: one-hot value indices (D = sum_k r_k features, N active) -> H -> H
+ * -> H (ReLU) -> 1.  Parameters are fp32 masters, flat:
+ *   W1[H][D], b1[H], W2[H][H], b2[H], W3[H][H], b3[H], W4[H], b4.
+ * Forward uses bf16(W) (round to nearest even) with fp32 accumulation in
+ * ascending input order: dense layers acc = fmaf(a_i, w_ji, acc) from 0, then
+ * z = acc + b; the one-hot layer adds the active weights in ascending feature
+ * order.  Loss: mean squared error against log-fitness. */
+
+static float bf16r(float f)
+{
+    union { float f; uint32_t u; } v;
+    v.f = f;
+    uint32_t lsb = (v.u >> 16) & 1u;
+    v.u += 0x7FFFu + lsb;
+    v.u &= 0xFFFF0000u;
+    return v.f;
+}
+
+float or_bf16_round(float f) { return bf16r(f); }
+
+int64_t or_mlp_param_count(int D, int H) { return (int64_t)H * D + H + 2 * ((int64_t)H * H + H) + H + 1; }
+
+typedef struct { float *W1, *b1, *W2, *b2, *W3, *b3, *W4, *b4; } mlp_view;
+
+static mlp_view view_of(float *p, int D, int H)
+{
+    mlp_view v;
+    v.W1 = p; p += (size_t)H * D;
+    v.b1 = p; p += H;
+    v.W2 = p; p += (size_t)H * H;
+    v.b2 = p; p += H;
+    v.W3 = p; p += (size_t)H * H;
+    v.b3 = p; p += H;
+    v.W4 = p; p += H;
+    v.b4 = p;
+    return v;
+}
+
+/* Glorot-uniform weights from the MLP_INIT stream (individual = tensor 1..4,
+ * generation 0, word = element index), zero biases. */
+void or_mlp_init(int D, int H, uint64_t seed, float *params)
+{
+    mlp_view v = view_of(params, D, H);
+    memset(params, 0, sizeof(float) * (size_t)or_mlp_param_count(D, H));
+    float *W[4] = {v.W1, v.W2, v.W3, v.W4};
+    int64_t n[4] = {(int64_t)H * D, (int64_t)H * H, (int64_t)H * H, H};
+    int fin[4] = {D, H, H, H}, fout[4] = {H, H, H, 1};
+    for (int t = 0; t < 4; t++) {
+        float a = sqrtf(6.0f / (float)(fin[t] + fout[t]));
+        for (int64_t e = 0; e < n[t]; e++) {
+            float u = u01(rng_word(seed, (uint32_t)(t + 1), 0, P_MLP_INIT, (uint32_t)e));
+            W[t][e] = (2.0f * u - 1.0f) * a;
+        }
+    }
+}
+
+/* feats: B rows of N ascending feature indices.  acts (optional): per sample
+ * z1,z2,z3 (3H) then h1,h2,h3 (3H), for the backward pass. */
+void or_mlp_forward(const float *params, int D, int H, int N, const int32_t *feats, int B, float *pred, float *acts)
+{
+    mlp_view v = view_of((float *)params, D, H);
+    float *z = (float *)malloc(sizeof(float) * 6 * (size_t)H);
+    for (int b = 0; b < B; b++) {
+        float *z1 = z, *z2 = z + H, *z3 = z + 2 * H, *h1 = z + 3 * H, *h2 = z + 4 * H, *h3 = z + 5 * H;
+        const int32_t *f = feats + (size_t)b * N;
+        for (int j = 0; j < H; j++) {
+            float acc = 0.0f;
+            for (int k = 0; k < N; k++) acc = acc + bf16r(v.W1[(size_t)j * D + f[k]]);
+            z1[j] = acc + v.b1[j];
+            h1[j] = z1[j] > 0.0f ? z1[j] : 0.0f;
+        }
+        for (int j = 0; j < H; j++) {
+            float acc = 0.0f;
+            for (int i = 0; i < H; i++) acc = fmaf(h1[i], bf16r(v.W2[(size_t)j * H + i]), acc);
+            z2[j] = acc + v.b2[j];
+            h2[j] = z2[j] > 0.0f ? z2[j] : 0.0f;
+        }
+        for (int j = 0; j < H; j++) {
+            float acc = 0.0f;
+            for (int i = 0; i < H; i++) acc = fmaf(h2[i], bf16r(v.W3[(size_t)j * H + i]), acc);
+            z3[j] = acc + v.b3[j];
+            h3[j] = z3[j] > 0.0f ? z3[j] : 0.0f;
+        }
+        float acc = 0.0f;
+        for (int i = 0; i < H; i++) acc = fmaf(h3[i], bf16r(v.W4[i]), acc);
+        pred[b] = acc + v.b4[0];
+        if (acts) memcpy(acts + (size_t)b * 6 * H, z, sizeof(float) * 6 * (size_t)H);
+    }
+    free(z);
+}
+
+/* Gradient of the batch MSE (fp32, fixed order: every reduction over the batch
+ * runs in ascending sample index, over neurons in ascending index). */
+void or_mlp_grad(const float *params, int D, int H, int N, const int32_t *feats, const float *y, int B, float *grad)
+{
+    mlp_view v = view_of((float *)params, D, H);
+    mlp_view g = view_of(grad, D, H);
+    size_t np = (size_t)or_mlp_param_count(D, H);
+    memset(grad, 0, sizeof(float) * np);
+    float *acts = (float *)malloc(sizeof(float) * 6 * (size_t)H * B);
+    float *pred = (float *)malloc(sizeof(float) * B);
+    float *gout = (float *)malloc(sizeof(float) * B);
+    float *d3 = (float *)malloc(sizeof(float) * (size_t)H * B);
+    float *d2 = (float *)malloc(sizeof(float) * (size_t)H * B);
+    float *d1 = (float *)malloc(sizeof(float) * (size_t)H * B);
+    or_mlp_forward(params, D, H, N, feats, B, pred, acts);
+    const float scale = 2.0f / (float)B;
+#define Z(b, l, j) acts[(size_t)(b) * 6 * H + (size_t)(l) * H + (j)]
+#define A(b, l, j) acts[(size_t)(b) * 6 * H + (size_t)(3 + (l)) * H + (j)]
+    for (int b = 0; b < B; b++) gout[b] = scale * (pred[b] - y[b]);
+    for (int b = 0; b < B; b++)
+        for (int j = 0; j < H; j++) d3[(size_t)b * H + j] = Z(b, 2, j) > 0.0f ? gout[b] * bf16r(v.W4[j]) : 0.0f;
+    for (int b = 0; b < B; b++)
+        for (int i = 0; i < H; i++) {
+            float acc = 0.0f;
+            for (int j = 0; j < H; j++) acc = fmaf(d3[(size_t)b * H + j], bf16r(v.W3[(size_t)j * H + i]), acc);
+            d2[(size_t)b * H + i] = Z(b, 1, i) > 0.0f ? acc : 0.0f;
+        }
+    for (int b = 0; b < B; b++)
+        for (int i = 0; i < H; i++) {
+            float acc = 0.0f;
+            for (int j = 0; j < H; j++) acc = fmaf(d2[(size_t)b * H + j], bf16r(v.W2[(size_t)j * H + i]), acc);
+            d1[(size_t)b * H + i] = Z(b, 0, i) > 0.0f ? acc : 0.0f;
+        }
+    /* weight and bias gradients, reductions over the batch in ascending b */
+    for (int j = 0; j < H; j++) {
+        float acc = 0.0f;
+        for (int b = 0; b < B; b++) acc = fmaf(gout[b], A(b, 2, j), acc);
+        g.W4[j] = acc;
+    }
+    { float acc = 0.0f; for (int b = 0; b < B; b++) acc = acc + gout[b]; g.b4[0] = acc; }
+    for (int j = 0; j < H; j++) {
+        for (int i = 0; i < H; i++) {
+            float a3 = 0.0f, a2 = 0.0f;
+            for (int b = 0; b < B; b++) {
+                a3 = fmaf(d3[(size_t)b * H + j], A(b, 1, i), a3);
+                a2 = fmaf(d2[(size_t)b * H + j], A(b, 0, i), a2);
+            }
+            g.W3[(size_t)j * H + i] = a3;
+            g.W2[(size_t)j * H + i] = a2;
+        }
+        float s3 = 0.0f, s2 = 0.0f, s1 = 0.0f;
+        for (int b = 0; b < B; b++) { s3 = s3 + d3[(size_t)b * H + j]; s2 = s2 + d2[(size_t)b * H + j]; s1 = s1 + d1[(size_t)b * H + j]; }
+        g.b3[j] = s3;
+        g.b2[j] = s2;
+        g.b1[j] = s1;
+        for (int b = 0; b < B; b++) {      /* one-hot layer: each active feature, samples in ascending order */
+            const int32_t *f = feats + (size_t)b * N;
+            for (int k = 0; k < N; k++) g.W1[(size_t)j * D + f[k]] = g.W1[(size_t)j * D + f[k]] + d1[(size_t)b * H + j];
+        }
+    }
+#undef Z
+#undef A
+    free(acts); free(pred); free(gout); free(d3); free(d2); free(d1);
+}
+
+/* SGD with momentum on the fp32 masters: v = mu*v + g; p = p - lr*v. */
+void or_mlp_sgd(float *params, float *mom, const float *grad, int64_t n, float lr, float mu)
+{
+    for (int64_t e = 0; e < n; e++) {
+        mom[e] = mu * mom[e] + grad[e];
+        params[e] = params[e] - lr * mom[e];
+    }
+}
+
+/* fp64 forward/gradient on the given (unrounded) weights, for the finite-difference check */
+double or_mlp_loss64(const double *params, int D, int H, int N, const int32_t *feats, const double *y, int B, double *grad)
+{
+    const double *W1 = params, *b1 = W1 + (size_t)H * D, *W2 = b1 + H, *b2 = W2 + (size_t)H * H, *W3 = b2 + H,
+                 *b3 = W3 + (size_t)H * H, *W4 = b3 + H, *b4 = W4 + H;
+    double *g = grad;
+    size_t np = (size_t)or_mlp_param_count(D, H);
+    if (g) memset(g, 0, sizeof(double) * np);
+    double *gW1 = g, *gb1 = g ? gW1 + (size_t)H * D : 0, *gW2 = g ? gb1 + H : 0, *gb2 = g ? gW2 + (size_t)H * H : 0,
+           *gW3 = g ? gb2 + H : 0, *gb3 = g ? gW3 + (size_t)H * H : 0, *gW4 = g ? gb3 + H : 0, *gb4 = g ? gW4 + H : 0;
+    double *z = (double *)malloc(sizeof(double) * 9 * (size_t)H);
+    double loss = 0;
+    for (int b = 0; b < B; b++) {
+        double *z1 = z, *z2 = z + H, *z3 = z + 2 * H, *h1 = z + 3 * H, *h2 = z + 4 * H, *h3 = z + 5 * H;
+        double *d1 = z + 6 * H, *d2 = z + 7 * H, *d3 = z + 8 * H;
+        const int32_t *f = feats + (size_t)b * N;
+        for (int j = 0; j < H; j++) {
+            double acc = b1[j];
+            for (int k = 0; k < N; k++) acc += W1[(size_t)j * D + f[k]];
+            z1[j] = acc; h1[j] = acc > 0 ? acc : 0;
+        }
+        for (int j = 0; j < H; j++) {
+            double acc = b2[j];
+            for (int i = 0; i < H; i++) acc += W2[(size_t)j * H + i] * h1[i];
+            z2[j] = acc; h2[j] = acc > 0 ? acc : 0;
+        }
+        for (int j = 0; j < H; j++) {
+            double acc = b3[j];
+            for (int i = 0; i < H; i++) acc += W3[(size_t)j * H + i] * h2[i];
+            z3[j] = acc; h3[j] = acc > 0 ? acc : 0;
+        }
+        double out = b4[0];
+        for (int i = 0; i < H; i++) out += W4[i] * h3[i];
+        double e = out - y[b];
+        loss += e * e / B;
+        if (!g) continue;
+        double go = 2.0 * e / B;
+        gb4[0] += go;
+        for (int j = 0; j < H; j++) { gW4[j] += go * h3[j]; d3[j] = z3[j] > 0 ? go * W4[j] : 0; }
+        for (int i = 0; i < H; i++) {
+            double acc = 0;
+            for (int j = 0; j < H; j++) acc += d3[j] * W3[(size_t)j * H + i];
+            d2[i] = z2[i] > 0 ? acc : 0;
+        }
+        for (int i = 0; i < H; i++) {
+            double acc = 0;
+            for (int j = 0; j < H; j++) acc += d2[j] * W2[(size_t)j * H + i];
+            d1[i] = z1[i] > 0 ? acc : 0;
+        }
+        for (int j = 0; j < H; j++) {
+            gb3[j] += d3[j]; gb2[j] += d2[j]; gb1[j] += d1[j];
+            for (int i = 0; i < H; i++) { gW3[(size_t)j * H + i] += d3[j] * h2[i]; gW2[(size_t)j * H + i] += d2[j] * h1[i]; }
+            for (int k = 0; k < N; k++) gW1[(size_t)j * D + f[k]] += d1[j];
+        }
+    }
+    free(z);
+    return loss;
+}

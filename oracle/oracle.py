@@ -50,6 +50,16 @@ class _Params(C.Structure):
                 ("target", C.c_float)]
 
 
+class _Surr(C.Structure):
+    _fields_ = [("pool", C.c_int), ("H", C.c_int), ("batch", C.c_int), ("steps", C.c_int), ("warm_mult", C.c_int),
+                ("lr", C.c_float), ("mu", C.c_float), ("mae_ratio", C.c_float), ("logt", C.c_void_p)]
+
+
+class _STrace(C.Structure):
+    _fields_ = [("used", C.c_void_p), ("mae", C.c_void_p), ("tau", C.c_void_p), ("n_e", C.c_void_p),
+                ("params", C.c_void_p)]
+
+
 class _Trace(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in
                 ("cand", "rep", "evalk", "fit", "popk", "popf", "pos", "best_key", "best_fit",
@@ -82,7 +92,17 @@ def lib():
         L.or_u01.argtypes = [C.c_uint32]
         L.or_run.restype = C.c_int
         L.or_run.argtypes = [C.c_int, C.c_int, p, p, C.c_int64, p, C.c_int, C.c_int, C.c_uint64,
-                             C.POINTER(_Params), C.POINTER(_Trace)]
+                             C.POINTER(_Params), C.POINTER(_Trace), C.c_void_p, C.c_void_p]
+        L.or_mlp_param_count.restype = C.c_int64
+        L.or_mlp_param_count.argtypes = [C.c_int, C.c_int]
+        L.or_mlp_init.argtypes = [C.c_int, C.c_int, C.c_uint64, p]
+        L.or_mlp_forward.argtypes = [p, C.c_int, C.c_int, C.c_int, p, C.c_int, p, p]
+        L.or_mlp_grad.argtypes = [p, C.c_int, C.c_int, C.c_int, p, p, C.c_int, p]
+        L.or_mlp_sgd.argtypes = [p, p, p, C.c_int64, C.c_float, C.c_float]
+        L.or_mlp_loss64.restype = C.c_double
+        L.or_mlp_loss64.argtypes = [p, C.c_int, C.c_int, C.c_int, p, p, C.c_int, p]
+        L.or_bf16_round.restype = C.c_float
+        L.or_bf16_round.argtypes = [C.c_float]
         _lib = L
     return _lib
 
@@ -274,11 +294,16 @@ DEFAULTS = dict(de_F=0.7, de_CR=0.6, pso_w=0.5, pso_c1=3.0, pso_c2=0.5, fa_beta0
                 fa_alpha=0.2, ga_pmut=0.2, target=-np.inf)
 
 
+SURROGATE_DEFAULTS = dict(pool=16, H=256, batch=256, steps=8, warm_mult=4, lr=1e-3, mu=0.9, mae_ratio=0.5)
+
+
 def run(kind: str, sp: OracleSpace, keys: np.ndarray, table: np.ndarray, pop: int, gens: int,
-        seed: int, **params):
+        seed: int, surrogate=None, log_table=None, **params):
     """One optimizer run: generation 0 (initial sample) plus ``gens`` generations.
 
-    Returns a dict of per-generation arrays (rows = generations 0..gens)."""
+    With ``surrogate`` (a dict overriding SURROGATE_DEFAULTS) and ``log_table`` (log-fitness per
+    valid rank), DE and GA proposals are screened by the MLP surrogate.  Returns a dict of
+    per-generation arrays (rows = generations 0..gens)."""
     prm = dict(DEFAULTS)
     prm.update(params)
     P, G, n = pop, gens, sp.n
@@ -294,7 +319,81 @@ def run(kind: str, sp: OracleSpace, keys: np.ndarray, table: np.ndarray, pop: in
     }
     tr = _Trace(*[T[f].ctypes.data for f, _ in _Trace._fields_])
     pr = _Params(*[float(np.float32(prm[f])) for f, _ in _Params._fields_])
+    sg = st = None
+    if surrogate is not None:
+        cfg = dict(SURROGATE_DEFAULTS)
+        cfg.update(surrogate)
+        logt = np.ascontiguousarray(log_table, dtype=np.float32)
+        D = int(sp.r.sum())
+        T["logt_ref"] = logt
+        T["s_used"] = np.zeros(G + 1, np.int8)
+        T["s_mae"] = np.zeros(G + 1, np.float32)
+        T["s_tau"] = np.zeros(G + 1, np.float32)
+        T["s_ne"] = np.zeros(G + 1, np.int64)
+        T["s_params"] = np.zeros(int(lib().or_mlp_param_count(D, cfg["H"])), np.float32)
+        sg = _Surr(cfg["pool"], cfg["H"], cfg["batch"], cfg["steps"], cfg["warm_mult"], float(np.float32(cfg["lr"])),
+                   float(np.float32(cfg["mu"])), float(np.float32(cfg["mae_ratio"])), logt.ctypes.data)
+        st = _STrace(T["s_used"].ctypes.data, T["s_mae"].ctypes.data, T["s_tau"].ctypes.data, T["s_ne"].ctypes.data,
+                     T["s_params"].ctypes.data)
     rc = lib().or_run(KIND[kind], n, _ptr(sp.r), _ptr(keys), C.c_int64(len(keys)), _ptr(table),
-                      P, G, C.c_uint64(seed), C.byref(pr), C.byref(tr))
+                      P, G, C.c_uint64(seed), C.byref(pr), C.byref(tr),
+                      C.cast(C.byref(sg), C.c_void_p) if sg else None, C.cast(C.byref(st), C.c_void_p) if st else None)
     assert rc == 0
+    T.pop("logt_ref", None)
     return T
+
+
+# ------------------------------------------------------------------------------------
+# MLP surrogate pieces
+# ------------------------------------------------------------------------------------
+def mlp_param_count(D, H):
+    return int(lib().or_mlp_param_count(D, H))
+
+
+def mlp_init(D, H, seed):
+    p = np.zeros(mlp_param_count(D, H), np.float32)
+    lib().or_mlp_init(D, H, C.c_uint64(seed), _ptr(p))
+    return p
+
+
+def mlp_forward(params, D, H, feats):
+    feats = np.ascontiguousarray(feats, dtype=np.int32)
+    B, N = feats.shape
+    out = np.zeros(B, np.float32)
+    lib().or_mlp_forward(_ptr(np.ascontiguousarray(params, np.float32)), D, H, N, _ptr(feats), B, _ptr(out), None)
+    return out
+
+
+def mlp_grad(params, D, H, feats, y):
+    feats = np.ascontiguousarray(feats, dtype=np.int32)
+    B, N = feats.shape
+    g = np.zeros(mlp_param_count(D, H), np.float32)
+    lib().or_mlp_grad(_ptr(np.ascontiguousarray(params, np.float32)), D, H, N, _ptr(feats),
+                      _ptr(np.ascontiguousarray(y, np.float32)), B, _ptr(g))
+    return g
+
+
+def mlp_sgd(params, mom, grad, lr=1e-3, mu=0.9):
+    lib().or_mlp_sgd(_ptr(params), _ptr(mom), _ptr(np.ascontiguousarray(grad, np.float32)), C.c_int64(len(params)),
+                     C.c_float(lr), C.c_float(mu))
+
+
+def mlp_loss64(params, D, H, feats, y, want_grad=True):
+    feats = np.ascontiguousarray(feats, dtype=np.int32)
+    B, N = feats.shape
+    p = np.ascontiguousarray(params, np.float64)
+    g = np.zeros(len(p), np.float64) if want_grad else None
+    loss = lib().or_mlp_loss64(_ptr(p), D, H, N, _ptr(feats), _ptr(np.ascontiguousarray(y, np.float64)), B,
+                               _ptr(g) if g is not None else None)
+    return loss, g
+
+
+def bf16_round(x):
+    return float(lib().or_bf16_round(C.c_float(x)))
+
+
+def features(sp: OracleSpace, keys):
+    """One-hot feature indices (ascending) of keys: base_k + idx_k."""
+    idx = unpack(sp, keys)
+    base = np.concatenate([[0], np.cumsum(sp.r)[:-1]]).astype(np.int64)
+    return (idx + base).astype(np.int32)
