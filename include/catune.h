@@ -250,6 +250,60 @@ ct_status ct_opt_state(const ct_opt *opt, uint64_t *d_keys, float *d_fit, float 
 ct_status ct_opt_save(const ct_opt *opt, void *buf, size_t *len, ct_stream stream);
 ct_status ct_opt_load(ct_opt *opt, const void *buf, size_t len, ct_stream stream);
 
+/* Copies the last generation's chosen proposals (before repair), repaired keys,
+ * evaluated keys (GA: after mutation) and their fitness, pop entries each. */
+ct_status ct_opt_last_generation(const ct_opt *opt, uint64_t *d_cand, uint64_t *d_rep, uint64_t *d_eval, float *d_fit,
+                                 ct_stream stream);
+
+/* ------------------------------------------------------------------------- */
+/* MLP surrogate screening (an addition to the paper's method)               */
+/* ------------------------------------------------------------------------- */
+/* A small network on one-hot value indices (D = sum_k n_values[k] inputs) ->
+ * hidden -> hidden -> hidden (ReLU) -> 1 predicts log-fitness.  fp32 master
+ * weights, bf16 (round to nearest even) weights in the forward and backward
+ * passes, fp32 accumulation in ascending index order on CUDA cores.  Flat
+ * parameter layout: W1[H][D], b1[H], W2[H][H], b2[H], W3[H][H], b3[H], W4[H], b4.
+ * Trained by SGD with momentum on mean squared error. */
+typedef struct {
+    int32_t pool;        /* proposals per population slot (16) */
+    int32_t hidden;      /* width H (256) */
+    int32_t batch;       /* training batch (256) */
+    int32_t steps;       /* SGD steps per generation (8) */
+    int32_t warmup_mult; /* screening needs >= warmup_mult * pop evaluations (4) */
+    float lr, momentum;  /* 1e-3, 0.9 */
+    float mae_ratio;     /* screening needs MAE <= mae_ratio * mean |y - mean y| of the generation (0.5) */
+} ct_surrogate_params;
+void ct_surrogate_params_default(ct_surrogate_params *p);
+
+/* Turns on screening for a DE or GA run before its generation 0.  d_log_table:
+ * log-fitness per valid rank (caller-owned, borrowed).  Each generation the
+ * surrogate is judged on the configurations just evaluated and trained on
+ * batches drawn from everything evaluated; while it is accurate enough, the run
+ * proposes `pool` candidates per slot, repairs all of them and evaluates only the
+ * lowest-predicted one per slot.  Such runs advance with ct_opt_step only (which
+ * then synchronises once per generation); ct_opt_run_graph returns STATE. */
+ct_status ct_opt_set_surrogate(ct_opt *opt, const ct_surrogate_params *params, const float *d_log_table);
+/* Last generation: screened or not, screening next, MAE, threshold, evaluated-set
+ * size; d_params (nullable) receives the fp32 master parameters.  Synchronises. */
+ct_status ct_opt_surrogate_info(ct_opt *opt, int32_t *screened, int32_t *use_next, float *mae, float *tau,
+                                uint64_t *n_evaluated, float *d_params, ct_stream stream);
+
+/* The network on its own (caller-owned device buffers). */
+int64_t ct_mlp_param_count(int32_t D, int32_t H);
+/* Glorot-uniform weights from the counter-based RNG, zero biases. */
+ct_status ct_mlp_init(int32_t D, int32_t H, uint64_t seed, float *d_params, ct_stream stream);
+size_t ct_mlp_workspace_bytes(int32_t D, int32_t H, int32_t B);
+/* d_feats: B rows of N ascending feature indices (one active input per parameter). */
+ct_status ct_mlp_forward(int32_t D, int32_t H, int32_t N, const float *d_params, const int32_t *d_feats, int32_t B,
+                         float *d_pred, void *d_work, ct_stream stream);
+/* Gradient of the batch mean squared error; d_param_of[f] = parameter owning feature f. */
+ct_status ct_mlp_grad(int32_t D, int32_t H, int32_t N, const float *d_params, const int32_t *d_feats,
+                      const int32_t *d_param_of, const float *d_y, int32_t B, float *d_grad, void *d_work,
+                      ct_stream stream);
+/* v = momentum*v + g; p = p - lr*v, elementwise. */
+ct_status ct_mlp_sgd(float *d_params, float *d_mom, const float *d_grad, int64_t n, float lr, float momentum,
+                     ct_stream stream);
+
 /* ------------------------------------------------------------------------- */
 /* batched runs                                                              */
 /* ------------------------------------------------------------------------- */

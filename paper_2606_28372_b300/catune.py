@@ -50,6 +50,11 @@ class ct_build_stats(C.Structure):
                 ("emit_ms", C.c_float * MAX_PARAMS)]
 
 
+class ct_surrogate_params(C.Structure):
+    _fields_ = [("pool", C.c_int32), ("hidden", C.c_int32), ("batch", C.c_int32), ("steps", C.c_int32),
+                ("warmup_mult", C.c_int32), ("lr", C.c_float), ("momentum", C.c_float), ("mae_ratio", C.c_float)]
+
+
 class ct_opt_params(C.Structure):
     _fields_ = [(n, C.c_float) for n in ("de_F", "de_CR", "pso_w", "pso_c1", "pso_c2", "fa_beta0",
                                          "fa_gamma", "fa_alpha", "ga_pmut", "target")]
@@ -94,6 +99,19 @@ _SIGS = {
     "ct_batch_set_launch": [C.c_void_p, C.c_int32, C.c_int32],
     "ct_batch_autotune": [C.c_void_p, C.c_char_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                           C.POINTER(C.c_float), C.c_void_p],
+    "ct_opt_last_generation": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "ct_surrogate_params_default": [C.c_void_p],
+    "ct_opt_set_surrogate": [C.c_void_p, C.c_void_p, C.c_void_p],
+    "ct_opt_surrogate_info": [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_float),
+                              C.POINTER(C.c_float), C.POINTER(C.c_uint64), C.c_void_p, C.c_void_p],
+    "ct_mlp_param_count": [C.c_int32, C.c_int32],
+    "ct_mlp_init": [C.c_int32, C.c_int32, C.c_uint64, C.c_void_p, C.c_void_p],
+    "ct_mlp_workspace_bytes": [C.c_int32, C.c_int32, C.c_int32],
+    "ct_mlp_forward": [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                       C.c_void_p],
+    "ct_mlp_grad": [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                    C.c_void_p, C.c_void_p, C.c_void_p],
+    "ct_mlp_sgd": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float, C.c_void_p],
     "ct_space_set_timing": [C.c_void_p, C.c_int32],
     "ct_space_build_stats": [C.c_void_p, C.c_void_p],
     "ct_launch_count": [],
@@ -118,6 +136,9 @@ def lib():
         L.ct_space_destroy.restype = None
         L.ct_opt_destroy.restype = None
         L.ct_batch_destroy.restype = None
+        L.ct_surrogate_params_default.restype = None
+        L.ct_mlp_param_count.restype = C.c_int64
+        L.ct_mlp_workspace_bytes.restype = C.c_size_t
         L.ct_opt_params_default.restype = None
         L.ct_launch_count.restype = C.c_uint64
         _lib = L
@@ -368,6 +389,24 @@ class Opt:
         check(lib().ct_opt_best(self.h, C.byref(k), C.byref(f), C.byref(u), C.byref(hg), C.byref(he), _stream(stream)))
         return dict(best_key=int(k.value), best_fit=float(f.value), n_unique=int(u.value), hit_gen=int(hg.value),
                     hit_evals=int(he.value))
+
+    def set_surrogate(self, log_table, **cfg):
+        """Screen DE/GA proposals with the MLP surrogate (before generation 0)."""
+        p = ct_surrogate_params()
+        lib().ct_surrogate_params_default(C.byref(p))
+        for k, v in cfg.items():
+            setattr(p, k, v)
+        self._logt = log_table
+        check(lib().ct_opt_set_surrogate(self.h, C.byref(p), _ptr(log_table)))
+
+    def surrogate_info(self, params=None, stream=None):
+        sc, un, mae, tau, ne = C.c_int32(), C.c_int32(), C.c_float(), C.c_float(), C.c_uint64()
+        check(lib().ct_opt_surrogate_info(self.h, C.byref(sc), C.byref(un), C.byref(mae), C.byref(tau), C.byref(ne),
+                                          _ptr(params), _stream(stream)))
+        return dict(screened=sc.value, use_next=un.value, mae=mae.value, tau=tau.value, n_e=int(ne.value))
+
+    def last_generation(self, cand=None, rep=None, evk=None, fit=None, stream=None):
+        check(lib().ct_opt_last_generation(self.h, _ptr(cand), _ptr(rep), _ptr(evk), _ptr(fit), _stream(stream)))
 
     def state(self, keys=None, fit=None, pos=None, stream=None):
         check(lib().ct_opt_state(self.h, _ptr(keys), _ptr(fit), _ptr(pos), _stream(stream)))

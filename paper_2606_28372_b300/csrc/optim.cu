@@ -44,38 +44,9 @@ __global__ void k_set_gen(OptDev* st, uint32_t g) { st->gen = g; }
 
 using namespace ct;
 
-struct ct_opt {
-    ct_space* s = nullptr;
-    int kind = 0, P = 0, N = 0;
-    uint64_t seed = 0;
-    ct_opt_params prm{};
-    float eps = 1.0f;
-    DevBuf<OptDev> st;
-    DevBuf<uint64_t> X, cand, rep;
-    DevBuf<float> FX, pos, vel, pb, fpb, gb, ynew, fit;
-    DevBuf<uint32_t> memo;
-    size_t memo_words = 0;
-    std::map<uint32_t, cudaGraphExec_t> graphs;
-    std::map<uint32_t, uint64_t> graph_kernels;   // kernels per replay of each graph
-    const void* graph_keys = nullptr;             // space key buffer the graphs were captured with
-    RepairScratch rs;                             // run-owned repair scratch (fixed size: pop)
-    ~ct_opt() {
-        for (auto& g : graphs) cudaGraphExecDestroy(g.second);
-        st.release(); X.release(); cand.release(); rep.release(); FX.release(); pos.release(); vel.release();
-        pb.release(); fpb.release(); gb.release(); ynew.release(); fit.release(); memo.release();
-        rs.pend_a.release(); rs.pend_b.release(); rs.counts.release(); rs.best.release();
-    }
-    OptArgs args() const {
-        OptArgs a;
-        a.kind = kind; a.P = P; a.N = N; a.seed = seed; a.prm = prm; a.eps = eps;
-        a.sp = s->d; a.tables = s->tables.p; a.keys = s->keys.p; a.nv = (int64_t)s->n_valid;
-        a.st = st.p; a.X = X.p; a.FX = FX.p; a.pos = pos.p; a.vel = vel.p; a.pb = pb.p; a.fpb = fpb.p; a.gb = gb.p;
-        a.ynew = ynew.p;
-        return a;
-    }
-};
-
 namespace ct {
+ct_status surrogate_step(ct_opt* o, uint32_t gen, cudaStream_t st);
+
 static ct_status step_impl(ct_opt* o, uint32_t gen, int use_dev, cudaStream_t st) {
     const OptArgs a = o->args();
     k_propose<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->cand.p);
@@ -184,11 +155,13 @@ ct_status ct_evaluate(ct_space* s, ct_opt* o, const uint64_t* d_keys, int64_t n,
 
 ct_status ct_opt_step(ct_opt* o, uint32_t gen, ct_stream stream) {
     if (!o) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    if (o->sg) return surrogate_step(o, gen, (cudaStream_t)stream);
     return step_impl(o, gen, 0, (cudaStream_t)stream);
 }
 
 ct_status ct_opt_run_graph(ct_opt* o, uint32_t first, uint32_t count, ct_stream stream) {
     if (!o || count == 0) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
+    if (o->sg) { set_error("runs with a surrogate advance with ct_opt_step"); return CT_ERR_STATE; }
     cudaStream_t st = (cudaStream_t)stream;
     if (o->graph_keys != (const void*)o->s->keys.p) {   // the space was rebuilt into a new buffer
         for (auto& gx : o->graphs) cudaGraphExecDestroy(gx.second);

@@ -1,6 +1,8 @@
 // Per-run optimizer logic as CTA-level device functions (Sections IV-B..IV-D, Table IV),
 // shared by the single-run kernels and the batched persistent kernel.
 #pragma once
+#include <map>
+
 #include "internal.hpp"
 
 namespace ct {
@@ -108,8 +110,10 @@ __device__ __forceinline__ uint32_t gen_of(const OptArgs& a, uint32_t gen_arg, i
 }
 
 // Proposals of one generation for one run; every thread of the CTA takes part.
-// `order` is shared scratch of at least P ints.
-static __device__ void propose_dev(const OptArgs& a, uint32_t gen, uint64_t* __restrict__ cand, int* order) {
+// `order` is shared scratch of at least P ints.  `s` selects the RNG streams of
+// proposal s of a screening pool (DE individual i + s*P, GA pair c + s*ceil(P/2));
+// s = 0 is the plain method.
+static __device__ void propose_dev(const OptArgs& a, uint32_t gen, uint64_t* __restrict__ cand, int* order, int s = 0) {
     const int P = a.P, N = a.N;
     const bool init = gen == 0 || (a.kind == CT_DE && a.st->reinit_pending);
     if (init) {
@@ -122,7 +126,8 @@ static __device__ void propose_dev(const OptArgs& a, uint32_t gen, uint64_t* __r
         const uint64_t best = a.st->de_best;
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
             uint32_t w[4];
-            rng_block(a.seed, i, gen, PU_MUT_PICK, 0, w);
+            const uint32_t si = (uint32_t)(i + s * P);
+            rng_block(a.seed, si, gen, PU_MUT_PICK, 0, w);
             uint32_t r2 = uint_below(w[0], (uint32_t)P - 1);
             if (r2 >= (uint32_t)i) ++r2;
             uint32_t r3 = uint_below(w[1], (uint32_t)P - 2);
@@ -131,7 +136,7 @@ static __device__ void propose_dev(const OptArgs& a, uint32_t gen, uint64_t* __r
             if (r3 >= hi) ++r3;
             const uint64_t x2 = a.X[r2], x3 = a.X[r3], xi = a.X[i];
             uint32_t cw[4];
-            rng_block(a.seed, i, gen, PU_CROSS, 0, cw);
+            rng_block(a.seed, si, gen, PU_CROSS, 0, cw);
             const uint32_t jrand = uint_below(cw[0], (uint32_t)N);
             uint64_t key = 0;
             for (int j = 0; j < N; ++j) {
@@ -142,7 +147,7 @@ static __device__ void propose_dev(const OptArgs& a, uint32_t gen, uint64_t* __r
                 if (q < 0.0f) v = 0;
                 if (v > sp->r[j] - 1) v = sp->r[j] - 1;
                 const uint32_t t = 1u + (uint32_t)j;
-                if ((t & 3u) == 0) rng_block(a.seed, i, gen, PU_CROSS, t >> 2, cw);
+                if ((t & 3u) == 0) rng_block(a.seed, si, gen, PU_CROSS, t >> 2, cw);
                 const float rr = u01(cw[t & 3u]);
                 const int pick = (rr < a.prm.de_CR || (uint32_t)j == jrand) ? v : field(sp, xi, j);
                 key |= (uint64_t)pick << sp->off[j];
@@ -210,14 +215,16 @@ static __device__ void propose_dev(const OptArgs& a, uint32_t gen, uint64_t* __r
             order[rk] = i;
         }
         __syncthreads();
+        const uint32_t npairs = (uint32_t)(P + 1) / 2;
         for (int c = threadIdx.x; 2 * c < P; c += blockDim.x) {
             uint32_t w[4];
-            rng_block(a.seed, c, gen, PU_GA_SEL, 0, w);
+            const uint32_t sc = (uint32_t)c + (uint32_t)s * npairs;
+            rng_block(a.seed, sc, gen, PU_GA_SEL, 0, w);
             const uint32_t pa = beta_pick(w[0], (uint32_t)P), pbk = beta_pick(w[1], (uint32_t)P);
             uint32_t cut = 1;
             if (N >= 2) {
                 uint32_t cw[4];
-                rng_block(a.seed, c, gen, PU_GA_CUT, 0, cw);
+                rng_block(a.seed, sc, gen, PU_GA_CUT, 0, cw);
                 cut = 1u + uint_below(cw[0], (uint32_t)N - 1);
             }
             const uint64_t A = a.X[order[pa]], B = a.X[order[pbk]];
@@ -230,12 +237,12 @@ static __device__ void propose_dev(const OptArgs& a, uint32_t gen, uint64_t* __r
 }
 
 // GA mutation: with probability p_mut, a random valid Hamming neighbour
-static __device__ void post_repair_dev(const OptArgs& a, uint32_t gen, uint64_t* __restrict__ keys) {
+static __device__ void post_repair_dev(const OptArgs& a, uint32_t gen, uint64_t* __restrict__ keys, int s = 0) {
     if (a.kind != CT_GA || gen == 0) return;
     const DevSpace* sp = a.sp;
     for (int i = threadIdx.x; i < a.P; i += blockDim.x) {
         uint32_t w[4];
-        rng_block(a.seed, i, gen, PU_GA_MUT, 0, w);
+        rng_block(a.seed, (uint32_t)(i + s * a.P), gen, PU_GA_MUT, 0, w);
         if (!(u01(w[0]) < a.prm.ga_pmut)) continue;
         const uint64_t u = keys[i];
         uint32_t cnt = 0;
@@ -395,4 +402,46 @@ static __device__ void select_dev(const OptArgs& a, uint32_t gen, const uint64_t
 }
 
 
+struct SurrogateState;
+void surrogate_free(SurrogateState* sg);
+
 }  // namespace ct
+
+using ct::DevBuf;
+using ct::OptArgs;
+using ct::OptDev;
+using ct::RepairScratch;
+
+struct ct_opt {
+    ct_space* s = nullptr;
+    int kind = 0, P = 0, N = 0;
+    uint64_t seed = 0;
+    ct_opt_params prm{};
+    float eps = 1.0f;
+    DevBuf<OptDev> st;
+    DevBuf<uint64_t> X, cand, rep;
+    DevBuf<float> FX, pos, vel, pb, fpb, gb, ynew, fit;
+    DevBuf<uint32_t> memo;
+    size_t memo_words = 0;
+    std::map<uint32_t, cudaGraphExec_t> graphs;
+    std::map<uint32_t, uint64_t> graph_kernels;   // kernels per replay of each graph
+    const void* graph_keys = nullptr;             // space key buffer the graphs were captured with
+    RepairScratch rs;                             // run-owned repair scratch (fixed size: pop)
+    ct::SurrogateState* sg = nullptr;             // MLP surrogate screening (DE, GA), or none
+    ~ct_opt() {
+        ct::surrogate_free(sg);
+        for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+        st.release(); X.release(); cand.release(); rep.release(); FX.release(); pos.release(); vel.release();
+        pb.release(); fpb.release(); gb.release(); ynew.release(); fit.release(); memo.release();
+        rs.pend_a.release(); rs.pend_b.release(); rs.counts.release(); rs.best.release();
+    }
+    OptArgs args() const {
+        OptArgs a;
+        a.kind = kind; a.P = P; a.N = N; a.seed = seed; a.prm = prm; a.eps = eps;
+        a.sp = s->d; a.tables = s->tables.p; a.keys = s->keys.p; a.nv = (int64_t)s->n_valid;
+        a.st = st.p; a.X = X.p; a.FX = FX.p; a.pos = pos.p; a.vel = vel.p; a.pb = pb.p; a.fpb = fpb.p; a.gb = gb.p;
+        a.ynew = ynew.p;
+        return a;
+    }
+};
+

@@ -1,0 +1,102 @@
+"""GPU parity of the MLP surrogate: initial weights, forward, gradient and SGD bit-exact against
+the oracle's same-order fp32 code, and surrogate-screened DE/GA trajectories equal to the oracle's."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_28372_b300 import workloads as W
+from tests.helpers import Pair, from_dev_u64
+
+pytestmark = pytest.mark.gpu
+
+
+def _feats(D, N, B, seed):
+    rng = np.random.default_rng(seed)
+    per = D // N
+    return (np.arange(N) * per + (rng.random((B, N)) * per).astype(np.int64)).astype(np.int32)
+
+
+@pytest.mark.parametrize("D,H,N,B", [(53, 256, 10, 256), (24, 32, 4, 37)])
+def test_mlp_kernels_bit_exact(oracle_mod, D, H, N, B):
+    from paper_2606_28372_b300 import catune as ct
+    L = ct.lib()
+    O = oracle_mod
+    n = int(L.ct_mlp_param_count(D, H))
+    assert n == O.mlp_param_count(D, H)
+    p = torch.empty(n, dtype=torch.float32, device="cuda")
+    ct.check(L.ct_mlp_init(D, H, 11, ct._ptr(p), ct._stream(None)))
+    p0 = O.mlp_init(D, H, 11)
+    assert np.array_equal(p.cpu().numpy(), p0)
+    # perturb so that biases are non-zero and ReLUs mixed
+    p0 = p0 + np.random.default_rng(2).normal(scale=0.05, size=n).astype(np.float32)
+    p.copy_(torch.from_numpy(p0))
+    feats = _feats(D, N, B, 3)
+    y = np.random.default_rng(4).normal(size=B).astype(np.float32)
+    df = torch.from_numpy(feats).cuda()
+    dy = torch.from_numpy(y).cuda()
+    work = torch.empty(int(L.ct_mlp_workspace_bytes(D, H, B)) // 4 + 1, dtype=torch.float32, device="cuda")
+    pred = torch.empty(B, dtype=torch.float32, device="cuda")
+    ct.check(L.ct_mlp_forward(D, H, N, ct._ptr(p), ct._ptr(df), B, ct._ptr(pred), ct._ptr(work), ct._stream(None)))
+    assert np.array_equal(pred.cpu().numpy(), O.mlp_forward(p0, D, H, feats))
+    pof = torch.from_numpy(np.repeat(np.arange(N), D // N).astype(np.int32)).cuda()
+    g = torch.empty(n, dtype=torch.float32, device="cuda")
+    ct.check(L.ct_mlp_grad(D, H, N, ct._ptr(p), ct._ptr(df), ct._ptr(pof), ct._ptr(dy), B, ct._ptr(g), ct._ptr(work),
+                           ct._stream(None)))
+    g0 = O.mlp_grad(p0, D, H, feats, y)
+    assert np.array_equal(g.cpu().numpy(), g0)
+    mom = torch.zeros(n, dtype=torch.float32, device="cuda")
+    ct.check(L.ct_mlp_sgd(ct._ptr(p), ct._ptr(mom), ct._ptr(g), n, ct.C.c_float(1e-3), ct.C.c_float(0.9), ct._stream(None)))
+    m0 = np.zeros(n, np.float32)
+    O.mlp_sgd(p0, m0, g0, 1e-3, 0.9)
+    assert np.array_equal(p.cpu().numpy(), p0) and np.array_equal(mom.cpu().numpy(), m0)
+
+
+def _gpu_surrogate_trace(pair, kind, pop, gens, seed, cfg, logt):
+    from paper_2606_28372_b300 import catune as ct
+    o = ct.Opt(pair.sp, kind, pop, seed)
+    dl = torch.from_numpy(logt).cuda()
+    o.set_surrogate(dl, **cfg)
+    T = {k: [] for k in ("cand", "rep", "evalk", "fit", "popk", "n_unique", "best_key", "used", "mae", "tau", "ne")}
+    bufs = [torch.empty(pop, dtype=torch.int64, device="cuda") for _ in range(4)]
+    fit = torch.empty(pop, dtype=torch.float32, device="cuda")
+    for g in range(gens + 1):
+        o.step(g)
+        o.last_generation(bufs[0], bufs[1], bufs[2], fit)
+        o.state(bufs[3])
+        for name, b in zip(("cand", "rep", "evalk", "popk"), bufs):
+            T[name].append(from_dev_u64(b))
+        T["fit"].append(fit.cpu().numpy())
+        info = o.surrogate_info()
+        T["used"].append(info["screened"])
+        T["mae"].append(np.float32(info["mae"]))
+        T["tau"].append(np.float32(info["tau"]))
+        T["ne"].append(info["n_e"])
+        b = o.best()
+        T["n_unique"].append(b["n_unique"])
+        T["best_key"].append(b["best_key"])
+    params = torch.empty(int(ct.lib().ct_mlp_param_count(sum(pair.sd.n_values), cfg["hidden"])), device="cuda")
+    o.surrogate_info(params)
+    T = {k: np.array(v) for k, v in T.items()}
+    T["params"] = params.cpu().numpy()
+    return T
+
+
+@pytest.mark.parametrize("kind", ["de", "ga"])
+@pytest.mark.parametrize("space,pop,gens,cfg", [
+    ("medium", 32, 7, dict(pool=4, hidden=32, batch=64, steps=4, warmup_mult=1, mae_ratio=10.0)),
+    ("tiny", 20, 5, dict(pool=16, hidden=256, batch=256, steps=8, warmup_mult=1, mae_ratio=10.0)),
+])
+def test_surrogate_trajectory(oracle_mod, kind, space, pop, gens, cfg):
+    p = Pair(W.SPACES[space](), oracle_mod)
+    logt = np.log(p.table.astype(np.float64)).astype(np.float32)
+    ocfg = dict(pool=cfg["pool"], H=cfg["hidden"], batch=cfg["batch"], steps=cfg["steps"], warm_mult=cfg["warmup_mult"],
+                mae_ratio=cfg["mae_ratio"])
+    E = oracle_mod.run(kind, p.osp, p.okeys, p.table, pop=pop, gens=gens, seed=5, surrogate=ocfg, log_table=logt)
+    T = _gpu_surrogate_trace(p, kind, pop, gens, 5, cfg, logt)
+    assert T["used"][1:].any()                      # screening was exercised
+    for f, e in (("cand", "cand"), ("rep", "rep"), ("evalk", "evalk"), ("fit", "fit"), ("popk", "popk"),
+                 ("n_unique", "n_unique"), ("best_key", "best_key"), ("used", "s_used"), ("mae", "s_mae"),
+                 ("tau", "s_tau"), ("ne", "s_ne")):
+        a, b = T[f], E[e]
+        assert np.array_equal(a.astype(b.dtype) if f in ("used", "ne") else a, b), f
+    assert np.array_equal(T["params"], E["s_params"])
