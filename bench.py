@@ -325,6 +325,7 @@ def run_ours(args):
     sub.update(repair_rates(sp, sd, torch, ct, dev))
     sub.update(plain_runs(torch, ct, W, dev))
     sub.update(batched_runs(torch, ct, W, dev))
+    sub.update(surrogate_vs_plain(torch, ct, W, dev))
     del opt, table
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -467,6 +468,44 @@ def batched_runs(torch, ct, W, dev, n_runs=4096, gens=100, plain_sample=48):
             "batched_vs_plain": batched / plain,
             "batched_runs_within_1pct": int(len(hits)),
             "batched_median_evals_to_1pct": float(np.median(hits)) if len(hits) else None}
+
+
+def surrogate_vs_plain(torch, ct, W, dev, seeds=16, gens=150):
+    """Unique evaluations to come within 1/2/5 % of the table optimum, and the best fitness after
+    1000 unique evaluations (medians over seeds), for plain and surrogate-screened DE and GA on
+    the medium space at pop 128."""
+    sd = W.medium_space()
+    sp = ct.Space.from_def(sd)
+    sp.build()
+    keys = sp.keys().cpu().numpy().view(np.uint64)
+    table = W.smooth_table(sd, sp.unpack(keys), seed=0)
+    dt = torch.from_numpy(table).to(dev)
+    sp.set_fitness(dt)
+    logt = torch.from_numpy(np.log(table.astype(np.float64)).astype(np.float32)).to(dev)
+    opt = float(table.min())
+    out = {}
+    for kind in ("de", "ga"):
+        for mode in ("plain", "surrogate"):
+            curves = []
+            for seed in range(seeds):
+                o = ct.Opt(sp, kind, 128, seed)
+                if mode == "surrogate":
+                    o.set_surrogate(logt)
+                cu = []
+                for g in range(gens + 1):
+                    o.step(g)
+                    b = o.best()
+                    cu.append((b["n_unique"], b["best_fit"] / opt))
+                curves.append(cu)
+            rec = {}
+            for pct in (1, 2, 5):
+                first = [next((n for n, f in cu if f <= 1 + pct / 100), None) for cu in curves]
+                hit = [x for x in first if x is not None]
+                rec[f"evals_to_{pct}pct_median"] = float(np.median(hit)) if len(hit) * 2 > len(first) else None
+                rec[f"reached_{pct}pct"] = f"{len(hit)}/{len(first)}"
+            rec["best_rel_after_1000_evals"] = float(np.median([[f for n, f in cu if n <= 1000][-1] for cu in curves]))
+            out[f"surrogate_cmp_{kind}_{mode}"] = rec
+    return out
 
 
 if __name__ == "__main__":

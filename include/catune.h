@@ -270,8 +270,9 @@ typedef struct {
     int32_t batch;       /* training batch (256) */
     int32_t steps;       /* SGD steps per generation (8) */
     int32_t warmup_mult; /* screening needs >= warmup_mult * pop evaluations (4) */
-    float lr, momentum;  /* 1e-3, 0.9 */
-    float mae_ratio;     /* screening needs MAE <= mae_ratio * mean |y - mean y| of the generation (0.5) */
+    float lr, momentum;  /* 1e-2, 0.9 */
+    float mae_ratio;     /* screening needs MAE <= mae_ratio * mean |y - mean y| of the generation (1.0:
+                            the surrogate must predict the new evaluations better than their mean) */
 } ct_surrogate_params;
 void ct_surrogate_params_default(ct_surrogate_params *p);
 

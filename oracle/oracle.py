@@ -294,7 +294,7 @@ DEFAULTS = dict(de_F=0.7, de_CR=0.6, pso_w=0.5, pso_c1=3.0, pso_c2=0.5, fa_beta0
                 fa_alpha=0.2, ga_pmut=0.2, target=-np.inf)
 
 
-SURROGATE_DEFAULTS = dict(pool=16, H=256, batch=256, steps=8, warm_mult=4, lr=1e-3, mu=0.9, mae_ratio=0.5)
+SURROGATE_DEFAULTS = dict(pool=16, H=256, batch=256, steps=8, warm_mult=4, lr=1e-2, mu=0.9, mae_ratio=1.0)
 
 
 def run(kind: str, sp: OracleSpace, keys: np.ndarray, table: np.ndarray, pop: int, gens: int,

@@ -476,7 +476,7 @@ extern "C" {
 void ct_surrogate_params_default(ct_surrogate_params* p) {
     if (!p) return;
     p->pool = 16; p->hidden = 256; p->batch = 256; p->steps = 8; p->warmup_mult = 4;
-    p->lr = 1e-3f; p->momentum = 0.9f; p->mae_ratio = 0.5f;
+    p->lr = 1e-2f; p->momentum = 0.9f; p->mae_ratio = 1.0f;
 }
 
 int64_t ct_mlp_param_count(int32_t D, int32_t H) { return (int64_t)mlp_off(D, H).total; }

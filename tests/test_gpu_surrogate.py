@@ -100,3 +100,43 @@ def test_surrogate_trajectory(oracle_mod, kind, space, pop, gens, cfg):
         a, b = T[f], E[e]
         assert np.array_equal(a.astype(b.dtype) if f in ("used", "ne") else a, b), f
     assert np.array_equal(T["params"], E["s_params"])
+
+
+def _curves(sp, kind, seeds, gens, logt=None):
+    from paper_2606_28372_b300 import catune as ct
+    out = []
+    for seed in range(seeds):
+        o = ct.Opt(sp, kind, 128, seed)
+        if logt is not None:
+            o.set_surrogate(logt)
+        cu = []
+        for g in range(gens + 1):
+            o.step(g)
+            b = o.best()
+            cu.append((b["n_unique"], b["best_fit"]))
+        out.append(cu)
+    return out
+
+
+def _evals_to(curves, thr):
+    r = []
+    for cu in curves:
+        e = [n for n, f in cu if f <= thr]
+        r.append(e[0] if e else np.inf)
+    return float(np.median(r))
+
+
+def test_surrogate_gain_de(oracle_mod):
+    """What the trained network gains: on the medium space, surrogate-screened DE (pop 128, 16
+    seeds) needs fewer unique evaluations than plain DE to come within 2 % and 5 % of the table's
+    optimum.  (Within 1 % is reached by neither in 150 generations on this table.)"""
+    p = Pair(W.medium_space(), oracle_mod)
+    logt = torch.from_numpy(np.log(p.table.astype(np.float64)).astype(np.float32)).cuda()
+    opt = float(p.table.min())
+    plain = _curves(p.sp, "de", 16, 150)
+    surr = _curves(p.sp, "de", 16, 150, logt)
+    for pct in (2, 5):
+        thr = np.float32(opt * (1 + pct / 100))
+        ep, es = _evals_to(plain, thr), _evals_to(surr, thr)
+        print(f"DE evals to within {pct}%: plain {ep}, surrogate {es}")
+        assert es < 0.85 * ep
