@@ -380,6 +380,24 @@ def repair_rates(sp, sd, torch, ct, dev):
         d = np.concatenate(ds)
         res[f"repaired_candidates_per_s_{kind}"] = reps * len(batches) * 256 / (ms / 1000.0)
         res[f"repair_distance_hist_{kind}"] = np.bincount(d, minlength=8)[:8].tolist()
+    # exhaustive scan alone (scan-only mode): one pass over the 5.56 GB of keys per call
+    unif = torch.from_numpy(sp.pack(W.uniform_tuples(sd, 64, seed=999)).view(np.int64)).to(dev)
+    sp.set_repair_mode(1, 0)
+    scan = {}
+    for q in (1, 2, 4, 8, 32):
+        c = unif[:q].contiguous()
+        o = torch.empty(q, dtype=torch.int64, device=dev)
+        sp.repair(c, o)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            sp.repair(c, o)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        scan[f"q{q}"] = {"ms_per_pass": ms, "key_stream_GBps": 8 * keys.numel() / (ms / 1000.0) / 1e9}
+    sp.set_repair_mode(0, 0)
+    res["scan_only_repair"] = scan
     return res
 
 

@@ -280,85 +280,127 @@ __device__ __forceinline__ bool lex_less(float fa, uint64_t ka, float fb, uint64
 // Shared scratch of select_dev (block size <= SEL_MAX_THREADS, pop <= CT_MAX_POP).
 constexpr int SEL_MAX_THREADS = 512;
 struct SelectSmem {
-    float sf[SEL_MAX_THREADS];
-    uint64_t sk[SEL_MAX_THREADS];
+    float rf[SEL_MAX_THREADS];
+    uint64_t rk[SEL_MAX_THREADS];
+    int ri[SEL_MAX_THREADS];
+    uint64_t xs[CT_MAX_POP];      // population keys before selection
+    uint64_t us[CT_MAX_POP];      // evaluated keys
     uint8_t pass[CT_MAX_POP];
     uint8_t acc[CT_MAX_POP];
     int init_s;
 };
 
-// Selection / update after evaluation; every thread of the CTA takes part.
+// Block-wide argmin of (f, index) over the entries each thread offers: smallest f;
+// among equal f the largest index when last_tie, else the smallest.  Entries with
+// idx < 0 are absent.  Returns the winning index (-1 if none) in every thread.
+__device__ __forceinline__ int block_argmin(float f, int idx, bool last_tie, SelectSmem& sm) {
+    const int t = threadIdx.x;
+    sm.rf[t] = f;
+    sm.ri[t] = idx;
+    __syncthreads();
+    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+        if (t < w) {
+            const float f2 = sm.rf[t + w];
+            const int i2 = sm.ri[t + w];
+            const int i1 = sm.ri[t];
+            bool take = false;
+            if (i2 >= 0) {
+                if (i1 < 0) take = true;
+                else if (f2 < sm.rf[t]) take = true;
+                else if (f2 == sm.rf[t]) take = last_tie ? (i2 > i1) : (i2 < i1);
+            }
+            if (take) { sm.rf[t] = f2; sm.ri[t] = i2; }
+        }
+        __syncthreads();
+    }
+    const int r = sm.ri[0];
+    __syncthreads();
+    return r;
+}
+
+// Selection / update after evaluation; every thread of the CTA takes part (block size a
+// power of two).  Sequential update rules are applied in closed form:
+//   "best <- x_i if f_i <= f(best)" over ascending i ends at the last index with the
+//   minimal f (if that minimum is <= the old best), "... if f_i < ..." at the first.
 static __device__ void select_dev(const OptArgs& a, uint32_t gen, const uint64_t* __restrict__ keys,
-                           const float* __restrict__ fit, SelectSmem& sm) {
+                                  const float* __restrict__ fit, SelectSmem& sm) {
     const int P = a.P, N = a.N;
     OptDev* st = a.st;
-    float* sf = sm.sf;
-    uint64_t* sk = sm.sk;
-    uint8_t* pass = sm.pass;
-    uint8_t* acc = sm.acc;
-    int& init_s = sm.init_s;
-    // run best = min (fitness, key) over everything evaluated
+    const int t = threadIdx.x, nt = blockDim.x;
+    if (t == 0) sm.init_s = gen == 0 || (a.kind == CT_DE && st->reinit_pending);
+    for (int i = t; i < P; i += nt) { sm.us[i] = keys[i]; sm.xs[i] = a.X[i]; }
+    // run best: min (fitness, key) over this generation's evaluations
     float bf = __int_as_float(0x7f800000);
     uint64_t bk = ~0ull;
-    for (int i = threadIdx.x; i < P; i += blockDim.x)
-        if (lex_less(fit[i], keys[i], bf, bk)) { bf = fit[i]; bk = keys[i]; }
-    sf[threadIdx.x] = bf;
-    sk[threadIdx.x] = bk;
-    if (threadIdx.x == 0) init_s = gen == 0 || (a.kind == CT_DE && st->reinit_pending);
+    for (int i = t; i < P; i += nt)
+        if (lex_less(fit[i], sm.us[i], bf, bk)) { bf = fit[i]; bk = sm.us[i]; }
+    sm.rf[t] = bf;
+    sm.rk[t] = bk;
     __syncthreads();
-    const bool init = init_s;
-    if (threadIdx.x == 0) {
-        for (int t = 1; t < blockDim.x; ++t)
-            if (lex_less(sf[t], sk[t], bf, bk)) { bf = sf[t]; bk = sk[t]; }
-        if (lex_less(bf, bk, st->best_fit, st->best_key)) { st->best_fit = bf; st->best_key = bk; }
+    for (int w = nt >> 1; w > 0; w >>= 1) {
+        if (t < w && lex_less(sm.rf[t + w], sm.rk[t + w], sm.rf[t], sm.rk[t])) { sm.rf[t] = sm.rf[t + w]; sm.rk[t] = sm.rk[t + w]; }
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (lex_less(sm.rf[0], sm.rk[0], st->best_fit, st->best_key)) { st->best_fit = sm.rf[0]; st->best_key = sm.rk[0]; }
         if (st->hit_gen < 0 && st->best_fit <= a.prm.target) { st->hit_gen = gen; st->hit_evals = (long long)st->n_unique; }
     }
+    __syncthreads();
+    const bool init = sm.init_s;
     if (a.kind == CT_DE) {
         if (init) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) { a.X[i] = keys[i]; a.FX[i] = fit[i]; }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int i0 = 0;
-                if (gen == 0) { st->de_best = a.X[0]; st->de_fbest = a.FX[0]; i0 = 1; }
-                for (int i = i0; i < P; ++i)
-                    if (a.FX[i] <= st->de_fbest) { st->de_best = a.X[i]; st->de_fbest = a.FX[i]; }
+            int last = -1;
+            float lf = 0.0f;
+            for (int i = t; i < P; i += nt) {
+                a.X[i] = sm.us[i];
+                a.FX[i] = fit[i];
+                if (last < 0 || fit[i] <= lf) { last = i; lf = fit[i]; }   // ascending i: ties keep the later
+            }
+            const int w = block_argmin(last >= 0 ? lf : 0.0f, last, true, sm);
+            if (t == 0) {
+                if (gen == 0 || fit[w] <= st->de_fbest) { st->de_best = sm.us[w]; st->de_fbest = fit[w]; }
                 st->reinit_pending = 0;
                 st->stag = 0;
             }
         } else {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                const uint64_t u = keys[i];
+            for (int i = t; i < P; i += nt) {
+                const uint64_t u = sm.us[i];
                 bool in_x = false;
-                for (int k = 0; k < P && !in_x; ++k) in_x = a.X[k] == u;
-                pass[i] = fit[i] <= a.FX[i] && !in_x;
+                for (int k = 0; k < P && !in_x; ++k) in_x = sm.xs[k] == u;
+                sm.pass[i] = fit[i] <= a.FX[i] && !in_x;
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                bool ok = pass[i];
-                const uint64_t u = keys[i];
-                for (int k = 0; k < i && ok; ++k) ok = !(pass[k] && keys[k] == u);
-                acc[i] = ok;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < P; i += blockDim.x)
-                if (acc[i]) { a.X[i] = keys[i]; a.FX[i] = fit[i]; }
-            if (threadIdx.x == 0) {
-                int n_acc = 0;
-                for (int i = 0; i < P; ++i) {
-                    if (!acc[i]) continue;
+            int last = -1, n_acc = 0;
+            float lf = 0.0f;
+            for (int i = t; i < P; i += nt) {
+                bool ok = sm.pass[i];
+                const uint64_t u = sm.us[i];
+                for (int k = 0; k < i && ok; ++k) ok = !(sm.pass[k] && sm.us[k] == u);
+                sm.acc[i] = ok;
+                if (ok) {
+                    a.X[i] = u;
+                    a.FX[i] = fit[i];
                     ++n_acc;
-                    if (fit[i] <= st->de_fbest) { st->de_best = keys[i]; st->de_fbest = fit[i]; }
+                    if (last < 0 || fit[i] <= lf) { last = i; lf = fit[i]; }
                 }
-                st->stag = n_acc ? 0 : st->stag + 1;
+            }
+            const int w = block_argmin(last >= 0 ? lf : 0.0f, last, true, sm);
+            sm.ri[t] = n_acc;
+            __syncthreads();
+            if (t == 0) {
+                int total = 0;
+                for (int k = 0; k < nt; ++k) total += sm.ri[k];
+                if (w >= 0 && fit[w] <= st->de_fbest) { st->de_best = sm.us[w]; st->de_fbest = fit[w]; }
+                st->stag = total ? 0 : st->stag + 1;
                 if (st->stag >= 2) { st->reinit_pending = 1; st->stag = 0; }
             }
         }
     } else if (a.kind == CT_PSO || a.kind == CT_FIREFLY) {
         if (gen == 0) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            for (int i = t; i < P; i += nt) {
                 uint32_t w[4];
                 for (int j = 0; j < N; ++j) {
-                    const float x0 = __fmul_rn((float)field(a.sp, keys[i], j), a.eps);
+                    const float x0 = __fmul_rn((float)field(a.sp, sm.us[i], j), a.eps);
                     a.pos[(size_t)i * N + j] = x0;
                     a.pb[(size_t)i * N + j] = x0;
                     if (a.kind == CT_PSO) {
@@ -370,34 +412,42 @@ static __device__ void select_dev(const OptArgs& a, uint32_t gen, const uint64_t
                 a.FX[i] = fit[i];
             }
         } else if (a.kind == CT_PSO) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x)
+            for (int i = t; i < P; i += nt)
                 if (fit[i] < a.fpb[i]) {
                     a.fpb[i] = fit[i];
                     for (int j = 0; j < N; ++j) a.pb[(size_t)i * N + j] = a.pos[(size_t)i * N + j];
                 }
         } else {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            for (int i = t; i < P; i += nt) {
                 for (int j = 0; j < N; ++j) a.pos[(size_t)i * N + j] = a.ynew[(size_t)i * N + j];
                 a.FX[i] = fit[i];
             }
         }
         __syncthreads();
-        if (a.kind == CT_PSO && threadIdx.x == 0) {
-            for (int i = 0; i < P; ++i)
-                if (a.fpb[i] < st->fgb) {
-                    st->fgb = a.fpb[i];
-                    for (int j = 0; j < N; ++j) a.gb[j] = a.pb[(size_t)i * N + j];
-                }
+        if (a.kind == CT_PSO) {
+            int first = -1;
+            float ff = 0.0f;
+            for (int i = t; i < P; i += nt)
+                if (first < 0 || a.fpb[i] < ff) { first = i; ff = a.fpb[i]; }   // ascending i: ties keep the earlier
+            const int w = block_argmin(first >= 0 ? ff : 0.0f, first, false, sm);
+            __shared__ int upd;
+            if (t == 0) {
+                upd = w >= 0 && a.fpb[w] < st->fgb;
+                if (upd) st->fgb = a.fpb[w];
+            }
+            __syncthreads();
+            if (upd)
+                for (int j = t; j < N; j += nt) a.gb[j] = a.pb[(size_t)w * N + j];
         }
-        for (int i = threadIdx.x; i < P; i += blockDim.x) {
-            a.X[i] = keys[i];
+        for (int i = t; i < P; i += nt) {
+            a.X[i] = sm.us[i];
             if (a.kind == CT_PSO) a.FX[i] = a.fpb[i];
         }
     } else {  // GA: generational replacement
-        for (int i = threadIdx.x; i < P; i += blockDim.x) { a.X[i] = keys[i]; a.FX[i] = fit[i]; }
+        for (int i = t; i < P; i += nt) { a.X[i] = sm.us[i]; a.FX[i] = fit[i]; }
     }
     __syncthreads();
-    if (threadIdx.x == 0) st->gen = gen + 1;
+    if (t == 0) st->gen = gen + 1;
     __syncthreads();
 }
 

@@ -125,7 +125,71 @@ __global__ void k_ball_resolve(int d, const int32_t* __restrict__ pend_in, const
     }
 }
 
-// exhaustive streaming argmin of (distance, rank) for up to 32 candidates per CTA
+// Exhaustive streaming argmin of (distance, rank) for up to 32 candidates per CTA.
+// Each thread reads two keys per 16-byte load and keeps, per candidate, the packed
+// minimum (distance << 26 | iteration << 1 | which); keys ascend within a thread, so
+// the smallest packed value is the smallest distance and, among equal distances, the
+// smallest key.  The inner loop is instantiated for the number of pending candidates
+// (1, 2, 4, 8, 16, 32), on 32-bit words when every field lies in the low 32 bits.
+template <int Q, bool NARROW>
+__device__ __forceinline__ void scan_run(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_t highm,
+                                         const uint64_t* cq, int nq, unsigned long long* __restrict__ best,
+                                         unsigned long long (*red)[SCAN_CHUNK]) {
+    uint64_t c[Q];
+    uint32_t b[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) { c[q] = cq[q < nq ? q : 0]; b[q] = 0xFFFFFFFFu; }
+    const int64_t stride = (int64_t)gridDim.x * SCAN_THREADS * 2;
+    const int64_t start = ((int64_t)blockIdx.x * SCAN_THREADS + threadIdx.x) * 2;
+    const uint32_t lo32 = (uint32_t)lowm, hi32 = (uint32_t)highm;
+    uint32_t it = 0;
+    int64_t i = start;
+    for (; i + 1 < nv; i += stride, ++it) {
+        const ulonglong2 kk = __ldg(reinterpret_cast<const ulonglong2*>(keys + i));
+        const uint32_t tag = it << 1;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            uint32_t d0, d1;
+            if (NARROW) {
+                const uint32_t x0 = (uint32_t)kk.x ^ (uint32_t)c[q], x1 = (uint32_t)kk.y ^ (uint32_t)c[q];
+                d0 = __popc((((x0 & lo32) + lo32) | x0) & hi32);
+                d1 = __popc((((x1 & lo32) + lo32) | x1) & hi32);
+            } else {
+                d0 = hamming_keys(kk.x, c[q], lowm, highm);
+                d1 = hamming_keys(kk.y, c[q], lowm, highm);
+            }
+            const uint32_t p0 = (d0 << 26) | tag, p1 = (d1 << 26) | tag | 1u;
+            b[q] = min(b[q], min(p0, p1));
+        }
+    }
+    if (i < nv) {   // last key when nv is odd
+        const uint64_t k = __ldg(keys + i);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) b[q] = min(b[q], ((uint32_t)hamming_keys(k, c[q], lowm, highm) << 26) | (it << 1));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        unsigned long long v = ~0ull;
+        if (b[q] != 0xFFFFFFFFu) {
+            const uint32_t t = b[q] & ((1u << 26) - 1);
+            const int64_t idx = start + (int64_t)(t >> 1) * stride + (t & 1u);
+            v = ((unsigned long long)(b[q] >> 26) << 57) | (unsigned long long)idx;
+        }
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = w < v ? w : v;
+        }
+        if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nq) {
+        unsigned long long v = ~0ull;
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) v = red[w][threadIdx.x] < v ? red[w][threadIdx.x] : v;
+        atomicMin(best + threadIdx.x, v);
+    }
+}
+
 __global__ void __launch_bounds__(SCAN_THREADS)
 k_scan(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_t highm,
        const uint64_t* __restrict__ cand, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
@@ -138,21 +202,82 @@ k_scan(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_t hi
     const int nq = min((uint32_t)SCAN_CHUNK, cnt - q0);
     if (threadIdx.x < SCAN_CHUNK) cq[threadIdx.x] = threadIdx.x < nq ? cand[pend[q0 + threadIdx.x]] : 0ull;
     __syncthreads();
-    unsigned long long b[SCAN_CHUNK];
+    unsigned long long* bq = best + q0;
+    if ((highm >> 32) == 0) {
+        if (nq <= 1) scan_run<1, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else if (nq <= 2) scan_run<2, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else if (nq <= 4) scan_run<4, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else if (nq <= 8) scan_run<8, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else if (nq <= 16) scan_run<16, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else scan_run<32, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+    } else {
+        if (nq <= 1) scan_run<1, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else if (nq <= 2) scan_run<2, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else if (nq <= 4) scan_run<4, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else if (nq <= 8) scan_run<8, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else if (nq <= 16) scan_run<16, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else scan_run<32, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+    }
+}
+
+// Few pending candidates (<= 4): one candidate set per CTA, high occupancy, four
+// independent 16-byte key loads in flight per thread.  CTAs whose chunk holds more
+// than four candidates leave it to k_scan_wide.
+template <int Q, bool NARROW>
+__device__ __forceinline__ void scan_run4(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm,
+                                          uint64_t highm, const uint64_t* cq, int nq,
+                                          unsigned long long* __restrict__ best, unsigned long long (*red)[SCAN_CHUNK]) {
+    constexpr int U = 4;
+    uint64_t c[Q];
+    uint32_t b[Q];
 #pragma unroll
-    for (int q = 0; q < SCAN_CHUNK; ++q) b[q] = NONE;
-    for (int64_t i = (int64_t)blockIdx.x * SCAN_THREADS + threadIdx.x; i < nv; i += (int64_t)gridDim.x * SCAN_THREADS) {
-        const uint64_t k = __ldg(keys + i);
+    for (int q = 0; q < Q; ++q) { c[q] = cq[q < nq ? q : 0]; b[q] = 0xFFFFFFFFu; }
+    const int64_t stride = (int64_t)gridDim.x * SCAN_THREADS * 2;
+    const int64_t start = ((int64_t)blockIdx.x * SCAN_THREADS + threadIdx.x) * 2;
+    const uint32_t lo32 = (uint32_t)lowm, hi32 = (uint32_t)highm;
+    uint32_t it = 0;
+    int64_t i = start;
+    for (; i + (U - 1) * stride + 1 < nv; i += U * stride, it += U) {
+        ulonglong2 kk[U];
 #pragma unroll
-        for (int q = 0; q < SCAN_CHUNK; ++q) {
-            const unsigned long long p = ((unsigned long long)hamming_keys(k, cq[q], lowm, highm) << 57) | (unsigned long long)i;
-            b[q] = p < b[q] ? p : b[q];
+        for (int u = 0; u < U; ++u) kk[u] = __ldg(reinterpret_cast<const ulonglong2*>(keys + i + u * stride));
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t tag = (it + u) << 1;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                uint32_t d0, d1;
+                if (NARROW) {
+                    const uint32_t x0 = (uint32_t)kk[u].x ^ (uint32_t)c[q], x1 = (uint32_t)kk[u].y ^ (uint32_t)c[q];
+                    d0 = __popc((((x0 & lo32) + lo32) | x0) & hi32);
+                    d1 = __popc((((x1 & lo32) + lo32) | x1) & hi32);
+                } else {
+                    d0 = hamming_keys(kk[u].x, c[q], lowm, highm);
+                    d1 = hamming_keys(kk[u].y, c[q], lowm, highm);
+                }
+                b[q] = min(b[q], min((d0 << 26) | tag, (d1 << 26) | tag | 1u));
+            }
+        }
+    }
+    for (; i < nv; i += stride, ++it) {   // remainder, one pair (or the odd last key) at a time
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            if (i + w >= nv) break;
+            const uint64_t k = __ldg(keys + i + w);
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                b[q] = min(b[q], ((uint32_t)hamming_keys(k, c[q], lowm, highm) << 26) | (it << 1) | (uint32_t)w);
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < SCAN_CHUNK; ++q) {
-        unsigned long long v = b[q];
+    for (int q = 0; q < Q; ++q) {
+        unsigned long long v = ~0ull;
+        if (b[q] != 0xFFFFFFFFu) {
+            const uint32_t t = b[q] & ((1u << 26) - 1);
+            const int64_t idx = start + (int64_t)(t >> 1) * stride + (t & 1u);
+            v = ((unsigned long long)(b[q] >> 26) << 57) | (unsigned long long)idx;
+        }
         for (int o = 16; o; o >>= 1) {
             const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
             v = w < v ? w : v;
@@ -161,9 +286,64 @@ k_scan(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_t hi
     }
     __syncthreads();
     if (threadIdx.x < nq) {
-        unsigned long long v = NONE;
+        unsigned long long v = ~0ull;
         for (int w = 0; w < SCAN_THREADS / 32; ++w) v = red[w][threadIdx.x] < v ? red[w][threadIdx.x] : v;
-        atomicMin(best + q0 + threadIdx.x, v);
+        atomicMin(best + threadIdx.x, v);
+    }
+}
+
+// The last chunk of pending candidates, when it holds at most four (every other
+// chunk is full).  One wave of CTAs; each scans its slice of the keys.
+__global__ void __launch_bounds__(SCAN_THREADS, 4)
+k_scan_few(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_t highm,
+           const uint64_t* __restrict__ cand, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
+           unsigned long long* __restrict__ best) {
+    __shared__ uint64_t cq[SCAN_CHUNK];
+    __shared__ unsigned long long red[SCAN_THREADS / 32][SCAN_CHUNK];
+    const uint32_t cnt = *count;
+    if (cnt == 0) return;
+    const uint32_t q0 = (cnt - 1) / SCAN_CHUNK * SCAN_CHUNK;
+    const int nq = (int)(cnt - q0);
+    if (nq > 4) return;
+    if (threadIdx.x < SCAN_CHUNK) cq[threadIdx.x] = threadIdx.x < nq ? cand[pend[q0 + threadIdx.x]] : 0ull;
+    __syncthreads();
+    unsigned long long* bq = best + q0;
+    if ((highm >> 32) == 0) {
+        if (nq <= 1) scan_run4<1, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else if (nq <= 2) scan_run4<2, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else scan_run4<4, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+    } else {
+        if (nq <= 1) scan_run4<1, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else if (nq <= 2) scan_run4<2, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+        else scan_run4<4, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+    }
+}
+
+// Every chunk with more than four pending candidates.  One wave of CTAs; each CTA
+// scans its slice of the keys once per chunk.
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_scan_wide(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_t highm,
+            const uint64_t* __restrict__ cand, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
+            unsigned long long* __restrict__ best) {
+    __shared__ uint64_t cq[SCAN_CHUNK];
+    __shared__ unsigned long long red[SCAN_THREADS / 32][SCAN_CHUNK];
+    const uint32_t cnt = *count;
+    for (uint32_t q0 = 0; q0 < cnt; q0 += SCAN_CHUNK) {
+        const int nq = (int)min((uint32_t)SCAN_CHUNK, cnt - q0);
+        if (nq <= 4) break;                       // only the last chunk can be that small
+        __syncthreads();                          // previous chunk done with cq / red
+        if (threadIdx.x < SCAN_CHUNK) cq[threadIdx.x] = threadIdx.x < nq ? cand[pend[q0 + threadIdx.x]] : 0ull;
+        __syncthreads();
+        unsigned long long* bq = best + q0;
+        if ((highm >> 32) == 0) {
+            if (nq <= 8) scan_run<8, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+            else if (nq <= 16) scan_run<16, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+            else scan_run<32, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+        } else {
+            if (nq <= 8) scan_run<8, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+            else if (nq <= 16) scan_run<16, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+            else scan_run<32, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+        }
     }
 }
 
@@ -233,7 +413,7 @@ ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, in
     for (int d = 1; d <= dmax; ++d) {
         const BallRadius& br = s->balls[d - 1];
         const uint64_t work = (uint64_t)n * br.total;
-        const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 16);
+        const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 4);   // one wave
         k_ball<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
                                    d_cand, pend[cur], cnt[cur], best[cur]);
         count_launch();
@@ -244,11 +424,15 @@ ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, in
         cur ^= 1;
     }
     // whatever is left: exhaustive scan (a full ball search always ends here as well)
-    const unsigned chunks = (unsigned)((n + SCAN_CHUNK - 1) / SCAN_CHUNK);
-    const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)s->n_valid + SCAN_THREADS * 8 - 1) / (SCAN_THREADS * 8), (int64_t)sms * 4));
-    k_scan<<<dim3(gx, chunks), SCAN_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, s->h.swar_low, s->h.swar_high,
-                                                     d_cand, pend[cur], cnt[cur], best[cur]);
-    count_launch();
+    // one wave each: 4 resident CTAs per SM for the few-candidate scan, 2 for the wide one
+    const int64_t need = ((int64_t)s->n_valid + SCAN_THREADS * 8 - 1) / (SCAN_THREADS * 8);
+    const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 4));
+    const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 2));
+    k_scan_few<<<gf, SCAN_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, s->h.swar_low, s->h.swar_high, d_cand,
+                                            pend[cur], cnt[cur], best[cur]);
+    k_scan_wide<<<gw, SCAN_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, s->h.swar_low, s->h.swar_high, d_cand,
+                                             pend[cur], cnt[cur], best[cur]);
+    count_launch(2);
     k_scan_resolve<<<g1, 256, 0, st>>>(s->keys.p, pend[cur], cnt[cur], best[cur], d_out, d_dist);
     count_launch();
     CT_TRY_CUDA(cudaGetLastError());

@@ -129,3 +129,36 @@ def test_large_repair_properties(oracle_mod):
                 assert pk.min() == k
         checked += 1
     assert checked >= 64
+
+
+@pytest.fixture(scope="module")
+def scan_spaces(oracle_mod):
+    """Spaces with keys narrower and wider than 32 bits and with even and odd |V|."""
+    from paper_2606_28372_b300 import catune as ct
+    defs = [W.tiny_space(), W.batched_space(3),
+            W._space("wide33_odd", [(f"p{i}", range(1, 6)) for i in range(11)], ["(p0*p1 + p2*p3 + p4) % 17 == 2"])]
+    out = []
+    for sd in defs:
+        osp = oracle_mod.from_def(sd)
+        okeys = oracle_mod.valid_keys(osp)
+        sp = ct.Space.from_def(sd)
+        assert sp.build() == len(okeys)
+        out.append((sd, osp, okeys, sp))
+    assert len(out[2][2]) % 2 == 1 and out[2][3].info().key_bits == 33
+    return out
+
+
+@pytest.mark.parametrize("count", [1, 2, 3, 4, 5, 9, 17, 33, 70])
+def test_scan_widths_and_odd_tail(oracle_mod, scan_spaces, count):
+    """Scan-only repair for every pending-candidate width."""
+    for sd, osp, okeys, sp in scan_spaces:
+        inv = np.setdiff1d(oracle_mod.pack(osp, W.uniform_tuples(sd, 4 * count + 40, seed=count)), okeys)[:count]
+        assert len(inv) == count
+        sp.set_repair_mode(1, 0)
+        out = torch.empty(count, dtype=torch.int64, device="cuda")
+        dist = torch.empty(count, dtype=torch.uint8, device="cuda")
+        sp.repair(to_dev_u64(inv), out, dist)
+        sp.set_repair_mode(0, 0)
+        eo, ed = oracle_mod.repair(osp, okeys, inv)
+        assert np.array_equal(from_dev_u64(out), eo), sd.name
+        assert np.array_equal(dist.cpu().numpy(), ed), sd.name
