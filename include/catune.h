@@ -369,6 +369,13 @@ typedef struct {
 ct_status ct_space_set_timing(ct_space *space, int32_t enable);
 ct_status ct_space_build_stats(const ct_space *space, ct_build_stats *stats);
 
+/* Device memory released by the library (destroyed spaces and runs, shrunk
+ * buffers) is kept in a process-wide cache, at most 64 GiB per device, and reused
+ * by later allocations of a similar size; an allocation that fails empties the cache
+ * and retries.  ct_trim_cache returns the current device's cached blocks to the
+ * driver. */
+void ct_trim_cache(void);
+
 /* Number of kernels this library has launched in this process (all devices). */
 uint64_t ct_launch_count(void);
 

@@ -115,6 +115,7 @@ _SIGS = {
     "ct_space_set_timing": [C.c_void_p, C.c_int32],
     "ct_space_build_stats": [C.c_void_p, C.c_void_p],
     "ct_launch_count": [],
+    "ct_trim_cache": [],
     "ct_last_error": [],
     "ct_version": [],
 }
@@ -141,6 +142,7 @@ def lib():
         L.ct_mlp_workspace_bytes.restype = C.c_size_t
         L.ct_opt_params_default.restype = None
         L.ct_launch_count.restype = C.c_uint64
+        L.ct_trim_cache.restype = None
         _lib = L
     return _lib
 

@@ -28,29 +28,32 @@ void count_launch(uint64_t n = 1);
         if (s_ != CT_OK) return s_;    \
     } while (0)
 
-// Device buffer with grow-only capacity.
+// Process-wide cache of device blocks: a released block is kept for reuse by a later
+// request of at most its size and at least half of it; on an allocation failure the
+// cache is emptied and the allocation retried.  ct_trim_cache() returns it to the driver.
+void* dev_alloc(size_t bytes, cudaError_t* err);
+void dev_free(void* p, size_t bytes);
+
+// Device buffer with grow-only capacity (blocks come from the cache above).
 template <class T>
 struct DevBuf {
     T* p = nullptr;
     size_t cap = 0;
     ct_status ensure(size_t n) {
         if (n <= cap && p) return CT_OK;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-        size_t want = n ? n : 1;
-        cudaError_t e = cudaMalloc(&p, want * sizeof(T));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            set_error("cudaMalloc(%zu bytes) failed: %s", want * sizeof(T), cudaGetErrorString(e));
-            p = nullptr;
+        release();
+        const size_t want = n ? n : 1;
+        cudaError_t e = cudaSuccess;
+        p = static_cast<T*>(dev_alloc(want * sizeof(T), &e));
+        if (!p) {
+            set_error("device allocation of %zu bytes failed: %s", want * sizeof(T), cudaGetErrorString(e));
             return e == cudaErrorMemoryAllocation ? CT_ERR_OOM : CT_ERR_CUDA;
         }
         cap = want;
         return CT_OK;
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) dev_free(p, cap * sizeof(T));
         p = nullptr;
         cap = 0;
     }
@@ -99,7 +102,7 @@ struct ct_space {
     ct::DevBuf<uint32_t> tile_counts;
     ct::DevBuf<unsigned long long> tile_base;
     ct::DevBuf<unsigned long long> d_total;
-    unsigned long long* h_total = nullptr; // pinned
+    unsigned long long h_total = 0;
 
     // repair
     std::vector<ct::BallRadius> balls;     // radius 1..max_ball

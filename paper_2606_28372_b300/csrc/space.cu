@@ -20,6 +20,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -44,6 +46,69 @@ void set_error(const char* fmt, ...) {
 const char* last_error() { return g_err.c_str(); }
 
 static std::atomic<uint64_t> g_launches{0};
+
+// ---- device block cache ----
+namespace {
+struct BlockCache {
+    std::mutex mu;
+    std::multimap<size_t, void*> free_blocks[64];   // per device: bytes -> block
+    size_t held[64] = {};
+};
+BlockCache& cache() {
+    static BlockCache* c = new BlockCache();   // lives until exit
+    return *c;
+}
+constexpr size_t CACHE_MAX_BYTES = 64ull << 30;
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d >= 0 && d < 64 ? d : 0;
+}
+void flush_device(BlockCache& c, int d) {
+    for (auto& kv : c.free_blocks[d]) cudaFree(kv.second);
+    c.free_blocks[d].clear();
+    c.held[d] = 0;
+}
+}  // namespace
+
+void* dev_alloc(size_t bytes, cudaError_t* err) {
+    BlockCache& c = cache();
+    const int d = current_device();
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        auto it = c.free_blocks[d].lower_bound(bytes);
+        if (it != c.free_blocks[d].end() && it->first <= 2 * bytes) {
+            void* p = it->second;
+            c.held[d] -= it->first;
+            c.free_blocks[d].erase(it);
+            return p;
+        }
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        std::lock_guard<std::mutex> lk(c.mu);
+        flush_device(c, d);
+        e = cudaMalloc(&p, bytes);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (err) *err = e;
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void* p, size_t bytes) {
+    if (!p) return;
+    BlockCache& c = cache();
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (c.held[d] + bytes > CACHE_MAX_BYTES) { cudaFree(p); return; }
+    c.free_blocks[d].emplace(bytes, p);
+    c.held[d] += bytes;
+}
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 constexpr int EXP_THREADS = 256;
@@ -569,7 +634,11 @@ ct_status ensure_device(ct_space* s) {
     if (s->d) return CT_OK;
     const DevSpace& h = s->h;
     cudaGetDevice(&s->device);
-    CT_TRY_CUDA(cudaMalloc(&s->d, sizeof(DevSpace)));
+    {
+        cudaError_t e = cudaSuccess;
+        s->d = static_cast<DevSpace*>(dev_alloc(sizeof(DevSpace), &e));
+        if (!s->d) { set_error("device allocation failed: %s", cudaGetErrorString(e)); return CT_ERR_OOM; }
+    }
     CT_TRY_CUDA(cudaMemcpy(s->d, &h, sizeof(DevSpace), cudaMemcpyHostToDevice));
     CT_TRY(s->innerkey.ensure(s->ik_host.size()));
     CT_TRY_CUDA(cudaMemcpy(s->innerkey.p, s->ik_host.data(), s->ik_host.size() * 4, cudaMemcpyHostToDevice));
@@ -582,7 +651,6 @@ ct_status ensure_device(ct_space* s) {
     }
     CT_TRY(s->status.ensure(1));
     CT_TRY_CUDA(cudaMemset(s->status.p, 0, 4));
-    CT_TRY_CUDA(cudaMallocHost(&s->h_total, sizeof(unsigned long long)));
     for (auto& br : s->balls) {
         CT_TRY(br.d_masks.ensure(br.masks.size()));
         CT_TRY(br.d_prefix.ensure(br.prefix.size()));
@@ -677,8 +745,7 @@ using namespace ct;
 
 ct_space::~ct_space() {
     for (auto& e : events) cudaEventDestroy(e);
-    if (d) cudaFree(d);
-    if (h_total) cudaFreeHost(h_total);
+    if (d) dev_free(d, sizeof(ct::DevSpace));
     pat_cnt.release(); pat_list.release();
     tables.release(); d_tab_cons.release(); d_tab_prefix.release(); innerkey.release();
     keys.release(); tile_counts.release(); tile_base.release(); d_total.release(); status.release();
@@ -785,9 +852,9 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
         if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j + 1], st));
         k_scan_tiles<<<1, 1024, 0, st>>>(s->tile_counts.p, tiles, s->tile_base.p, s->d_total.p);
         count_launch(2);
-        CT_TRY_CUDA(cudaMemcpyAsync(s->h_total, s->d_total.p, 8, cudaMemcpyDeviceToHost, st));
+        CT_TRY_CUDA(cudaMemcpyAsync(&s->h_total, s->d_total.p, 8, cudaMemcpyDeviceToHost, st));
         CT_TRY_CUDA(cudaStreamSynchronize(st));
-        const uint64_t Fn = *s->h_total;
+        const uint64_t Fn = s->h_total;
         DevBuf<uint64_t>& dst = (j == h.n_blocks - 1) ? s->keys : s->frontier[j];
         CT_TRY(dst.ensure(Fn));
         if (Fn) {
@@ -835,6 +902,12 @@ ct_status ct_space_build_stats(const ct_space* s, ct_build_stats* out) {
 }
 
 uint64_t ct_launch_count(void) { return g_launches.load(); }
+
+void ct_trim_cache(void) {
+    BlockCache& c = cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    flush_device(c, current_device());
+}
 
 ct_status ct_space_keys(const ct_space* s, const uint64_t** d_keys, uint64_t* n) {
     if (!s || !d_keys) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
