@@ -297,18 +297,30 @@ def run_ours(args):
     kd = torch.empty(POP, dtype=torch.int64, device=dev)
     fd = torch.empty(POP, dtype=torch.float32, device=dev)
 
-    def e2e_step():
+    phases = {k: [] for k in ("define", "build", "create", "generations", "read_back", "destroy")}
+
+    def e2e_step(record=False):
+        t = [time.perf_counter()]
         s2 = ct.Space.from_def(sd)              # host lists -> library (H2D of the definition)
+        t.append(time.perf_counter())
         n2 = s2.build()                          # D2H of |V|
+        t.append(time.perf_counter())
         s2.set_fitness(table)
         o2 = ct.Opt(s2, "de", POP, seed=rank)
+        t.append(time.perf_counter())
         o2.step(0)
         o2.step(1)
+        t.append(time.perf_counter())
         o2.state(kd, fd)
         keys_h.copy_(kd, non_blocking=True)
         fit_h.copy_(fd, non_blocking=True)
         b = o2.best()                            # syncs
+        t.append(time.perf_counter())
         del o2, s2
+        t.append(time.perf_counter())
+        if record:
+            for k, a, z in zip(phases, t, t[1:]):
+                phases[k].append(1000 * (z - a))
         return n2, b
 
     if args.quick:
@@ -324,13 +336,14 @@ def run_ours(args):
     e2e_steps = max(3, min(args.steps, 10))
     ta = time.perf_counter()
     for _ in range(e2e_steps):
-        e2e_step()
+        e2e_step(record=True)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - ta) / e2e_steps
     e2e = {"value": world * nv / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "ms_per_step": 1000 * e2e_s,
            "note": "define_space from host lists + build (5.6 GB key array from the library's block cache) + "
-                   "DE generations 0 and 1 + population and best read back to pinned host buffers, per step"}
+                   "DE generations 0 and 1 + population and best read back to pinned host buffers, per step",
+           "phase_ms_median": {k: float(np.median(v)) for k, v in phases.items()}}
 
     # ---- sub-metrics ----
     sub = {"valid_configs_per_s": value, "cartesian_points_covered_per_s": world * sd.cartesian_size * args.steps / (ms / 1000.0)}

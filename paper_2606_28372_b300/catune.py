@@ -223,8 +223,14 @@ class _Postfix:
         raise ValueError(f"unsupported constraint syntax: {ast.dump(e)}")
 
 
+_COMPILED = {}
+
+
 def compile_constraints(names, constraints):
-    """Constraint strings -> concatenated postfix program (ct_instr array)."""
+    """Constraint strings -> concatenated postfix program (ct_instr array); memoised."""
+    key = (tuple(names), tuple(constraints))
+    if key in _COMPILED:
+        return _COMPILED[key]
     pf = _Postfix(names)
     for c in constraints:
         pf.gen(ast.parse(c, mode="eval").body)
@@ -232,6 +238,8 @@ def compile_constraints(names, constraints):
     arr = (ct_instr * max(1, len(pf.code)))()
     for i, (op, arg, imm) in enumerate(pf.code):
         arr[i].op, arr[i].arg, arr[i].imm = op, arg, imm
+    if len(_COMPILED) < 4096:
+        _COMPILED[key] = (arr, len(pf.code))
     return arr, len(pf.code)
 
 

@@ -295,7 +295,8 @@ ct_status ct_batch_create(ct_space* const* spaces, int32_t n_spaces, const ct_ba
         BatchSpace& b = bsp[s];
         memset(&b, 0, sizeof b);
         b.sp = sp->d; b.tables = sp->tables.p; b.keys = sp->keys.p; b.nv = (int64_t)sp->n_valid; b.fit = sp->fit;
-        b.dmax = std::min<int>(auto_radius(sp), MAX_RADIUS);
+        if (ensure_balls(sp, auto_radius(sp)) != CT_OK) return CT_ERR_CUDA;
+        b.dmax = std::min<int>(auto_radius(sp), (int)sp->balls.size());
         for (int d = 0; d < b.dmax; ++d) {
             b.masks[d] = sp->balls[d].d_masks.p;
             b.prefix[d] = sp->balls[d].d_prefix.p;

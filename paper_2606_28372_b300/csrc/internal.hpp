@@ -105,7 +105,9 @@ struct ct_space {
     unsigned long long h_total = 0;
 
     // repair
-    std::vector<ct::BallRadius> balls;     // radius 1..max_ball
+    std::vector<ct::BallRadius> balls;     // enumerated radii 1..balls.size() (planned on demand)
+    uint64_t ball_total[ct::MAX_RADIUS + 1] = {};   // points at distance d (sizes only)
+    int ball_max = 0;                      // largest radius the ball tables may cover
     int repair_mode = 0, repair_max_radius = 0;
     ct::RepairScratch rs;
 
@@ -124,6 +126,8 @@ struct ct_space {
 
 namespace ct {
 ct_status ensure_device(ct_space* s);
+ct_status ensure_balls(ct_space* s, int dmax);
+int wanted_radius(const ct_space* s);
 ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, int64_t n, uint64_t* d_out,
                       uint8_t* d_dist, cudaStream_t st);
 int auto_radius(const ct_space* s);

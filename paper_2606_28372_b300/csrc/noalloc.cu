@@ -104,10 +104,9 @@ extern "C" ct_status ct_repair_noalloc(ct_space* s, const uint64_t* d_cand, int6
     k_repair_init<<<g1, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, pend[0], cnt[0], best[0],
                                       s->status.p);
     count_launch();
-    int dmax;
-    if (s->repair_mode == 1) dmax = 0;
-    else if (s->repair_mode == 2) dmax = std::min<int>(s->repair_max_radius, (int)s->balls.size());
-    else dmax = auto_radius(s);
+    // ball radii already enumerated (the build plans the ones the repair path uses); any
+    // candidate left over goes to the exhaustive scan, so the result is exact either way
+    const int dmax = std::min<int>(wanted_radius(s), (int)s->balls.size());
     int cur = 0;
     for (int d = 1; d <= dmax; ++d) {
         const BallRadius& br = s->balls[d - 1];

@@ -376,10 +376,10 @@ int auto_radius(const ct_space* s) {
     const double budget = (double)s->n_valid / 8.0;
     double cum = 0;
     int d = 0;
-    for (const auto& br : s->balls) {
-        cum += (double)br.total;
+    for (int r = 1; r <= s->ball_max; ++r) {
+        cum += (double)s->ball_total[r];
         if (cum > budget) break;
-        d = br.d;
+        d = r;
     }
     return d;
 }
@@ -405,10 +405,8 @@ ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, in
     CT_TRY_CUDA(cudaMemsetAsync(rs.counts.p, 0, 8, st));
     k_repair_init<<<g1, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, pend[0], cnt[0], best[0], s->status.p);
     count_launch();
-    int dmax;
-    if (s->repair_mode == 1) dmax = 0;
-    else if (s->repair_mode == 2) dmax = std::min<int>(s->repair_max_radius, (int)s->balls.size());
-    else dmax = auto_radius(s);
+    const int dmax = wanted_radius(s);
+    CT_TRY(ensure_balls(s, dmax));   // normally planned already (after the build, at run creation)
     int cur = 0;
     for (int d = 1; d <= dmax; ++d) {
         const BallRadius& br = s->balls[d - 1];
@@ -467,6 +465,7 @@ ct_status ct_set_repair_mode(ct_space* s, int32_t mode, int32_t max_radius) {
     if (!s || mode < 0 || mode > 2 || max_radius < 0) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
     s->repair_mode = mode;
     s->repair_max_radius = max_radius;
+    if (s->built && s->n_valid) return ensure_balls(s, wanted_radius(s));
     return CT_OK;
 }
 

@@ -651,12 +651,6 @@ ct_status ensure_device(ct_space* s) {
     }
     CT_TRY(s->status.ensure(1));
     CT_TRY_CUDA(cudaMemset(s->status.p, 0, 4));
-    for (auto& br : s->balls) {
-        CT_TRY(br.d_masks.ensure(br.masks.size()));
-        CT_TRY(br.d_prefix.ensure(br.prefix.size()));
-        CT_TRY_CUDA(cudaMemcpy(br.d_masks.p, br.masks.data(), br.masks.size() * 4, cudaMemcpyHostToDevice));
-        CT_TRY_CUDA(cudaMemcpy(br.d_prefix.p, br.prefix.data(), br.prefix.size() * 8, cudaMemcpyHostToDevice));
-    }
     CT_TRY(s->pat_cnt.ensure(s->pat_cnt_words));
     CT_TRY(s->pat_list.ensure(s->pat_list_words));
     CT_TRY_CUDA(cudaFuncSetAttribute(k_expand_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -664,21 +658,59 @@ ct_status ensure_device(ct_space* s) {
     return CT_OK;
 }
 
-// Hamming-ball tables (radius 1..): subsets of the parameters with r_k > 1.
-static void plan_balls(ct_space* s) {
+// Hamming-ball sizes: the number of points at distance exactly d is the d-th elementary
+// symmetric polynomial of (r_k - 1) over the parameters with r_k > 1.  Radii stop where the
+// subsets, the points or one subset's size outgrow the enumeration tables.
+static void plan_ball_sizes(ct_space* s) {
+    const DevSpace& h = s->h;
+    std::vector<uint64_t> a;
+    for (int k = 0; k < h.n; ++k) if (h.r[k] > 1) a.push_back((uint64_t)(h.r[k] - 1));
+    const int m = (int)a.size();
+    const uint64_t SUBSET_CAP = 1u << 20, POINT_CAP = 1ull << 40, BIG = POINT_CAP + 1;
+    std::vector<uint64_t> e(MAX_RADIUS + 1, 0);
+    e[0] = 1;
+    for (uint64_t ak : a)
+        for (int d = MAX_RADIUS; d >= 1; --d) {
+            const unsigned __int128 v = (unsigned __int128)e[d] + (unsigned __int128)e[d - 1] * ak;
+            e[d] = v > BIG ? BIG : (uint64_t)v;
+        }
+    std::vector<uint64_t> desc = a;
+    std::sort(desc.rbegin(), desc.rend());
+    s->ball_max = 0;
+    unsigned __int128 subsets = 1, largest = 1;
+    for (int d = 1; d <= std::min(m, MAX_RADIUS); ++d) {
+        subsets = subsets * (unsigned)(m - d + 1) / (unsigned)d;   // C(m, d)
+        largest *= desc[d - 1];
+        if (subsets > SUBSET_CAP || e[d] > POINT_CAP || largest >= ((unsigned __int128)1 << 32)) break;
+        s->ball_total[d] = e[d];
+        s->ball_max = d;
+    }
+}
+
+// Radius the repair path will use: the cost-model radius, or the one set by ct_set_repair_mode.
+int wanted_radius(const ct_space* s) {
+    if (s->repair_mode == 1) return 0;
+    if (s->repair_mode == 2) return std::min(s->repair_max_radius, s->ball_max);
+    return auto_radius(s);
+}
+
+// Enumerates and uploads the ball tables of radii balls.size()+1 .. dmax (subsets of the
+// parameters with r_k > 1, in lexicographic order, with prefix sums of their sizes).
+ct_status ensure_balls(ct_space* s, int dmax) {
+    dmax = std::min(dmax, s->ball_max);
+    if ((int)s->balls.size() >= dmax) return CT_OK;
+    CT_TRY(ensure_device(s));
     const DevSpace& h = s->h;
     std::vector<int> free_k;
     for (int k = 0; k < h.n; ++k) if (h.r[k] > 1) free_k.push_back(k);
     const int m = (int)free_k.size();
-    s->balls.clear();
-    const uint64_t SUBSET_CAP = 1u << 20, POINT_CAP = 1ull << 40;
-    for (int d = 1; d <= std::min(m, MAX_RADIUS); ++d) {
+    for (int d = (int)s->balls.size() + 1; d <= dmax; ++d) {
         BallRadius br;
         br.d = d;
+        br.prefix.reserve(s->ball_total[d] ? 1024 : 1);
         br.prefix.push_back(0);
         std::vector<int> idx(d);
         for (int i = 0; i < d; ++i) idx[i] = i;
-        bool ok = true;
         while (true) {
             uint32_t mask = 0;
             uint64_t sz = 1;
@@ -686,16 +718,19 @@ static void plan_balls(ct_space* s) {
             br.masks.push_back(mask);
             br.total += sz;
             br.prefix.push_back(br.total);
-            if (br.masks.size() > SUBSET_CAP || br.total > POINT_CAP || sz >= (1ull << 32)) { ok = false; break; }
             int i = d - 1;
             while (i >= 0 && idx[i] == m - d + i) --i;
             if (i < 0) break;
             ++idx[i];
             for (int t = i + 1; t < d; ++t) idx[t] = idx[t - 1] + 1;
         }
-        if (!ok) break;
+        CT_TRY(br.d_masks.ensure(br.masks.size()));
+        CT_TRY(br.d_prefix.ensure(br.prefix.size()));
+        CT_TRY_CUDA(cudaMemcpy(br.d_masks.p, br.masks.data(), br.masks.size() * 4, cudaMemcpyHostToDevice));
+        CT_TRY_CUDA(cudaMemcpy(br.d_prefix.p, br.prefix.data(), br.prefix.size() * 8, cudaMemcpyHostToDevice));
         s->balls.push_back(std::move(br));
     }
+    return CT_OK;
 }
 
 static ct_status ensure_tables(ct_space* s, cudaStream_t st) {
@@ -766,7 +801,7 @@ ct_status ct_define_space(int32_t n_params, const int32_t* n_values, const int64
     ct_space* s = new (std::nothrow) ct_space();
     if (!s) { set_error("host allocation failed"); return CT_ERR_OOM; }
     ct_status st = lower(s, n_params, n_values, values_flat, program, n_instr);
-    if (st == CT_OK) plan_balls(s);
+    if (st == CT_OK) plan_ball_sizes(s);
     if (st != CT_OK) { delete s; return st; }
     *out = s;
     return CT_OK;
@@ -885,6 +920,7 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
     s->n_valid = F;
     s->built = true;
     if (n_valid_out) *n_valid_out = F;
+    if (F) CT_TRY(ensure_balls(s, wanted_radius(s)));
     if (F == 0) { set_error("no configuration satisfies the constraints"); return CT_ERR_EMPTY_SPACE; }
     return CT_OK;
 }
