@@ -310,7 +310,7 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
 enum {
     P_INIT = 1, P_MUT_PICK = 2, P_CROSS = 3, P_PSO_R = 4, P_FA_ALPHA = 5, P_GA_SEL = 6,
     P_GA_CUT = 7, P_GA_MUT = 8, P_REINIT = 9, P_POOL = 10, P_MLP_INIT = 11, P_MLP_BATCH = 12,
-    P_PSO_VEL = 13
+    P_PSO_VEL = 13, P_GA_REPAIR = 14
 };
 
 /* word t of the stream (individual, generation, purpose) under seed */
@@ -376,6 +376,7 @@ typedef struct {
     float fa_beta0, fa_gamma, fa_alpha;
     float ga_pmut;
     float target;        /* record unique evaluations when best <= target */
+    int repair_rule;     /* 0: Hamming argmin for all; 1: the paper's rule per optimizer */
 } or_params;
 
 typedef struct {         /* per-generation trace, arrays of (G+1) x P unless noted */
@@ -415,6 +416,101 @@ static float evaluate(ctx_t *C, uint64_t key)
         C->best_key = key;
     }
     return f;
+}
+
+static uint64_t repair_key(ctx_t *C, uint64_t key);
+
+/* ---- the paper's neighbour rules (Section IV-A) and repairs (Algorithms 1-3) ---- */
+
+/* values of each parameter that occur in some valid configuration (bit v of occ[k]) */
+static void occurring_values(ctx_t *C, uint8_t *occ /* n x 4096 */)
+{
+    memset(occ, 0, (size_t)C->L.n * 4096);
+    for (int64_t i = 0; i < C->nv; i++)
+        for (int k = 0; k < C->L.n; k++) occ[(size_t)k * 4096 + C->vt[i * C->L.n + k]] = 1;
+}
+
+/* 1: every parameter identical or the previous/next value index (strictly adjacent);
+ * 2: every parameter identical or the nearest lower/higher value occurring in V (adjacent);
+ * 3: exactly one parameter differs (Hamming).  u itself is never a neighbour. */
+static int in_rule(const ctx_t *C, const uint8_t *occ, const int32_t *u, const int32_t *v, int rule)
+{
+    int ndiff = 0;
+    for (int k = 0; k < C->L.n; k++) {
+        int d = v[k] - u[k];
+        if (d == 0) continue;
+        ndiff++;
+        if (rule == 1 && (d > 1 || d < -1)) return 0;
+        if (rule == 2) {
+            int lo = -1, hi = -1;
+            for (int t = u[k] - 1; t >= 0; t--) if (occ[(size_t)k * 4096 + t]) { lo = t; break; }
+            for (int t = u[k] + 1; t < C->L.r[k]; t++) if (occ[(size_t)k * 4096 + t]) { hi = t; break; }
+            if (v[k] != lo && v[k] != hi) return 0;
+        }
+    }
+    if (ndiff == 0) return 0;
+    return rule == 3 ? ndiff == 1 : 1;
+}
+
+/* DE (Algorithm 1 Repair, Section IV-B): the valid configuration with the smallest sum of
+ * absolute value-index differences; ties to the smallest key. */
+static uint64_t repair_l1(ctx_t *C, uint64_t key)
+{
+    if (rank_of(C->keys, C->nv, key) >= 0) return key;
+    int32_t u[OR_MAXP];
+    unpack(&C->L, key, u);
+    int64_t best = -1;
+    int bd = 1 << 30;
+    for (int64_t i = 0; i < C->nv; i++) {
+        const int32_t *v = C->vt + i * C->L.n;
+        int d = 0;
+        for (int k = 0; k < C->L.n; k++) d += v[k] > u[k] ? v[k] - u[k] : u[k] - v[k];
+        if (d < bd) { bd = d; best = i; }
+    }
+    return C->keys[best];
+}
+
+/* PSO / Firefly (Algorithm 2): the first non-empty neighbour set of the snapped point, the
+ * member closest to the position x in continuous space (ties to the smallest key). */
+static uint64_t repair_alg2(ctx_t *C, const uint8_t *occ, uint64_t key, const float *x, float eps)
+{
+    if (rank_of(C->keys, C->nv, key) >= 0) return key;
+    int32_t u[OR_MAXP];
+    unpack(&C->L, key, u);
+    for (int rule = 1; rule <= 3; rule++) {
+        int64_t best = -1;
+        float bd = 0.0f;
+        for (int64_t i = 0; i < C->nv; i++) {
+            const int32_t *v = C->vt + i * C->L.n;
+            if (!in_rule(C, occ, u, v, rule)) continue;
+            float s = 0.0f;
+            for (int k = 0; k < C->L.n; k++) {
+                float d = (float)v[k] * eps - x[k];
+                s = s + d * d;
+            }
+            if (best < 0 || s < bd) { bd = s; best = i; }
+        }
+        if (best >= 0) return C->keys[best];
+    }
+    return repair_key(C, key);   /* no neighbour in any set: the nearest valid (Hamming) */
+}
+
+/* GA (Algorithm 3): a uniformly random member (U[0, |n|) from word w, in key order) of the
+ * first non-empty neighbour set. */
+static uint64_t repair_alg3(ctx_t *C, const uint8_t *occ, uint64_t key, uint32_t w)
+{
+    if (rank_of(C->keys, C->nv, key) >= 0) return key;
+    int32_t u[OR_MAXP];
+    unpack(&C->L, key, u);
+    for (int rule = 1; rule <= 3; rule++) {
+        int64_t cnt = 0;
+        for (int64_t i = 0; i < C->nv; i++) cnt += in_rule(C, occ, u, C->vt + i * C->L.n, rule);
+        if (!cnt) continue;
+        int64_t pick = (int64_t)uint_below(w, (uint32_t)cnt), seen = 0;
+        for (int64_t i = 0; i < C->nv; i++)
+            if (in_rule(C, occ, u, C->vt + i * C->L.n, rule) && seen++ == pick) return C->keys[i];
+    }
+    return repair_key(C, key);
 }
 
 static uint64_t repair_key(ctx_t *C, uint64_t key)
@@ -613,6 +709,28 @@ static float predict1(const ctx_t *C, const float *params, int D, int H, uint64_
     return y;
 }
 
+/* Direct access to the paper's repairs for the pins: rule 1 = index distance (DE),
+ * 2 = Algorithm 2 with positions pos (nc x n) and grid spacing eps, 3 = Algorithm 3 with
+ * one RNG word per candidate. */
+void or_repair_paper(int rule, int n, const int32_t *r, const uint64_t *keys, int64_t nv, const uint64_t *cand,
+                     int64_t nc, const float *pos, float eps, const uint32_t *words, uint64_t *out)
+{
+    ctx_t C;
+    make_layout(&C.L, n, r);
+    C.keys = keys;
+    C.nv = nv;
+    C.vt = tuples_of(&C.L, keys, nv);
+    uint8_t *occ = (uint8_t *)malloc((size_t)n * 4096);
+    occurring_values(&C, occ);
+    for (int64_t i = 0; i < nc; i++) {
+        if (rule == 1) out[i] = repair_l1(&C, cand[i]);
+        else if (rule == 2) out[i] = repair_alg2(&C, occ, cand[i], pos + (size_t)i * n, eps);
+        else out[i] = repair_alg3(&C, occ, cand[i], words[i]);
+    }
+    free(occ);
+    free(C.vt);
+}
+
 /* Runs G generations after the initial one; writes the trace.  Returns 0. */
 int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, const float *table,
            int P, int G, uint64_t seed, const or_params *prm, or_trace *T, const or_surr *sg, or_strace *ST)
@@ -670,6 +788,11 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
     int64_t n_e = 0;
     int use_surr = 0;
     if (sg) or_mlp_init(D, sg->H, seed, mlp);
+    uint8_t *occ = NULL;
+    if (prm->repair_rule) {
+        occ = (uint8_t *)malloc((size_t)N * 4096);
+        occurring_values(&C, occ);
+    }
 
     for (int g = 0; g <= G; g++) {
         int init_mode = (g == 0) || (kind == K_DE && reinit_pending);
@@ -730,7 +853,11 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
         }
         /* ---------------- repair (+ GA mutation), evaluate ---------------- */
         for (int i = 0; i < P; i++) {
-            UR[i] = init_mode ? U[i] : repair_key(&C, U[i]);
+            if (init_mode) UR[i] = U[i];
+            else if (!prm->repair_rule) UR[i] = repair_key(&C, U[i]);
+            else if (kind == K_DE) UR[i] = repair_l1(&C, U[i]);
+            else if (kind == K_GA) UR[i] = repair_alg3(&C, occ, U[i], rng_word(seed, i, g, P_GA_REPAIR, 0));
+            else UR[i] = repair_alg2(&C, occ, U[i], (kind == K_PSO ? pos : ynew) + (size_t)i * N, eps);
             UE[i] = (kind == K_GA && !init_mode) ? ga_mutate(&C, UR[i], (uint32_t)i, g, seed, prm) : UR[i];
         }
         /* surrogate screening: proposals s = 1..pool-1 from streams offset by s, all
@@ -879,7 +1006,7 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
     free(X); free(FX); free(U); free(UR); free(UE); free(FU); free(pos); free(vel); free(pb);
     free(fpb); free(gb); free(ynew); free(tmp); free(pass); free(order); free(C.vt); free(C.memo);
     if (sg && ST && ST->params) memcpy(ST->params, mlp, sizeof(float) * (size_t)n_par);
-    free(mlp); free(mom); free(grad); free(EK); free(EY); free(bf); free(by); free(spred); free(newi);
+    free(mlp); free(mom); free(grad); free(EK); free(EY); free(bf); free(by); free(spred); free(newi); free(occ);
     return 0;
 }
 

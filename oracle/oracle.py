@@ -47,7 +47,7 @@ class _Params(C.Structure):
     _fields_ = [("de_F", C.c_float), ("de_CR", C.c_float), ("pso_w", C.c_float),
                 ("pso_c1", C.c_float), ("pso_c2", C.c_float), ("fa_beta0", C.c_float),
                 ("fa_gamma", C.c_float), ("fa_alpha", C.c_float), ("ga_pmut", C.c_float),
-                ("target", C.c_float)]
+                ("target", C.c_float), ("repair_rule", C.c_int)]
 
 
 class _Surr(C.Structure):
@@ -101,6 +101,7 @@ def lib():
         L.or_mlp_sgd.argtypes = [p, p, p, C.c_int64, C.c_float, C.c_float]
         L.or_mlp_loss64.restype = C.c_double
         L.or_mlp_loss64.argtypes = [p, C.c_int, C.c_int, C.c_int, p, p, C.c_int, p]
+        L.or_repair_paper.argtypes = [C.c_int, C.c_int, p, p, C.c_int64, p, C.c_int64, p, C.c_float, p, p]
         L.or_bf16_round.restype = C.c_float
         L.or_bf16_round.argtypes = [C.c_float]
         _lib = L
@@ -270,6 +271,19 @@ def repair(sp: OracleSpace, keys: np.ndarray, cand):
     return out, dist
 
 
+def repair_paper(rule, sp: OracleSpace, keys, cand, pos=None, eps=0.0, words=None):
+    """The paper's repairs: 1 = index distance (DE), 2 = Algorithm 2 (PSO/Firefly, positions
+    pos), 3 = Algorithm 3 (GA, one RNG word per candidate)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    cand = np.ascontiguousarray(cand, dtype=np.uint64)
+    out = np.zeros(len(cand), np.uint64)
+    pos = np.ascontiguousarray(pos if pos is not None else np.zeros((len(cand), sp.n)), dtype=np.float32)
+    words = np.ascontiguousarray(words if words is not None else np.zeros(len(cand)), dtype=np.uint32)
+    lib().or_repair_paper(rule, sp.n, _ptr(sp.r), _ptr(keys), C.c_int64(len(keys)), _ptr(cand),
+                          C.c_int64(len(cand)), _ptr(pos), C.c_float(eps), _ptr(words), _ptr(out))
+    return out
+
+
 def philox(ctr, key):
     c = np.array(ctr, dtype=np.uint32)
     k = np.array(key, dtype=np.uint32)
@@ -291,7 +305,7 @@ def beta_pick(w: int, P: int) -> int:
 
 
 DEFAULTS = dict(de_F=0.7, de_CR=0.6, pso_w=0.5, pso_c1=3.0, pso_c2=0.5, fa_beta0=1.0, fa_gamma=1.0,
-                fa_alpha=0.2, ga_pmut=0.2, target=-np.inf)
+                fa_alpha=0.2, ga_pmut=0.2, target=-np.inf, repair_rule=0)
 
 
 SURROGATE_DEFAULTS = dict(pool=16, H=256, batch=256, steps=8, warm_mult=4, lr=1e-2, mu=0.9, mae_ratio=1.0)
@@ -318,7 +332,7 @@ def run(kind: str, sp: OracleSpace, keys: np.ndarray, table: np.ndarray, pop: in
         "hit": np.zeros(2, np.int64),
     }
     tr = _Trace(*[T[f].ctypes.data for f, _ in _Trace._fields_])
-    pr = _Params(*[float(np.float32(prm[f])) for f, _ in _Params._fields_])
+    pr = _Params(*[int(prm[f]) if f == "repair_rule" else float(np.float32(prm[f])) for f, _ in _Params._fields_])
     sg = st = None
     if surrogate is not None:
         cfg = dict(SURROGATE_DEFAULTS)
