@@ -171,6 +171,23 @@ ct_status ct_repair(ct_space *space, const uint64_t *d_cand, int64_t n, uint64_t
 ct_status ct_repair_noalloc(ct_space *space, const uint64_t *d_cand, int64_t n, uint64_t *d_out,
                             uint8_t *d_dist, ct_stream stream);
 
+/* The paper's own repair rules.  Neighbours of u (Section IV-A): strictly adjacent
+ * (every parameter equal or the previous/next value index), adjacent (every parameter
+ * equal or the nearest lower/higher value occurring in some valid configuration),
+ * Hamming (exactly one parameter differs).  Invalid candidates are repaired by
+ *   rule 1 (DE, Algorithm 1 Repair): the valid configuration with the smallest sum of
+ *          absolute value-index differences, ties to the smallest key;
+ *   rule 2 (PSO/Firefly, Algorithm 2): the first non-empty neighbour set's member nearest,
+ *          by squared Euclidean distance in fp32, to the position d_pos[i*n_params ...] in the
+ *          continuous embedding with grid spacing eps (ties to the smallest key);
+ *   rule 3 (GA, Algorithm 3): member U[0, size) of the first non-empty neighbour set, in key
+ *          order, drawn from the 32-bit word d_words[i].
+ * Candidates with no neighbour in any set get the Hamming nearest valid key.  Valid
+ * candidates map to themselves.  Exact streaming pass over the valid keys (cost grows with
+ * |V| x n); requires |V| < 2^32.  Library-owned scratch. */
+ct_status ct_repair_paper(ct_space *space, int32_t rule, const uint64_t *d_cand, int64_t n, const float *d_pos,
+                          float eps, const uint32_t *d_words, uint64_t *d_out, ct_stream stream);
+
 /* Repair strategy knob (tests and the autotuner): mode 0 = automatic (Hamming
  * ball search up to a radius chosen from a cost model, then an exhaustive key
  * scan), 1 = exhaustive scan only, 2 = ball search up to max_radius then scan. */
@@ -197,6 +214,10 @@ typedef struct {
     float fa_beta0, fa_gamma, fa_alpha; /* Table IV: 1.0, 1.0, 0.2 */
     float ga_pmut;                   /* Table IV: mutation_chance 5 -> 0.2 */
     float target;                    /* record unique evaluations when best <= target */
+    int32_t repair_rule;             /* 0: Hamming nearest valid for every optimizer (default);
+                                        1: the paper's rule per optimizer (ct_repair_paper: DE
+                                        rule 1, PSO/Firefly rule 2 on the particle position, GA
+                                        rule 3).  Single runs only (not batches, not surrogates). */
 } ct_opt_params;
 
 /* Fills *p with the Table IV values and target = -inf. */

@@ -57,7 +57,7 @@ class ct_surrogate_params(C.Structure):
 
 class ct_opt_params(C.Structure):
     _fields_ = [(n, C.c_float) for n in ("de_F", "de_CR", "pso_w", "pso_c1", "pso_c2", "fa_beta0",
-                                         "fa_gamma", "fa_alpha", "ga_pmut", "target")]
+                                         "fa_gamma", "fa_alpha", "ga_pmut", "target")] + [("repair_rule", C.c_int32)]
 
 
 _lib = None
@@ -74,6 +74,8 @@ _SIGS = {
     "ct_repair": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_set_repair_mode": [C.c_void_p, C.c_int32, C.c_int32],
     "ct_repair_noalloc": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
+    "ct_repair_paper": [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_float, C.c_void_p, C.c_void_p,
+                        C.c_void_p],
     "ct_evaluate": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_space_status": [C.c_void_p, C.c_void_p],
     "ct_opt_params_default": [C.POINTER(ct_opt_params)],
@@ -321,6 +323,11 @@ class Space:
         REPAIR_NOALLOC_MAX candidates per call; calls must not overlap on the GPU)."""
         check(lib().ct_repair_noalloc(self.h, _ptr(cand), cand.numel(), _ptr(out), _ptr(dist), _stream(stream)))
 
+    def repair_paper(self, rule, cand, out, pos=None, eps=0.0, words=None, stream=None):
+        """The paper's repair rules: 1 index distance (DE), 2 Algorithm 2 (PSO/Firefly), 3 Algorithm 3 (GA)."""
+        check(lib().ct_repair_paper(self.h, rule, _ptr(cand), cand.numel(), _ptr(pos), C.c_float(eps), _ptr(words),
+                                    _ptr(out), _stream(stream)))
+
     def set_repair_mode(self, mode, max_radius=0):
         check(lib().ct_set_repair_mode(self.h, mode, max_radius))
 
@@ -357,7 +364,7 @@ def default_params(**over):
     p = ct_opt_params()
     lib().ct_opt_params_default(C.byref(p))
     for k, v in over.items():
-        setattr(p, k, float(np.float32(v)))
+        setattr(p, k, int(v) if k == "repair_rule" else float(np.float32(v)))
     return p
 
 

@@ -309,6 +309,7 @@ ct_status ct_batch_create(ct_space* const* spaces, int32_t n_spaces, const ct_ba
         b.eps = rmax > 1 ? 1.0f / (float)(rmax - 1) : 1.0f;
         b.N = sp->h.n;
     }
+    if (params && params->repair_rule) { set_error("batches use the Hamming repair (repair_rule 0)"); return CT_ERR_INVALID_ARG; }
     ct_batch* bt = new (std::nothrow) ct_batch();
     if (!bt) { set_error("host allocation failed"); return CT_ERR_OOM; }
     bt->spaces.assign(spaces, spaces + n_spaces);

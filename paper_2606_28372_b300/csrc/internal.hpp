@@ -77,6 +77,20 @@ struct RepairScratch {
     DevBuf<unsigned long long> best;   // per pending slot: best key / packed (dist, rank)
 };
 
+// Scratch of the paper's repair rules (candidates, adjacency bounds, per-set minima,
+// per-slice counts, chosen members, RNG words).
+struct RuleScratch {
+    DevBuf<int32_t> pend;
+    DevBuf<uint8_t> rc;
+    DevBuf<unsigned long long> best;
+    DevBuf<uint32_t> count, cnt, words;
+    DevBuf<int32_t> target;
+    void release_all() {
+        pend.release(); rc.release(); best.release(); count.release(); cnt.release(); words.release();
+        target.release();
+    }
+};
+
 }  // namespace ct
 
 struct ct_space {
@@ -110,6 +124,9 @@ struct ct_space {
     int ball_max = 0;                      // largest radius the ball tables may cover
     int repair_mode = 0, repair_max_radius = 0;
     ct::RepairScratch rs;
+    ct::RuleScratch rules;                 // the paper's repair rules (public entry point)
+    ct::DevBuf<uint32_t> occ;              // values of each parameter occurring in V
+    bool occ_ready = false;
 
     // evaluate
     const float* fit = nullptr;
@@ -132,4 +149,10 @@ ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, in
                       uint8_t* d_dist, cudaStream_t st);
 int auto_radius(const ct_space* s);
 ct_status repair_reserve(RepairScratch& rs, int64_t n);
+ct_status rule_reserve(RuleScratch& r, int64_t n, int slices);
+int rule_slices_for(const ct_space* s);
+ct_status ensure_occ(ct_space* s, cudaStream_t st);
+ct_status repair_rule_impl(ct_space* s, RuleScratch& r, int rule, const uint64_t* d_cand, int64_t n,
+                           const float* d_pos, float eps, const uint32_t* d_words, uint64_t* d_out,
+                           RepairScratch& rs, cudaStream_t st);
 }  // namespace ct

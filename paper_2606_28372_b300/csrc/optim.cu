@@ -47,11 +47,30 @@ using namespace ct;
 namespace ct {
 ct_status surrogate_step(ct_opt* o, uint32_t gen, cudaStream_t st);
 
+__global__ void k_ga_repair_words(OptArgs a, uint32_t gen_arg, int use_dev, uint32_t* __restrict__ words) {
+    const uint32_t gen = gen_of(a, gen_arg, use_dev);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.P; i += gridDim.x * blockDim.x)
+        words[i] = rng_word(a.seed, (uint32_t)i, gen, PU_GA_REPAIR, 0);
+}
+
+static ct_status repair_step(ct_opt* o, const OptArgs& a, uint32_t gen, int use_dev, cudaStream_t st) {
+    if (!o->prm.repair_rule) return repair_impl(o->s, o->rs, o->cand.p, o->P, o->rep.p, nullptr, st);
+    if (o->kind == CT_DE)
+        return repair_rule_impl(o->s, o->rules, 1, o->cand.p, o->P, nullptr, 0.0f, nullptr, o->rep.p, o->rs, st);
+    if (o->kind == CT_GA) {
+        k_ga_repair_words<<<(o->P + 255) / 256, 256, 0, st>>>(a, gen, use_dev, o->rules.words.p);
+        count_launch();
+        return repair_rule_impl(o->s, o->rules, 3, o->cand.p, o->P, nullptr, 0.0f, o->rules.words.p, o->rep.p, o->rs, st);
+    }
+    return repair_rule_impl(o->s, o->rules, 2, o->cand.p, o->P, o->kind == CT_PSO ? a.pos : a.ynew, a.eps, nullptr,
+                            o->rep.p, o->rs, st);
+}
+
 static ct_status step_impl(ct_opt* o, uint32_t gen, int use_dev, cudaStream_t st) {
     const OptArgs a = o->args();
     k_propose<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->cand.p);
     count_launch();
-    CT_TRY(repair_impl(o->s, o->rs, o->cand.p, o->P, o->rep.p, nullptr, st));
+    CT_TRY(repair_step(o, a, gen, use_dev, st));
     k_post_repair<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->rep.p);
     count_launch();
     CT_TRY(evaluate_impl(o->s, o->memo.p, &o->st.p->n_unique, o->rep.p, o->P, o->fit.p, nullptr, st));
@@ -96,6 +115,12 @@ ct_status ct_opt_create(ct_space* s, ct_opt_kind kind, const ct_opt_params* para
     ALLOC(memo, o->memo_words);
 #undef ALLOC
     if (e == CT_OK) e = repair_reserve(o->rs, pop);
+    if (e == CT_OK && o->prm.repair_rule) {   // everything the rule path needs, before any capture
+        if (s->n_valid >= (1ull << 32)) { set_error("the paper's repair rules need |V| < 2^32"); e = CT_ERR_LIMIT; }
+        if (e == CT_OK) e = rule_reserve(o->rules, pop, rule_slices_for(s));
+        if (e == CT_OK) e = ensure_occ(s, nullptr);
+        if (e == CT_OK && cudaDeviceSynchronize() != cudaSuccess) { set_error("occurrence table failed"); e = CT_ERR_CUDA; }
+    }
     if (e != CT_OK) { delete o; return e; }
     OptDev init{};
     init.de_fbest = __builtin_inff();

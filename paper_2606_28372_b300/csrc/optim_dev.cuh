@@ -477,9 +477,11 @@ struct ct_opt {
     std::map<uint32_t, uint64_t> graph_kernels;   // kernels per replay of each graph
     const void* graph_keys = nullptr;             // space key buffer the graphs were captured with
     RepairScratch rs;                             // run-owned repair scratch (fixed size: pop)
+    ct::RuleScratch rules;                        // paper's repair rules (repair_rule = 1)
     ct::SurrogateState* sg = nullptr;             // MLP surrogate screening (DE, GA), or none
     ~ct_opt() {
         ct::surrogate_free(sg);
+        rules.release_all();
         for (auto& g : graphs) cudaGraphExecDestroy(g.second);
         st.release(); X.release(); cand.release(); rep.release(); FX.release(); pos.release(); vel.release();
         pb.release(); fpb.release(); gb.release(); ynew.release(); fit.release(); memo.release();

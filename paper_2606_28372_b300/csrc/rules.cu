@@ -1,0 +1,347 @@
+// The paper's own repair rules (Section IV-A neighbour definitions; Algorithm 1's
+// index-distance repair for DE, Algorithm 2 for PSO/Firefly, Algorithm 3 for GA),
+// as an exact streaming pass over the sorted valid keys.
+//
+// For every (valid key v, pending candidate u) one pass computes, field by field:
+//   rule 1: the index distance sum_k |v_k - u_k|, kept as the packed minimum
+//           (distance << 32 | rank): the nearest, smallest key among ties;
+//   rule 2: membership of v in the strictly-adjacent, adjacent and Hamming sets of u
+//           and the squared Euclidean distance between v's grid coordinates and the
+//           particle position, summed in ascending parameter order in fp32; one packed
+//           minimum (distance bits << 32 | rank) per set;
+//   rule 3: the size of each set within each contiguous slice of keys.  A second
+//           kernel picks a uniform member of the first non-empty set from one RNG word
+//           and the slice holding it walks its keys in order to find it.
+// "Adjacent" uses, per parameter, the nearest lower and higher value that occurs in
+// some valid configuration.  Candidates whose three sets are all empty keep the
+// Hamming nearest valid key.  Ranks are packed in 32 bits: |V| < 2^32.
+#include <cuda_runtime.h>
+
+#include "internal.hpp"
+
+namespace ct {
+
+constexpr int RT = 256;   // threads per CTA
+constexpr int RQ = 8;     // candidates per CTA
+constexpr int OCC_WORDS = BLOCK_BITS_MAX / 32;   // per parameter
+
+struct RuleCand {
+    uint64_t u;
+    int32_t lo[MAXP], hi[MAXP];
+};
+
+// values of each parameter occurring in some valid key (bit v of occ[k * OCC_WORDS ...])
+__global__ void __launch_bounds__(RT) k_occ(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys,
+                                            int64_t nv, uint32_t* __restrict__ occ) {
+    __shared__ uint32_t s[MAXP * OCC_WORDS];
+    const int n = sp->n;
+    for (int e = threadIdx.x; e < n * OCC_WORDS; e += RT) s[e] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < nv; i += (int64_t)gridDim.x * RT) {
+        const uint64_t key = keys[i];
+        for (int k = 0; k < n; ++k) {
+            const int v = field(sp, key, k);
+            atomicOr(&s[k * OCC_WORDS + (v >> 5)], 1u << (v & 31));
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * OCC_WORDS; e += RT)
+        if (s[e]) atomicOr(&occ[e], s[e]);
+}
+
+// valid candidates map to themselves; the others are queued with their adjacency bounds
+__global__ void k_rule_prep(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
+                            const uint32_t* __restrict__ occ, const uint64_t* __restrict__ cand, int64_t n,
+                            uint64_t* __restrict__ out, int32_t* __restrict__ pend, uint32_t* __restrict__ count,
+                            RuleCand* __restrict__ rc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t c = cand[i];
+        if (valid_key(sp, tables, c)) { out[i] = c; continue; }
+        const uint32_t slot = atomicAdd(count, 1u);
+        pend[slot] = (int32_t)i;
+        RuleCand& r = rc[slot];
+        r.u = c;
+        for (int k = 0; k < sp->n; ++k) {
+            const int uk = field(sp, c, k);
+            int lo = -1, hi = -1;
+            if (occ) {
+                for (int t = uk - 1; t >= 0; --t) if ((occ[k * OCC_WORDS + (t >> 5)] >> (t & 31)) & 1u) { lo = t; break; }
+                for (int t = uk + 1; t < sp->r[k]; ++t) if ((occ[k * OCC_WORDS + (t >> 5)] >> (t & 31)) & 1u) { hi = t; break; }
+            }
+            r.lo[k] = lo;
+            r.hi[k] = hi;
+        }
+    }
+}
+
+// membership bits of v in the three sets of candidate r: bit0 strictly adjacent, bit1
+// adjacent, bit2 Hamming; optionally the squared distance to the position x
+__device__ __forceinline__ uint32_t rule_sets(const DevSpace* __restrict__ sp, uint64_t v, const RuleCand& r,
+                                              const float* x, float eps, float* eu) {
+    int nd = 0;
+    bool sa = true, adj = true;
+    float s = 0.0f;
+    for (int k = 0; k < sp->n; ++k) {
+        const int vk = field(sp, v, k), uk = field(sp, r.u, k);
+        const int d = vk - uk;
+        if (x) {
+            const float dd = __fsub_rn(__fmul_rn((float)vk, eps), x[k]);
+            s = __fadd_rn(s, __fmul_rn(dd, dd));
+        }
+        if (d == 0) continue;
+        ++nd;
+        if (d > 1 || d < -1) sa = false;
+        if (vk != r.lo[k] && vk != r.hi[k]) adj = false;
+    }
+    if (eu) *eu = s;
+    if (nd == 0) return 0u;
+    return (sa ? 1u : 0u) | (adj ? 2u : 0u) | (nd == 1 ? 4u : 0u);
+}
+
+template <int RULE>
+__global__ void __launch_bounds__(RT)
+k_rule_scan(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, int64_t nv, int64_t slice,
+            const RuleCand* __restrict__ rc, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
+            const float* __restrict__ pos, float eps, unsigned long long* __restrict__ best,
+            uint32_t* __restrict__ cnt) {
+    __shared__ RuleCand cs[RQ];
+    __shared__ float xs[RQ][MAXP];
+    __shared__ unsigned long long red[RT / 32][RQ][3];
+    const uint32_t total = *count;
+    const uint32_t q0 = blockIdx.y * RQ;
+    if (q0 >= total) return;
+    const int nq = min((uint32_t)RQ, total - q0);
+    const int N = sp->n;
+    for (int e = threadIdx.x; e < nq; e += RT) cs[e] = rc[q0 + e];
+    if (RULE == 2)
+        for (int e = threadIdx.x; e < nq * N; e += RT) xs[e / N][e % N] = pos[(size_t)pend[q0 + e / N] * N + e % N];
+    __syncthreads();
+    const int64_t lo = (int64_t)blockIdx.x * slice, hi = min(nv, lo + slice);
+    unsigned long long b[RQ][3];
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) b[q][0] = b[q][1] = b[q][2] = ~0ull;
+    uint32_t c3[RQ][3];
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) c3[q][0] = c3[q][1] = c3[q][2] = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += RT) {
+        const uint64_t v = __ldg(keys + i);
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+            if (q >= nq) break;
+            if (RULE == 1) {
+                int l1 = 0;
+                for (int k = 0; k < N; ++k) l1 += abs(field(sp, v, k) - field(sp, cs[q].u, k));
+                const unsigned long long p = ((unsigned long long)l1 << 32) | (unsigned long long)i;
+                b[q][0] = p < b[q][0] ? p : b[q][0];
+            } else if (RULE == 2) {
+                float eu;
+                const uint32_t m = rule_sets(sp, v, cs[q], xs[q], eps, &eu);
+                const unsigned long long p = ((unsigned long long)__float_as_uint(eu) << 32) | (unsigned long long)i;
+#pragma unroll
+                for (int t = 0; t < 3; ++t)
+                    if ((m >> t) & 1u) b[q][t] = p < b[q][t] ? p : b[q][t];
+            } else {
+                const uint32_t m = rule_sets(sp, v, cs[q], nullptr, 0.0f, nullptr);
+#pragma unroll
+                for (int t = 0; t < 3; ++t) c3[q][t] += (m >> t) & 1u;
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < RQ; ++q)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            unsigned long long v = RULE == 3 ? (unsigned long long)c3[q][t] : b[q][t];
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+                v = RULE == 3 ? v + w : (w < v ? w : v);
+            }
+            if (lane == 0) red[warp][q][t] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < nq * 3) {
+        const int q = threadIdx.x / 3, t = threadIdx.x % 3;
+        unsigned long long v = RULE == 3 ? 0ull : ~0ull;
+        for (int w = 0; w < RT / 32; ++w) {
+            const unsigned long long x = red[w][q][t];
+            v = RULE == 3 ? v + x : (x < v ? x : v);
+        }
+        if (RULE == 3) cnt[((size_t)(q0 + q) * 3 + t) * gridDim.x + blockIdx.x] = (uint32_t)v;
+        else if (RULE == 1 && t == 0) atomicMin(best + (size_t)(q0 + q) * 3, v);
+        else if (RULE == 2) atomicMin(best + (size_t)(q0 + q) * 3 + t, v);
+    }
+}
+
+// rules 1 and 2: the winner of the first non-empty set (rule 1: the only one)
+__global__ void k_rule_finish(const uint64_t* __restrict__ keys, const int32_t* __restrict__ pend,
+                              const uint32_t* __restrict__ count, const unsigned long long* __restrict__ best,
+                              uint64_t* __restrict__ out) {
+    const uint32_t total = *count;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x)
+        for (int t = 0; t < 3; ++t) {
+            const unsigned long long b = best[(size_t)q * 3 + t];
+            if (b != ~0ull) { out[pend[q]] = keys[b & 0xffffffffull]; break; }
+        }
+}
+
+// rule 3: choose the set and the member's slice and index within the slice
+__global__ void k_rule3_pick(const uint32_t* __restrict__ count, const int32_t* __restrict__ pend,
+                             const uint32_t* __restrict__ cnt, int slices, const uint32_t* __restrict__ words,
+                             int32_t* __restrict__ target) {
+    const uint32_t total = *count;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        target[q * 3] = -1;
+        for (int t = 0; t < 3; ++t) {
+            const uint32_t* c = cnt + ((size_t)q * 3 + t) * slices;
+            uint64_t sum = 0;
+            for (int s = 0; s < slices; ++s) sum += c[s];
+            if (!sum) continue;
+            uint32_t pick = uint_below(words[pend[q]], (uint32_t)sum);
+            int s = 0;
+            while (pick >= c[s]) { pick -= c[s]; ++s; }
+            target[q * 3] = s;
+            target[q * 3 + 1] = t;
+            target[q * 3 + 2] = (int32_t)pick;
+            break;
+        }
+    }
+}
+
+// rule 3: the slice holding the chosen member walks its keys in order and writes it
+__global__ void __launch_bounds__(RT)
+k_rule3_select(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, int64_t nv, int64_t slice,
+               const RuleCand* __restrict__ rc, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
+               const int32_t* __restrict__ target, uint64_t* __restrict__ out) {
+    __shared__ uint32_t wsum[RT / 32];
+    __shared__ int found;
+    const uint32_t total = *count;
+    const int64_t lo = (int64_t)blockIdx.x * slice, hi = min(nv, lo + slice);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t q = blockIdx.y; q < total; q += gridDim.y) {
+        if (target[q * 3] != (int)blockIdx.x) continue;   // uniform across the CTA
+        const int set = target[q * 3 + 1];
+        uint32_t want = (uint32_t)target[q * 3 + 2];
+        const RuleCand r = rc[q];
+        if (threadIdx.x == 0) found = 0;
+        __syncthreads();
+        for (int64_t base = lo; base < hi; base += RT) {
+            const int64_t i = base + threadIdx.x;
+            bool m = false;
+            if (i < hi) m = (rule_sets(sp, __ldg(keys + i), r, nullptr, 0.0f, nullptr) >> set) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, m);
+            if (lane == 0) wsum[warp] = __popc(bal);
+            __syncthreads();
+            uint32_t before = 0, all = 0;
+            for (int w = 0; w < RT / 32; ++w) { before += w < warp ? wsum[w] : 0u; all += wsum[w]; }
+            if (want < all) {
+                const uint32_t mine = before + __popc(bal & ((1u << lane) - 1u));
+                if (m && mine == want) { out[pend[q]] = keys[i]; found = 1; }
+            }
+            __syncthreads();
+            if (want < all || found) break;
+            want -= all;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_rule_words(uint64_t seed, uint32_t gen, int P, uint32_t* __restrict__ words) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P) words[i] = rng_word(seed, (uint32_t)i, gen, PU_GA_REPAIR, 0);
+}
+
+ct_status rule_reserve(RuleScratch& r, int64_t n, int slices) {
+    CT_TRY(r.pend.ensure(n));
+    CT_TRY(r.rc.ensure(n * sizeof(RuleCand)));
+    CT_TRY(r.best.ensure(3 * (size_t)n));
+    CT_TRY(r.count.ensure(1));
+    CT_TRY(r.cnt.ensure(3 * (size_t)n * slices));
+    CT_TRY(r.target.ensure(3 * (size_t)n));
+    CT_TRY(r.words.ensure(n));
+    return CT_OK;
+}
+
+static int rule_slices(const ct_space* s) {
+    int sms = 148, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = ((int64_t)s->n_valid + 4095) / 4096;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 4));
+}
+
+ct_status ensure_occ(ct_space* s, cudaStream_t st) {
+    if (s->occ_ready) return CT_OK;
+    CT_TRY(s->occ.ensure((size_t)MAXP * OCC_WORDS));
+    CT_TRY_CUDA(cudaMemsetAsync(s->occ.p, 0, (size_t)MAXP * OCC_WORDS * 4, st));
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)s->n_valid + RT - 1) / RT, 148 * 8));
+    k_occ<<<g, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, s->occ.p);
+    count_launch();
+    CT_TRY_CUDA(cudaGetLastError());
+    s->occ_ready = true;
+    return CT_OK;
+}
+
+int rule_slices_for(const ct_space* s) { return rule_slices(s); }
+
+ct_status repair_rule_impl(ct_space* s, RuleScratch& r, int rule, const uint64_t* d_cand, int64_t n,
+                           const float* d_pos, float eps, const uint32_t* d_words, uint64_t* d_out,
+                           RepairScratch& rs, cudaStream_t st) {
+    if (n == 0) return CT_OK;
+    if (s->n_valid >= (1ull << 32)) { set_error("the paper's repair rules need |V| < 2^32"); return CT_ERR_LIMIT; }
+    const int slices = rule_slices(s);
+    CT_TRY(rule_reserve(r, n, slices));
+    if (rule != 1) {
+        CT_TRY(ensure_occ(s, st));
+        CT_TRY(repair_impl(s, rs, d_cand, n, d_out, nullptr, st));   // fallback: Hamming nearest
+    }
+    CT_TRY_CUDA(cudaMemsetAsync(r.count.p, 0, 4, st));
+    CT_TRY_CUDA(cudaMemsetAsync(r.best.p, 0xff, 3 * (size_t)n * 8, st));
+    const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 8);
+    k_rule_prep<<<g1, 256, 0, st>>>(s->d, s->tables.p, rule == 1 ? nullptr : s->occ.p, d_cand, n, d_out, r.pend.p,
+                                    r.count.p, (RuleCand*)r.rc.p);
+    const int64_t slice = ((int64_t)s->n_valid + slices - 1) / slices;
+    const dim3 grid(slices, (unsigned)((n + RQ - 1) / RQ));
+    RuleCand* rc = (RuleCand*)r.rc.p;
+    if (rule == 1) {
+        k_rule_scan<1><<<grid, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p,
+                                            nullptr, 0.0f, r.best.p, nullptr);
+        k_rule_finish<<<g1, 256, 0, st>>>(s->keys.p, r.pend.p, r.count.p, r.best.p, d_out);
+    } else if (rule == 2) {
+        k_rule_scan<2><<<grid, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p,
+                                            d_pos, eps, r.best.p, nullptr);
+        k_rule_finish<<<g1, 256, 0, st>>>(s->keys.p, r.pend.p, r.count.p, r.best.p, d_out);
+    } else {
+        k_rule_scan<3><<<grid, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p,
+                                            nullptr, 0.0f, nullptr, r.cnt.p);
+        k_rule3_pick<<<g1, 256, 0, st>>>(r.count.p, r.pend.p, r.cnt.p, slices, d_words, r.target.p);
+        k_rule3_select<<<dim3(slices, (unsigned)std::min<int64_t>(n, 64)), RT, 0, st>>>(
+            s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p, r.target.p, d_out);
+    }
+    count_launch(rule == 3 ? 4 : 3);
+    CT_TRY_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+ct_status rule_words(uint64_t seed, uint32_t gen, int P, uint32_t* words, cudaStream_t st) {
+    k_rule_words<<<(P + 255) / 256, 256, 0, st>>>(seed, gen, P, words);
+    count_launch();
+    CT_TRY_CUDA(cudaGetLastError());
+    return CT_OK;
+}
+
+}  // namespace ct
+
+using namespace ct;
+
+extern "C" ct_status ct_repair_paper(ct_space* s, int32_t rule, const uint64_t* d_cand, int64_t n, const float* d_pos,
+                                     float eps, const uint32_t* d_words, uint64_t* d_out, ct_stream stream) {
+    if (!s || n < 0 || (n > 0 && (!d_cand || !d_out)) || rule < 1 || rule > 3 || (rule == 2 && n > 0 && !d_pos) ||
+        (rule == 3 && n > 0 && !d_words)) {
+        set_error("bad argument");
+        return CT_ERR_INVALID_ARG;
+    }
+    if (!s->built) { set_error("space not built"); return CT_ERR_STATE; }
+    if (s->n_valid == 0) { set_error("empty valid space"); return CT_ERR_EMPTY_SPACE; }
+    return repair_rule_impl(s, s->rules, rule, d_cand, n, d_pos, eps, d_words, d_out, s->rs, (cudaStream_t)stream);
+}

@@ -787,6 +787,8 @@ ct_space::~ct_space() {
     for (auto& f : frontier) f.release();
     for (auto& b : balls) { b.d_masks.release(); b.d_prefix.release(); }
     rs.pend_a.release(); rs.pend_b.release(); rs.counts.release(); rs.best.release();
+    rules.release_all();
+    occ.release();
 }
 
 extern "C" {
@@ -861,6 +863,7 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
     const uint64_t* parents = nullptr;
     uint64_t F = 1;
     s->built = false;
+    s->occ_ready = false;
     memset(&s->stats, 0, sizeof s->stats);
     s->stats.timed = s->timing;
     if (s->timing && s->events.empty()) {

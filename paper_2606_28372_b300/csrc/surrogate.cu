@@ -525,6 +525,7 @@ ct_status ct_opt_set_surrogate(ct_opt* o, const ct_surrogate_params* prm, const 
     if (!o || !d_log_table) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
     if (o->kind != CT_DE && o->kind != CT_GA) { set_error("the surrogate screens DE and GA runs only"); return CT_ERR_INVALID_ARG; }
     if (o->sg) { set_error("surrogate already set"); return CT_ERR_STATE; }
+    if (o->prm.repair_rule) { set_error("surrogate screening uses the Hamming repair (repair_rule 0)"); return CT_ERR_INVALID_ARG; }
     ct_surrogate_params cfg;
     if (prm) cfg = *prm; else ct_surrogate_params_default(&cfg);
     if (cfg.pool < 1 || cfg.pool > 64 || cfg.hidden < 1 || cfg.hidden > 1024 || cfg.batch < 1 || cfg.batch > 4096 ||
