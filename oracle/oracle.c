@@ -310,8 +310,12 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
 enum {
     P_INIT = 1, P_MUT_PICK = 2, P_CROSS = 3, P_PSO_R = 4, P_FA_ALPHA = 5, P_GA_SEL = 6,
     P_GA_CUT = 7, P_GA_MUT = 8, P_REINIT = 9, P_POOL = 10, P_MLP_INIT = 11, P_MLP_BATCH = 12,
-    P_PSO_VEL = 13, P_GA_REPAIR = 14
+    P_PSO_VEL = 13, P_GA_REPAIR = 14, P_RAND_INIT = 15
 };
+
+/* static penalty of an invalid configuration in the non-constraint-aware runs (the
+ * magnitude of Kernel Tuner's default, positive because fitness is minimised) */
+#define OR_PENALTY 1e20f
 
 /* word t of the stream (individual, generation, purpose) under seed */
 static uint32_t rng_word(uint64_t seed, uint32_t indiv, uint32_t gen, uint32_t purpose, uint32_t t)
@@ -377,6 +381,7 @@ typedef struct {
     float ga_pmut;
     float target;        /* record unique evaluations when best <= target */
     int repair_rule;     /* 0: Hamming argmin for all; 1: the paper's rule per optimizer */
+    int aware;           /* 1: constraint-aware; 0: random Cartesian start, no repair, penalty */
 } or_params;
 
 typedef struct {         /* per-generation trace, arrays of (G+1) x P unless noted */
@@ -408,9 +413,13 @@ typedef struct {
 static float evaluate(ctx_t *C, uint64_t key)
 {
     int64_t rk = rank_of(C->keys, C->nv, key);
-    if (rk < 0) return INFINITY;            /* unreachable after repair */
-    if (!C->memo[rk]) { C->memo[rk] = 1; C->n_unique++; }
-    float f = C->table[rk];
+    float f;
+    if (rk < 0) {
+        f = OR_PENALTY;                     /* only without constraint awareness: nothing is run */
+    } else {
+        if (!C->memo[rk]) { C->memo[rk] = 1; C->n_unique++; }
+        f = C->table[rk];
+    }
     if (f < C->best_fit || (f == C->best_fit && key < C->best_key)) {
         C->best_fit = f;
         C->best_key = key;
@@ -678,6 +687,27 @@ static uint64_t ga_mutate(ctx_t *C, uint64_t key, uint32_t si, int g, uint64_t s
     return key;
 }
 
+/* non-constraint-aware start: a uniform Cartesian tuple (stream RAND_INIT, word k) */
+static uint64_t random_tuple(ctx_t *C, uint64_t seed, uint32_t i, uint32_t g)
+{
+    int32_t t[OR_MAXP];
+    for (int k = 0; k < C->L.n; k++) t[k] = (int32_t)uint_below(rng_word(seed, i, g, P_RAND_INIT, (uint32_t)k), (uint32_t)C->L.r[k]);
+    return pack(&C->L, t);
+}
+
+/* non-constraint-aware GA mutation: one random parameter takes one of its other values */
+static uint64_t ga_mutate_plain(ctx_t *C, uint64_t key, uint32_t si, int g, uint64_t seed, const or_params *prm)
+{
+    if (!(u01(rng_word(seed, si, g, P_GA_MUT, 0)) < prm->ga_pmut)) return key;
+    int32_t u[OR_MAXP];
+    unpack(&C->L, key, u);
+    int k = (int)uint_below(rng_word(seed, si, g, P_GA_MUT, 1), (uint32_t)C->L.n);
+    if (C->L.r[k] < 2) return key;
+    int v = (int)uint_below(rng_word(seed, si, g, P_GA_MUT, 2), (uint32_t)(C->L.r[k] - 1));
+    u[k] = v < u[k] ? v : v + 1;
+    return pack(&C->L, u);
+}
+
 /* surrogate configuration and per-generation trace */
 typedef struct {
     int pool, H, batch, steps, warm_mult;
@@ -797,7 +827,16 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
     for (int g = 0; g <= G; g++) {
         int init_mode = (g == 0) || (kind == K_DE && reinit_pending);
         /* ---------------- propose ---------------- */
-        if (init_mode) {
+        if (init_mode && !prm->aware && (kind == K_PSO || kind == K_FIREFLY)) {
+            /* random coordinates in [0,1]^N, snapped */
+            for (int i = 0; i < P; i++) {
+                float *x = pos + (size_t)i * N;
+                for (int j = 0; j < N; j++) x[j] = u01(rng_word(seed, i, g, P_RAND_INIT, (uint32_t)j));
+                U[i] = snap_key(&C.L, x, eps);
+            }
+        } else if (init_mode && !prm->aware) {
+            for (int i = 0; i < P; i++) U[i] = random_tuple(&C, seed, (uint32_t)i, (uint32_t)g);
+        } else if (init_mode) {
             uint32_t purpose = g == 0 ? P_INIT : P_REINIT;
             for (int i = 0; i < P; i++) U[i] = stratified_key(&C, seed, (uint32_t)i, (uint32_t)P, (uint32_t)g, purpose);
         } else if (kind == K_DE) {
@@ -853,12 +892,15 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
         }
         /* ---------------- repair (+ GA mutation), evaluate ---------------- */
         for (int i = 0; i < P; i++) {
-            if (init_mode) UR[i] = U[i];
+            if (init_mode || !prm->aware) UR[i] = U[i];
             else if (!prm->repair_rule) UR[i] = repair_key(&C, U[i]);
             else if (kind == K_DE) UR[i] = repair_l1(&C, U[i]);
             else if (kind == K_GA) UR[i] = repair_alg3(&C, occ, U[i], rng_word(seed, i, g, P_GA_REPAIR, 0));
             else UR[i] = repair_alg2(&C, occ, U[i], (kind == K_PSO ? pos : ynew) + (size_t)i * N, eps);
-            UE[i] = (kind == K_GA && !init_mode) ? ga_mutate(&C, UR[i], (uint32_t)i, g, seed, prm) : UR[i];
+            UE[i] = (kind == K_GA && !init_mode)
+                        ? (prm->aware ? ga_mutate(&C, UR[i], (uint32_t)i, g, seed, prm)
+                                      : ga_mutate_plain(&C, UR[i], (uint32_t)i, g, seed, prm))
+                        : UR[i];
         }
         /* surrogate screening: proposals s = 1..pool-1 from streams offset by s, all
          * repaired (and mutated), the lowest prediction wins each slot */
@@ -962,7 +1004,7 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
                 for (int i = 0; i < P; i++) {
                     unpack(&C.L, UE[i], ia);
                     for (int j = 0; j < N; j++) {
-                        float x0 = (float)ia[j] * eps;
+                        float x0 = prm->aware ? (float)ia[j] * eps : pos[(size_t)i * N + j];
                         pos[(size_t)i * N + j] = x0;
                         pb[(size_t)i * N + j] = x0;
                         if (kind == K_PSO) {

@@ -47,7 +47,7 @@ class _Params(C.Structure):
     _fields_ = [("de_F", C.c_float), ("de_CR", C.c_float), ("pso_w", C.c_float),
                 ("pso_c1", C.c_float), ("pso_c2", C.c_float), ("fa_beta0", C.c_float),
                 ("fa_gamma", C.c_float), ("fa_alpha", C.c_float), ("ga_pmut", C.c_float),
-                ("target", C.c_float), ("repair_rule", C.c_int)]
+                ("target", C.c_float), ("repair_rule", C.c_int), ("constraint_aware", C.c_int)]
 
 
 class _Surr(C.Structure):
@@ -305,7 +305,7 @@ def beta_pick(w: int, P: int) -> int:
 
 
 DEFAULTS = dict(de_F=0.7, de_CR=0.6, pso_w=0.5, pso_c1=3.0, pso_c2=0.5, fa_beta0=1.0, fa_gamma=1.0,
-                fa_alpha=0.2, ga_pmut=0.2, target=-np.inf, repair_rule=0)
+                fa_alpha=0.2, ga_pmut=0.2, target=-np.inf, repair_rule=0, constraint_aware=1)
 
 
 SURROGATE_DEFAULTS = dict(pool=16, H=256, batch=256, steps=8, warm_mult=4, lr=1e-2, mu=0.9, mae_ratio=1.0)
@@ -332,7 +332,7 @@ def run(kind: str, sp: OracleSpace, keys: np.ndarray, table: np.ndarray, pop: in
         "hit": np.zeros(2, np.int64),
     }
     tr = _Trace(*[T[f].ctypes.data for f, _ in _Trace._fields_])
-    pr = _Params(*[int(prm[f]) if f == "repair_rule" else float(np.float32(prm[f])) for f, _ in _Params._fields_])
+    pr = _Params(*[int(prm[f]) if f in ("repair_rule", "constraint_aware") else float(np.float32(prm[f])) for f, _ in _Params._fields_])
     sg = st = None
     if surrogate is not None:
         cfg = dict(SURROGATE_DEFAULTS)
