@@ -351,6 +351,7 @@ def run_ours(args):
     sub.update(plain_runs(torch, ct, W, dev))
     sub.update(batched_runs(torch, ct, W, dev))
     sub.update(surrogate_vs_plain(torch, ct, W, dev))
+    sub.update(aware_vs_unaware(torch, ct, W, dev))
     del opt, table
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -513,6 +514,14 @@ def batched_runs(torch, ct, W, dev, n_runs=4096, gens=100, plain_sample=48):
             "batched_median_evals_to_1pct": float(np.median(hits)) if len(hits) else None}
 
 
+def run_aware(args):
+    import torch
+    from paper_2606_28372_b300 import catune as ct
+    from paper_2606_28372_b300 import workloads as W
+    print(json.dumps(aware_vs_unaware(torch, ct, W, torch.device("cuda", 0))))
+    return 0
+
+
 def run_scan(args):
     """Exhaustive repair scan alone: scan-only repair of 1, 2 and 4 uniform candidates per call,
     one pass over the valid keys each (timed with CUDA events on the launching stream)."""
@@ -587,6 +596,218 @@ def surrogate_vs_plain(torch, ct, W, dev, seeds=16, gens=150):
     return out
 
 
+PAPER_POP = {"de": 160, "pso": 30, "firefly": 20, "ga": 20}   # Table IV (DE: 16 x 10 parameters)
+
+
+def aware_vs_unaware(torch, ct, W, dev, seeds=32, gens=500):
+    """Synthetic analogue of the aware-vs-default comparison of Section V-B: the four optimizers
+    with Table IV's population sizes, constraint-aware and not (random Cartesian start, no repair,
+    static penalty), `seeds` runs each on the eight spaces of the density ladder (1.5 % .. 100 %)
+    and the tiny space (56 %), every run of one mode in one batched launch per generation.  Per
+    space and optimizer: the fraction of runs within 1 % of the optimum after `gens` generations,
+    the median unique evaluations and generations to get there (when more than half do), and the
+    median best/optimum; per optimizer, the Spearman correlation between density and the aware
+    gain in that fraction."""
+    from scipy.stats import spearmanr
+    kinds = ["de", "pso", "firefly", "ga"]
+    defs = [W.density_space(j) for j in range(8)] + [W.tiny_space()]
+    spaces, dens, opt = [], [], []
+    for j, sd in enumerate(defs):
+        sp = ct.Space.from_def(sd)
+        nv = sp.build()
+        keys = sp.keys().cpu().numpy().view(np.uint64)
+        t = W.lognormal_table(nv, seed=0) if sd.name == "tiny" else W.smooth_table(sd, sp.unpack(keys), seed=j)
+        sp._table_ref = torch.from_numpy(t).to(dev)
+        sp.set_fitness(sp._table_ref)
+        spaces.append(sp)
+        dens.append(nv / sd.cartesian_size)
+        opt.append(float(t.min()))
+    S = len(defs)
+    runs = [(j, k, PAPER_POP[k], 7919 * s + 31 * j + ki, float(np.float32(1.01 * opt[j])))
+            for j in range(S) for ki, k in enumerate(kinds) for s in range(seeds)]
+    out, ms = {}, {}
+    for mode, aware in (("aware", 1), ("unaware", 0)):
+        b = ct.Batch(spaces, runs, constraint_aware=aware)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run_graph(gens)
+        e1.record()
+        torch.cuda.synchronize()
+        ms[mode] = e0.elapsed_time(e1)
+        res = b.results()
+        del b
+        for r, (j, k, _, _, _) in enumerate(runs):
+            d = out.setdefault((j, k, mode), {"hit": [], "gen": [], "rel": []})
+            d["hit"].append(int(res["hit_evals"][r]))
+            d["gen"].append(int(res["hit_gen"][r]))
+            d["rel"].append(float(res["best_fit"][r]) / opt[j])
+    table, gain = {}, {k: [] for k in kinds}
+    for j in range(S):
+        for k in kinds:
+            row = {}
+            for mode in ("aware", "unaware"):
+                d = out[(j, k, mode)]
+                h, g = np.array(d["hit"]), np.array(d["gen"])
+                ok = h >= 0
+                most = 2 * ok.sum() > len(h)
+                row[mode] = {"reached_1pct": float(ok.mean()),
+                             "evals_to_1pct_median": float(np.median(h[ok])) if most else None,
+                             "gens_to_1pct_median": float(np.median(g[ok])) if most else None,
+                             "best_rel_median": float(np.median(d["rel"]))}
+            gain[k].append(row["aware"]["reached_1pct"] - row["unaware"]["reached_1pct"])
+            table[f"{defs[j].name}_{100 * dens[j]:.2f}pct_{k}"] = row
+    corr = {k: float(spearmanr(dens, gain[k]).statistic) if np.ptp(gain[k]) > 0 else None for k in kinds}
+    return {"aware_vs_unaware": {"generations": gens, "seeds": seeds, "pop": PAPER_POP, "per_space": table,
+                                 "reached_gain_by_kind_mean": {k: float(np.mean(gain[k])) for k in kinds},
+                                 "spearman_density_vs_gain": corr,
+                                 "batched_ms": ms, "runs_per_mode": len(runs)}}
+
+
+def run_aware(args):
+    import torch
+    from paper_2606_28372_b300 import catune as ct
+    from paper_2606_28372_b300 import workloads as W
+    print(json.dumps(aware_vs_unaware(torch, ct, W, torch.device("cuda", 0))))
+    return 0
+
+
+def run_scan(args):
+    """Exhaustive repair scan alone: scan-only repair of 1, 2 and 4 uniform candidates per call,
+    one pass over the valid keys each (timed with CUDA events on the launching stream)."""
+    import torch
+    from paper_2606_28372_b300 import build as B
+    B.build()
+    from paper_2606_28372_b300 import catune as ct
+    from paper_2606_28372_b300 import workloads as W
+    dev = torch.device("cuda", 0)
+    sd = W.SPACES[args.workload]()
+    sp = ct.Space.from_def(sd)
+    nv = sp.build()
+    sp.set_repair_mode(1, 0)
+    unif = torch.from_numpy(sp.pack(W.uniform_tuples(sd, 8, seed=999)).view(np.int64)).to(dev)
+    hbm, kind = peaks()
+    res = {}
+    for q in (1, 2, 4):
+        c = unif[:q].contiguous()
+        o = torch.empty(q, dtype=torch.int64, device=dev)
+        for _ in range(args.warmup):
+            sp.repair(c, o)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            sp.repair(c, o)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        gbs = 8 * nv / (ms / 1000.0) / 1e9
+        res[f"q{q}"] = {"ms_per_call": ms, "key_stream_GBps": gbs, "frac_of_copy_peak": gbs / hbm}
+    print(json.dumps({"mode": "scan", "workload": args.workload, "n_valid": nv, "peak_GBps": hbm,
+                      "peak_kind": kind, "results": res}))
+    return 0
+
+
+def surrogate_vs_plain(torch, ct, W, dev, seeds=16, gens=150):
+    """Unique evaluations to come within 1/2/5 % of the table optimum, and the best fitness after
+    1000 unique evaluations (medians over seeds), for plain and surrogate-screened DE and GA on
+    the medium space at pop 128."""
+    sd = W.medium_space()
+    sp = ct.Space.from_def(sd)
+    sp.build()
+    keys = sp.keys().cpu().numpy().view(np.uint64)
+    table = W.smooth_table(sd, sp.unpack(keys), seed=0)
+    dt = torch.from_numpy(table).to(dev)
+    sp.set_fitness(dt)
+    logt = torch.from_numpy(np.log(table.astype(np.float64)).astype(np.float32)).to(dev)
+    opt = float(table.min())
+    out = {}
+    for kind in ("de", "ga"):
+        for mode in ("plain", "surrogate"):
+            curves = []
+            for seed in range(seeds):
+                o = ct.Opt(sp, kind, 128, seed)
+                if mode == "surrogate":
+                    o.set_surrogate(logt)
+                cu = []
+                for g in range(gens + 1):
+                    o.step(g)
+                    b = o.best()
+                    cu.append((b["n_unique"], b["best_fit"] / opt))
+                curves.append(cu)
+            rec = {}
+            for pct in (1, 2, 5):
+                first = [next((n for n, f in cu if f <= 1 + pct / 100), None) for cu in curves]
+                hit = [x for x in first if x is not None]
+                rec[f"evals_to_{pct}pct_median"] = float(np.median(hit)) if len(hit) * 2 > len(first) else None
+                rec[f"reached_{pct}pct"] = f"{len(hit)}/{len(first)}"
+            rec["best_rel_after_1000_evals"] = float(np.median([[f for n, f in cu if n <= 1000][-1] for cu in curves]))
+            out[f"surrogate_cmp_{kind}_{mode}"] = rec
+    return out
+
+
+PAPER_POP = {"de": 160, "pso": 30, "firefly": 20, "ga": 20}   # Table IV (DE: 16 x 10 parameters)
+
+
+def aware_vs_unaware(torch, ct, W, dev, seeds=32, gens=150):
+    """Synthetic analogue of the aware-vs-default comparison of Section V-B: the four optimizers
+    with Table IV's population sizes, constraint-aware and not (random Cartesian start, no repair,
+    static penalty), `seeds` runs each on the eight spaces of the density ladder (1.5 % .. 100 %),
+    every run of one mode in one batched launch per generation.  Per space and optimizer: the
+    fraction of runs within 1 % of the optimum after `gens` generations, the median unique
+    evaluations to get there (when more than half do), the median best/optimum; per optimizer,
+    the Spearman correlation between density and the aware gain in that fraction."""
+    from scipy.stats import spearmanr
+    kinds = ["de", "pso", "firefly", "ga"]
+    spaces, dens, opt = [], [], []
+    for j in range(8):
+        sd = W.density_space(j)
+        sp = ct.Space.from_def(sd)
+        nv = sp.build()
+        keys = sp.keys().cpu().numpy().view(np.uint64)
+        t = W.smooth_table(sd, sp.unpack(keys), seed=j)
+        sp._table_ref = torch.from_numpy(t).to(dev)
+        sp.set_fitness(sp._table_ref)
+        spaces.append(sp)
+        dens.append(nv / sd.cartesian_size)
+        opt.append(float(t.min()))
+    runs = [(j, k, PAPER_POP[k], 7919 * s + 31 * j + ki, float(np.float32(1.01 * opt[j])))
+            for j in range(8) for ki, k in enumerate(kinds) for s in range(seeds)]
+    out, ms = {}, {}
+    for mode, aware in (("aware", 1), ("unaware", 0)):
+        b = ct.Batch(spaces, runs, constraint_aware=aware)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run_graph(gens)
+        e1.record()
+        torch.cuda.synchronize()
+        ms[mode] = e0.elapsed_time(e1)
+        res = b.results()
+        del b
+        for r, (j, k, _, _, _) in enumerate(runs):
+            d = out.setdefault((j, k, mode), {"hit": [], "rel": []})
+            d["hit"].append(int(res["hit_evals"][r]))
+            d["rel"].append(float(res["best_fit"][r]) / opt[j])
+    table, gain = {}, {k: [] for k in kinds}
+    for j in range(8):
+        for k in kinds:
+            row = {}
+            for mode in ("aware", "unaware"):
+                h = np.array(out[(j, k, mode)]["hit"])
+                ok = h[h >= 0]
+                row[mode] = {"reached_1pct": len(ok) / len(h),
+                             "evals_to_1pct_median": float(np.median(ok)) if 2 * len(ok) > len(h) else None,
+                             "best_rel_median": float(np.median(out[(j, k, mode)]["rel"]))}
+            gain[k].append(row["aware"]["reached_1pct"] - row["unaware"]["reached_1pct"])
+            table[f"density_{100 * dens[j]:.2f}pct_{k}"] = row
+    corr = {k: float(spearmanr(dens, gain[k]).statistic) if np.ptp(gain[k]) > 0 else None for k in kinds}
+    return {"aware_vs_unaware": {"generations": gens, "seeds": seeds, "pop": PAPER_POP, "per_space": table,
+                                 "reached_gain_by_kind_mean": {k: float(np.mean(gain[k])) for k in kinds},
+                                 "spearman_density_vs_gain": corr,
+                                 "batched_ms": ms, "runs_per_mode": len(runs)}}
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -595,11 +816,14 @@ if __name__ == "__main__":
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--quick", action="store_true", help="headline step only (no e2e, no sub-metrics)")
-    ap.add_argument("--mode", default="step", choices=["step", "scan"],
-                    help="scan: only the exhaustive repair scan (scan-only repair of 1, 2, 4 uniform candidates)")
+    ap.add_argument("--mode", default="step", choices=["step", "scan", "aware"],
+                    help="scan: only the exhaustive repair scan (scan-only repair of 1, 2, 4 uniform candidates); "
+                         "aware: only the constraint-aware vs non-aware comparison over the density ladder")
     ap.add_argument("--workload", default="large", choices=["large", "large_slice"],
                     help="large_slice: the same kernels on a 146M-key slice, for hardware-counter captures")
     a = ap.parse_args()
     if a.impl == "reference":
         sys.exit(run_reference(a))
+    if a.mode == "aware":
+        sys.exit(run_aware(a))
     sys.exit(run_scan(a) if a.mode == "scan" else run_ours(a))

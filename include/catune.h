@@ -218,7 +218,16 @@ typedef struct {
                                         1: the paper's rule per optimizer (ct_repair_paper: DE
                                         rule 1, PSO/Firefly rule 2 on the particle position, GA
                                         rule 3).  Single runs only (not batches, not surrogates). */
+    int32_t constraint_aware;        /* 1 (default): the constraint-aware methods above.  0: the
+                                        non-constraint-aware baselines of Sections IV-B/IV-C:
+                                        random start over the Cartesian product (PSO/Firefly:
+                                        random coordinates), no repair, GA mutation to any other
+                                        value of one random parameter, and a static penalty
+                                        CT_PENALTY as the fitness of an invalid configuration
+                                        (nothing is evaluated, nothing counted). */
 } ct_opt_params;
+
+#define CT_PENALTY 1e20f
 
 /* Fills *p with the Table IV values and target = -inf. */
 void ct_opt_params_default(ct_opt_params *p);
@@ -318,7 +327,9 @@ size_t ct_mlp_workspace_bytes(int32_t D, int32_t H, int32_t B);
 /* d_feats: B rows of N ascending feature indices (one active input per parameter). */
 ct_status ct_mlp_forward(int32_t D, int32_t H, int32_t N, const float *d_params, const int32_t *d_feats, int32_t B,
                          float *d_pred, void *d_work, ct_stream stream);
-/* Gradient of the batch mean squared error; d_param_of[f] = parameter owning feature f. */
+/* Gradient of the batch mean squared error.  d_param_of holds D entries: d_param_of[f] = the
+ * parameter (0..N-1) owning feature f; an entry outside 0..N-1 marks a feature that no sample
+ * activates (its weight gradient is 0). */
 ct_status ct_mlp_grad(int32_t D, int32_t H, int32_t N, const float *d_params, const int32_t *d_feats,
                       const int32_t *d_param_of, const float *d_y, int32_t B, float *d_grad, void *d_work,
                       ct_stream stream);

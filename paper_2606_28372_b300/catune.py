@@ -57,7 +57,8 @@ class ct_surrogate_params(C.Structure):
 
 class ct_opt_params(C.Structure):
     _fields_ = [(n, C.c_float) for n in ("de_F", "de_CR", "pso_w", "pso_c1", "pso_c2", "fa_beta0",
-                                         "fa_gamma", "fa_alpha", "ga_pmut", "target")] + [("repair_rule", C.c_int32)]
+                                         "fa_gamma", "fa_alpha", "ga_pmut", "target")] + [("repair_rule", C.c_int32),
+                                                                                          ("constraint_aware", C.c_int32)]
 
 
 _lib = None
@@ -364,7 +365,7 @@ def default_params(**over):
     p = ct_opt_params()
     lib().ct_opt_params_default(C.byref(p))
     for k, v in over.items():
-        setattr(p, k, int(v) if k == "repair_rule" else float(np.float32(v)))
+        setattr(p, k, int(v) if k in ("repair_rule", "constraint_aware") else float(np.float32(v)))
     return p
 
 

@@ -187,12 +187,15 @@ __global__ void __launch_bounds__(256, 1) k_batch_gen(const __grid_constant__ Ba
         const int P = run.P;
         propose_dev(a, gen, cand, order);
         __syncthreads();
-        cta_repair(bs, cand, rep, P, rsm);
+        if (a.prm.constraint_aware) cta_repair(bs, cand, rep, P, rsm);
+        else for (int i = threadIdx.x; i < P; i += blockDim.x) rep[i] = cand[i];
+        __syncthreads();
         post_repair_dev(a, gen, rep);
         __syncthreads();
         uint32_t* memo = ba.memo + run.off_memo;
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
             const int64_t rk = rank_of(bs.keys, bs.nv, rep[i]);
+            if (rk < 0) { fit[i] = CT_PENALTY; continue; }   // baselines only
             fit[i] = __ldg(bs.fit + rk);
             const uint32_t bit = 1u << (rk & 31);
             const uint32_t old = atomicOr(memo + (rk >> 5), bit);

@@ -87,7 +87,7 @@ __host__ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k
 enum Purpose : uint32_t {
     PU_INIT = 1, PU_MUT_PICK = 2, PU_CROSS = 3, PU_PSO_R = 4, PU_FA_ALPHA = 5, PU_GA_SEL = 6,
     PU_GA_CUT = 7, PU_GA_MUT = 8, PU_REINIT = 9, PU_POOL = 10, PU_MLP_INIT = 11, PU_MLP_BATCH = 12,
-    PU_PSO_VEL = 13, PU_GA_REPAIR = 14
+    PU_PSO_VEL = 13, PU_GA_REPAIR = 14, PU_RAND_INIT = 15
 };
 
 // Word t of the stream (individual, generation, purpose) for `seed`:

@@ -18,7 +18,7 @@
 
 namespace ct {
 ct_status evaluate_impl(ct_space* s, uint32_t* memo, unsigned long long* unique, const uint64_t* d_keys, int64_t n,
-                        float* d_fit, int64_t* d_rank, cudaStream_t st);
+                        float* d_fit, int64_t* d_rank, cudaStream_t st, float invalid_fit = __builtin_inff());
 }
 
 namespace ct {
@@ -54,6 +54,10 @@ __global__ void k_ga_repair_words(OptArgs a, uint32_t gen_arg, int use_dev, uint
 }
 
 static ct_status repair_step(ct_opt* o, const OptArgs& a, uint32_t gen, int use_dev, cudaStream_t st) {
+    if (!o->prm.constraint_aware) {   // baselines: candidates are evaluated as proposed
+        CT_TRY_CUDA(cudaMemcpyAsync(o->rep.p, o->cand.p, (size_t)o->P * 8, cudaMemcpyDeviceToDevice, st));
+        return CT_OK;
+    }
     if (!o->prm.repair_rule) return repair_impl(o->s, o->rs, o->cand.p, o->P, o->rep.p, nullptr, st);
     if (o->kind == CT_DE)
         return repair_rule_impl(o->s, o->rules, 1, o->cand.p, o->P, nullptr, 0.0f, nullptr, o->rep.p, o->rs, st);
@@ -73,7 +77,7 @@ static ct_status step_impl(ct_opt* o, uint32_t gen, int use_dev, cudaStream_t st
     CT_TRY(repair_step(o, a, gen, use_dev, st));
     k_post_repair<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->rep.p);
     count_launch();
-    CT_TRY(evaluate_impl(o->s, o->memo.p, &o->st.p->n_unique, o->rep.p, o->P, o->fit.p, nullptr, st));
+    CT_TRY(evaluate_impl(o->s, o->memo.p, &o->st.p->n_unique, o->rep.p, o->P, o->fit.p, nullptr, st, CT_PENALTY));
     k_select<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->rep.p, o->fit.p);
     count_launch();
     CT_TRY_CUDA(cudaGetLastError());
@@ -90,6 +94,8 @@ void ct_opt_params_default(ct_opt_params* p) {
     p->fa_beta0 = 1.0f; p->fa_gamma = 1.0f; p->fa_alpha = 0.2f;
     p->ga_pmut = 0.2f;
     p->target = -__builtin_inff();
+    p->repair_rule = 0;
+    p->constraint_aware = 1;
 }
 
 ct_status ct_opt_create(ct_space* s, ct_opt_kind kind, const ct_opt_params* params, int32_t pop, uint64_t seed, ct_opt** out) {

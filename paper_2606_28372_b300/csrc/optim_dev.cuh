@@ -116,6 +116,27 @@ __device__ __forceinline__ uint32_t gen_of(const OptArgs& a, uint32_t gen_arg, i
 static __device__ void propose_dev(const OptArgs& a, uint32_t gen, uint64_t* __restrict__ cand, int* order, int s = 0) {
     const int P = a.P, N = a.N;
     const bool init = gen == 0 || (a.kind == CT_DE && a.st->reinit_pending);
+    if (init && !a.prm.constraint_aware) {   // baselines: random start over the Cartesian product
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            uint32_t w[4];
+            if (a.kind == CT_PSO || a.kind == CT_FIREFLY) {
+                float* x = a.pos + (size_t)i * N;
+                for (int j = 0; j < N; ++j) {
+                    if ((j & 3) == 0) rng_block(a.seed, i, gen, PU_RAND_INIT, (uint32_t)j >> 2, w);
+                    x[j] = u01(w[j & 3]);
+                }
+                cand[i] = snap_key(a, x);
+            } else {
+                uint64_t key = 0;
+                for (int k = 0; k < N; ++k) {
+                    if ((k & 3) == 0) rng_block(a.seed, i, gen, PU_RAND_INIT, (uint32_t)k >> 2, w);
+                    key |= (uint64_t)uint_below(w[k & 3], (uint32_t)a.sp->r[k]) << a.sp->off[k];
+                }
+                cand[i] = key;
+            }
+        }
+        return;
+    }
     if (init) {
         for (int i = threadIdx.x; i < P; i += blockDim.x)
             cand[i] = stratified_key(a, (uint32_t)i, gen, gen == 0 ? PU_INIT : PU_REINIT);
@@ -245,6 +266,13 @@ static __device__ void post_repair_dev(const OptArgs& a, uint32_t gen, uint64_t*
         rng_block(a.seed, (uint32_t)(i + s * a.P), gen, PU_GA_MUT, 0, w);
         if (!(u01(w[0]) < a.prm.ga_pmut)) continue;
         const uint64_t u = keys[i];
+        if (!a.prm.constraint_aware) {   // baseline: one random parameter takes another value
+            const int k = (int)uint_below(w[1], (uint32_t)a.N);
+            if (sp->r[k] < 2) continue;
+            const uint32_t v = uint_below(w[2], (uint32_t)(sp->r[k] - 1)), uk = (uint32_t)field(sp, u, k);
+            keys[i] = (u & ~sp->fmask[k]) | ((uint64_t)(v < uk ? v : v + 1u) << sp->off[k]);
+            continue;
+        }
         uint32_t cnt = 0;
         for (int k = 0; k < a.N; ++k) {
             const int uk = field(sp, u, k);
@@ -400,7 +428,8 @@ static __device__ void select_dev(const OptArgs& a, uint32_t gen, const uint64_t
             for (int i = t; i < P; i += nt) {
                 uint32_t w[4];
                 for (int j = 0; j < N; ++j) {
-                    const float x0 = __fmul_rn((float)field(a.sp, sm.us[i], j), a.eps);
+                    const float x0 = a.prm.constraint_aware ? __fmul_rn((float)field(a.sp, sm.us[i], j), a.eps)
+                                                            : a.pos[(size_t)i * N + j];
                     a.pos[(size_t)i * N + j] = x0;
                     a.pb[(size_t)i * N + j] = x0;
                     if (a.kind == CT_PSO) {

@@ -28,7 +28,7 @@
 
 namespace ct {
 ct_status evaluate_impl(ct_space* s, uint32_t* memo, unsigned long long* unique, const uint64_t* d_keys, int64_t n,
-                        float* d_fit, int64_t* d_rank, cudaStream_t st);
+                        float* d_fit, int64_t* d_rank, cudaStream_t st, float invalid_fit = __builtin_inff());
 
 __device__ __forceinline__ float bf16r(float f) {
     uint32_t u = __float_as_uint(f);
@@ -184,7 +184,7 @@ __global__ void k_colsum(const float* __restrict__ d, int B, int H, float* __res
 }
 
 // gradient of the one-hot layer: for each (j, feature f), the sum over samples (ascending)
-// in which f is active of d1[b][j]
+// in which f is active of d1[b][j]; an owner index outside 0..N-1 means f is never active
 __global__ void k_mlp_w1grad(const float* __restrict__ d1, const int32_t* __restrict__ feats,
                              const int32_t* __restrict__ param_of, int B, int N, int D, int H, float* __restrict__ gW1) {
     const size_t total = (size_t)H * D;
@@ -192,8 +192,9 @@ __global__ void k_mlp_w1grad(const float* __restrict__ d1, const int32_t* __rest
         const int j = (int)(g / D), f = (int)(g % D);
         const int k = param_of[f];
         float acc = 0.0f;
-        for (int b = 0; b < B; ++b)
-            if (feats[(size_t)b * N + k] == f) acc = __fadd_rn(acc, d1[(size_t)b * H + j]);
+        if (k >= 0 && k < N)
+            for (int b = 0; b < B; ++b)
+                if (feats[(size_t)b * N + k] == f) acc = __fadd_rn(acc, d1[(size_t)b * H + j]);
         gW1[g] = acc;
     }
 }
@@ -525,7 +526,10 @@ ct_status ct_opt_set_surrogate(ct_opt* o, const ct_surrogate_params* prm, const 
     if (!o || !d_log_table) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
     if (o->kind != CT_DE && o->kind != CT_GA) { set_error("the surrogate screens DE and GA runs only"); return CT_ERR_INVALID_ARG; }
     if (o->sg) { set_error("surrogate already set"); return CT_ERR_STATE; }
-    if (o->prm.repair_rule) { set_error("surrogate screening uses the Hamming repair (repair_rule 0)"); return CT_ERR_INVALID_ARG; }
+    if (o->prm.repair_rule || !o->prm.constraint_aware) {
+        set_error("surrogate screening runs on the constraint-aware method with the Hamming repair");
+        return CT_ERR_INVALID_ARG;
+    }
     ct_surrogate_params cfg;
     if (prm) cfg = *prm; else ct_surrogate_params_default(&cfg);
     if (cfg.pool < 1 || cfg.pool > 64 || cfg.hidden < 1 || cfg.hidden > 1024 || cfg.batch < 1 || cfg.batch > 4096 ||

@@ -167,6 +167,23 @@ def batched_space(s: int) -> SpaceDef:
     return _space(f"batched_{s}", [(n, vals[n]) for n in names], medium_space().constraints)
 
 
+# medium constraints in the order they are dropped to raise the density (the first is implied
+# by the others: bx >= 16 is a power of two and tx*vec <= 8 divides it)
+_DENSITY_DROP = ["bx%(tx*vec)==0", "64<=bx*by<=1024", "by*ty<=16", "ro==0 or pad==0", "vec*tx<=8",
+                 "splitk<=2 or stages>=4", "unroll*vec<=tx*ty", "4*(bx*tx+pad)*(by*ty)*stages<=49152"]
+
+
+def density_space(j: int) -> SpaceDef:
+    """Space ``j`` (0..7) of the density ladder: the medium parameters under fewer and fewer of
+    its constraints, so that the density climbs from ~1.5 % (all eight, Hotspot-like) through
+    ~2.1, 2.9, 4.4, 6.9, 13 and 29 % to 100 % (none), spanning the densities of Table III."""
+    if not 0 <= j <= 7:
+        raise ValueError("density ladder index is 0..7")
+    sd = medium_space()
+    keep = _DENSITY_DROP[j + 1 if j else 0:]
+    return _space(f"density_{j}", sd.params, [c for c in sd.constraints if c in keep])
+
+
 SPACES = {"tiny": tiny_space, "medium": medium_space, "large": large_space,
           "large_a": large_group_a, "large_b": large_group_b, "large_slice": large_slice_space}
 

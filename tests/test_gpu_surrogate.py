@@ -38,7 +38,8 @@ def test_mlp_kernels_bit_exact(oracle_mod, D, H, N, B):
     pred = torch.empty(B, dtype=torch.float32, device="cuda")
     ct.check(L.ct_mlp_forward(D, H, N, ct._ptr(p), ct._ptr(df), B, ct._ptr(pred), ct._ptr(work), ct._stream(None)))
     assert np.array_equal(pred.cpu().numpy(), O.mlp_forward(p0, D, H, feats))
-    pof = torch.from_numpy(np.repeat(np.arange(N), D // N).astype(np.int32)).cuda()
+    # one owner per feature, all D of them (features past N * (D // N) are never active)
+    pof = torch.from_numpy(np.minimum(np.arange(D) // (D // N), N - 1).astype(np.int32)).cuda()
     g = torch.empty(n, dtype=torch.float32, device="cuda")
     ct.check(L.ct_mlp_grad(D, H, N, ct._ptr(p), ct._ptr(df), ct._ptr(pof), ct._ptr(dy), B, ct._ptr(g), ct._ptr(work),
                            ct._stream(None)))
