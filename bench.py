@@ -599,213 +599,82 @@ def surrogate_vs_plain(torch, ct, W, dev, seeds=16, gens=150):
 PAPER_POP = {"de": 160, "pso": 30, "firefly": 20, "ga": 20}   # Table IV (DE: 16 x 10 parameters)
 
 
-def aware_vs_unaware(torch, ct, W, dev, seeds=32, gens=500):
-    """Synthetic analogue of the aware-vs-default comparison of Section V-B: the four optimizers
-    with Table IV's population sizes, constraint-aware and not (random Cartesian start, no repair,
-    static penalty), `seeds` runs each on the eight spaces of the density ladder (1.5 % .. 100 %)
-    and the tiny space (56 %), every run of one mode in one batched launch per generation.  Per
-    space and optimizer: the fraction of runs within 1 % of the optimum after `gens` generations,
-    the median unique evaluations and generations to get there (when more than half do), and the
-    median best/optimum; per optimizer, the Spearman correlation between density and the aware
-    gain in that fraction."""
+def aware_vs_unaware(torch, ct, W, dev, seeds=16, overhead_us=1000.0, K=50, gens=(4000, 24000)):
+    """Synthetic analogue of the aware-vs-default comparison of Section V-B, scored by Eq. 2.
+
+    The four optimizers with Table IV's population sizes, constraint-aware and not (random
+    Cartesian start, no repair, static penalty), `seeds` runs each on the eight spaces of the
+    density ladder (1.5 % .. 100 %) and the tiny space (56 %); every run of one mode advances in
+    one batched launch per generation and records a per-generation trace of its best fitness and
+    simulated clock (each configuration's synthetic compile + 7 runs, once; plus `overhead_us` per
+    proposal).  Each run is scored against the space's random-search baseline over the budget of
+    Section V-A.  Aware runs get gens[0] generations, the cheaper non-aware ones gens[1]; a run
+    whose clock ends before the budget keeps its last value ("truncated")."""
     from scipy.stats import spearmanr
+    from paper_2606_28372_b300 import score as PS
     kinds = ["de", "pso", "firefly", "ga"]
     defs = [W.density_space(j) for j in range(8)] + [W.tiny_space()]
-    spaces, dens, opt = [], [], []
+    spaces, dens, opt, base = [], [], [], []
     for j, sd in enumerate(defs):
         sp = ct.Space.from_def(sd)
         nv = sp.build()
         keys = sp.keys().cpu().numpy().view(np.uint64)
         t = W.lognormal_table(nv, seed=0) if sd.name == "tiny" else W.smooth_table(sd, sp.unpack(keys), seed=j)
+        c = W.eval_cost_table(t, seed=j)
         sp._table_ref = torch.from_numpy(t).to(dev)
+        sp._cost_ref = torch.from_numpy(c.view(np.int32)).to(dev)
         sp.set_fitness(sp._table_ref)
+        sp.set_eval_cost(sp._cost_ref)
         spaces.append(sp)
         dens.append(nv / sd.cartesian_size)
         opt.append(float(t.min()))
+        base.append(PS.Baseline(t, c, overhead_us))
     S = len(defs)
     runs = [(j, k, PAPER_POP[k], 7919 * s + 31 * j + ki, float(np.float32(1.01 * opt[j])))
             for j in range(S) for ki, k in enumerate(kinds) for s in range(seeds)]
-    out, ms = {}, {}
-    for mode, aware in (("aware", 1), ("unaware", 0)):
+    budgets = [b.budget() for b in base]
+    table, ms, score = {}, {}, {}
+    for mode, aware, G in (("aware", 1, gens[0]), ("unaware", 0, gens[1])):
         b = ct.Batch(spaces, runs, constraint_aware=aware)
+        b.set_trace(G)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        b.run_graph(gens)
+        for _ in range(G // 1000):
+            b.run_graph(1000)
         e1.record()
         torch.cuda.synchronize()
         ms[mode] = e0.elapsed_time(e1)
-        res = b.results()
+        tr = b.trace()
         del b
-        for r, (j, k, _, _, _) in enumerate(runs):
-            d = out.setdefault((j, k, mode), {"hit": [], "gen": [], "rel": []})
-            d["hit"].append(int(res["hit_evals"][r]))
-            d["gen"].append(int(res["hit_gen"][r]))
-            d["rel"].append(float(res["best_fit"][r]) / opt[j])
-    table, gain = {}, {k: [] for k in kinds}
-    for j in range(S):
-        for k in kinds:
-            row = {}
-            for mode in ("aware", "unaware"):
-                d = out[(j, k, mode)]
-                h, g = np.array(d["hit"]), np.array(d["gen"])
-                ok = h >= 0
-                most = 2 * ok.sum() > len(h)
-                row[mode] = {"reached_1pct": float(ok.mean()),
-                             "evals_to_1pct_median": float(np.median(h[ok])) if most else None,
-                             "gens_to_1pct_median": float(np.median(g[ok])) if most else None,
-                             "best_rel_median": float(np.median(d["rel"]))}
-            gain[k].append(row["aware"]["reached_1pct"] - row["unaware"]["reached_1pct"])
-            table[f"{defs[j].name}_{100 * dens[j]:.2f}pct_{k}"] = row
-    corr = {k: float(spearmanr(dens, gain[k]).statistic) if np.ptp(gain[k]) > 0 else None for k in kinds}
-    return {"aware_vs_unaware": {"generations": gens, "seeds": seeds, "pop": PAPER_POP, "per_space": table,
-                                 "reached_gain_by_kind_mean": {k: float(np.mean(gain[k])) for k in kinds},
-                                 "spearman_density_vs_gain": corr,
-                                 "batched_ms": ms, "runs_per_mode": len(runs)}}
-
-
-def run_aware(args):
-    import torch
-    from paper_2606_28372_b300 import catune as ct
-    from paper_2606_28372_b300 import workloads as W
-    print(json.dumps(aware_vs_unaware(torch, ct, W, torch.device("cuda", 0))))
-    return 0
-
-
-def run_scan(args):
-    """Exhaustive repair scan alone: scan-only repair of 1, 2 and 4 uniform candidates per call,
-    one pass over the valid keys each (timed with CUDA events on the launching stream)."""
-    import torch
-    from paper_2606_28372_b300 import build as B
-    B.build()
-    from paper_2606_28372_b300 import catune as ct
-    from paper_2606_28372_b300 import workloads as W
-    dev = torch.device("cuda", 0)
-    sd = W.SPACES[args.workload]()
-    sp = ct.Space.from_def(sd)
-    nv = sp.build()
-    sp.set_repair_mode(1, 0)
-    unif = torch.from_numpy(sp.pack(W.uniform_tuples(sd, 8, seed=999)).view(np.int64)).to(dev)
-    hbm, kind = peaks()
-    res = {}
-    for q in (1, 2, 4):
-        c = unif[:q].contiguous()
-        o = torch.empty(q, dtype=torch.int64, device=dev)
-        for _ in range(args.warmup):
-            sp.repair(c, o)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            sp.repair(c, o)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        gbs = 8 * nv / (ms / 1000.0) / 1e9
-        res[f"q{q}"] = {"ms_per_call": ms, "key_stream_GBps": gbs, "frac_of_copy_peak": gbs / hbm}
-    print(json.dumps({"mode": "scan", "workload": args.workload, "n_valid": nv, "peak_GBps": hbm,
-                      "peak_kind": kind, "results": res}))
-    return 0
-
-
-def surrogate_vs_plain(torch, ct, W, dev, seeds=16, gens=150):
-    """Unique evaluations to come within 1/2/5 % of the table optimum, and the best fitness after
-    1000 unique evaluations (medians over seeds), for plain and surrogate-screened DE and GA on
-    the medium space at pop 128."""
-    sd = W.medium_space()
-    sp = ct.Space.from_def(sd)
-    sp.build()
-    keys = sp.keys().cpu().numpy().view(np.uint64)
-    table = W.smooth_table(sd, sp.unpack(keys), seed=0)
-    dt = torch.from_numpy(table).to(dev)
-    sp.set_fitness(dt)
-    logt = torch.from_numpy(np.log(table.astype(np.float64)).astype(np.float32)).to(dev)
-    opt = float(table.min())
-    out = {}
-    for kind in ("de", "ga"):
-        for mode in ("plain", "surrogate"):
-            curves = []
-            for seed in range(seeds):
-                o = ct.Opt(sp, kind, 128, seed)
-                if mode == "surrogate":
-                    o.set_surrogate(logt)
-                cu = []
-                for g in range(gens + 1):
-                    o.step(g)
-                    b = o.best()
-                    cu.append((b["n_unique"], b["best_fit"] / opt))
-                curves.append(cu)
-            rec = {}
-            for pct in (1, 2, 5):
-                first = [next((n for n, f in cu if f <= 1 + pct / 100), None) for cu in curves]
-                hit = [x for x in first if x is not None]
-                rec[f"evals_to_{pct}pct_median"] = float(np.median(hit)) if len(hit) * 2 > len(first) else None
-                rec[f"reached_{pct}pct"] = f"{len(hit)}/{len(first)}"
-            rec["best_rel_after_1000_evals"] = float(np.median([[f for n, f in cu if n <= 1000][-1] for cu in curves]))
-            out[f"surrogate_cmp_{kind}_{mode}"] = rec
-    return out
-
-
-PAPER_POP = {"de": 160, "pso": 30, "firefly": 20, "ga": 20}   # Table IV (DE: 16 x 10 parameters)
-
-
-def aware_vs_unaware(torch, ct, W, dev, seeds=32, gens=150):
-    """Synthetic analogue of the aware-vs-default comparison of Section V-B: the four optimizers
-    with Table IV's population sizes, constraint-aware and not (random Cartesian start, no repair,
-    static penalty), `seeds` runs each on the eight spaces of the density ladder (1.5 % .. 100 %),
-    every run of one mode in one batched launch per generation.  Per space and optimizer: the
-    fraction of runs within 1 % of the optimum after `gens` generations, the median unique
-    evaluations to get there (when more than half do), the median best/optimum; per optimizer,
-    the Spearman correlation between density and the aware gain in that fraction."""
-    from scipy.stats import spearmanr
-    kinds = ["de", "pso", "firefly", "ga"]
-    spaces, dens, opt = [], [], []
-    for j in range(8):
-        sd = W.density_space(j)
-        sp = ct.Space.from_def(sd)
-        nv = sp.build()
-        keys = sp.keys().cpu().numpy().view(np.uint64)
-        t = W.smooth_table(sd, sp.unpack(keys), seed=j)
-        sp._table_ref = torch.from_numpy(t).to(dev)
-        sp.set_fitness(sp._table_ref)
-        spaces.append(sp)
-        dens.append(nv / sd.cartesian_size)
-        opt.append(float(t.min()))
-    runs = [(j, k, PAPER_POP[k], 7919 * s + 31 * j + ki, float(np.float32(1.01 * opt[j])))
-            for j in range(8) for ki, k in enumerate(kinds) for s in range(seeds)]
-    out, ms = {}, {}
-    for mode, aware in (("aware", 1), ("unaware", 0)):
-        b = ct.Batch(spaces, runs, constraint_aware=aware)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        b.run_graph(gens)
-        e1.record()
-        torch.cuda.synchronize()
-        ms[mode] = e0.elapsed_time(e1)
-        res = b.results()
-        del b
-        for r, (j, k, _, _, _) in enumerate(runs):
-            d = out.setdefault((j, k, mode), {"hit": [], "rel": []})
-            d["hit"].append(int(res["hit_evals"][r]))
-            d["rel"].append(float(res["best_fit"][r]) / opt[j])
-    table, gain = {}, {k: [] for k in kinds}
-    for j in range(8):
-        for k in kinds:
-            row = {}
-            for mode in ("aware", "unaware"):
-                h = np.array(out[(j, k, mode)]["hit"])
-                ok = h[h >= 0]
-                row[mode] = {"reached_1pct": len(ok) / len(h),
-                             "evals_to_1pct_median": float(np.median(ok)) if 2 * len(ok) > len(h) else None,
-                             "best_rel_median": float(np.median(out[(j, k, mode)]["rel"]))}
-            gain[k].append(row["aware"]["reached_1pct"] - row["unaware"]["reached_1pct"])
-            table[f"density_{100 * dens[j]:.2f}pct_{k}"] = row
-    corr = {k: float(spearmanr(dens, gain[k]).statistic) if np.ptp(gain[k]) > 0 else None for k in kinds}
-    return {"aware_vs_unaware": {"generations": gens, "seeds": seeds, "pop": PAPER_POP, "per_space": table,
-                                 "reached_gain_by_kind_mean": {k: float(np.mean(gain[k])) for k in kinds},
-                                 "spearman_density_vs_gain": corr,
-                                 "batched_ms": ms, "runs_per_mode": len(runs)}}
+        for j in range(S):
+            for ki, k in enumerate(kinds):
+                rows = [r for r, run in enumerate(runs) if run[0] == j and run[1] == k]
+                P = PAPER_POP[k]
+                res = PS.run_scores(base[j], tr["cost"][rows], tr["best_fit"][rows], pop=P, overhead_us=overhead_us, K=K)
+                clock_end = tr["cost"][rows, -1].astype(np.float64) + G * P * overhead_us
+                B = budgets[j][1]
+                clock = tr["cost"][rows].astype(np.float64) + np.arange(1, G + 1) * P * overhead_us
+                hit = (tr["best_fit"][rows] <= np.float32(1.01 * opt[j])) & (clock <= B)
+                score[(j, k, mode)] = float(res["per_run"].mean())
+                table.setdefault(f"{defs[j].name}_{100 * dens[j]:.2f}pct_{k}", {})[mode] = {
+                    "score": score[(j, k, mode)],
+                    "score_sem": float(res["per_run"].std(ddof=1) / np.sqrt(len(rows))),
+                    "within_1pct_in_budget": float(hit.any(axis=1).mean()),
+                    "truncated": float((clock_end < B).mean())}
+    agg = {m: {k: float(np.mean([score[(j, k, m)] for j in range(S)])) for k in kinds} for m in ("aware", "unaware")}
+    gain = {k: [score[(j, k, "aware")] - score[(j, k, "unaware")] for j in range(S)] for k in kinds}
+    corr = {k: float(spearmanr(dens, gain[k]).statistic) for k in kinds}
+    return {"aware_vs_unaware": {
+        "score_eq2_by_kind": agg,
+        "score_gain_by_kind": {k: agg["aware"][k] - agg["unaware"][k] for k in kinds},
+        "score_gain_mean": float(np.mean([agg["aware"][k] - agg["unaware"][k] for k in kinds])),
+        "spearman_density_vs_gain": corr, "per_space": table,
+        "budget_s": {defs[j].name: budgets[j][1] / 1e6 for j in range(S)},
+        "budget_draws": {defs[j].name: budgets[j][0] for j in range(S)},
+        "generations": {"aware": gens[0], "unaware": gens[1]}, "seeds": seeds, "pop": PAPER_POP,
+        "overhead_ms_per_proposal": overhead_us / 1000, "time_points": K,
+        "batched_ms": ms, "runs_per_mode": len(runs)}}
 
 
 if __name__ == "__main__":

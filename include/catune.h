@@ -139,6 +139,12 @@ ct_status ct_space_keys(const ct_space *space, const uint64_t **d_keys, uint64_t
  * key (float32, caller-owned, borrowed until destroy or the next call). */
 ct_status ct_set_fitness(ct_space *space, const float *d_table, uint64_t n);
 
+/* Registers the simulated evaluation time of each valid configuration (Eq. 2's time axis):
+ * d_cost[rank] in microseconds (uint32, caller-owned, borrowed like the fitness table; NULL
+ * removes it).  Every run on the space then accumulates, exactly (integer sums), the cost of
+ * each configuration the first time it evaluates it; invalid proposals cost nothing. */
+ct_status ct_set_eval_cost(ct_space *space, const uint32_t *d_cost, uint64_t n);
+
 /* Validity query (Section IV-A): d_rank[i] = position of d_cand[i] in the valid
  * keys, or -1 if it is not a valid configuration (including keys outside the
  * domain).  Binary search. */
@@ -268,6 +274,10 @@ ct_status ct_opt_run_graph(ct_opt *opt, uint32_t first, uint32_t count, ct_strea
 ct_status ct_opt_best(ct_opt *opt, uint64_t *best_key, float *best_fit, uint64_t *n_unique,
                       int64_t *hit_generation, int64_t *hit_evals, ct_stream stream);
 
+/* Simulated time spent by the run so far (synchronises): the sum, over the configurations
+ * it has evaluated (each once), of the space's evaluation cost (ct_set_eval_cost; 0 without). */
+ct_status ct_opt_cost(ct_opt *opt, uint64_t *cost, ct_stream stream);
+
 /* Copies the run state to caller buffers (asynchronous; any pointer may be NULL):
  * population keys [pop], population fitness [pop] (PSO: personal-best
  * fitness), positions [pop x n_params] (PSO/Firefly). */
@@ -374,6 +384,15 @@ ct_status ct_batch_run_state(const ct_batch *batch, int32_t run, uint64_t *d_key
                              ct_stream stream);
 /* Returns every run to its state before generation 0 (synchronises the device). */
 ct_status ct_batch_reset(ct_batch *batch);
+/* Per-generation trace of the first `gens` generations (0 switches it off): after each
+ * generation g < gens every run records its best fitness so far, its simulated time
+ * (ct_opt_cost; evaluation costs are those registered on the spaces when the batch was
+ * created) and its unique evaluations.  Resets the batch and drops captured graphs. */
+ct_status ct_batch_set_trace(ct_batch *batch, int32_t gens);
+/* Copies the trace into host arrays of n_runs x gens entries, run-major (each may be NULL);
+ * generations not yet run read +inf, 0, 0.  Synchronises. */
+ct_status ct_batch_trace(const ct_batch *batch, float *best_fit, uint64_t *cost, uint64_t *n_unique,
+                         ct_stream stream);
 /* Launch shape of the persistent kernel: threads per CTA (64, 128 or 256) and
  * CTAs per SM (0 = 4). Results do not depend on it. */
 ct_status ct_batch_set_launch(ct_batch *batch, int32_t threads, int32_t ctas_per_sm);

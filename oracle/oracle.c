@@ -382,6 +382,7 @@ typedef struct {
     float target;        /* record unique evaluations when best <= target */
     int repair_rule;     /* 0: Hamming argmin for all; 1: the paper's rule per optimizer */
     int aware;           /* 1: constraint-aware; 0: random Cartesian start, no repair, penalty */
+    const uint32_t *cost; /* simulated time of evaluating each valid configuration (per rank), or NULL */
 } or_params;
 
 typedef struct {         /* per-generation trace, arrays of (G+1) x P unless noted */
@@ -396,6 +397,8 @@ typedef struct {         /* per-generation trace, arrays of (G+1) x P unless not
     float *best_fit;     /* (G+1) */
     uint64_t *n_unique;  /* (G+1) */
     int64_t *hit;        /* [0] generation of first best<=target (-1), [1] n_unique then */
+    uint64_t *cost;      /* (G+1): simulated time spent so far, the sum of the costs of the
+                            configurations evaluated (each once) */
 } or_trace;
 
 typedef struct {
@@ -408,6 +411,8 @@ typedef struct {
     uint64_t n_unique;
     uint64_t best_key;
     float best_fit;
+    const uint32_t *cost_tab;
+    uint64_t cost;
 } ctx_t;
 
 static float evaluate(ctx_t *C, uint64_t key)
@@ -417,7 +422,11 @@ static float evaluate(ctx_t *C, uint64_t key)
     if (rk < 0) {
         f = OR_PENALTY;                     /* only without constraint awareness: nothing is run */
     } else {
-        if (!C->memo[rk]) { C->memo[rk] = 1; C->n_unique++; }
+        if (!C->memo[rk]) {
+            C->memo[rk] = 1;
+            C->n_unique++;
+            if (C->cost_tab) C->cost += C->cost_tab[rk];   /* a configuration is compiled and run once */
+        }
         f = C->table[rk];
     }
     if (f < C->best_fit || (f == C->best_fit && key < C->best_key)) {
@@ -563,6 +572,7 @@ static void record(ctx_t *C, const or_trace *T, int g, int P, const or_params *p
     T->best_key[g] = C->best_key;
     T->best_fit[g] = C->best_fit;
     T->n_unique[g] = C->n_unique;
+    T->cost[g] = C->cost;
     if (T->hit[0] < 0 && C->best_fit <= prm->target) {
         T->hit[0] = g;
         T->hit[1] = (int64_t)C->n_unique;
@@ -773,6 +783,8 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
     C.vt = tuples_of(&C.L, keys, nv);
     C.memo = (uint8_t *)calloc((size_t)(nv > 0 ? nv : 1), 1);
     C.n_unique = 0;
+    C.cost_tab = prm->cost;
+    C.cost = 0;
     C.best_key = ~0ull;
     C.best_fit = INFINITY;
     T->hit[0] = -1;

@@ -47,7 +47,8 @@ class _Params(C.Structure):
     _fields_ = [("de_F", C.c_float), ("de_CR", C.c_float), ("pso_w", C.c_float),
                 ("pso_c1", C.c_float), ("pso_c2", C.c_float), ("fa_beta0", C.c_float),
                 ("fa_gamma", C.c_float), ("fa_alpha", C.c_float), ("ga_pmut", C.c_float),
-                ("target", C.c_float), ("repair_rule", C.c_int), ("constraint_aware", C.c_int)]
+                ("target", C.c_float), ("repair_rule", C.c_int), ("constraint_aware", C.c_int),
+                ("cost", C.c_void_p)]
 
 
 class _Surr(C.Structure):
@@ -63,7 +64,7 @@ class _STrace(C.Structure):
 class _Trace(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in
                 ("cand", "rep", "evalk", "fit", "popk", "popf", "pos", "best_key", "best_fit",
-                 "n_unique", "hit")]
+                 "n_unique", "hit", "cost")]
 
 
 _lib = None
@@ -312,7 +313,7 @@ SURROGATE_DEFAULTS = dict(pool=16, H=256, batch=256, steps=8, warm_mult=4, lr=1e
 
 
 def run(kind: str, sp: OracleSpace, keys: np.ndarray, table: np.ndarray, pop: int, gens: int,
-        seed: int, surrogate=None, log_table=None, **params):
+        seed: int, surrogate=None, log_table=None, cost=None, **params):
     """One optimizer run: generation 0 (initial sample) plus ``gens`` generations.
 
     With ``surrogate`` (a dict overriding SURROGATE_DEFAULTS) and ``log_table`` (log-fitness per
@@ -329,10 +330,15 @@ def run(kind: str, sp: OracleSpace, keys: np.ndarray, table: np.ndarray, pop: in
         "popk": np.zeros((G + 1, P), np.uint64), "popf": np.zeros((G + 1, P), np.float32),
         "pos": np.zeros((G + 1, P, n), np.float32), "best_key": np.zeros(G + 1, np.uint64),
         "best_fit": np.zeros(G + 1, np.float32), "n_unique": np.zeros(G + 1, np.uint64),
-        "hit": np.zeros(2, np.int64),
+        "hit": np.zeros(2, np.int64), "cost": np.zeros(G + 1, np.uint64),
     }
     tr = _Trace(*[T[f].ctypes.data for f, _ in _Trace._fields_])
-    pr = _Params(*[int(prm[f]) if f in ("repair_rule", "constraint_aware") else float(np.float32(prm[f])) for f, _ in _Params._fields_])
+    cost_arr = None if cost is None else np.ascontiguousarray(cost, dtype=np.uint32)
+    if cost_arr is not None:
+        assert len(cost_arr) == len(keys)
+    pr = _Params(*[int(prm[f]) if f in ("repair_rule", "constraint_aware") else float(np.float32(prm[f]))
+                   for f, _ in _Params._fields_ if f != "cost"],
+                 None if cost_arr is None else cost_arr.ctypes.data)
     sg = st = None
     if surrogate is not None:
         cfg = dict(SURROGATE_DEFAULTS)

@@ -71,6 +71,7 @@ _SIGS = {
     "ct_build_valid_space": [C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)],
     "ct_space_keys": [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint64)],
     "ct_set_fitness": [C.c_void_p, C.c_void_p, C.c_uint64],
+    "ct_set_eval_cost": [C.c_void_p, C.c_void_p, C.c_uint64],
     "ct_lookup": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p],
     "ct_repair": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_set_repair_mode": [C.c_void_p, C.c_int32, C.c_int32],
@@ -90,6 +91,7 @@ _SIGS = {
     "ct_opt_best": [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_float), C.POINTER(C.c_uint64),
                     C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_void_p],
     "ct_opt_state": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "ct_opt_cost": [C.c_void_p, C.POINTER(C.c_uint64), C.c_void_p],
     "ct_opt_save": [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t), C.c_void_p],
     "ct_opt_load": [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p],
     "ct_batch_create": [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.POINTER(ct_opt_params), C.POINTER(C.c_void_p)],
@@ -99,6 +101,8 @@ _SIGS = {
     "ct_batch_results": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_batch_run_state": [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_batch_reset": [C.c_void_p],
+    "ct_batch_set_trace": [C.c_void_p, C.c_int32],
+    "ct_batch_trace": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_batch_set_launch": [C.c_void_p, C.c_int32, C.c_int32],
     "ct_batch_autotune": [C.c_void_p, C.c_char_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                           C.POINTER(C.c_float), C.c_void_p],
@@ -313,6 +317,12 @@ class Space:
         check(lib().ct_set_fitness(self.h, _ptr(table), table.numel()))
         self._fit = table
 
+    def set_eval_cost(self, cost):
+        """Simulated evaluation time per valid rank (device int32 tensor read as uint32 microseconds;
+        None removes it)."""
+        check(lib().ct_set_eval_cost(self.h, _ptr(cost), 0 if cost is None else cost.numel()))
+        self._cost = cost
+
     def lookup(self, cand, rank, stream=None):
         check(lib().ct_lookup(self.h, _ptr(cand), cand.numel(), _ptr(rank), _stream(stream)))
 
@@ -408,6 +418,11 @@ class Opt:
         return dict(best_key=int(k.value), best_fit=float(f.value), n_unique=int(u.value), hit_gen=int(hg.value),
                     hit_evals=int(he.value))
 
+    def cost(self, stream=None):
+        c = C.c_uint64()
+        check(lib().ct_opt_cost(self.h, C.byref(c), _stream(stream)))
+        return int(c.value)
+
     def set_surrogate(self, log_table, **cfg):
         """Screen DE/GA proposals with the MLP surrogate (before generation 0)."""
         p = ct_surrogate_params()
@@ -501,6 +516,20 @@ class Batch:
 
     def run_state(self, run, keys=None, fit=None, pos=None, stream=None):
         check(lib().ct_batch_run_state(self.h, run, _ptr(keys), _ptr(fit), _ptr(pos), _stream(stream)))
+
+    def set_trace(self, gens):
+        check(lib().ct_batch_set_trace(self.h, gens))
+        self.trace_gens = gens
+
+    def trace(self, stream=None):
+        """Per-run, per-generation best fitness, simulated time and unique evaluations
+        (arrays of shape [runs, gens])."""
+        g = self.trace_gens
+        bf = np.zeros((self.n, g), np.float32)
+        co = np.zeros((self.n, g), np.uint64)
+        nu = np.zeros((self.n, g), np.uint64)
+        check(lib().ct_batch_trace(self.h, *[a.ctypes.data_as(C.c_void_p) for a in (bf, co, nu)], _stream(stream)))
+        return dict(best_fit=bf, cost=co, n_unique=nu)
 
 
 def u64(t):

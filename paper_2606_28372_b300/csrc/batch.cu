@@ -35,6 +35,7 @@ struct BatchSpace {
     const uint64_t* keys;
     int64_t nv;
     const float* fit;
+    const uint32_t* cost;   // simulated evaluation time per rank, or null
     int32_t dmax;
     int32_t pad_;
     const uint32_t* masks[MAX_RADIUS];
@@ -72,6 +73,10 @@ struct BatchArgs {
     uint32_t* memo;
     uint32_t* work;
     const uint32_t* gen;
+    float* tr_fit;                      // per-generation trace [run][generation], or null
+    unsigned long long* tr_cost;
+    unsigned long long* tr_unique;
+    uint32_t tr_gens;
 };
 
 struct RepairSmem {
@@ -199,10 +204,22 @@ __global__ void __launch_bounds__(256, 1) k_batch_gen(const __grid_constant__ Ba
             fit[i] = __ldg(bs.fit + rk);
             const uint32_t bit = 1u << (rk & 31);
             const uint32_t old = atomicOr(memo + (rk >> 5), bit);
-            if (!(old & bit)) atomicAdd(&a.st->n_unique, 1ull);
+            if (!(old & bit)) {
+                atomicAdd(&a.st->n_unique, 1ull);
+                if (bs.cost) atomicAdd(&a.st->cost, (unsigned long long)__ldg(bs.cost + rk));
+            }
         }
         __syncthreads();
         select_dev(a, gen, rep, fit, sel);
+        if (gen < ba.tr_gens) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const size_t o = (size_t)r * ba.tr_gens + gen;
+                ba.tr_fit[o] = a.st->best_fit;
+                ba.tr_cost[o] = a.st->cost;
+                ba.tr_unique[o] = a.st->n_unique;
+            }
+        }
     }
 }
 
@@ -226,6 +243,9 @@ struct ct_batch {
     DevBuf<uint64_t> X;
     DevBuf<float> FX, pos, vel, pb, fpb, gb, ynew;
     DevBuf<uint32_t> memo, ctr;   // ctr[0] = generation, ctr[1] = work counter
+    DevBuf<float> tr_fit;
+    DevBuf<unsigned long long> tr_cost, tr_unique;
+    uint32_t tr_gens = 0;
     std::vector<BatchRun> brun;
     uint64_t n_pop = 0, n_pn = 0, n_n = 0, n_memo = 0;
     int threads = 256, ctas_per_sm = 0, sms = 148;
@@ -235,13 +255,14 @@ struct ct_batch {
         for (auto& g : graphs) cudaGraphExecDestroy(g.second);
         d_spaces.release(); d_runs.release(); d_order.release(); st.release(); X.release(); FX.release();
         pos.release(); vel.release(); pb.release(); fpb.release(); gb.release(); ynew.release(); memo.release();
-        ctr.release();
+        ctr.release(); tr_fit.release(); tr_cost.release(); tr_unique.release();
     }
     BatchArgs args() const {
         BatchArgs a;
         a.spaces = d_spaces.p; a.runs = d_runs.p; a.order = d_order.p; a.n_runs = (int)runs_h.size(); a.prm = prm;
         a.st = st.p; a.X = X.p; a.FX = FX.p; a.pos = pos.p; a.vel = vel.p; a.pb = pb.p; a.fpb = fpb.p; a.gb = gb.p;
         a.ynew = ynew.p; a.memo = memo.p; a.work = ctr.p + 1; a.gen = ctr.p;
+        a.tr_fit = tr_fit.p; a.tr_cost = tr_cost.p; a.tr_unique = tr_unique.p; a.tr_gens = tr_gens;
         return a;
     }
     int grid() const {
@@ -280,6 +301,13 @@ static ct_status batch_reset(ct_batch* b) {
     CT_TRY_CUDA(cudaMemset(b->ynew.p, 0, b->n_pn * 4));
     CT_TRY_CUDA(cudaMemset(b->gb.p, 0, b->n_n * 4));
     CT_TRY_CUDA(cudaMemset(b->ctr.p, 0, 8));
+    if (b->tr_gens) {
+        const size_t n = R * b->tr_gens;
+        std::vector<float> inf(n, __builtin_inff());
+        CT_TRY_CUDA(cudaMemcpy(b->tr_fit.p, inf.data(), n * 4, cudaMemcpyHostToDevice));
+        CT_TRY_CUDA(cudaMemset(b->tr_cost.p, 0, n * 8));
+        CT_TRY_CUDA(cudaMemset(b->tr_unique.p, 0, n * 8));
+    }
     b->generation = 0;
     return CT_OK;
 }
@@ -298,6 +326,7 @@ ct_status ct_batch_create(ct_space* const* spaces, int32_t n_spaces, const ct_ba
         BatchSpace& b = bsp[s];
         memset(&b, 0, sizeof b);
         b.sp = sp->d; b.tables = sp->tables.p; b.keys = sp->keys.p; b.nv = (int64_t)sp->n_valid; b.fit = sp->fit;
+        b.cost = sp->cost;
         if (ensure_balls(sp, auto_radius(sp)) != CT_OK) return CT_ERR_CUDA;
         b.dmax = std::min<int>(auto_radius(sp), (int)sp->balls.size());
         for (int d = 0; d < b.dmax; ++d) {
@@ -450,6 +479,39 @@ ct_status ct_batch_reset(ct_batch* b) {
     if (!b) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
     CT_TRY_CUDA(cudaDeviceSynchronize());
     return batch_reset(b);
+}
+
+ct_status ct_batch_set_trace(ct_batch* b, int32_t gens) {
+    if (!b || gens < 0) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
+    CT_TRY_CUDA(cudaDeviceSynchronize());
+    for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);   // they captured the old arguments
+    b->graphs.clear();
+    b->tr_fit.release(); b->tr_cost.release(); b->tr_unique.release();
+    b->tr_gens = 0;
+    if (gens > 0) {
+        const size_t n = b->runs_h.size() * (size_t)gens;
+        ct_status e = b->tr_fit.ensure(n);
+        if (e == CT_OK) e = b->tr_cost.ensure(n);
+        if (e == CT_OK) e = b->tr_unique.ensure(n);
+        if (e != CT_OK) {
+            b->tr_fit.release(); b->tr_cost.release(); b->tr_unique.release();
+            return e;
+        }
+        b->tr_gens = (uint32_t)gens;
+    }
+    return batch_reset(b);
+}
+
+ct_status ct_batch_trace(const ct_batch* b, float* best_fit, uint64_t* cost, uint64_t* n_unique, ct_stream stream) {
+    if (!b) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    if (!b->tr_gens) { set_error("no trace: call ct_batch_set_trace first"); return CT_ERR_STATE; }
+    const size_t n = b->runs_h.size() * (size_t)b->tr_gens;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (best_fit) CT_TRY_CUDA(cudaMemcpyAsync(best_fit, b->tr_fit.p, n * 4, cudaMemcpyDeviceToHost, st));
+    if (cost) CT_TRY_CUDA(cudaMemcpyAsync(cost, b->tr_cost.p, n * 8, cudaMemcpyDeviceToHost, st));
+    if (n_unique) CT_TRY_CUDA(cudaMemcpyAsync(n_unique, b->tr_unique.p, n * 8, cudaMemcpyDeviceToHost, st));
+    CT_TRY_CUDA(cudaStreamSynchronize(st));
+    return CT_OK;
 }
 
 // Autotuner: times `gens` generations for every (threads, CTAs per SM) variant from a reset

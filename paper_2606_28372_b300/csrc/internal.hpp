@@ -131,6 +131,7 @@ struct ct_space {
     // evaluate
     const float* fit = nullptr;
     uint64_t n_fit = 0;
+    const uint32_t* cost = nullptr;        // simulated evaluation time per rank (borrowed), or null
 
     ct::DevBuf<uint32_t> status;           // device status word
 

@@ -17,8 +17,9 @@
 #include "optim_dev.cuh"
 
 namespace ct {
-ct_status evaluate_impl(ct_space* s, uint32_t* memo, unsigned long long* unique, const uint64_t* d_keys, int64_t n,
-                        float* d_fit, int64_t* d_rank, cudaStream_t st, float invalid_fit = __builtin_inff());
+ct_status evaluate_impl(ct_space* s, uint32_t* memo, unsigned long long* unique, unsigned long long* cost_acc,
+                        const uint64_t* d_keys, int64_t n, float* d_fit, int64_t* d_rank, cudaStream_t st,
+                        float invalid_fit = __builtin_inff());
 }
 
 namespace ct {
@@ -77,7 +78,8 @@ static ct_status step_impl(ct_opt* o, uint32_t gen, int use_dev, cudaStream_t st
     CT_TRY(repair_step(o, a, gen, use_dev, st));
     k_post_repair<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->rep.p);
     count_launch();
-    CT_TRY(evaluate_impl(o->s, o->memo.p, &o->st.p->n_unique, o->rep.p, o->P, o->fit.p, nullptr, st, CT_PENALTY));
+    CT_TRY(evaluate_impl(o->s, o->memo.p, &o->st.p->n_unique, &o->st.p->cost, o->rep.p, o->P, o->fit.p, nullptr, st,
+                         CT_PENALTY));
     k_select<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->rep.p, o->fit.p);
     count_launch();
     CT_TRY_CUDA(cudaGetLastError());
@@ -180,8 +182,8 @@ ct_status ct_evaluate(ct_space* s, ct_opt* o, const uint64_t* d_keys, int64_t n,
     if (!s->built) { set_error("space not built"); return CT_ERR_STATE; }
     if (!s->fit && d_fit) { set_error("no fitness table"); return CT_ERR_STATE; }
     if (o && o->s != s) { set_error("run belongs to another space"); return CT_ERR_INVALID_ARG; }
-    return evaluate_impl(s, o ? o->memo.p : nullptr, o ? &o->st.p->n_unique : nullptr, d_keys, n, d_fit, d_rank,
-                         (cudaStream_t)stream);
+    return evaluate_impl(s, o ? o->memo.p : nullptr, o ? &o->st.p->n_unique : nullptr, o ? &o->st.p->cost : nullptr,
+                         d_keys, n, d_fit, d_rank, (cudaStream_t)stream);
 }
 
 ct_status ct_opt_step(ct_opt* o, uint32_t gen, ct_stream stream) {
@@ -246,6 +248,16 @@ ct_status ct_opt_best(ct_opt* o, uint64_t* best_key, float* best_fit, uint64_t* 
     if (hit_generation) *hit_generation = h.hit_gen;
     if (hit_evals) *hit_evals = h.hit_evals;
     return ct_space_status(o->s, stream);
+}
+
+ct_status ct_opt_cost(ct_opt* o, uint64_t* cost, ct_stream stream) {
+    if (!o || !cost) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long h = 0;
+    CT_TRY_CUDA(cudaMemcpyAsync(&h, &o->st.p->cost, sizeof h, cudaMemcpyDeviceToHost, st));
+    CT_TRY_CUDA(cudaStreamSynchronize(st));
+    *cost = h;
+    return CT_OK;
 }
 
 ct_status ct_opt_state(const ct_opt* o, uint64_t* d_keys, float* d_fit, float* d_pos, ct_stream stream) {

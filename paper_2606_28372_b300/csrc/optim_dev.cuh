@@ -18,6 +18,7 @@ struct OptDev {
     uint32_t gen;              // next generation (advanced by select)
     unsigned long long n_unique;
     long long hit_gen, hit_evals;
+    unsigned long long cost;   // simulated time of the configurations evaluated (each once)
 };
 
 struct OptArgs {

@@ -36,7 +36,8 @@ __global__ void k_lookup(const DevSpace* __restrict__ sp, const uint64_t* __rest
 __global__ void k_evaluate(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, int64_t nv,
                            const float* __restrict__ table, const uint64_t* __restrict__ cand, int64_t n,
                            float* __restrict__ fit, int64_t* __restrict__ rank_out, uint32_t* __restrict__ memo,
-                           unsigned long long* __restrict__ unique, float invalid_fit) {
+                           unsigned long long* __restrict__ unique, const uint32_t* __restrict__ cost,
+                           unsigned long long* __restrict__ cost_acc, float invalid_fit) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t c = cand[i];
         const int64_t r = in_domain(sp, c) ? rank_of(keys, nv, c) : -1;
@@ -45,7 +46,10 @@ __global__ void k_evaluate(const DevSpace* __restrict__ sp, const uint64_t* __re
         if (memo && r >= 0) {
             const uint32_t bit = 1u << (r & 31);
             const uint32_t old = atomicOr(memo + (r >> 5), bit);
-            if (!(old & bit)) atomicAdd(unique, 1ull);
+            if (!(old & bit)) {   // first evaluation of this configuration
+                atomicAdd(unique, 1ull);
+                if (cost) atomicAdd(cost_acc, (unsigned long long)__ldg(cost + r));
+            }
         }
     }
 }
@@ -472,12 +476,13 @@ ct_status ct_set_repair_mode(ct_space* s, int32_t mode, int32_t max_radius) {
 }  // extern "C"
 
 namespace ct {
-ct_status evaluate_impl(ct_space* s, uint32_t* memo, unsigned long long* unique, const uint64_t* d_keys, int64_t n,
-                        float* d_fit, int64_t* d_rank, cudaStream_t st, float invalid_fit) {
+ct_status evaluate_impl(ct_space* s, uint32_t* memo, unsigned long long* unique, unsigned long long* cost_acc,
+                        const uint64_t* d_keys, int64_t n, float* d_fit, int64_t* d_rank, cudaStream_t st,
+                        float invalid_fit) {
     if (n == 0) return CT_OK;
     const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
     k_evaluate<<<g, 256, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, s->fit, d_keys, n, d_fit, d_rank, memo, unique,
-                                  invalid_fit);
+                                  memo && cost_acc ? s->cost : nullptr, cost_acc, invalid_fit);
     count_launch();
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;

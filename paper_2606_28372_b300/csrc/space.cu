@@ -965,6 +965,15 @@ ct_status ct_set_fitness(ct_space* s, const float* d_table, uint64_t n) {
     return CT_OK;
 }
 
+ct_status ct_set_eval_cost(ct_space* s, const uint32_t* d_cost, uint64_t n) {
+    if (!s) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    if (!d_cost) { s->cost = nullptr; return CT_OK; }
+    if (!s->built) { set_error("space not built"); return CT_ERR_STATE; }
+    if (n != s->n_valid) { set_error("cost table has %llu entries, space has %llu valid", (unsigned long long)n, (unsigned long long)s->n_valid); return CT_ERR_INVALID_ARG; }
+    s->cost = d_cost;
+    return CT_OK;
+}
+
 ct_status ct_space_status(ct_space* s, ct_stream stream) {
     if (!s) { set_error("space is NULL"); return CT_ERR_INVALID_ARG; }
     uint32_t v = 0;

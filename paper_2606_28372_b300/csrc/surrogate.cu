@@ -27,8 +27,9 @@
 #include "optim_dev.cuh"
 
 namespace ct {
-ct_status evaluate_impl(ct_space* s, uint32_t* memo, unsigned long long* unique, const uint64_t* d_keys, int64_t n,
-                        float* d_fit, int64_t* d_rank, cudaStream_t st, float invalid_fit = __builtin_inff());
+ct_status evaluate_impl(ct_space* s, uint32_t* memo, unsigned long long* unique, unsigned long long* cost_acc,
+                        const uint64_t* d_keys, int64_t n, float* d_fit, int64_t* d_rank, cudaStream_t st,
+                        float invalid_fit = __builtin_inff());
 
 __device__ __forceinline__ float bf16r(float f) {
     uint32_t u = __float_as_uint(f);
@@ -443,7 +444,7 @@ ct_status surrogate_step(ct_opt* o, uint32_t gen, cudaStream_t st) {
         k_post_pool<<<1, 256, 0, st>>>(a, gen, evk);
         count_launch();
     }
-    CT_TRY(evaluate_impl(s, o->memo.p, &o->st.p->n_unique, evk, P, o->fit.p, nullptr, st));
+    CT_TRY(evaluate_impl(s, o->memo.p, &o->st.p->n_unique, &o->st.p->cost, evk, P, o->fit.p, nullptr, st));
     CT_TRY(predict_keys(o, evk, P, g->pred.p, st));
     k_surr_judge<<<1, 32, 0, st>>>(s->keys.p, (int64_t)s->n_valid, g->logt, evk, g->pred.p, P, g->cfg.warmup_mult,
                                    g->cfg.mae_ratio, screened ? 1 : 0, g->in_e.p, g->ek.p, g->ey.p, g->by.p, g->sd.p);

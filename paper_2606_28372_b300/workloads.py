@@ -220,6 +220,16 @@ def smooth_table(space: SpaceDef, idx_tuples: np.ndarray, seed: int = 0,
     return (bowl * np.exp(noise * z)).astype(np.float32)
 
 
+def eval_cost_table(table: np.ndarray, seed: int = 0, compile_s: float = 1.5, sigma: float = 0.25,
+                    repeats: int = 7) -> np.ndarray:
+    """Simulated time, in whole microseconds (uint32), of evaluating each valid configuration:
+    a compile time lognormal around ``compile_s`` seconds plus ``repeats`` runs of the kernel,
+    reading the fitness table as kernel runtimes in milliseconds."""
+    g = np.random.Generator(np.random.Philox(key=0xC0575EED + seed))
+    compile_us = 1e6 * compile_s * np.exp(sigma * g.standard_normal(len(table)))
+    return np.rint(compile_us + repeats * 1e3 * np.asarray(table, np.float64)).astype(np.uint32)
+
+
 # ---------------------------------------------------------------------------------------
 # candidate tuples for repair workloads (value-index tuples; packing is each side's job)
 # ---------------------------------------------------------------------------------------
