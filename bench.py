@@ -605,9 +605,9 @@ def aware_vs_unaware(torch, ct, W, dev, seeds=16, overhead_us=1000.0, K=50, gens
     The four optimizers with Table IV's population sizes, constraint-aware and not (random
     Cartesian start, no repair, static penalty), `seeds` runs each on the eight spaces of the
     density ladder (1.5 % .. 100 %) and the tiny space (56 %); every run of one mode advances in
-    one batched launch per generation and records a per-generation trace of its best fitness and
-    simulated clock (each configuration's synthetic compile + 7 runs, once; plus `overhead_us` per
-    proposal).  Each run is scored against the space's random-search baseline over the budget of
+    one batched launch per generation and logs every improvement of its best with the simulated
+    clock at that evaluation (proposals evaluated one at a time; each configuration's synthetic
+    compile + 7 runs charged once, plus `overhead_us` per proposal).  Each run is scored against the space's random-search baseline over the budget of
     Section V-A.  Aware runs get gens[0] generations, the cheaper non-aware ones gens[1]; a run
     whose clock ends before the budget keeps its last value ("truncated")."""
     from scipy.stats import spearmanr
@@ -636,7 +636,7 @@ def aware_vs_unaware(torch, ct, W, dev, seeds=16, overhead_us=1000.0, K=50, gens
     table, ms, score = {}, {}, {}
     for mode, aware, G in (("aware", 1, gens[0]), ("unaware", 0, gens[1])):
         b = ct.Batch(spaces, runs, constraint_aware=aware)
-        b.set_trace(G)
+        b.set_trace(G, events=4096)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -646,12 +646,13 @@ def aware_vs_unaware(torch, ct, W, dev, seeds=16, overhead_us=1000.0, K=50, gens
         torch.cuda.synchronize()
         ms[mode] = e0.elapsed_time(e1)
         tr = b.trace()
+        ev = b.events()
         del b
         for j in range(S):
             for ki, k in enumerate(kinds):
                 rows = [r for r, run in enumerate(runs) if run[0] == j and run[1] == k]
                 P = PAPER_POP[k]
-                res = PS.run_scores(base[j], tr["cost"][rows], tr["best_fit"][rows], pop=P, overhead_us=overhead_us, K=K)
+                res = PS.run_scores(base[j], [ev[r] for r in rows], pop=P, overhead_us=overhead_us, K=K)
                 clock_end = tr["cost"][rows, -1].astype(np.float64) + G * P * overhead_us
                 B = budgets[j][1]
                 clock = tr["cost"][rows].astype(np.float64) + np.arange(1, G + 1) * P * overhead_us

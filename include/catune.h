@@ -387,8 +387,16 @@ ct_status ct_batch_reset(ct_batch *batch);
 /* Per-generation trace of the first `gens` generations (0 switches it off): after each
  * generation g < gens every run records its best fitness so far, its simulated time
  * (ct_opt_cost; evaluation costs are those registered on the spaces when the batch was
- * created) and its unique evaluations.  Resets the batch and drops captured graphs. */
-ct_status ct_batch_set_trace(ct_batch *batch, int32_t gens);
+ * created) and its unique evaluations.  With events > 0 every run also logs, up to `events`
+ * entries, each strict improvement of its best in evaluation order (a generation's proposals
+ * are evaluated one at a time in population order): generation, population index, simulated
+ * time after that evaluation, new best.  Resets the batch and drops captured graphs. */
+ct_status ct_batch_set_trace(ct_batch *batch, int32_t gens, int32_t events);
+/* Copies the event log into host arrays: count[n_runs] (events seen; entries past the capacity
+ * are dropped), and n_runs x capacity entries, run-major, of generation, index, simulated time
+ * and best (each may be NULL).  Synchronises. */
+ct_status ct_batch_events(const ct_batch *batch, uint32_t *count, int32_t *gen, int32_t *idx, uint64_t *clock,
+                          float *fit, ct_stream stream);
 /* Copies the trace into host arrays of n_runs x gens entries, run-major (each may be NULL);
  * generations not yet run read +inf, 0, 0.  Synchronises. */
 ct_status ct_batch_trace(const ct_batch *batch, float *best_fit, uint64_t *cost, uint64_t *n_unique,

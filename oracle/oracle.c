@@ -399,6 +399,12 @@ typedef struct {         /* per-generation trace, arrays of (G+1) x P unless not
     int64_t *hit;        /* [0] generation of first best<=target (-1), [1] n_unique then */
     uint64_t *cost;      /* (G+1): simulated time spent so far, the sum of the costs of the
                             configurations evaluated (each once) */
+    /* every strict improvement of the run's best, in evaluation order (capacity P x (G+1)):
+     * generation, population index, simulated time after that evaluation, new best */
+    int32_t *ev_gen, *ev_idx;
+    uint64_t *ev_clock;
+    float *ev_fit;
+    int64_t *ev_n;       /* [0]: number of events */
 } or_trace;
 
 typedef struct {
@@ -413,6 +419,8 @@ typedef struct {
     float best_fit;
     const uint32_t *cost_tab;
     uint64_t cost;
+    const or_trace *T;   /* event log */
+    int g, i;            /* generation and population index being evaluated */
 } ctx_t;
 
 static float evaluate(ctx_t *C, uint64_t key)
@@ -428,6 +436,13 @@ static float evaluate(ctx_t *C, uint64_t key)
             if (C->cost_tab) C->cost += C->cost_tab[rk];   /* a configuration is compiled and run once */
         }
         f = C->table[rk];
+    }
+    if (f < C->best_fit && C->T) {          /* the best value improves: log it */
+        int64_t e = C->T->ev_n[0]++;
+        C->T->ev_gen[e] = C->g;
+        C->T->ev_idx[e] = C->i;
+        C->T->ev_clock[e] = C->cost;
+        C->T->ev_fit[e] = f;
     }
     if (f < C->best_fit || (f == C->best_fit && key < C->best_key)) {
         C->best_fit = f;
@@ -785,6 +800,9 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
     C.n_unique = 0;
     C.cost_tab = prm->cost;
     C.cost = 0;
+    C.T = T;
+    C.g = C.i = 0;
+    T->ev_n[0] = 0;
     C.best_key = ~0ull;
     C.best_fit = INFINITY;
     T->hit[0] = -1;
@@ -944,6 +962,8 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
         for (int i = 0; i < P; i++) {
             int64_t rk = rank_of(C.keys, C.nv, UE[i]);
             if (sg && rk >= 0 && !C.memo[rk]) newi[n_new++] = i;
+            C.g = g;
+            C.i = i;
             FU[i] = evaluate(&C, UE[i]);
         }
         if (sg) {   /* judge on this generation's evaluations, then learn from them */

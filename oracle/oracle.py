@@ -64,7 +64,7 @@ class _STrace(C.Structure):
 class _Trace(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in
                 ("cand", "rep", "evalk", "fit", "popk", "popf", "pos", "best_key", "best_fit",
-                 "n_unique", "hit", "cost")]
+                 "n_unique", "hit", "cost", "ev_gen", "ev_idx", "ev_clock", "ev_fit", "ev_n")]
 
 
 _lib = None
@@ -331,6 +331,9 @@ def run(kind: str, sp: OracleSpace, keys: np.ndarray, table: np.ndarray, pop: in
         "pos": np.zeros((G + 1, P, n), np.float32), "best_key": np.zeros(G + 1, np.uint64),
         "best_fit": np.zeros(G + 1, np.float32), "n_unique": np.zeros(G + 1, np.uint64),
         "hit": np.zeros(2, np.int64), "cost": np.zeros(G + 1, np.uint64),
+        "ev_gen": np.zeros(P * (G + 1), np.int32), "ev_idx": np.zeros(P * (G + 1), np.int32),
+        "ev_clock": np.zeros(P * (G + 1), np.uint64), "ev_fit": np.zeros(P * (G + 1), np.float32),
+        "ev_n": np.zeros(1, np.int64),
     }
     tr = _Trace(*[T[f].ctypes.data for f, _ in _Trace._fields_])
     cost_arr = None if cost is None else np.ascontiguousarray(cost, dtype=np.uint32)
@@ -360,6 +363,9 @@ def run(kind: str, sp: OracleSpace, keys: np.ndarray, table: np.ndarray, pop: in
                       C.cast(C.byref(sg), C.c_void_p) if sg else None, C.cast(C.byref(st), C.c_void_p) if st else None)
     assert rc == 0
     T.pop("logt_ref", None)
+    ne = int(T.pop("ev_n")[0])
+    for f in ("ev_gen", "ev_idx", "ev_clock", "ev_fit"):
+        T[f] = T[f][:ne]
     return T
 
 

@@ -10,10 +10,11 @@ and defers the details to the methodology it cites; the readings taken here:
   before the first draw it stands at the median;
 - every draw of the baseline takes the mean evaluation time of the space plus the per-proposal
   overhead, so its value at time t is the expectation after floor(t / that) draws;
-- a run's simulated clock after generation g is the evaluation time of every configuration it
-  evaluated (each once) plus the overhead of every proposal it made (P per generation); its
-  value at time t is its best fitness at the last generation that ended by t, or the median
-  while it has evaluated nothing valid;
+- a run evaluates its proposals one at a time, in population order within a generation; its
+  simulated clock after an evaluation is the evaluation time of every configuration evaluated
+  so far (each once) plus the overhead of every proposal made so far; its value at time t is
+  its best fitness after the last evaluation that ended by t, or the median while it has
+  evaluated nothing valid;
 - the score of a run at t is (baseline(t) - value(t)) / (baseline(t) - optimum): 0 on the
   baseline, 1 at the optimum; it is averaged over K evenly spaced times in (0, budget] and
   over runs (and Eq. 2 averages that over spaces).
@@ -56,26 +57,30 @@ def budget(fit, cost_us, overhead_us=0.0):
     return n, n * per
 
 
-def run_score(fit, cost_us, trace_cost, trace_best, pop, overhead_us=0.0, K=50, penalty=1e20):
-    """Score of each run (rows of the traces: per generation, simulated evaluation time spent
-    and best fitness so far) and the per-time-point scores averaged over runs."""
+def run_score(fit, cost_us, events, pop, overhead_us=0.0, K=50, penalty=1e20):
+    """Score of each run from its event log and the per-time-point scores averaged over runs.
+
+    ``events`` holds, per run, the improvements of its best in evaluation order as four
+    sequences: generation, population index, simulated evaluation time after that evaluation
+    (each configuration charged once), new best.  The clock of an event adds the overhead of
+    every proposal up to and including it: (generation * pop + index + 1) * overhead."""
     f = np.asarray(fit, np.float64)
     med, opt = float(np.median(f)), float(f.min())
     nstar, B = budget(f, cost_us, overhead_us)
     per = float(np.mean(np.asarray(cost_us, np.float64))) + overhead_us
     times = [B * k / K for k in range(1, K + 1)]
     base = [expected_best(f, min(int(t // per), len(f))) for t in times]
-    R, G = np.shape(trace_cost)
+    R = len(events)
     scores = np.zeros((R, K))
     for r in range(R):
+        gen, idx, clk, val = events[r]
         for k, t in enumerate(times):
             value = med
-            for g in range(G):
-                clock = float(trace_cost[r][g]) + (g + 1) * pop * overhead_us
+            for e in range(len(gen)):
+                clock = float(clk[e]) + (int(gen[e]) * pop + int(idx[e]) + 1) * overhead_us
                 if clock > t:
                     break
-                b = float(trace_best[r][g])
-                value = b if b < penalty else med
+                value = float(val[e]) if float(val[e]) < penalty else med
             den = base[k] - opt
             if den > 0:
                 scores[r, k] = (base[k] - value) / den

@@ -101,7 +101,8 @@ _SIGS = {
     "ct_batch_results": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_batch_run_state": [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_batch_reset": [C.c_void_p],
-    "ct_batch_set_trace": [C.c_void_p, C.c_int32],
+    "ct_batch_set_trace": [C.c_void_p, C.c_int32, C.c_int32],
+    "ct_batch_events": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_batch_trace": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_batch_set_launch": [C.c_void_p, C.c_int32, C.c_int32],
     "ct_batch_autotune": [C.c_void_p, C.c_char_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -517,9 +518,25 @@ class Batch:
     def run_state(self, run, keys=None, fit=None, pos=None, stream=None):
         check(lib().ct_batch_run_state(self.h, run, _ptr(keys), _ptr(fit), _ptr(pos), _stream(stream)))
 
-    def set_trace(self, gens):
-        check(lib().ct_batch_set_trace(self.h, gens))
+    def set_trace(self, gens, events=0):
+        check(lib().ct_batch_set_trace(self.h, gens, events))
         self.trace_gens = gens
+        self.event_cap = events
+
+    def events(self, stream=None):
+        """Per run, the improvements of its best in evaluation order: (generation, index,
+        simulated time, best) arrays; raises if a run overflowed the capacity."""
+        cap = self.event_cap
+        cnt = np.zeros(self.n, np.uint32)
+        gen = np.zeros((self.n, cap), np.int32)
+        idx = np.zeros((self.n, cap), np.int32)
+        clk = np.zeros((self.n, cap), np.uint64)
+        fit = np.zeros((self.n, cap), np.float32)
+        check(lib().ct_batch_events(self.h, *[a.ctypes.data_as(C.c_void_p) for a in (cnt, gen, idx, clk, fit)],
+                                    _stream(stream)))
+        if (cnt > cap).any():
+            raise CatuneError(CT_ERR_LIMIT, f"event log overflow: {int(cnt.max())} events, capacity {cap}")
+        return [(gen[r, :c], idx[r, :c], clk[r, :c], fit[r, :c]) for r, c in enumerate(cnt)]
 
     def trace(self, stream=None):
         """Per-run, per-generation best fitness, simulated time and unique evaluations

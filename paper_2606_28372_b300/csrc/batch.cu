@@ -77,6 +77,20 @@ struct BatchArgs {
     unsigned long long* tr_cost;
     unsigned long long* tr_unique;
     uint32_t tr_gens;
+    uint32_t ev_cap;                    // event log: improvements of each run's best, [run][ev_cap]
+    uint32_t* ev_count;                 // per run (may exceed ev_cap: entries past it are dropped)
+    int32_t* ev_gen;
+    int32_t* ev_idx;
+    unsigned long long* ev_clock;
+    float* ev_fit;
+};
+
+// Per-evaluation bookkeeping for the event log: whether the memo bit was first set by this
+// evaluation, and the evaluation cost of the configuration.
+struct EventSmem {
+    unsigned long long chg[BATCH_MAX_POP];   // cost charged at this position (first evaluation)
+    uint32_t c[BATCH_MAX_POP];
+    uint8_t fresh[BATCH_MAX_POP];
 };
 
 struct RepairSmem {
@@ -172,6 +186,7 @@ __global__ void __launch_bounds__(256, 1) k_batch_gen(const __grid_constant__ Ba
     __shared__ int order[BATCH_MAX_POP];
     __shared__ SelectSmem sel;
     __shared__ RepairSmem rsm;
+    __shared__ EventSmem evs;
     __shared__ int slot_s;
     const uint32_t gen = *ba.gen;
     while (true) {
@@ -200,16 +215,61 @@ __global__ void __launch_bounds__(256, 1) k_batch_gen(const __grid_constant__ Ba
         uint32_t* memo = ba.memo + run.off_memo;
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
             const int64_t rk = rank_of(bs.keys, bs.nv, rep[i]);
-            if (rk < 0) { fit[i] = CT_PENALTY; continue; }   // baselines only
+            if (rk < 0) {   // baselines only
+                fit[i] = CT_PENALTY;
+                if (ba.ev_cap) { evs.fresh[i] = 0; evs.c[i] = 0; }
+                continue;
+            }
             fit[i] = __ldg(bs.fit + rk);
             const uint32_t bit = 1u << (rk & 31);
             const uint32_t old = atomicOr(memo + (rk >> 5), bit);
+            const uint32_t cst = bs.cost ? __ldg(bs.cost + rk) : 0u;
             if (!(old & bit)) {
                 atomicAdd(&a.st->n_unique, 1ull);
-                if (bs.cost) atomicAdd(&a.st->cost, (unsigned long long)__ldg(bs.cost + rk));
+                if (bs.cost) atomicAdd(&a.st->cost, (unsigned long long)cst);
             }
+            if (ba.ev_cap) { evs.fresh[i] = !(old & bit); evs.c[i] = cst; }
         }
         __syncthreads();
+        if (ba.ev_cap) {
+            // Evaluations happen one at a time in population order: a configuration is charged
+            // at its first position in this generation if no earlier generation evaluated it
+            // (exactly one position of such a group won the memo bit above).
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const uint64_t k = rep[i];
+                bool first = true, fresh = false;
+                for (int j = 0; j < P; ++j) {
+                    if (rep[j] != k) continue;
+                    first = first && j >= i;
+                    fresh = fresh || evs.fresh[j];
+                }
+                evs.chg[i] = (first && fresh) ? (unsigned long long)evs.c[i] : 0ull;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned long long tot = 0;
+                for (int i = 0; i < P; ++i) tot += evs.chg[i];
+                unsigned long long clk = a.st->cost - tot;   // clock before this generation
+                float b = a.st->best_fit;
+                uint32_t n = ba.ev_count[r];
+                for (int i = 0; i < P; ++i) {
+                    clk += evs.chg[i];
+                    if (fit[i] < b) {
+                        b = fit[i];
+                        if (n < ba.ev_cap) {
+                            const size_t o = (size_t)r * ba.ev_cap + n;
+                            ba.ev_gen[o] = (int32_t)gen;
+                            ba.ev_idx[o] = i;
+                            ba.ev_clock[o] = clk;
+                            ba.ev_fit[o] = b;
+                        }
+                        ++n;
+                    }
+                }
+                ba.ev_count[r] = n;
+            }
+            __syncthreads();
+        }
         select_dev(a, gen, rep, fit, sel);
         if (gen < ba.tr_gens) {
             __syncthreads();
@@ -246,6 +306,11 @@ struct ct_batch {
     DevBuf<float> tr_fit;
     DevBuf<unsigned long long> tr_cost, tr_unique;
     uint32_t tr_gens = 0;
+    DevBuf<uint32_t> ev_count;
+    DevBuf<int32_t> ev_gen, ev_idx;
+    DevBuf<unsigned long long> ev_clock;
+    DevBuf<float> ev_fit;
+    uint32_t ev_cap = 0;
     std::vector<BatchRun> brun;
     uint64_t n_pop = 0, n_pn = 0, n_n = 0, n_memo = 0;
     int threads = 256, ctas_per_sm = 0, sms = 148;
@@ -256,6 +321,7 @@ struct ct_batch {
         d_spaces.release(); d_runs.release(); d_order.release(); st.release(); X.release(); FX.release();
         pos.release(); vel.release(); pb.release(); fpb.release(); gb.release(); ynew.release(); memo.release();
         ctr.release(); tr_fit.release(); tr_cost.release(); tr_unique.release();
+        ev_count.release(); ev_gen.release(); ev_idx.release(); ev_clock.release(); ev_fit.release();
     }
     BatchArgs args() const {
         BatchArgs a;
@@ -263,6 +329,8 @@ struct ct_batch {
         a.st = st.p; a.X = X.p; a.FX = FX.p; a.pos = pos.p; a.vel = vel.p; a.pb = pb.p; a.fpb = fpb.p; a.gb = gb.p;
         a.ynew = ynew.p; a.memo = memo.p; a.work = ctr.p + 1; a.gen = ctr.p;
         a.tr_fit = tr_fit.p; a.tr_cost = tr_cost.p; a.tr_unique = tr_unique.p; a.tr_gens = tr_gens;
+        a.ev_cap = ev_cap; a.ev_count = ev_count.p; a.ev_gen = ev_gen.p; a.ev_idx = ev_idx.p;
+        a.ev_clock = ev_clock.p; a.ev_fit = ev_fit.p;
         return a;
     }
     int grid() const {
@@ -308,6 +376,7 @@ static ct_status batch_reset(ct_batch* b) {
         CT_TRY_CUDA(cudaMemset(b->tr_cost.p, 0, n * 8));
         CT_TRY_CUDA(cudaMemset(b->tr_unique.p, 0, n * 8));
     }
+    if (b->ev_cap) CT_TRY_CUDA(cudaMemset(b->ev_count.p, 0, R * 4));
     b->generation = 0;
     return CT_OK;
 }
@@ -481,13 +550,28 @@ ct_status ct_batch_reset(ct_batch* b) {
     return batch_reset(b);
 }
 
-ct_status ct_batch_set_trace(ct_batch* b, int32_t gens) {
-    if (!b || gens < 0) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
+ct_status ct_batch_set_trace(ct_batch* b, int32_t gens, int32_t events) {
+    if (!b || gens < 0 || events < 0) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
     CT_TRY_CUDA(cudaDeviceSynchronize());
     for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);   // they captured the old arguments
     b->graphs.clear();
     b->tr_fit.release(); b->tr_cost.release(); b->tr_unique.release();
     b->tr_gens = 0;
+    b->ev_count.release(); b->ev_gen.release(); b->ev_idx.release(); b->ev_clock.release(); b->ev_fit.release();
+    b->ev_cap = 0;
+    if (events > 0) {
+        const size_t R = b->runs_h.size(), n = R * (size_t)events;
+        ct_status e = b->ev_count.ensure(R);
+        if (e == CT_OK) e = b->ev_gen.ensure(n);
+        if (e == CT_OK) e = b->ev_idx.ensure(n);
+        if (e == CT_OK) e = b->ev_clock.ensure(n);
+        if (e == CT_OK) e = b->ev_fit.ensure(n);
+        if (e != CT_OK) {
+            b->ev_count.release(); b->ev_gen.release(); b->ev_idx.release(); b->ev_clock.release(); b->ev_fit.release();
+            return e;
+        }
+        b->ev_cap = (uint32_t)events;
+    }
     if (gens > 0) {
         const size_t n = b->runs_h.size() * (size_t)gens;
         ct_status e = b->tr_fit.ensure(n);
@@ -500,6 +584,21 @@ ct_status ct_batch_set_trace(ct_batch* b, int32_t gens) {
         b->tr_gens = (uint32_t)gens;
     }
     return batch_reset(b);
+}
+
+ct_status ct_batch_events(const ct_batch* b, uint32_t* count, int32_t* gen, int32_t* idx, uint64_t* clock, float* fit,
+                          ct_stream stream) {
+    if (!b) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    if (!b->ev_cap) { set_error("no event log: call ct_batch_set_trace with events > 0 first"); return CT_ERR_STATE; }
+    const size_t R = b->runs_h.size(), n = R * (size_t)b->ev_cap;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (count) CT_TRY_CUDA(cudaMemcpyAsync(count, b->ev_count.p, R * 4, cudaMemcpyDeviceToHost, st));
+    if (gen) CT_TRY_CUDA(cudaMemcpyAsync(gen, b->ev_gen.p, n * 4, cudaMemcpyDeviceToHost, st));
+    if (idx) CT_TRY_CUDA(cudaMemcpyAsync(idx, b->ev_idx.p, n * 4, cudaMemcpyDeviceToHost, st));
+    if (clock) CT_TRY_CUDA(cudaMemcpyAsync(clock, b->ev_clock.p, n * 8, cudaMemcpyDeviceToHost, st));
+    if (fit) CT_TRY_CUDA(cudaMemcpyAsync(fit, b->ev_fit.p, n * 4, cudaMemcpyDeviceToHost, st));
+    CT_TRY_CUDA(cudaStreamSynchronize(st));
+    return CT_OK;
 }
 
 ct_status ct_batch_trace(const ct_batch* b, float* best_fit, uint64_t* cost, uint64_t* n_unique, ct_stream stream) {

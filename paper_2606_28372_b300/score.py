@@ -1,15 +1,17 @@
-"""Performance score of Eq. 2 over simulated time (Section V-A), from per-generation run traces.
+"""Performance score of Eq. 2 over simulated time (Section V-A), from the runs' event logs.
 
-This is host-side analysis of the traces the library records (ct_batch_trace: best fitness and
-simulated time per run and generation); it is not a step of the search itself.  Definitions:
+This is host-side analysis of what the library records (ct_batch_events: each improvement of a
+run's best with the simulated time at that evaluation); it is not a step of the search itself.
+Definitions:
 
 - baseline: valid configurations drawn uniformly without replacement; expected best after n
   draws E_n = sum_i f_(i) C(M-i, n-1) / C(M, n) over the sorted fitness values f_(1) <= ...;
   E_0 is the median.  A draw takes the mean evaluation time plus the per-proposal overhead.
 - budget: the first n with E_n <= median - 0.95 (median - optimum), times the time per draw.
-- a run's clock after generation g: its trace's evaluation time plus (g + 1) * pop * overhead;
-  its value at time t: the best fitness at the last generation that ended by t, or the median
-  while nothing valid has been evaluated (penalised or infinite best).
+- a run evaluates its proposals one at a time in population order; its clock after the
+  evaluation of index i in generation g: the evaluation time of every configuration evaluated
+  so far (each once) plus (g * pop + i + 1) * overhead; its value at time t: its best after the
+  last evaluation that ended by t, or the median while nothing valid has been evaluated.
 - score at t: (E(t) - value(t)) / (E(t) - optimum), averaged over K times in (0, budget].
 """
 from __future__ import annotations
@@ -65,23 +67,21 @@ class Baseline:
         return lo, lo * self.per_draw
 
 
-def run_scores(base: Baseline, trace_cost, trace_best, pop, overhead_us: float = 0.0, K: int = 50):
+def run_scores(base: Baseline, events, pop, overhead_us: float = 0.0, K: int = 50):
     """Per-run scores (mean over the K sampled times) and per-time scores (mean over runs).
-    trace_cost / trace_best: [runs, generations] arrays of simulated evaluation time and best."""
+    events: per run, (generation, index, evaluation time, best) arrays of its improvements in
+    evaluation order (ct_batch_events)."""
     n_star, B = base.budget()
     times = B * np.arange(1, K + 1) / K
     draws = np.minimum((times // base.per_draw).astype(np.int64), base.M)
     E = np.array([base.expected(int(n)) for n in draws])
-    tc = np.asarray(trace_cost, np.float64)
-    tb = np.asarray(trace_best, np.float64)
-    R, G = tc.shape
-    clock = tc + (np.arange(1, G + 1) * pop * overhead_us)[None, :]
-    val = np.where(tb < PENALTY, tb, base.median)
-    score = np.empty((R, K))
-    for r in range(R):
-        g = np.searchsorted(clock[r], times, side="right") - 1      # last generation ended by t
-        v = np.where(g >= 0, val[r, np.maximum(g, 0)], base.median)
-        den = E - base.opt
+    den = E - base.opt
+    score = np.empty((len(events), K))
+    for r, (gen, idx, clk, val) in enumerate(events):
+        clock = np.asarray(clk, np.float64) + (np.asarray(gen, np.float64) * pop + np.asarray(idx, np.float64) + 1) * overhead_us
+        v_ev = np.where(np.asarray(val, np.float64) < PENALTY, np.asarray(val, np.float64), base.median)
+        e = np.searchsorted(clock, times, side="right") - 1          # last event by time t
+        v = np.where(e >= 0, v_ev[np.maximum(e, 0)] if len(v_ev) else base.median, base.median)
         score[r] = np.where(den > 0, (E - v) / np.where(den > 0, den, 1.0), (v <= base.opt).astype(np.float64))
     return {"per_run": score.mean(axis=1), "per_time": score.mean(axis=0), "budget_us": B,
             "budget_draws": n_star, "times_us": times, "baseline": E}

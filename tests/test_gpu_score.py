@@ -11,6 +11,8 @@ from tests.helpers import Pair
 
 pytestmark = pytest.mark.gpu
 
+P_EVENTS = 512
+
 
 @pytest.fixture(scope="module")
 def spaces(oracle_mod):
@@ -45,13 +47,14 @@ def test_batch_trace_matches_oracle(oracle_mod, spaces, aware, mode):
             (0, "firefly", 20, 10, -np.inf), (1, "de", 160, 11, -np.inf)]
     b = ct.Batch([q.sp for q in spaces], runs, constraint_aware=aware)
     G = 14
-    b.set_trace(G)
+    b.set_trace(G, events=P_EVENTS)
     if mode == "step":
         for _ in range(G):
             b.step()
     else:
         b.run_graph(G)
     tr = b.trace()
+    ev = b.events()
     for r, (si, kind, pop, seed, _) in enumerate(runs):
         q = spaces[si]
         E = oracle_mod.run(kind, q.osp, q.okeys, q.table, pop=pop, gens=G - 1, seed=seed, cost=q.cost,
@@ -59,23 +62,27 @@ def test_batch_trace_matches_oracle(oracle_mod, spaces, aware, mode):
         assert np.array_equal(tr["cost"][r], E["cost"]), (r, kind)
         assert np.array_equal(tr["best_fit"][r], E["best_fit"]), (r, kind)
         assert np.array_equal(tr["n_unique"][r], E["n_unique"]), (r, kind)
+        for a, f in zip(ev[r], ("ev_gen", "ev_idx", "ev_clock", "ev_fit")):
+            assert np.array_equal(a, E[f].astype(a.dtype)), (r, kind, f)
 
 
-def test_score_from_gpu_traces_matches_oracle(oracle_mod, spaces):
+def test_score_from_gpu_events_matches_oracle(oracle_mod, spaces):
     from paper_2606_28372_b300 import catune as ct
     q = spaces[1]
-    G, P = 60, 20
-    runs = [(0, "ga", P, s, -np.inf) for s in range(8)]
+    G = 60
+    runs = [(0, k, P, s, -np.inf) for s in range(4) for k, P in (("ga", 20), ("de", 160), ("pso", 30))]
     b = ct.Batch([q.sp], runs)
-    b.set_trace(G)
+    b.set_trace(G, events=P_EVENTS)
     b.run_graph(G)
-    tr = b.trace()
-    got = PS.run_scores(PS.Baseline(q.table, q.cost, 1000.0), tr["cost"], tr["best_fit"], pop=P, overhead_us=1000.0)
-    ec, eb = [], []
-    for _, _, _, seed, _ in runs:
-        E = oracle_mod.run("ga", q.osp, q.okeys, q.table, pop=P, gens=G - 1, seed=seed, cost=q.cost)
-        ec.append(E["cost"])
-        eb.append(E["best_fit"])
-    exp = OS.run_score(q.table, q.cost, np.array(ec), np.array(eb), pop=P, overhead_us=1000.0)
-    assert np.allclose(got["per_run"], exp["per_run"], rtol=1e-9, atol=1e-9)
-    assert (got["per_run"] > -5).all() and (got["per_run"] <= 1).all()
+    ev = b.events()
+    base = PS.Baseline(q.table, q.cost, 1000.0)
+    for kind, P in (("ga", 20), ("de", 160), ("pso", 30)):
+        rows = [r for r, run in enumerate(runs) if run[1] == kind]
+        got = PS.run_scores(base, [ev[r] for r in rows], pop=P, overhead_us=1000.0)
+        oev = []
+        for r in rows:
+            E = oracle_mod.run(kind, q.osp, q.okeys, q.table, pop=P, gens=G - 1, seed=runs[r][3], cost=q.cost)
+            oev.append((E["ev_gen"], E["ev_idx"], E["ev_clock"], E["ev_fit"]))
+        exp = OS.run_score(q.table, q.cost, oev, pop=P, overhead_us=1000.0)
+        assert np.allclose(got["per_run"], exp["per_run"], rtol=1e-9, atol=1e-9), kind
+        assert (got["per_run"] <= 1).all()

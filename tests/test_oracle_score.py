@@ -38,30 +38,34 @@ def test_budget_is_the_first_crossing():
     assert B == pytest.approx(n * (c.mean() + 500.0))
 
 
+def _ev(gen, idx, clk, val):
+    return (np.asarray(gen), np.asarray(idx), np.asarray(clk, np.float64), np.asarray(val, np.float64))
+
+
 def test_score_fixed_points():
     rng = np.random.default_rng(5)
     f = rng.lognormal(size=2000)
     c = np.full(2000, 1000)
     P, K = 4, 20
-    out = S.run_score(f, c, np.zeros((1, 1)), np.zeros((1, 1)), pop=P, K=K)
+    out = S.run_score(f, c, [_ev([0], [0], [0], [f.max()])], pop=P, K=K)
     times, base = out["times_us"], out["baseline"]
     # a run that holds the optimum from the first instant scores 1
-    r1 = S.run_score(f, c, np.array([[0]]), np.array([[f.min()]]), pop=P, K=K)
+    r1 = S.run_score(f, c, [_ev([0], [0], [0], [f.min()])], pop=P, K=K)
     assert r1["per_run"][0] == pytest.approx(1.0)
     # a run whose value is the baseline's at every sampled time scores 0
-    tc = (times - 0.5).reshape(1, -1)
-    r0 = S.run_score(f, c, tc, base.reshape(1, -1), pop=P, K=K)
+    z = np.zeros(K, int)
+    r0 = S.run_score(f, c, [_ev(z, z, times - 0.5, base)], pop=P, K=K)
     assert r0["per_run"][0] == pytest.approx(0.0, abs=1e-12)
     # a run that never evaluates a valid configuration scores below 0
-    rn = S.run_score(f, c, np.zeros((1, 30)), np.full((1, 30), 1e20), pop=P, K=K)
+    rn = S.run_score(f, c, [_ev([0], [0], [0], [1e20])], pop=P, K=K)
     assert rn["per_run"][0] < 0
-    # value is taken at the last generation that ended by t, with the per-proposal overhead
+    # an event counts from its own evaluation on, proposal overheads included
     o = 10.0
-    ref = S.run_score(f, c, np.zeros((1, 1)), np.zeros((1, 1)), pop=P, overhead_us=o, K=K)
+    ref = S.run_score(f, c, [_ev([], [], [], [])], pop=P, overhead_us=o, K=K)
     times, base = ref["times_us"], ref["baseline"]
-    assert P * o <= times[0]
-    tc = np.array([[0, times[4] - 2 * P * o]])      # generation 1 ends exactly at the 5th time
-    tr = S.run_score(f, c, tc, np.array([[np.median(f), f.min()]]), pop=P, overhead_us=o, K=K)
+    assert o <= times[0]
+    ev = _ev([0, 1], [0, P - 1], [0, times[4] - 2 * P * o], [np.median(f), f.min()])
+    tr = S.run_score(f, c, [ev], pop=P, overhead_us=o, K=K)     # the second ends exactly at the 5th time
     head = sum((b - np.median(f)) / (b - f.min()) for b in base[:4])
     assert tr["per_run"][0] == pytest.approx((head + (K - 4)) / K, rel=1e-12)
 
@@ -84,3 +88,32 @@ def test_run_clock_is_the_cost_of_each_configuration_evaluated_once(oracle_mod, 
     assert (T0["cost"] == 0).all()
     for f in ("evalk", "best_fit", "n_unique"):      # the clock does not steer the run
         assert np.array_equal(T0[f], T[f])
+
+
+@pytest.mark.parametrize("kind", ["de", "ga", "pso"])
+@pytest.mark.parametrize("aware", [1, 0])
+def test_event_log_is_the_running_best_in_evaluation_order(oracle_mod, kind, aware):
+    """Events = strict improvements of the running minimum over the evaluated fitness, read
+    generation by generation in population order; each carries the running sum of the costs of
+    first evaluations up to it."""
+    from paper_2606_28372_b300 import workloads as W
+    sd = W.medium_space()
+    sp = oracle_mod.from_def(sd)
+    keys = oracle_mod.valid_keys(sp)
+    table = W.smooth_table(sd, oracle_mod.unpack(sp, keys), seed=0)
+    cost = W.eval_cost_table(table, seed=1)
+    T = oracle_mod.run(kind, sp, keys, table, pop=24, gens=20, seed=6, cost=cost, constraint_aware=aware)
+    fit, evk = T["fit"].ravel(), T["evalk"].ravel()
+    rk = oracle_mod.lookup(keys, evk)
+    seen, clock, best = set(), 0, np.inf
+    exp = []
+    for e in range(len(fit)):
+        if rk[e] >= 0 and rk[e] not in seen:
+            seen.add(rk[e])
+            clock += int(cost[rk[e]])
+        if fit[e] < best:
+            best = fit[e]
+            exp.append((e // 24, e % 24, clock, fit[e]))
+    got = list(zip(T["ev_gen"], T["ev_idx"], T["ev_clock"], T["ev_fit"]))
+    assert [(int(a), int(b), int(c), np.float32(d)) for a, b, c, d in got] == \
+        [(int(a), int(b), int(c), np.float32(d)) for a, b, c, d in exp]

@@ -20,24 +20,29 @@ def test_baseline_and_budget_match_the_oracle(M, seed):
     assert n1 == n2 and B1 == pytest.approx(B2, rel=1e-12)
 
 
-def _traces(f, R, G, P, seed):
-    """Monotone synthetic traces: per generation some new evaluations and a non-increasing best;
-    some runs start with penalised (nothing valid yet) generations."""
+def _events(f, R, P, seed):
+    """Synthetic event logs: increasing (generation, index) positions and clocks, decreasing
+    values; some runs start with penalised events (nothing valid yet)."""
     rng = np.random.default_rng(seed)
-    cost = np.cumsum(rng.integers(0, P, size=(R, G)) * 1_600_000, axis=1).astype(np.uint64)
-    best = np.minimum.accumulate(rng.choice(f, size=(R, G)), axis=1).astype(np.float32)
-    for r in range(0, R, 3):
-        best[r, : rng.integers(0, G)] = 1e20
-    return cost, best
+    out = []
+    for r in range(R):
+        n = int(rng.integers(0, 30))
+        pos = np.sort(rng.choice(60 * P, size=n, replace=False))
+        clk = np.cumsum(rng.integers(0, 40, size=n)) * 1_600_000
+        val = np.sort(rng.choice(f, size=n))[::-1].astype(np.float32)
+        if r % 3 == 0 and n:
+            val[: rng.integers(0, n)] = 1e20
+        out.append((pos // P, pos % P, clk.astype(np.uint64), val))
+    return out
 
 
 @pytest.mark.parametrize("overhead", [0.0, 1000.0])
 def test_scores_match_the_oracle(overhead):
     f = W.lognormal_table(5000, seed=3)
     c = W.eval_cost_table(f, seed=3)
-    cost, best = _traces(f, 12, 60, 20, 4)
-    a = PS.run_scores(PS.Baseline(f, c, overhead), cost, best, pop=20, overhead_us=overhead, K=40)
-    e = OS.run_score(f, c, cost, best, pop=20, overhead_us=overhead, K=40)
+    ev = _events(f, 12, 20, 4)
+    a = PS.run_scores(PS.Baseline(f, c, overhead), ev, pop=20, overhead_us=overhead, K=40)
+    e = OS.run_score(f, c, ev, pop=20, overhead_us=overhead, K=40)
     assert np.allclose(a["per_run"], e["per_run"], rtol=1e-9, atol=1e-9)
     assert np.allclose(a["per_time"], e["per_time"], rtol=1e-9, atol=1e-9)
     assert a["budget_draws"] == e["budget_draws"]
