@@ -348,6 +348,12 @@ def run_ours(args):
     # ---- sub-metrics ----
     sub = {"valid_configs_per_s": value, "cartesian_points_covered_per_s": world * sd.cartesian_size * args.steps / (ms / 1000.0)}
     sub.update(repair_rates(sp, sd, torch, ct, dev))
+    sub.update(repair_paper_rates(sp, sd, torch, ct, dev, "large"))
+    med_sd = W.medium_space()
+    med = ct.Space.from_def(med_sd)
+    med.build()
+    sub.update(repair_paper_rates(med, med_sd, torch, ct, dev, "medium", n=256))
+    del med
     sub.update(plain_runs(torch, ct, W, dev))
     sub.update(batched_runs(torch, ct, W, dev))
     sub.update(surrogate_vs_plain(torch, ct, W, dev))
@@ -425,6 +431,42 @@ def repair_rates(sp, sd, torch, ct, dev):
     sp.set_repair_mode(0, 0)
     res["scan_only_repair"] = scan
     return res
+
+
+def repair_paper_rates(sp, sd, torch, ct, dev, label, n=64, reps=3):
+    """The paper's repair rules (index distance, Algorithm 2, Algorithm 3) on `n` DE-like
+    perturbations of valid keys: candidates/s, and the streaming pass's rate in
+    (valid key, pending candidate) pairs/s and key bytes/s (one pass per 8 pending)."""
+    from paper_2606_28372_b300 import workloads as W
+    keys = sp.keys()
+    nv = keys.numel()
+    ranks = torch.from_numpy(W.random_ranks(nv, n, seed=41)).to(dev)
+    base = sp.unpack(keys[ranks].cpu().numpy().view(np.uint64))
+    tup = W.perturbed_tuples(sd, base, seed=42)
+    cand = torch.from_numpy(sp.pack(tup).view(np.int64)).to(dev)
+    rk = torch.empty(n, dtype=torch.int64, device=dev)
+    sp.lookup(cand, rk)
+    pending = int((rk < 0).sum())
+    r = np.array(sd.n_values)
+    eps = float(np.float32(1.0 / (r.max() - 1)))
+    pos = torch.from_numpy((tup * eps).astype(np.float32).ravel()).to(dev)
+    words = torch.from_numpy(np.arange(n, dtype=np.int32) * 2654435761 % (1 << 31)).to(dev)
+    out = torch.empty(n, dtype=torch.int64, device=dev)
+    res = {"pending": pending, "candidates": n, "n_valid": nv}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for rule in (1, 2, 3):
+        sp.repair_paper(rule, cand, out, pos=pos, eps=eps, words=words)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            sp.repair_paper(rule, cand, out, pos=pos, eps=eps, words=words)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / reps / 1000.0
+        res[f"rule{rule}"] = {"ms_per_call": 1000 * sec, "candidates_per_s": n / sec,
+                              "pairs_per_s": nv * pending / sec,
+                              "key_stream_GBps": 8 * nv * ((pending + 7) // 8) / sec / 1e9}
+    return {f"repair_paper_{label}": res}
 
 
 def plain_runs(torch, ct, W, dev, gens=500, chunk=50):
