@@ -382,6 +382,9 @@ typedef struct {
     float target;        /* record unique evaluations when best <= target */
     int repair_rule;     /* 0: Hamming argmin for all; 1: the paper's rule per optimizer */
     int aware;           /* 1: constraint-aware; 0: random Cartesian start, no repair, penalty */
+    int de_mutation;     /* 0 best1, 1 rand1, 2 rand2, 3 best2, 4 currenttobest1, 5 randtobest1 */
+    int de_crossover;    /* 0 binomial, 1 exponential */
+    int ga_crossover;    /* 0 single point, 1 two point, 2 uniform, 3 disruptive uniform */
     const uint32_t *cost; /* simulated time of evaluating each valid configuration (per rank), or NULL */
 } or_params;
 
@@ -625,34 +628,90 @@ int64_t or_mlp_param_count(int D, int H);
 
 /* DE best1bin trial for target i, drawing from the RNG streams of individual si
  * (si = i for the plain method; i + s*P for proposal s of a surrogate pool). */
+/* k distinct population indices other than i, each uniform over what is left: draw t takes
+ * word t of MUT_PICK below P-1-t and steps over the excluded indices in ascending order */
+static void de_picks(int P, int i, int k, uint64_t seed, uint32_t si, int g, uint32_t *r)
+{
+    uint32_t ex[8];
+    int ne = 1;
+    ex[0] = (uint32_t)i;
+    for (int t = 0; t < k; t++) {
+        uint32_t v = uint_below(rng_word(seed, si, g, P_MUT_PICK, (uint32_t)t), (uint32_t)(P - 1 - t));
+        for (int e = 0; e < ne; e++)
+            if (v >= ex[e]) v++;
+        r[t] = v;
+        int p = ne++;                              /* keep ex sorted */
+        while (p > 0 && ex[p - 1] > v) { ex[p] = ex[p - 1]; p--; }
+        ex[p] = v;
+    }
+}
+
+/* random partners each DE mutation uses */
+int or_de_partners(int mutation)
+{
+    static const int k[6] = {2, 3, 5, 4, 2, 3};   /* best1 rand1 rand2 best2 currenttobest1 randtobest1 */
+    return mutation >= 0 && mutation < 6 ? k[mutation] : -1;
+}
+
 static uint64_t de_trial(ctx_t *C, const uint64_t *X, uint64_t de_best, int P, int i, uint32_t si, int g,
                          uint64_t seed, const or_params *prm)
 {
     const int N = C->L.n;
-    int32_t ia[OR_MAXP], ib[OR_MAXP], ic[OR_MAXP], id[OR_MAXP], t[OR_MAXP];
-    unpack(&C->L, de_best, ia);
-    uint32_t w0 = rng_word(seed, si, g, P_MUT_PICK, 0), w1 = rng_word(seed, si, g, P_MUT_PICK, 1);
-    uint32_t r2 = uint_below(w0, (uint32_t)P - 1);
-    if (r2 >= (uint32_t)i) r2++;
-    uint32_t r3 = uint_below(w1, (uint32_t)P - 2);
-    uint32_t lo = (uint32_t)i < r2 ? (uint32_t)i : r2, hi = (uint32_t)i < r2 ? r2 : (uint32_t)i;
-    if (r3 >= lo) r3++;
-    if (r3 >= hi) r3++;
-    unpack(&C->L, X[r2], ib);
-    unpack(&C->L, X[r3], ic);
-    unpack(&C->L, X[i], id);
-    uint32_t jrand = uint_below(rng_word(seed, si, g, P_CROSS, 0), (uint32_t)N);
+    const float F = prm->de_F;
+    int32_t best[OR_MAXP], xi[OR_MAXP], x[5][OR_MAXP], v[OR_MAXP], t[OR_MAXP];
+    uint32_t r[5];
+    const int k = or_de_partners(prm->de_mutation);
+    de_picks(P, i, k, seed, si, g, r);
+    unpack(&C->L, de_best, best);
+    unpack(&C->L, X[i], xi);
+    for (int q = 0; q < k; q++) unpack(&C->L, X[r[q]], x[q]);
+    /* Mutate (Algorithm 1 and the variants of Section IV-B), on value indices in fp32, one
+     * rounding per operation in the order written, then round half-even and clip */
     for (int j = 0; j < N; j++) {
-        /* Algorithm 1, Mutate: m = i_r1 + F*(i_r2 - i_r3), round and clip */
-        float diff = (float)(ib[j] - ic[j]);
-        float m = (float)ia[j] + prm->de_F * diff;
+        float m;
+        switch (prm->de_mutation) {
+        case 0:  /* best1: best + F (x0 - x1) */
+            m = (float)best[j] + F * (float)(x[0][j] - x[1][j]);
+            break;
+        case 1:  /* rand1: x0 + F (x1 - x2) */
+            m = (float)x[0][j] + F * (float)(x[1][j] - x[2][j]);
+            break;
+        case 2:  /* rand2: x0 + F (x1 - x2) + F (x3 - x4) */
+            m = ((float)x[0][j] + F * (float)(x[1][j] - x[2][j])) + F * (float)(x[3][j] - x[4][j]);
+            break;
+        case 3:  /* best2: best + F (x0 - x1) + F (x2 - x3) */
+            m = ((float)best[j] + F * (float)(x[0][j] - x[1][j])) + F * (float)(x[2][j] - x[3][j]);
+            break;
+        case 4:  /* currenttobest1: xi + F (best - xi) + F (x0 - x1) */
+            m = ((float)xi[j] + F * (float)(best[j] - xi[j])) + F * (float)(x[0][j] - x[1][j]);
+            break;
+        default: /* randtobest1: x0 + F (best - x0) + F (x1 - x2) */
+            m = ((float)x[0][j] + F * (float)(best[j] - x[0][j])) + F * (float)(x[1][j] - x[2][j]);
+            break;
+        }
         float q = rintf(m);
-        int v = (int)q;
-        if (q < 0.0f) v = 0;
-        if (v > C->L.r[j] - 1) v = C->L.r[j] - 1;
-        /* Algorithm 1, Crossover (binomial) */
-        float rr = u01(rng_word(seed, si, g, P_CROSS, 1 + (uint32_t)j));
-        t[j] = (rr < prm->de_CR || (uint32_t)j == jrand) ? v : id[j];
+        int vv = (int)q;
+        if (q < 0.0f) vv = 0;
+        if (vv > C->L.r[j] - 1) vv = C->L.r[j] - 1;
+        v[j] = vv;
+    }
+    uint32_t j0 = uint_below(rng_word(seed, si, g, P_CROSS, 0), (uint32_t)N);
+    if (prm->de_crossover == 0) {
+        /* binomial (Algorithm 1, Crossover): gene j from v with probability CR, gene j0 always */
+        for (int j = 0; j < N; j++) {
+            float rr = u01(rng_word(seed, si, g, P_CROSS, 1 + (uint32_t)j));
+            t[j] = (rr < prm->de_CR || (uint32_t)j == j0) ? v[j] : xi[j];
+        }
+    } else {
+        /* exponential: from gene j0 on (cyclically) genes come from v; after the first, each
+         * further one only while the draws stay below CR */
+        for (int j = 0; j < N; j++) t[j] = xi[j];
+        t[j0] = v[j0];
+        for (int L = 1; L < N; L++) {
+            if (!(u01(rng_word(seed, si, g, P_CROSS, (uint32_t)L)) < prm->de_CR)) break;
+            int j = (int)((j0 + (uint32_t)L) % (uint32_t)N);
+            t[j] = v[j];
+        }
     }
     return pack(&C->L, t);
 }
@@ -660,18 +719,43 @@ static uint64_t de_trial(ctx_t *C, const uint64_t *X, uint64_t de_best, int P, i
 /* GA pair c: two beta-selected parents of the ranked population, single-point
  * crossover; streams of pair sc. */
 static void ga_pair(ctx_t *C, const uint64_t *X, const int *order, int P, uint32_t sc, int g, uint64_t seed,
-                    uint64_t *child0, uint64_t *child1)
+                    const or_params *prm, uint64_t *child0, uint64_t *child1)
 {
     const int N = C->L.n;
     int32_t ia[OR_MAXP], ib[OR_MAXP], ic[OR_MAXP], id[OR_MAXP];
+    uint8_t from_b[OR_MAXP];                 /* child0 takes gene j from the second parent */
     uint32_t pa = beta_pick(rng_word(seed, sc, g, P_GA_SEL, 0), (uint32_t)P);
     uint32_t pbi = beta_pick(rng_word(seed, sc, g, P_GA_SEL, 1), (uint32_t)P);
-    uint32_t cut = N >= 2 ? 1 + uint_below(rng_word(seed, sc, g, P_GA_CUT, 0), (uint32_t)N - 1) : 1;
     unpack(&C->L, X[order[pa]], ia);
     unpack(&C->L, X[order[pbi]], ib);
+    for (int j = 0; j < N; j++) from_b[j] = 0;
+    int kind = prm->ga_crossover;
+    if (kind == 1 && N < 3) kind = 0;       /* two cut points need three genes */
+    if (kind == 0) {                         /* single point: genes from the cut on */
+        uint32_t cut = N >= 2 ? 1 + uint_below(rng_word(seed, sc, g, P_GA_CUT, 0), (uint32_t)N - 1) : 1;
+        for (int j = 0; j < N; j++) from_b[j] = (uint32_t)j >= cut;
+    } else if (kind == 1) {                  /* two points: genes in [lo, hi) */
+        uint32_t c1 = 1 + uint_below(rng_word(seed, sc, g, P_GA_CUT, 0), (uint32_t)N - 1);
+        uint32_t c2 = 1 + uint_below(rng_word(seed, sc, g, P_GA_CUT, 1), (uint32_t)N - 2);
+        if (c2 >= c1) c2++;
+        uint32_t lo = c1 < c2 ? c1 : c2, hi = c1 < c2 ? c2 : c1;
+        for (int j = 0; j < N; j++) from_b[j] = (uint32_t)j >= lo && (uint32_t)j < hi;
+    } else if (kind == 2) {                  /* uniform: each gene by a fair draw */
+        for (int j = 0; j < N; j++) from_b[j] = !(u01(rng_word(seed, sc, g, P_GA_CUT, (uint32_t)j)) < 0.5f);
+    } else {                                 /* disruptive uniform: exactly half (rounded down) of
+                                                the genes where the parents differ, chosen uniformly */
+        int D[OR_MAXP], nd = 0;
+        for (int j = 0; j < N; j++)
+            if (ia[j] != ib[j]) D[nd++] = j;
+        for (int t = 0; t < nd / 2; t++) {   /* partial Fisher-Yates over D */
+            int s2 = t + (int)uint_below(rng_word(seed, sc, g, P_GA_CUT, (uint32_t)t), (uint32_t)(nd - t));
+            int tmp = D[t]; D[t] = D[s2]; D[s2] = tmp;
+            from_b[D[t]] = 1;
+        }
+    }
     for (int j = 0; j < N; j++) {
-        ic[j] = (uint32_t)j < cut ? ia[j] : ib[j];
-        id[j] = (uint32_t)j < cut ? ib[j] : ia[j];
+        ic[j] = from_b[j] ? ib[j] : ia[j];
+        id[j] = from_b[j] ? ia[j] : ib[j];
     }
     *child0 = pack(&C->L, ic);
     *child1 = pack(&C->L, id);
@@ -790,6 +874,10 @@ void or_repair_paper(int rule, int n, const int32_t *r, const uint64_t *keys, in
 int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, const float *table,
            int P, int G, uint64_t seed, const or_params *prm, or_trace *T, const or_surr *sg, or_strace *ST)
 {
+    if (or_de_partners(prm->de_mutation) < 0 || prm->de_crossover < 0 || prm->de_crossover > 1 ||
+        prm->ga_crossover < 0 || prm->ga_crossover > 3)
+        return -2;
+    if (kind == K_DE && P < or_de_partners(prm->de_mutation) + 1) return -3;   /* too few partners */
     ctx_t C;
     make_layout(&C.L, n, r);
     C.keys = keys;
@@ -915,7 +1003,7 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
             }
             for (int c = 0; 2 * c < P; c++) {
                 uint64_t k0, k1;
-                ga_pair(&C, X, order, P, (uint32_t)c, g, seed, &k0, &k1);
+                ga_pair(&C, X, order, P, (uint32_t)c, g, seed, prm, &k0, &k1);
                 U[2 * c] = k0;
                 if (2 * c + 1 < P) U[2 * c + 1] = k1;
             }
@@ -943,7 +1031,7 @@ int or_run(int kind, int n, const int32_t *r, const uint64_t *keys, int64_t nv, 
                     uint64_t c0 = 0, c1 = 0;
                     if (kind == K_DE) c0 = de_trial(&C, X, de_best, P, i, (uint32_t)(i + s * P), g, seed, prm);
                     else {
-                        ga_pair(&C, X, order, P, (uint32_t)(i / 2 + s * npairs), g, seed, &c0, &c1);
+                        ga_pair(&C, X, order, P, (uint32_t)(i / 2 + s * npairs), g, seed, prm, &c0, &c1);
                         if (i & 1) c0 = c1;
                     }
                     uint64_t cr = repair_key(&C, c0);

@@ -48,6 +48,7 @@ class _Params(C.Structure):
                 ("pso_c1", C.c_float), ("pso_c2", C.c_float), ("fa_beta0", C.c_float),
                 ("fa_gamma", C.c_float), ("fa_alpha", C.c_float), ("ga_pmut", C.c_float),
                 ("target", C.c_float), ("repair_rule", C.c_int), ("constraint_aware", C.c_int),
+                ("de_mutation", C.c_int), ("de_crossover", C.c_int), ("ga_crossover", C.c_int),
                 ("cost", C.c_void_p)]
 
 
@@ -306,7 +307,12 @@ def beta_pick(w: int, P: int) -> int:
 
 
 DEFAULTS = dict(de_F=0.7, de_CR=0.6, pso_w=0.5, pso_c1=3.0, pso_c2=0.5, fa_beta0=1.0, fa_gamma=1.0,
-                fa_alpha=0.2, ga_pmut=0.2, target=-np.inf, repair_rule=0, constraint_aware=1)
+                fa_alpha=0.2, ga_pmut=0.2, target=-np.inf, repair_rule=0, constraint_aware=1,
+                de_mutation="best1", de_crossover="bin", ga_crossover="single_point")
+DE_MUTATIONS = ["best1", "rand1", "rand2", "best2", "currenttobest1", "randtobest1"]
+DE_CROSSOVERS = ["bin", "exp"]
+GA_CROSSOVERS = ["single_point", "two_point", "uniform", "disruptive_uniform"]
+_ENUMS = {"de_mutation": DE_MUTATIONS, "de_crossover": DE_CROSSOVERS, "ga_crossover": GA_CROSSOVERS}
 
 
 SURROGATE_DEFAULTS = dict(pool=16, H=256, batch=256, steps=8, warm_mult=4, lr=1e-2, mu=0.9, mae_ratio=1.0)
@@ -339,9 +345,18 @@ def run(kind: str, sp: OracleSpace, keys: np.ndarray, table: np.ndarray, pop: in
     cost_arr = None if cost is None else np.ascontiguousarray(cost, dtype=np.uint32)
     if cost_arr is not None:
         assert len(cost_arr) == len(keys)
-    pr = _Params(*[int(prm[f]) if f in ("repair_rule", "constraint_aware") else float(np.float32(prm[f]))
-                   for f, _ in _Params._fields_ if f != "cost"],
-                 None if cost_arr is None else cost_arr.ctypes.data)
+    vals = {}
+    for f, _ in _Params._fields_:
+        if f == "cost":
+            vals[f] = None if cost_arr is None else cost_arr.ctypes.data
+        elif f in _ENUMS:
+            v = prm[f]
+            vals[f] = _ENUMS[f].index(v) if isinstance(v, str) else int(v)
+        elif f in ("repair_rule", "constraint_aware"):
+            vals[f] = int(prm[f])
+        else:
+            vals[f] = float(np.float32(prm[f]))
+    pr = _Params(**vals)
     sg = st = None
     if surrogate is not None:
         cfg = dict(SURROGATE_DEFAULTS)
@@ -361,7 +376,8 @@ def run(kind: str, sp: OracleSpace, keys: np.ndarray, table: np.ndarray, pop: in
     rc = lib().or_run(KIND[kind], n, _ptr(sp.r), _ptr(keys), C.c_int64(len(keys)), _ptr(table),
                       P, G, C.c_uint64(seed), C.byref(pr), C.byref(tr),
                       C.cast(C.byref(sg), C.c_void_p) if sg else None, C.cast(C.byref(st), C.c_void_p) if st else None)
-    assert rc == 0
+    if rc != 0:
+        raise ValueError(f"oracle run rejected its arguments (code {rc})")
     T.pop("logt_ref", None)
     ne = int(T.pop("ev_n")[0])
     for f in ("ev_gen", "ev_idx", "ev_clock", "ev_fit"):
