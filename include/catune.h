@@ -214,6 +214,27 @@ ct_status ct_space_status(ct_space *space, ct_stream stream);
 /* ------------------------------------------------------------------------- */
 typedef enum { CT_DE = 0, CT_PSO = 1, CT_FIREFLY = 2, CT_GA = 3 } ct_opt_kind;
 
+/* DE mutation on value indices (Section IV-B; x0.. are distinct random members other than
+ * the target xi, best the best so far):  best1 = best + F(x0 - x1);  rand1 = x0 + F(x1 - x2);
+ * rand2 = x0 + F(x1 - x2) + F(x3 - x4);  best2 = best + F(x0 - x1) + F(x2 - x3);
+ * currenttobest1 = xi + F(best - xi) + F(x0 - x1);  randtobest1 = x0 + F(best - x0) + F(x1 - x2);
+ * fp32, left to right, then rounded half-even and clipped.  The population must exceed the
+ * number of random members (2, 3, 5, 4, 2, 3). */
+typedef enum {
+    CT_DE_BEST1 = 0, CT_DE_RAND1 = 1, CT_DE_RAND2 = 2, CT_DE_BEST2 = 3, CT_DE_CURRENTTOBEST1 = 4,
+    CT_DE_RANDTOBEST1 = 5
+} ct_de_mutation;
+/* DE crossover: binomial (each gene from the mutant with probability CR, one random gene
+ * always) or exponential (a cyclic run of genes from a random start, extended while the draws
+ * stay below CR). */
+typedef enum { CT_DE_BIN = 0, CT_DE_EXP = 1 } ct_de_crossover;
+/* GA crossover (Section IV-D): one cut point; two cut points (the middle segment swaps; with
+ * fewer than three parameters, one cut); uniform (each gene by a fair draw); disruptive uniform
+ * (exactly half, rounded down, of the genes where the parents differ, chosen uniformly). */
+typedef enum {
+    CT_GA_SINGLE_POINT = 0, CT_GA_TWO_POINT = 1, CT_GA_UNIFORM = 2, CT_GA_DISRUPTIVE_UNIFORM = 3
+} ct_ga_crossover;
+
 typedef struct {
     float de_F, de_CR;               /* Table IV: 0.7, 0.6 (best1bin) */
     float pso_w, pso_c1, pso_c2;     /* Table IV: 0.5, 3.0, 0.5 */
@@ -231,6 +252,9 @@ typedef struct {
                                         value of one random parameter, and a static penalty
                                         CT_PENALTY as the fitness of an invalid configuration
                                         (nothing is evaluated, nothing counted). */
+    int32_t de_mutation;             /* ct_de_mutation (default CT_DE_BEST1, Table IV) */
+    int32_t de_crossover;            /* ct_de_crossover (default CT_DE_BIN) */
+    int32_t ga_crossover;            /* ct_ga_crossover (default CT_GA_SINGLE_POINT, Table IV) */
 } ct_opt_params;
 
 #define CT_PENALTY 1e20f

@@ -58,7 +58,14 @@ class ct_surrogate_params(C.Structure):
 class ct_opt_params(C.Structure):
     _fields_ = [(n, C.c_float) for n in ("de_F", "de_CR", "pso_w", "pso_c1", "pso_c2", "fa_beta0",
                                          "fa_gamma", "fa_alpha", "ga_pmut", "target")] + [("repair_rule", C.c_int32),
-                                                                                          ("constraint_aware", C.c_int32)]
+                                                                                          ("constraint_aware", C.c_int32),
+                                                                                          ("de_mutation", C.c_int32),
+                                                                                          ("de_crossover", C.c_int32),
+                                                                                          ("ga_crossover", C.c_int32)]
+DE_MUTATIONS = ["best1", "rand1", "rand2", "best2", "currenttobest1", "randtobest1"]
+DE_CROSSOVERS = ["bin", "exp"]
+GA_CROSSOVERS = ["single_point", "two_point", "uniform", "disruptive_uniform"]
+_ENUMS = {"de_mutation": DE_MUTATIONS, "de_crossover": DE_CROSSOVERS, "ga_crossover": GA_CROSSOVERS}
 
 
 _lib = None
@@ -376,7 +383,10 @@ def default_params(**over):
     p = ct_opt_params()
     lib().ct_opt_params_default(C.byref(p))
     for k, v in over.items():
-        setattr(p, k, int(v) if k in ("repair_rule", "constraint_aware") else float(np.float32(v)))
+        if k in _ENUMS:
+            setattr(p, k, _ENUMS[k].index(v) if isinstance(v, str) else int(v))
+        else:
+            setattr(p, k, int(v) if k in ("repair_rule", "constraint_aware") else float(np.float32(v)))
     return p
 
 

@@ -416,6 +416,12 @@ ct_status ct_batch_create(ct_space* const* spaces, int32_t n_spaces, const ct_ba
     bt->spaces.assign(spaces, spaces + n_spaces);
     bt->runs_h.assign(runs, runs + n_runs);
     if (params) bt->prm = *params; else ct_opt_params_default(&bt->prm);
+    for (int r = 0; r < n_runs; ++r)
+        if (const char* why = check_operators(bt->prm, runs[r].kind, runs[r].pop)) {
+            delete bt;
+            set_error("run %d: %s", r, why);
+            return CT_ERR_INVALID_ARG;
+        }
     bt->brun.resize(n_runs);
     std::vector<std::pair<double, int>> cost(n_runs);
     for (int r = 0; r < n_runs; ++r) {

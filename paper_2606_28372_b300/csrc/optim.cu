@@ -98,6 +98,9 @@ void ct_opt_params_default(ct_opt_params* p) {
     p->target = -__builtin_inff();
     p->repair_rule = 0;
     p->constraint_aware = 1;
+    p->de_mutation = CT_DE_BEST1;
+    p->de_crossover = CT_DE_BIN;
+    p->ga_crossover = CT_GA_SINGLE_POINT;
 }
 
 ct_status ct_opt_create(ct_space* s, ct_opt_kind kind, const ct_opt_params* params, int32_t pop, uint64_t seed, ct_opt** out) {
@@ -107,6 +110,11 @@ ct_status ct_opt_create(ct_space* s, ct_opt_kind kind, const ct_opt_params* para
     if (pop < 3 || pop > CT_MAX_POP) { set_error("pop must be in [3, %d]", CT_MAX_POP); return CT_ERR_INVALID_ARG; }
     if (!s->built || s->n_valid == 0) { set_error("space not built or empty"); return CT_ERR_STATE; }
     if (!s->fit) { set_error("no fitness table"); return CT_ERR_STATE; }
+    {
+        ct_opt_params chk;
+        if (params) chk = *params; else ct_opt_params_default(&chk);
+        if (const char* why = check_operators(chk, kind, pop)) { set_error("%s", why); return CT_ERR_INVALID_ARG; }
+    }
     ct_opt* o = new (std::nothrow) ct_opt();
     if (!o) { set_error("host allocation failed"); return CT_ERR_OOM; }
     o->s = s; o->kind = kind; o->P = pop; o->N = s->h.n; o->seed = seed;

@@ -42,6 +42,27 @@ struct OptArgs {
 };
 
 constexpr int OPT_THREADS = 256;
+constexpr int DE_MAX_PARTNERS = 5;
+
+// random partners each DE mutation draws (-1: unknown mutation)
+__host__ __device__ __forceinline__ int de_partners(int mutation) {
+    switch (mutation) {
+    case CT_DE_BEST1: case CT_DE_CURRENTTOBEST1: return 2;
+    case CT_DE_RAND1: case CT_DE_RANDTOBEST1: return 3;
+    case CT_DE_BEST2: return 4;
+    case CT_DE_RAND2: return 5;
+    default: return -1;
+    }
+}
+
+// operator choices and population size: CT_OK or an error message
+static inline const char* check_operators(const ct_opt_params& p, int kind, int pop) {
+    if (de_partners(p.de_mutation) < 0) return "unknown DE mutation";
+    if (p.de_crossover != CT_DE_BIN && p.de_crossover != CT_DE_EXP) return "unknown DE crossover";
+    if (p.ga_crossover < CT_GA_SINGLE_POINT || p.ga_crossover > CT_GA_DISRUPTIVE_UNIFORM) return "unknown GA crossover";
+    if (kind == CT_DE && pop < de_partners(p.de_mutation) + 1) return "DE population too small for its mutation";
+    return nullptr;
+}
 
 __device__ __forceinline__ float clip01(float v) { return v < 0.0f ? 0.0f : (v > 1.0f ? 1.0f : v); }
 
@@ -146,32 +167,84 @@ static __device__ void propose_dev(const OptArgs& a, uint32_t gen, uint64_t* __r
     const DevSpace* sp = a.sp;
     if (a.kind == CT_DE) {
         const uint64_t best = a.st->de_best;
+        const int mut = a.prm.de_mutation;
+        const int k = de_partners(mut);
+        const float F = a.prm.de_F, CR = a.prm.de_CR;
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
-            uint32_t w[4];
             const uint32_t si = (uint32_t)(i + s * P);
-            rng_block(a.seed, si, gen, PU_MUT_PICK, 0, w);
-            uint32_t r2 = uint_below(w[0], (uint32_t)P - 1);
-            if (r2 >= (uint32_t)i) ++r2;
-            uint32_t r3 = uint_below(w[1], (uint32_t)P - 2);
-            const uint32_t lo = min((uint32_t)i, r2), hi = max((uint32_t)i, r2);
-            if (r3 >= lo) ++r3;
-            if (r3 >= hi) ++r3;
-            const uint64_t x2 = a.X[r2], x3 = a.X[r3], xi = a.X[i];
+            // k distinct partners other than i: draw t is uniform below P-1-t and steps over
+            // the excluded indices in ascending order
+            uint32_t ex[DE_MAX_PARTNERS + 1], w[4];
+            uint64_t xr[DE_MAX_PARTNERS];
+            int ne = 1;
+            ex[0] = (uint32_t)i;
+            for (int t = 0; t < k; ++t) {
+                if ((t & 3) == 0) rng_block(a.seed, si, gen, PU_MUT_PICK, (uint32_t)t >> 2, w);
+                uint32_t v = uint_below(w[t & 3], (uint32_t)(P - 1 - t));
+                for (int e = 0; e < ne; ++e)
+                    if (v >= ex[e]) ++v;
+                xr[t] = a.X[v];
+                int p = ne++;
+                while (p > 0 && ex[p - 1] > v) { ex[p] = ex[p - 1]; --p; }
+                ex[p] = v;
+            }
+            const uint64_t xi = a.X[i];
+            // crossover: which genes come from the mutant
             uint32_t cw[4];
             rng_block(a.seed, si, gen, PU_CROSS, 0, cw);
-            const uint32_t jrand = uint_below(cw[0], (uint32_t)N);
+            const uint32_t j0 = uint_below(cw[0], (uint32_t)N);
+            uint32_t take = 1u << j0;
+            if (a.prm.de_crossover == 0) {          // binomial
+                for (int j = 0; j < N; ++j) {
+                    const uint32_t t = 1u + (uint32_t)j;
+                    if ((t & 3u) == 0) rng_block(a.seed, si, gen, PU_CROSS, t >> 2, cw);
+                    if (u01(cw[t & 3u]) < CR) take |= 1u << j;
+                }
+            } else {                                 // exponential: a cyclic run from j0
+                for (int L = 1; L < N; ++L) {
+                    if ((L & 3) == 0) rng_block(a.seed, si, gen, PU_CROSS, (uint32_t)L >> 2, cw);
+                    if (!(u01(cw[L & 3]) < CR)) break;
+                    take |= 1u << ((j0 + (uint32_t)L) % (uint32_t)N);
+                }
+            }
             uint64_t key = 0;
             for (int j = 0; j < N; ++j) {
-                const int ib = field(sp, best, j), i2 = field(sp, x2, j), i3 = field(sp, x3, j);
-                const float m = __fadd_rn((float)ib, __fmul_rn(a.prm.de_F, (float)(i2 - i3)));
-                const float q = rintf(m);
-                int v = (int)q;
-                if (q < 0.0f) v = 0;
-                if (v > sp->r[j] - 1) v = sp->r[j] - 1;
-                const uint32_t t = 1u + (uint32_t)j;
-                if ((t & 3u) == 0) rng_block(a.seed, si, gen, PU_CROSS, t >> 2, cw);
-                const float rr = u01(cw[t & 3u]);
-                const int pick = (rr < a.prm.de_CR || (uint32_t)j == jrand) ? v : field(sp, xi, j);
+                const int ii = field(sp, xi, j);
+                int pick = ii;
+                if (take >> j & 1u) {
+                    const int ib = field(sp, best, j);
+                    int x[DE_MAX_PARTNERS];
+                    for (int t = 0; t < k; ++t) x[t] = field(sp, xr[t], j);
+                    float m;
+                    switch (mut) {   // fp32, one rounding per operation in this order
+                    case CT_DE_BEST1:
+                        m = __fadd_rn((float)ib, __fmul_rn(F, (float)(x[0] - x[1])));
+                        break;
+                    case CT_DE_RAND1:
+                        m = __fadd_rn((float)x[0], __fmul_rn(F, (float)(x[1] - x[2])));
+                        break;
+                    case CT_DE_RAND2:
+                        m = __fadd_rn(__fadd_rn((float)x[0], __fmul_rn(F, (float)(x[1] - x[2]))),
+                                      __fmul_rn(F, (float)(x[3] - x[4])));
+                        break;
+                    case CT_DE_BEST2:
+                        m = __fadd_rn(__fadd_rn((float)ib, __fmul_rn(F, (float)(x[0] - x[1]))),
+                                      __fmul_rn(F, (float)(x[2] - x[3])));
+                        break;
+                    case CT_DE_CURRENTTOBEST1:
+                        m = __fadd_rn(__fadd_rn((float)ii, __fmul_rn(F, (float)(ib - ii))),
+                                      __fmul_rn(F, (float)(x[0] - x[1])));
+                        break;
+                    default:   // CT_DE_RANDTOBEST1
+                        m = __fadd_rn(__fadd_rn((float)x[0], __fmul_rn(F, (float)(ib - x[0]))),
+                                      __fmul_rn(F, (float)(x[1] - x[2])));
+                        break;
+                    }
+                    const float q = rintf(m);
+                    pick = (int)q;
+                    if (q < 0.0f) pick = 0;
+                    if (pick > sp->r[j] - 1) pick = sp->r[j] - 1;
+                }
                 key |= (uint64_t)pick << sp->off[j];
             }
             cand[i] = key;
@@ -243,17 +316,42 @@ static __device__ void propose_dev(const OptArgs& a, uint32_t gen, uint64_t* __r
             const uint32_t sc = (uint32_t)c + (uint32_t)s * npairs;
             rng_block(a.seed, sc, gen, PU_GA_SEL, 0, w);
             const uint32_t pa = beta_pick(w[0], (uint32_t)P), pbk = beta_pick(w[1], (uint32_t)P);
-            uint32_t cut = 1;
-            if (N >= 2) {
-                uint32_t cw[4];
-                rng_block(a.seed, sc, gen, PU_GA_CUT, 0, cw);
-                cut = 1u + uint_below(cw[0], (uint32_t)N - 1);
-            }
             const uint64_t A = a.X[order[pa]], B = a.X[order[pbk]];
-            uint64_t hmask = 0;   // fields of params [0, cut)
-            for (int j = 0; j < (int)cut && j < N; ++j) hmask |= sp->fmask[j];
-            cand[2 * c] = (A & hmask) | (B & ~hmask);
-            if (2 * c + 1 < P) cand[2 * c + 1] = (B & hmask) | (A & ~hmask);
+            int kind = a.prm.ga_crossover;
+            if (kind == CT_GA_TWO_POINT && N < 3) kind = CT_GA_SINGLE_POINT;   // two cuts need three genes
+            uint32_t cw[4];
+            rng_block(a.seed, sc, gen, PU_GA_CUT, 0, cw);
+            uint32_t fromb = 0;   // genes child 0 takes from the second parent
+            if (kind == CT_GA_SINGLE_POINT) {
+                const uint32_t cut = N >= 2 ? 1u + uint_below(cw[0], (uint32_t)N - 1) : 1u;
+                for (int j = (int)cut; j < N; ++j) fromb |= 1u << j;
+            } else if (kind == CT_GA_TWO_POINT) {
+                const uint32_t c1 = 1u + uint_below(cw[0], (uint32_t)N - 1);
+                uint32_t c2 = 1u + uint_below(cw[1], (uint32_t)N - 2);
+                if (c2 >= c1) ++c2;
+                const uint32_t lo = min(c1, c2), hi = max(c1, c2);
+                for (uint32_t j = lo; j < hi; ++j) fromb |= 1u << j;
+            } else if (kind == CT_GA_UNIFORM) {
+                for (int j = 0; j < N; ++j) {
+                    if (j > 0 && (j & 3) == 0) rng_block(a.seed, sc, gen, PU_GA_CUT, (uint32_t)j >> 2, cw);
+                    if (!(u01(cw[j & 3]) < 0.5f)) fromb |= 1u << j;
+                }
+            } else {   // disruptive uniform: half (rounded down) of the differing genes, uniformly
+                int D[MAXP], nd = 0;
+                for (int j = 0; j < N; ++j)
+                    if (field(sp, A, j) != field(sp, B, j)) D[nd++] = j;
+                for (int t = 0; t < nd / 2; ++t) {   // partial Fisher-Yates
+                    if (t > 0 && (t & 3) == 0) rng_block(a.seed, sc, gen, PU_GA_CUT, (uint32_t)t >> 2, cw);
+                    const int s2 = t + (int)uint_below(cw[t & 3], (uint32_t)(nd - t));
+                    const int tmp = D[t]; D[t] = D[s2]; D[s2] = tmp;
+                    fromb |= 1u << D[t];
+                }
+            }
+            uint64_t bmask = 0;
+            for (int j = 0; j < N; ++j)
+                if (fromb >> j & 1u) bmask |= sp->fmask[j];
+            cand[2 * c] = (A & ~bmask) | (B & bmask);
+            if (2 * c + 1 < P) cand[2 * c + 1] = (B & ~bmask) | (A & bmask);
         }
     }
 }
