@@ -358,6 +358,7 @@ def run_ours(args):
     sub.update(batched_runs(torch, ct, W, dev))
     sub.update(surrogate_vs_plain(torch, ct, W, dev))
     sub.update(aware_vs_unaware(torch, ct, W, dev))
+    sub.update(operator_variants(torch, ct, W, dev))
     del opt, table
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -450,7 +451,7 @@ def repair_paper_rates(sp, sd, torch, ct, dev, label, n=64, reps=3):
     r = np.array(sd.n_values)
     eps = float(np.float32(1.0 / (r.max() - 1)))
     pos = torch.from_numpy((tup * eps).astype(np.float32).ravel()).to(dev)
-    words = torch.from_numpy(np.arange(n, dtype=np.int32) * 2654435761 % (1 << 31)).to(dev)
+    words = torch.from_numpy((np.arange(n, dtype=np.int64) * 2654435761 % (1 << 31)).astype(np.int32)).to(dev)
     out = torch.empty(n, dtype=torch.int64, device=dev)
     res = {"pending": pending, "candidates": n, "n_valid": nv}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -556,11 +557,63 @@ def batched_runs(torch, ct, W, dev, n_runs=4096, gens=100, plain_sample=48):
             "batched_median_evals_to_1pct": float(np.median(hits)) if len(hits) else None}
 
 
+def operator_variants(torch, ct, W, dev, seeds=16, gens=1500, overhead_us=1000.0):
+    """Every DE mutation x crossover and every GA crossover (constraint-aware, Table IV
+    populations), `seeds` runs on each of three spaces (density ladder 1.5 % and 6.9 %, tiny),
+    each setting one batch: batched runs/s and the mean Eq. 2 score over the three spaces."""
+    from paper_2606_28372_b300 import score as PS
+    defs = [W.density_space(0), W.density_space(4), W.tiny_space()]
+    spaces, base = [], []
+    for j, sd in enumerate(defs):
+        sp = ct.Space.from_def(sd)
+        nv = sp.build()
+        keys = sp.keys().cpu().numpy().view(np.uint64)
+        t = W.lognormal_table(nv, seed=0) if sd.name == "tiny" else W.smooth_table(sd, sp.unpack(keys), seed=j)
+        c = W.eval_cost_table(t, seed=j)
+        sp._t = torch.from_numpy(t).to(dev)
+        sp._c = torch.from_numpy(c.view(np.int32)).to(dev)
+        sp.set_fitness(sp._t)
+        sp.set_eval_cost(sp._c)
+        spaces.append(sp)
+        base.append(PS.Baseline(t, c, overhead_us))
+    settings = [("de", dict(de_mutation=m, de_crossover=x)) for m in ct.DE_MUTATIONS for x in ct.DE_CROSSOVERS]
+    settings += [("ga", dict(ga_crossover=x)) for x in ct.GA_CROSSOVERS]
+    out = {}
+    for kind, kw in settings:
+        P = PAPER_POP[kind]
+        runs = [(j, kind, P, 104729 * s + j, -np.inf) for j in range(len(defs)) for s in range(seeds)]
+        b = ct.Batch(spaces, runs, **kw)
+        b.set_trace(gens, events=4096)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run_graph(gens)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ev = b.events()
+        del b
+        sc = [float(PS.run_scores(base[j], [ev[r] for r, run in enumerate(runs) if run[0] == j], pop=P,
+                                  overhead_us=overhead_us)["per_run"].mean()) for j in range(len(defs))]
+        name = kind + "_" + "_".join(str(v) for v in kw.values())
+        out[name] = {"score_eq2": float(np.mean(sc)), "score_by_space": dict(zip([d.name for d in defs], sc)),
+                     "runs_per_s": len(runs) / (ms / 1000.0), "batched_ms": ms}
+    return {"operator_variants": {"generations": gens, "seeds": seeds, "settings": out}}
+
+
 def run_aware(args):
     import torch
     from paper_2606_28372_b300 import catune as ct
     from paper_2606_28372_b300 import workloads as W
     print(json.dumps(aware_vs_unaware(torch, ct, W, torch.device("cuda", 0))))
+    return 0
+
+
+def run_variants(args):
+    import torch
+    from paper_2606_28372_b300 import catune as ct
+    from paper_2606_28372_b300 import workloads as W
+    print(json.dumps(operator_variants(torch, ct, W, torch.device("cuda", 0))))
     return 0
 
 
@@ -728,9 +781,10 @@ if __name__ == "__main__":
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--quick", action="store_true", help="headline step only (no e2e, no sub-metrics)")
-    ap.add_argument("--mode", default="step", choices=["step", "scan", "aware"],
+    ap.add_argument("--mode", default="step", choices=["step", "scan", "aware", "variants"],
                     help="scan: only the exhaustive repair scan (scan-only repair of 1, 2, 4 uniform candidates); "
-                         "aware: only the constraint-aware vs non-aware comparison over the density ladder")
+                         "aware: only the constraint-aware vs non-aware comparison over the density ladder; "
+                         "variants: only the DE/GA operator comparison")
     ap.add_argument("--workload", default="large", choices=["large", "large_slice"],
                     help="large_slice: the same kernels on a 146M-key slice, for hardware-counter captures")
     a = ap.parse_args()
@@ -738,4 +792,6 @@ if __name__ == "__main__":
         sys.exit(run_reference(a))
     if a.mode == "aware":
         sys.exit(run_aware(a))
+    if a.mode == "variants":
+        sys.exit(run_variants(a))
     sys.exit(run_scan(a) if a.mode == "scan" else run_ours(a))
