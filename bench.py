@@ -609,6 +609,25 @@ def run_aware(args):
     return 0
 
 
+def run_batched(args):
+    import torch
+    from paper_2606_28372_b300 import catune as ct
+    from paper_2606_28372_b300 import workloads as W
+    print(json.dumps(batched_runs(torch, ct, W, torch.device("cuda", 0))))
+    return 0
+
+
+def run_rules(args):
+    import torch
+    from paper_2606_28372_b300 import catune as ct
+    from paper_2606_28372_b300 import workloads as W
+    sd = W.SPACES[args.workload]()
+    sp = ct.Space.from_def(sd)
+    sp.build()
+    print(json.dumps(repair_paper_rates(sp, sd, torch, ct, torch.device("cuda", 0), args.workload)))
+    return 0
+
+
 def run_variants(args):
     import torch
     from paper_2606_28372_b300 import catune as ct
@@ -781,10 +800,11 @@ if __name__ == "__main__":
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--quick", action="store_true", help="headline step only (no e2e, no sub-metrics)")
-    ap.add_argument("--mode", default="step", choices=["step", "scan", "aware", "variants"],
+    ap.add_argument("--mode", default="step", choices=["step", "scan", "aware", "variants", "batched", "rules"],
                     help="scan: only the exhaustive repair scan (scan-only repair of 1, 2, 4 uniform candidates); "
                          "aware: only the constraint-aware vs non-aware comparison over the density ladder; "
-                         "variants: only the DE/GA operator comparison")
+                         "variants: only the DE/GA operator comparison; batched: only the batched-runs "
+                         "comparison; rules: only the paper's repair rules on --workload")
     ap.add_argument("--workload", default="large", choices=["large", "large_slice"],
                     help="large_slice: the same kernels on a 146M-key slice, for hardware-counter captures")
     a = ap.parse_args()
@@ -794,4 +814,8 @@ if __name__ == "__main__":
         sys.exit(run_aware(a))
     if a.mode == "variants":
         sys.exit(run_variants(a))
+    if a.mode == "batched":
+        sys.exit(run_batched(a))
+    if a.mode == "rules":
+        sys.exit(run_rules(a))
     sys.exit(run_scan(a) if a.mode == "scan" else run_ours(a))
