@@ -404,23 +404,26 @@ __device__ __forceinline__ bool lex_less(float fa, uint64_t ka, float fb, uint64
     return fa < fb || (fa == fb && ka < kb);
 }
 
-// Shared scratch of select_dev (block size <= SEL_MAX_THREADS, pop <= CT_MAX_POP).
+// Shared scratch of select_dev (block size <= MAX_THREADS, pop <= MAX_POP).
 constexpr int SEL_MAX_THREADS = 512;
-struct SelectSmem {
-    float rf[SEL_MAX_THREADS];
-    uint64_t rk[SEL_MAX_THREADS];
-    int ri[SEL_MAX_THREADS];
-    uint64_t xs[CT_MAX_POP];      // population keys before selection
-    uint64_t us[CT_MAX_POP];      // evaluated keys
-    uint8_t pass[CT_MAX_POP];
-    uint8_t acc[CT_MAX_POP];
+template <int MAX_THREADS, int MAX_POP>
+struct SelectSmemT {
+    float rf[MAX_THREADS];
+    uint64_t rk[MAX_THREADS];
+    int ri[MAX_THREADS];
+    uint64_t xs[MAX_POP];      // population keys before selection
+    uint64_t us[MAX_POP];      // evaluated keys
+    uint8_t pass[MAX_POP];
+    uint8_t acc[MAX_POP];
     int init_s;
 };
+using SelectSmem = SelectSmemT<SEL_MAX_THREADS, CT_MAX_POP>;
 
 // Block-wide argmin of (f, index) over the entries each thread offers: smallest f;
 // among equal f the largest index when last_tie, else the smallest.  Entries with
 // idx < 0 are absent.  Returns the winning index (-1 if none) in every thread.
-__device__ __forceinline__ int block_argmin(float f, int idx, bool last_tie, SelectSmem& sm) {
+template <class SM>
+__device__ __forceinline__ int block_argmin(float f, int idx, bool last_tie, SM& sm) {
     const int t = threadIdx.x;
     sm.rf[t] = f;
     sm.ri[t] = idx;
@@ -449,8 +452,9 @@ __device__ __forceinline__ int block_argmin(float f, int idx, bool last_tie, Sel
 // power of two).  Sequential update rules are applied in closed form:
 //   "best <- x_i if f_i <= f(best)" over ascending i ends at the last index with the
 //   minimal f (if that minimum is <= the old best), "... if f_i < ..." at the first.
+template <class SM>
 static __device__ void select_dev(const OptArgs& a, uint32_t gen, const uint64_t* __restrict__ keys,
-                                  const float* __restrict__ fit, SelectSmem& sm) {
+                                  const float* __restrict__ fit, SM& sm) {
     const int P = a.P, N = a.N;
     OptDev* st = a.st;
     const int t = threadIdx.x, nt = blockDim.x;
