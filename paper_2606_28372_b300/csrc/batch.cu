@@ -98,6 +98,7 @@ struct EventSmem {
 struct RepairSmem {
     int32_t pend[BATCH_MAX_POP];
     unsigned long long best[BATCH_MAX_POP];
+    uint64_t fail[BATCH_MAX_POP];   // per pending slot: the constraints the candidate fails
     int npend;
 };
 
@@ -109,8 +110,14 @@ __device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t*
     __syncthreads();
     for (int i = t; i < P; i += nt) {
         const uint64_t c = cand[i];
-        if (valid_key(sp, bs.tables, c)) rep[i] = c;
-        else rs.pend[atomicAdd(&rs.npend, 1)] = i;
+        const uint64_t f = failing_mask(sp, bs.tables, c);
+        if (!f) {
+            rep[i] = c;
+        } else {
+            const int slot = atomicAdd(&rs.npend, 1);
+            rs.pend[slot] = i;
+            rs.fail[slot] = f;
+        }
     }
     __syncthreads();
     for (int d = 1; d <= bs.dmax; ++d) {
@@ -131,8 +138,10 @@ __device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t*
                 const int mid = (lo + hi + 1) >> 1;
                 if (__ldg(prefix + mid) <= j) lo = mid; else hi = mid - 1;
             }
+            const uint32_t S = __ldg(masks + lo);
+            if (!fixes_possible(sp, rs.fail[q], S)) continue;   // no point of S can be valid
             uint32_t local = (uint32_t)(j - __ldg(prefix + lo));
-            uint32_t m = __ldg(masks + lo);
+            uint32_t m = S;
             uint64_t key = u;
             while (m) {
                 const int k = 31 - __clz(m);
@@ -143,14 +152,18 @@ __device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t*
                 const uint32_t uk = (uint32_t)field(sp, u, k);
                 key = (key & ~sp->fmask[k]) | ((uint64_t)(a < uk ? a : a + 1u) << sp->off[k]);
             }
-            if (valid_key(sp, bs.tables, key)) atomicMin(&rs.best[q], (unsigned long long)key);
+            if (valid_changed(sp, bs.tables, key, S)) atomicMin(&rs.best[q], (unsigned long long)key);
         }
         __syncthreads();
         if (t == 0) {
             int n2 = 0;
             for (int q = 0; q < np; ++q) {
-                if (rs.best[q] != ~0ull) rep[rs.pend[q]] = rs.best[q];
-                else rs.pend[n2++] = rs.pend[q];
+                if (rs.best[q] != ~0ull) {
+                    rep[rs.pend[q]] = rs.best[q];
+                } else {
+                    rs.fail[n2] = rs.fail[q];
+                    rs.pend[n2++] = rs.pend[q];
+                }
             }
             rs.npend = n2;
         }

@@ -25,7 +25,7 @@ struct DevCons {
     int32_t outer_stride[MAXP];
     uint64_t table_off;       // word offset of row 0 in the table arena
     uint32_t rows;            // prod of outer value counts
-    uint32_t pad_;
+    uint32_t scope;           // parameters the constraint reads (bit k: parameter k)
 };
 
 // One enumeration block: consecutive parameters [s, e) whose Cartesian product
@@ -197,8 +197,23 @@ __device__ __forceinline__ bool vm_eval(const ct_instr* __restrict__ prog, int p
     return sp == 1 && !(poison & 1u) && st[0] != 0;
 }
 
-// Full-tuple constraint test of an in-domain key: AND over every constraint,
-// tabled ones by one bit of their truth-mask table, the rest interpreted.
+// One constraint at an in-domain key, given the key's point index p in the constraint's
+// block: one bit of its truth-mask table, or the interpreted program.
+__device__ __forceinline__ bool cons_holds(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
+                                          uint64_t key, const DevBlock& bl, int c, int32_t p) {
+    const DevCons& cs = sp->cons[c];
+    if (cs.tabled) {
+        uint32_t o = 0;
+        for (int q = 0; q < cs.n_outer; ++q) o += (uint32_t)field(sp, key, cs.outer_k[q]) * cs.outer_stride[q];
+        const uint32_t wv = __ldg(tables + cs.table_off + (uint64_t)o * bl.W + (p >> 5));
+        return (wv >> (p & 31)) & 1u;
+    }
+    int64_t pv[MAXP];
+    for (int k = 0; k < sp->n; ++k) pv[k] = sp->values[sp->vstart[k] + field(sp, key, k)];
+    return vm_eval(sp->prog, cs.pc, cs.len, pv);
+}
+
+// Full-tuple constraint test of an in-domain key: AND over every constraint.
 __device__ __forceinline__ bool valid_key(const DevSpace* __restrict__ sp,
                                           const uint32_t* __restrict__ tables, uint64_t key) {
     const int nb = sp->n_blocks;
@@ -206,19 +221,52 @@ __device__ __forceinline__ bool valid_key(const DevSpace* __restrict__ sp,
         const DevBlock& bl = sp->blocks[j];
         int32_t p = 0;
         for (int k = bl.s; k < bl.e; ++k) p += field(sp, key, k) * bl.pstride[k - bl.s];
-        for (int c = bl.cons_begin; c < bl.cons_end; ++c) {
-            const DevCons& cs = sp->cons[c];
-            if (cs.tabled) {
-                uint32_t o = 0;
-                for (int q = 0; q < cs.n_outer; ++q) o += (uint32_t)field(sp, key, cs.outer_k[q]) * cs.outer_stride[q];
-                uint32_t wv = __ldg(tables + cs.table_off + (uint64_t)o * bl.W + (p >> 5));
-                if (!((wv >> (p & 31)) & 1u)) return false;
-            } else {
-                int64_t pv[MAXP];
-                for (int k = 0; k < sp->n; ++k) pv[k] = sp->values[sp->vstart[k] + field(sp, key, k)];
-                if (!vm_eval(sp->prog, cs.pc, cs.len, pv)) return false;
-            }
-        }
+        for (int c = bl.cons_begin; c < bl.cons_end; ++c)
+            if (!cons_holds(sp, tables, key, bl, c, p)) return false;
+    }
+    return true;
+}
+
+// The constraints an in-domain key fails (bit c: constraint c); 0 for a valid key.
+__device__ __forceinline__ uint64_t failing_mask(const DevSpace* __restrict__ sp,
+                                                 const uint32_t* __restrict__ tables, uint64_t key) {
+    uint64_t f = 0;
+    const int nb = sp->n_blocks;
+    for (int j = 0; j < nb; ++j) {
+        const DevBlock& bl = sp->blocks[j];
+        int32_t p = 0;
+        for (int k = bl.s; k < bl.e; ++k) p += field(sp, key, k) * bl.pstride[k - bl.s];
+        for (int c = bl.cons_begin; c < bl.cons_end; ++c)
+            if (!cons_holds(sp, tables, key, bl, c, p)) f |= 1ull << c;
+    }
+    return f;
+}
+
+// Changing the parameters of S leaves every constraint that reads none of them as it was.  So
+// a point that differs from a candidate exactly in S can be valid only if each constraint the
+// candidate fails reads a parameter of S ...
+__device__ __forceinline__ bool fixes_possible(const DevSpace* __restrict__ sp, uint64_t fail, uint32_t S) {
+    while (fail) {
+        const int c = __ffsll((long long)fail) - 1;
+        fail &= fail - 1;
+        if (!(sp->cons[c].scope & S)) return false;
+    }
+    return true;
+}
+
+// ... and then it is valid iff the constraints reading a parameter of S hold at it.
+__device__ __forceinline__ bool valid_changed(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
+                                              uint64_t key, uint32_t S) {
+    const int nb = sp->n_blocks;
+    for (int j = 0; j < nb; ++j) {
+        const DevBlock& bl = sp->blocks[j];
+        bool any = false;
+        for (int c = bl.cons_begin; c < bl.cons_end; ++c) any = any || (sp->cons[c].scope & S);
+        if (!any) continue;
+        int32_t p = 0;
+        for (int k = bl.s; k < bl.e; ++k) p += field(sp, key, k) * bl.pstride[k - bl.s];
+        for (int c = bl.cons_begin; c < bl.cons_end; ++c)
+            if ((sp->cons[c].scope & S) && !cons_holds(sp, tables, key, bl, c, p)) return false;
     }
     return true;
 }

@@ -75,6 +75,7 @@ struct RepairScratch {
     DevBuf<int32_t> pend_a, pend_b;    // pending candidate indices
     DevBuf<uint32_t> counts;           // [0]: pending a, [1]: pending b
     DevBuf<unsigned long long> best;   // per pending slot: best key / packed (dist, rank)
+    DevBuf<uint64_t> fail;             // per candidate: the constraints it fails
 };
 
 // Scratch of the paper's repair rules (candidates, adjacency bounds, per-set minima,

@@ -29,10 +29,10 @@ namespace ct {
 // kernels of the regular repair path (search.cu), launched here on the fixed scratch
 __global__ void k_repair_init(const DevSpace* sp, const uint32_t* tables, const uint64_t* cand, int64_t n,
                               uint64_t* out, uint8_t* dist, int32_t* pend, uint32_t* count,
-                              unsigned long long* best, uint32_t* status);
+                              unsigned long long* best, uint32_t* status, uint64_t* fail);
 __global__ void k_ball(const DevSpace* sp, const uint32_t* tables, const uint32_t* masks, const uint64_t* prefix,
                        int n_subsets, uint64_t points, const uint64_t* cand, const int32_t* pend,
-                       const uint32_t* count, unsigned long long* best);
+                       const uint32_t* count, unsigned long long* best, const uint64_t* fail);
 __global__ void k_ball_resolve(int d, const int32_t* pend_in, const uint32_t* count_in,
                                const unsigned long long* best_in, uint64_t* out, uint8_t* dist, int32_t* pend_out,
                                uint32_t* count_out, unsigned long long* best_out);
@@ -102,7 +102,7 @@ extern "C" ct_status ct_repair_noalloc(ct_space* s, const uint64_t* d_cand, int6
     const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
     CT_TRY_CUDA(cudaMemsetAsync(sc->count, 0, sizeof sc->count, st));   // the counters must start at zero
     k_repair_init<<<g1, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, pend[0], cnt[0], best[0],
-                                      s->status.p);
+                                      s->status.p, nullptr);   // no failing-constraint masks: full tests
     count_launch();
     // ball radii already enumerated (the build plans the ones the repair path uses); any
     // candidate left over goes to the exhaustive scan, so the result is exact either way
@@ -113,7 +113,7 @@ extern "C" ct_status ct_repair_noalloc(ct_space* s, const uint64_t* d_cand, int6
         const uint64_t work = (uint64_t)n * br.total;
         const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 16);
         k_ball<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
-                                   d_cand, pend[cur], cnt[cur], best[cur]);
+                                   d_cand, pend[cur], cnt[cur], best[cur], nullptr);
         CT_TRY_CUDA(cudaMemsetAsync(cnt[cur ^ 1], 0, sizeof(uint32_t), st));
         k_ball_resolve<<<g1, 256, 0, st>>>(d, pend[cur], cnt[cur], best[cur], d_out, d_dist, pend[cur ^ 1],
                                            cnt[cur ^ 1], best[cur ^ 1]);

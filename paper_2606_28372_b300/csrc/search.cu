@@ -58,7 +58,8 @@ __global__ void k_evaluate(const DevSpace* __restrict__ sp, const uint64_t* __re
 __global__ void k_repair_init(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
                               const uint64_t* __restrict__ cand, int64_t n, uint64_t* __restrict__ out,
                               uint8_t* __restrict__ dist, int32_t* __restrict__ pend, uint32_t* __restrict__ count,
-                              unsigned long long* __restrict__ best, uint32_t* __restrict__ status) {
+                              unsigned long long* __restrict__ best, uint32_t* __restrict__ status,
+                              uint64_t* __restrict__ fail) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t c = cand[i];
         if (!in_domain(sp, c)) {
@@ -67,22 +68,27 @@ __global__ void k_repair_init(const DevSpace* __restrict__ sp, const uint32_t* _
             atomicOr(status, ST_BAD_CANDIDATE);
             continue;
         }
-        if (valid_key(sp, tables, c)) {
+        const uint64_t f = fail ? failing_mask(sp, tables, c) : (valid_key(sp, tables, c) ? 0ull : 1ull);
+        if (!f) {
             out[i] = c;
             if (dist) dist[i] = 0;
             continue;
         }
+        if (fail) fail[i] = f;   // the constraints the ball search has to fix
         const uint32_t slot = atomicAdd(count, 1u);
         pend[slot] = (int32_t)i;
         best[slot] = NONE;
     }
 }
 
-// every point at Hamming distance exactly d of each pending candidate
+// every point at Hamming distance exactly d of each pending candidate; with the candidates'
+// failing-constraint masks, subsets that cannot fix them are skipped and only the constraints
+// reading a changed parameter are tested
 __global__ void __launch_bounds__(256)
 k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, const uint32_t* __restrict__ masks,
        const uint64_t* __restrict__ prefix, int n_subsets, uint64_t points, const uint64_t* __restrict__ cand,
-       const int32_t* __restrict__ pend, const uint32_t* __restrict__ count, unsigned long long* __restrict__ best) {
+       const int32_t* __restrict__ pend, const uint32_t* __restrict__ count, unsigned long long* __restrict__ best,
+       const uint64_t* __restrict__ fail) {
     const uint64_t total = (uint64_t)(*count) * points;
     for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t q = g / points, j = g - q * points;
@@ -92,8 +98,10 @@ k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, con
             const int mid = (lo + hi + 1) >> 1;
             if (__ldg(prefix + mid) <= j) lo = mid; else hi = mid - 1;
         }
+        const uint32_t S = __ldg(masks + lo);
+        if (fail && !fixes_possible(sp, __ldg(fail + pend[q]), S)) continue;
         uint32_t local = (uint32_t)(j - __ldg(prefix + lo));
-        uint32_t m = __ldg(masks + lo);
+        uint32_t m = S;
         uint64_t key = u;
         while (m) {
             const int k = 31 - __clz(m);
@@ -105,7 +113,8 @@ k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, con
             const uint32_t v = a < uk ? a : a + 1u;
             key = (key & ~sp->fmask[k]) | ((uint64_t)v << sp->off[k]);
         }
-        if (valid_key(sp, tables, key)) atomicMin(best + q, (unsigned long long)key);
+        if (fail ? valid_changed(sp, tables, key, S) : valid_key(sp, tables, key))
+            atomicMin(best + q, (unsigned long long)key);
     }
 }
 
@@ -393,6 +402,7 @@ ct_status repair_reserve(RepairScratch& rs, int64_t n) {
     CT_TRY(rs.pend_b.ensure(n));
     CT_TRY(rs.counts.ensure(2));
     CT_TRY(rs.best.ensure(2 * (size_t)n));
+    CT_TRY(rs.fail.ensure(n));
     return CT_OK;
 }
 
@@ -407,7 +417,8 @@ ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, in
     const int sms = sm_count();
     const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
     CT_TRY_CUDA(cudaMemsetAsync(rs.counts.p, 0, 8, st));
-    k_repair_init<<<g1, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, pend[0], cnt[0], best[0], s->status.p);
+    k_repair_init<<<g1, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, pend[0], cnt[0], best[0], s->status.p,
+                                      rs.fail.p);
     count_launch();
     const int dmax = wanted_radius(s);
     CT_TRY(ensure_balls(s, dmax));   // normally planned already (after the build, at run creation)
@@ -417,7 +428,7 @@ ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, in
         const uint64_t work = (uint64_t)n * br.total;
         const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 4);   // one wave
         k_ball<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
-                                   d_cand, pend[cur], cnt[cur], best[cur]);
+                                   d_cand, pend[cur], cnt[cur], best[cur], rs.fail.p);
         count_launch();
         CT_TRY_CUDA(cudaMemsetAsync(cnt[cur ^ 1], 0, 4, st));
         k_ball_resolve<<<g1, 256, 0, st>>>(d, pend[cur], cnt[cur], best[cur], d_out, d_dist, pend[cur ^ 1],

@@ -569,6 +569,7 @@ static ct_status lower(ct_space* s, int32_t n, const int32_t* nv, const int64_t*
         DevCons& cs = h.cons[ci];
         memset(&cs, 0, sizeof cs);
         cs.pc = rc.pc; cs.len = rc.len; cs.level = rc.level; cs.block = block_of(rc.level);
+        cs.scope = (uint32_t)rc.scope;
         const DevBlock& bl = h.blocks[cs.block];
         uint64_t rows = 1;
         cs.n_outer = 0;
