@@ -402,23 +402,14 @@ static ct_status batch_reset(ct_batch* b) {
 }
 }  // namespace ct
 
-// Ball radius of the in-CTA repair.  One CTA enumerates a pending candidate's ball points
-// itself (subset search, mixed-radix decode, constraint-table tests), so a ball point costs
-// far more than one step of the CTA's key scan; the ball is cut where its cumulative size
-// passes |V| / 32 (the best of |V| / 8 .. |V| / 512 on the 4096-run batched workload: 3.66
-// against 4.85 ms per generation for |V| / 8), and never below radius 1.  An explicit
-// ct_set_repair_mode on the space takes precedence.
+// Ball radius of the in-CTA repair: the ball is cut where its cumulative size passes |V| / 8,
+// never below radius 1; an explicit ct_set_repair_mode on the space takes precedence.  With the
+// failing-constraint pruning a ball point is cheap, and on the 4096-run batched workload the
+// cut at |V| / 4 .. |V| / 16 is flat (2.84-2.88 ms per generation) against 3.19 at |V| / 32 and
+// 3.26 at |V| / 1.
 static int batch_radius(const ct_space* sp) {
     if (sp->repair_mode != 0) return wanted_radius(sp);
-    const double budget = (double)sp->n_valid / 32.0;
-    double cum = 0;
-    int d = 0;
-    for (int r = 1; r <= sp->ball_max; ++r) {
-        cum += (double)sp->ball_total[r];
-        if (cum > budget) break;
-        d = r;
-    }
-    return std::max(d, std::min(1, sp->ball_max));
+    return std::max(auto_radius(sp), std::min(1, sp->ball_max));
 }
 
 extern "C" {
