@@ -198,7 +198,7 @@ def run_reference(args):
 # our arm
 # ------------------------------------------------------------------------------------------
 def traffic_from_profile():
-    """Per-launch DRAM bytes of the emit kernel from the committed ncu summary, if the kernel
+    """Per-launch DRAM bytes of the emit kernel from the committed ncu summary, if the kernel's
     source is unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", "expand_emit_large.md")
     if not os.path.exists(path):
@@ -208,10 +208,20 @@ def traffic_from_profile():
     h = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
     if not (m and h):
         return None
-    src = open(os.path.join(ROOT, "paper_2606_28372_b300", "csrc", "space.cu"), "rb").read()
-    if hashlib.sha256(src).hexdigest()[:16] != h.group(1)[:16]:
+    if kernel_source_hash("k_pemit") != h.group(1)[:16]:
         return None
     return float(m.group(1))
+
+
+def kernel_source_hash(name):
+    """First 16 hex digits of the SHA-256 of a kernel's definition in space.cu (from its
+    `__global__` line to the closing brace at the start of a line)."""
+    src = open(os.path.join(ROOT, "paper_2606_28372_b300", "csrc", "space.cu")).read()
+    m = re.search(r"^__global__[^{;]*?\b" + name + r"\(", src, re.M | re.S)
+    if not m:
+        return None
+    end = src.index("\n}\n", m.start()) + 3
+    return hashlib.sha256(src[m.start():end].encode()).hexdigest()[:16]
 
 
 def run_ours(args):
