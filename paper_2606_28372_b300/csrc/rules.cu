@@ -17,6 +17,9 @@
 // Hamming nearest valid key.  Ranks are packed in 32 bits: |V| < 2^32.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+#include <mutex>
+
 #include "internal.hpp"
 
 namespace ct {
@@ -146,6 +149,197 @@ k_rule_scan(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, 
                 for (int t = 0; t < 3; ++t) c3[q][t] += (m >> t) & 1u;
             }
         }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < RQ; ++q)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            unsigned long long v = RULE == 3 ? (unsigned long long)c3[q][t] : b[q][t];
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+                v = RULE == 3 ? v + w : (w < v ? w : v);
+            }
+            if (lane == 0) red[warp][q][t] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < nq * 3) {
+        const int q = threadIdx.x / 3, t = threadIdx.x % 3;
+        unsigned long long v = RULE == 3 ? 0ull : ~0ull;
+        for (int w = 0; w < RT / 32; ++w) {
+            const unsigned long long x = red[w][q][t];
+            v = RULE == 3 ? v + x : (x < v ? x : v);
+        }
+        if (RULE == 3) cnt[((size_t)(q0 + q) * 3 + t) * gridDim.x + blockIdx.x] = (uint32_t)v;
+        else if (RULE == 1 && t == 0) atomicMin(best + (size_t)(q0 + q) * 3, v);
+        else if (RULE == 2) atomicMin(best + (size_t)(q0 + q) * 3 + t, v);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Table form of the scan for long key slices.  The key's fields are cut into groups of
+// adjacent fields (at most 8 bits, or one wider field of at most 12 bits); for each pending
+// candidate a CTA tabulates, per group and per bit pattern of the group, what the per-field
+// loop above computes for those fields, and a (key, candidate) pair then costs one table read
+// per group:
+//   rule 1: the group's index distance, four candidates to a 64-bit entry (16-bit lanes; the
+//           plan requires sum_k (r_k - 1) < 2^16, so lanes never carry);
+//   rules 2, 3: one byte per candidate: bit 0 "every field within +-1", bit 1 "every field
+//           unchanged or at its lower / higher occurring value", bits 2..7 the number of
+//           changed fields; groups combine by AND of the flags and a byte-wise sum of counts.
+// The minima, counts and (for set members) the fp32 Euclidean distance are those of the loop.
+// ------------------------------------------------------------------------------------
+constexpr int LUT_MAX_GROUPS = 16;
+constexpr int LUT_MIN_SLICE = 32768;             // keys per CTA that amortise the tables
+constexpr size_t LUT_MAX_BYTES = 64 * 1024;
+
+struct LutPlan {
+    int ng, entries;                             // groups; entries of one table set
+    int shift[LUT_MAX_GROUPS];                   // lowest key bit of the group
+    uint32_t mask[LUT_MAX_GROUPS];               // (1 << width) - 1
+    int base[LUT_MAX_GROUPS];                    // first entry of the group
+    int k0[LUT_MAX_GROUPS], k1[LUT_MAX_GROUPS];  // parameters k0..k1 of the group
+};
+
+static bool lut_plan(const ct_space* s, int rule, int64_t slice, LutPlan& pl) {
+    int64_t min_slice = LUT_MIN_SLICE;   // CATUNE_RULE_LUT_MIN_SLICE overrides it (tests)
+    if (const char* env = getenv("CATUNE_RULE_LUT_MIN_SLICE")) min_slice = strtoll(env, nullptr, 10);
+    if (slice < min_slice) return false;
+    const DevSpace& h = s->h;
+    int64_t sum_r = 0;
+    for (int k = 0; k < h.n; ++k) sum_r += h.r[k] - 1;
+    if (rule == 1 && sum_r >= 65536) return false;
+    pl.ng = 0;
+    pl.entries = 0;
+    int k = h.n - 1;                             // the last parameter holds the lowest bits
+    while (k >= 0) {
+        if (pl.ng == LUT_MAX_GROUPS) return false;
+        const int g = pl.ng++;
+        pl.k1[g] = k;
+        pl.shift[g] = h.off[k];
+        int width = h.w[k];
+        if (width > 12) return false;
+        --k;
+        while (k >= 0 && width <= 8 && width + h.w[k] <= 8) width += h.w[k--];
+        pl.k0[g] = k + 1;
+        pl.mask[g] = (1u << width) - 1u;
+        pl.base[g] = pl.entries;
+        pl.entries += 1 << width;
+    }
+    const size_t bytes = (size_t)pl.entries * 8 * (rule == 1 ? 2 : 1);
+    return bytes <= LUT_MAX_BYTES;
+}
+
+template <int RULE>
+__global__ void __launch_bounds__(RT)
+k_rule_scan_lut(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, int64_t nv, int64_t slice,
+                const RuleCand* __restrict__ rc, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
+                const float* __restrict__ pos, float eps, unsigned long long* __restrict__ best,
+                uint32_t* __restrict__ cnt, const __grid_constant__ LutPlan pl) {
+    extern __shared__ unsigned long long tab[];  // rule 1: [2][entries]; rules 2, 3: [entries]
+    __shared__ RuleCand cs[RQ];
+    __shared__ float xs[RQ][MAXP];
+    __shared__ unsigned long long red[RT / 32][RQ][3];
+    const uint32_t total = *count;
+    const uint32_t q0 = blockIdx.y * RQ;
+    if (q0 >= total) return;
+    const int nq = min((uint32_t)RQ, total - q0);
+    const int N = sp->n;
+    for (int e = threadIdx.x; e < nq; e += RT) cs[e] = rc[q0 + e];
+    if (RULE == 2)
+        for (int e = threadIdx.x; e < nq * N; e += RT) xs[e / N][e % N] = pos[(size_t)pend[q0 + e / N] * N + e % N];
+    __syncthreads();
+    for (int e = threadIdx.x; e < pl.entries; e += RT) {
+        int g = 0;
+        while (g + 1 < pl.ng && pl.base[g + 1] <= e) ++g;
+        const uint32_t local = (uint32_t)(e - pl.base[g]);
+        unsigned long long t0 = 0, t1 = 0;
+        for (int q = 0; q < nq; ++q) {
+            int l1 = 0, nd = 0;
+            bool sa = true, adj = true;
+            for (int k = pl.k0[g]; k <= pl.k1[g]; ++k) {
+                const int vk = (int)((local >> (sp->off[k] - pl.shift[g])) & ((1u << sp->w[k]) - 1u));
+                const int uk = field(sp, cs[q].u, k);
+                const int d = vk - uk;
+                l1 += abs(d);
+                if (d != 0) {
+                    ++nd;
+                    if (d > 1 || d < -1) sa = false;
+                    if (vk != cs[q].lo[k] && vk != cs[q].hi[k]) adj = false;
+                }
+            }
+            if (RULE == 1) {
+                if (q < 4) t0 |= (unsigned long long)l1 << (16 * q);
+                else t1 |= (unsigned long long)l1 << (16 * (q - 4));
+            } else {
+                const unsigned long long byte = (sa ? 1ull : 0ull) | (adj ? 2ull : 0ull) | ((unsigned long long)nd << 2);
+                t0 |= byte << (8 * q);
+            }
+        }
+        tab[e] = t0;
+        if (RULE == 1) tab[pl.entries + e] = t1;
+    }
+    __syncthreads();
+    const int64_t lo = (int64_t)blockIdx.x * slice, hi = min(nv, lo + slice);
+    unsigned long long b[RQ][3];
+    uint32_t c3[RQ][3], bl[RQ];
+    int64_t bi[RQ];
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+        b[q][0] = b[q][1] = b[q][2] = ~0ull;
+        c3[q][0] = c3[q][1] = c3[q][2] = 0;
+        bl[q] = ~0u;
+        bi[q] = 0;
+    }
+    for (int64_t i = lo + threadIdx.x; i < hi; i += RT) {
+        const uint64_t v = __ldg(keys + i);
+        if (RULE == 1) {
+            unsigned long long a0 = 0, a1 = 0;
+            for (int g = 0; g < pl.ng; ++g) {
+                const int e = pl.base[g] + (int)((v >> pl.shift[g]) & pl.mask[g]);
+                a0 += tab[e];
+                a1 += tab[pl.entries + e];
+            }
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) {   // first key of the thread's stride wins ties
+                const uint32_t l = (uint32_t)(((q < 4 ? a0 : a1) >> (16 * (q & 3))) & 0xffffu);
+                if (l < bl[q]) { bl[q] = l; bi[q] = i; }
+            }
+        } else {
+            unsigned long long fl = ~0ull, nd = 0;
+            for (int g = 0; g < pl.ng; ++g) {
+                const unsigned long long t = tab[pl.base[g] + (int)((v >> pl.shift[g]) & pl.mask[g])];
+                fl &= t;
+                nd += (t >> 2) & 0x3f3f3f3f3f3f3f3full;
+            }
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) {
+                if (q >= nq) break;
+                const uint32_t n = (uint32_t)((nd >> (8 * q)) & 0xffu);
+                if (n == 0) continue;
+                const uint32_t f = (uint32_t)((fl >> (8 * q)) & 3u);
+                const uint32_t m = f | (n == 1 ? 4u : 0u);
+                if (RULE == 3) {
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) c3[q][t] += (m >> t) & 1u;
+                } else if (m) {
+                    float s = 0.0f;
+                    for (int k = 0; k < N; ++k) {
+                        const float dd = __fsub_rn(__fmul_rn((float)field(sp, v, k), eps), xs[q][k]);
+                        s = __fadd_rn(s, __fmul_rn(dd, dd));
+                    }
+                    const unsigned long long p = ((unsigned long long)__float_as_uint(s) << 32) | (unsigned long long)i;
+#pragma unroll
+                    for (int t = 0; t < 3; ++t)
+                        if ((m >> t) & 1u) b[q][t] = p < b[q][t] ? p : b[q][t];
+                }
+            }
+        }
+    }
+    if (RULE == 1) {
+#pragma unroll
+        for (int q = 0; q < RQ; ++q)
+            if (bl[q] != ~0u) b[q][0] = ((unsigned long long)bl[q] << 32) | (unsigned long long)bi[q];
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -303,17 +497,40 @@ ct_status repair_rule_impl(ct_space* s, RuleScratch& r, int rule, const uint64_t
     const int64_t slice = ((int64_t)s->n_valid + slices - 1) / slices;
     const dim3 grid(slices, (unsigned)((n + RQ - 1) / RQ));
     RuleCand* rc = (RuleCand*)r.rc.p;
+    LutPlan pl;
+    const bool lut = lut_plan(s, rule, slice, pl);
+    const size_t lut_bytes = lut ? (size_t)pl.entries * 8 * (rule == 1 ? 2 : 1) : 0;
+    if (lut) {
+        static std::once_flag once;   // allow the largest table set as dynamic shared memory
+        std::call_once(once, [] {
+            cudaFuncSetAttribute(k_rule_scan_lut<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LUT_MAX_BYTES);
+            cudaFuncSetAttribute(k_rule_scan_lut<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LUT_MAX_BYTES);
+            cudaFuncSetAttribute(k_rule_scan_lut<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LUT_MAX_BYTES);
+        });
+    }
     if (rule == 1) {
-        k_rule_scan<1><<<grid, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p,
-                                            nullptr, 0.0f, r.best.p, nullptr);
+        if (lut)
+            k_rule_scan_lut<1><<<grid, RT, lut_bytes, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p,
+                                                            r.count.p, nullptr, 0.0f, r.best.p, nullptr, pl);
+        else
+            k_rule_scan<1><<<grid, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p,
+                                                nullptr, 0.0f, r.best.p, nullptr);
         k_rule_finish<<<g1, 256, 0, st>>>(s->keys.p, r.pend.p, r.count.p, r.best.p, d_out);
     } else if (rule == 2) {
-        k_rule_scan<2><<<grid, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p,
-                                            d_pos, eps, r.best.p, nullptr);
+        if (lut)
+            k_rule_scan_lut<2><<<grid, RT, lut_bytes, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p,
+                                                            r.count.p, d_pos, eps, r.best.p, nullptr, pl);
+        else
+            k_rule_scan<2><<<grid, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p,
+                                                d_pos, eps, r.best.p, nullptr);
         k_rule_finish<<<g1, 256, 0, st>>>(s->keys.p, r.pend.p, r.count.p, r.best.p, d_out);
     } else {
-        k_rule_scan<3><<<grid, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p,
-                                            nullptr, 0.0f, nullptr, r.cnt.p);
+        if (lut)
+            k_rule_scan_lut<3><<<grid, RT, lut_bytes, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p,
+                                                            r.count.p, nullptr, 0.0f, nullptr, r.cnt.p, pl);
+        else
+            k_rule_scan<3><<<grid, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p,
+                                                nullptr, 0.0f, nullptr, r.cnt.p);
         k_rule3_pick<<<g1, 256, 0, st>>>(r.count.p, r.pend.p, r.cnt.p, slices, d_words, r.target.p);
         k_rule3_select<<<dim3(slices, (unsigned)std::min<int64_t>(n, 64)), RT, 0, st>>>(
             s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p, r.target.p, d_out);

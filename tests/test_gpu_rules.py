@@ -19,7 +19,12 @@ def spaces(oracle_mod):
 
 @pytest.mark.parametrize("name", ["tiny", "medium", "b9"])
 @pytest.mark.parametrize("rule", [1, 2, 3])
-def test_repair_paper_matches_oracle(oracle_mod, spaces, name, rule):
+@pytest.mark.parametrize("lut", [False, True])
+def test_repair_paper_matches_oracle(oracle_mod, spaces, name, rule, lut, monkeypatch):
+    """Both forms of the scan: the per-field loop and the per-candidate tables (forced on these
+    short slices by lowering the slice threshold)."""
+    if lut:
+        monkeypatch.setenv("CATUNE_RULE_LUT_MIN_SLICE", "1")
     p = spaces[name]
     sd, O = p.sd, oracle_mod
     n = 150
@@ -80,6 +85,37 @@ def test_trajectory_with_paper_rules(oracle_mod, spaces, kind, name, pop, gens):
     # the rule changes the run: some evaluated configuration differs from the Hamming rule's
     H = oracle_mod.run(kind, p.osp, p.okeys, p.table, pop=pop, gens=gens, seed=4)
     assert not np.array_equal(H["evalk"], E["evalk"])
+
+
+@pytest.mark.parametrize("kind", ["de", "pso", "ga"])
+def test_trajectory_with_paper_rules_tables(oracle_mod, spaces, kind, monkeypatch):
+    monkeypatch.setenv("CATUNE_RULE_LUT_MIN_SLICE", "1")
+    p = spaces["medium"]
+    E = oracle_mod.run(kind, p.osp, p.okeys, p.table, pop=48, gens=8, seed=5, repair_rule=1)
+    T = step_trace(p, kind, 48, 8, 5, repair_rule=1)
+    for f in ("cand", "evalk", "fit", "popk", "best_key", "n_unique"):
+        assert np.array_equal(T[f], E[f].astype(T[f].dtype)), f
+
+
+def test_repair_paper_tables_at_size(oracle_mod):
+    """A 26.8M-key space: long enough slices that the table form runs by default."""
+    sd = W._space("wide", [(f"p{k}", list(range(8))) for k in range(8)] + [("q", [0, 1])], ["p0 + p1 <= 12"])
+    p = Pair(sd, oracle_mod, table=None)
+    assert len(p.okeys) > 20_000_000
+    n = 12
+    base = oracle_mod.unpack(p.osp, p.okeys[W.random_ranks(len(p.okeys), n, seed=3)])
+    cand = oracle_mod.pack(p.osp, np.clip(base + np.array([[7, 7] + [0] * 7]), 0, 7))   # p0 + p1 > 12
+    r = np.array(sd.n_values)
+    eps = np.float32(1.0 / (r.max() - 1))
+    rng = np.random.default_rng(4)
+    pos = np.clip(oracle_mod.unpack(p.osp, cand) * eps + rng.normal(scale=0.6 * eps, size=(n, len(r))), 0, 1).astype(np.float32)
+    words = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    for rule in (1, 2, 3):
+        exp = oracle_mod.repair_paper(rule, p.osp, p.okeys, cand, pos=pos, eps=eps, words=words)
+        out = torch.empty(n, dtype=torch.int64, device="cuda")
+        p.sp.repair_paper(rule, to_dev_u64(cand), out, pos=torch.from_numpy(pos).cuda(), eps=float(eps),
+                          words=torch.from_numpy(words.view(np.int32)).cuda())
+        assert np.array_equal(from_dev_u64(out), exp), rule
 
 
 @pytest.mark.parametrize("kind", ["de", "ga", "pso"])
