@@ -90,10 +90,15 @@ def test_exponential_crossover_copies_one_cyclic_window(oracle_mod):
     the target with one cyclic window of genes taken from some other member, and the window
     (the start gene plus every further gene while the draws stay below CR) averages about
     1 + CR / (1 - CR) genes."""
-    sd = W._space("free8", [(f"p{k}", list(range(8))) for k in range(8)], [])
+    sd = W._space("free8", [(f"p{k}", list(range(5))) for k in range(8)], [])
     sp = oracle_mod.from_def(sd)
     keys = oracle_mod.valid_keys(sp)
     table = W.lognormal_table(len(keys), seed=2)
+    L = np.arange(1, 9)
+    win = np.zeros((8, 8, 8), bool)                      # [start, length - 1, gene]
+    for s0 in range(8):
+        for li, ln in enumerate(L):
+            win[s0, li, (s0 + np.arange(ln)) % 8] = True
     windows = []
     for seed in range(60):
         T = oracle_mod.run("de", sp, keys, table, pop=4, gens=1, seed=seed, de_mutation="rand1", de_F=0.0,
@@ -101,14 +106,8 @@ def test_exponential_crossover_copies_one_cyclic_window(oracle_mod):
         t = oracle_mod.unpack(sp, T["cand"][1])
         x = oracle_mod.unpack(sp, T["popk"][0])
         for i in range(4):
-            fits = []
-            for y in (x[j] for j in range(4) if j != i):
-                for s0 in range(8):
-                    for L in range(1, 9):
-                        w = np.zeros(8, bool)
-                        w[(s0 + np.arange(L)) % 8] = True
-                        if (t[i] == np.where(w, y, x[i])).all():
-                            fits.append(L)
+            fits = [L[li] for j in range(4) if j != i
+                    for s0, li in zip(*np.nonzero((np.where(win, x[j], x[i]) == t[i]).all(axis=2)))]
             assert fits, (seed, i)
             windows.append(min(fits))
     assert 1.6 < np.mean(windows) < 2.4
