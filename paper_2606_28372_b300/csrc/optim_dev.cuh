@@ -424,32 +424,39 @@ using SelectSmem = SelectSmemT<SEL_MAX_THREADS, CT_MAX_POP>;
 // idx < 0 are absent.  Returns the winning index (-1 if none) in every thread.
 template <class SM>
 __device__ __forceinline__ int block_argmin(float f, int idx, bool last_tie, SM& sm) {
-    const int t = threadIdx.x;
-    sm.rf[t] = f;
-    sm.ri[t] = idx;
-    __syncthreads();
-    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
-        if (t < w) {
-            const float f2 = sm.rf[t + w];
-            const int i2 = sm.ri[t + w];
-            const int i1 = sm.ri[t];
-            bool take = false;
-            if (i2 >= 0) {
-                if (i1 < 0) take = true;
-                else if (f2 < sm.rf[t]) take = true;
-                else if (f2 == sm.rf[t]) take = last_tie ? (i2 > i1) : (i2 < i1);
-            }
-            if (take) { sm.rf[t] = f2; sm.ri[t] = i2; }
-        }
-        __syncthreads();
+    // (f, idx) pairs combine by a total order (absent entries lose), so any reduction order
+    // gives the same winner: shuffles within each warp, then one warp over the warp winners
+    auto better = [last_tie](float f2, int i2, float f1, int i1) {
+        if (i2 < 0) return false;
+        if (i1 < 0 || f2 < f1) return true;
+        return f2 == f1 && (last_tie ? i2 > i1 : i2 < i1);
+    };
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int o = 16; o; o >>= 1) {
+        const float f2 = __shfl_xor_sync(0xffffffffu, f, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (better(f2, i2, f, idx)) { f = f2; idx = i2; }
     }
+    if (lane == 0) { sm.rf[warp] = f; sm.ri[warp] = idx; }
+    __syncthreads();
+    if (warp == 0) {
+        float g = lane < nw ? sm.rf[lane] : 0.0f;
+        int j = lane < nw ? sm.ri[lane] : -1;
+        for (int o = 16; o; o >>= 1) {
+            const float f2 = __shfl_xor_sync(0xffffffffu, g, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, j, o);
+            if (better(f2, i2, g, j)) { g = f2; j = i2; }
+        }
+        if (lane == 0) sm.ri[0] = j;
+    }
+    __syncthreads();
     const int r = sm.ri[0];
     __syncthreads();
     return r;
 }
 
 // Selection / update after evaluation; every thread of the CTA takes part (block size a
-// power of two).  Sequential update rules are applied in closed form:
+// multiple of 32).  Sequential update rules are applied in closed form:
 //   "best <- x_i if f_i <= f(best)" over ascending i ends at the last index with the
 //   minimal f (if that minimum is <= the old best), "... if f_i < ..." at the first.
 template <class SM>
@@ -465,15 +472,18 @@ static __device__ void select_dev(const OptArgs& a, uint32_t gen, const uint64_t
     uint64_t bk = ~0ull;
     for (int i = t; i < P; i += nt)
         if (lex_less(fit[i], sm.us[i], bf, bk)) { bf = fit[i]; bk = sm.us[i]; }
-    sm.rf[t] = bf;
-    sm.rk[t] = bk;
-    __syncthreads();
-    for (int w = nt >> 1; w > 0; w >>= 1) {
-        if (t < w && lex_less(sm.rf[t + w], sm.rk[t + w], sm.rf[t], sm.rk[t])) { sm.rf[t] = sm.rf[t + w]; sm.rk[t] = sm.rk[t + w]; }
-        __syncthreads();
+    for (int o = 16; o; o >>= 1) {   // lexicographic minimum: a total order, any order of reduction
+        const float f2 = __shfl_xor_sync(0xffffffffu, bf, o);
+        const uint64_t k2 = __shfl_xor_sync(0xffffffffu, bk, o);
+        if (lex_less(f2, k2, bf, bk)) { bf = f2; bk = k2; }
     }
+    const int nw = (nt + 31) >> 5;
+    if ((t & 31) == 0) { sm.rf[t >> 5] = bf; sm.rk[t >> 5] = bk; }
+    __syncthreads();
     if (t == 0) {
-        if (lex_less(sm.rf[0], sm.rk[0], st->best_fit, st->best_key)) { st->best_fit = sm.rf[0]; st->best_key = sm.rk[0]; }
+        for (int w = 1; w < nw; ++w)
+            if (lex_less(sm.rf[w], sm.rk[w], bf, bk)) { bf = sm.rf[w]; bk = sm.rk[w]; }
+        if (lex_less(bf, bk, st->best_fit, st->best_key)) { st->best_fit = bf; st->best_key = bk; }
         if (st->hit_gen < 0 && st->best_fit <= a.prm.target) { st->hit_gen = gen; st->hit_evals = (long long)st->n_unique; }
     }
     __syncthreads();
@@ -516,11 +526,12 @@ static __device__ void select_dev(const OptArgs& a, uint32_t gen, const uint64_t
                 }
             }
             const int w = block_argmin(last >= 0 ? lf : 0.0f, last, true, sm);
-            sm.ri[t] = n_acc;
+            n_acc = __reduce_add_sync(0xffffffffu, n_acc);
+            if ((t & 31) == 0) sm.ri[t >> 5] = n_acc;
             __syncthreads();
             if (t == 0) {
                 int total = 0;
-                for (int k = 0; k < nt; ++k) total += sm.ri[k];
+                for (int k = 0; k < nw; ++k) total += sm.ri[k];
                 if (w >= 0 && fit[w] <= st->de_fbest) { st->de_best = sm.us[w]; st->de_fbest = fit[w]; }
                 st->stag = total ? 0 : st->stag + 1;
                 if (st->stag >= 2) { st->reinit_pending = 1; st->stag = 0; }
