@@ -448,6 +448,10 @@ typedef struct {
     uint64_t children[CT_MAX_PARAMS];
     float count_ms[CT_MAX_PARAMS];
     float emit_ms[CT_MAX_PARAMS];
+    /* host wall time of the call's phases (always recorded): device setup of the space
+     * description and the one-off table kernels, the levels (launches and the per-level size
+     * reads), the ball tables after the build, and the whole call */
+    float host_setup_ms, host_levels_ms, host_balls_ms, host_total_ms;
 } ct_build_stats;
 ct_status ct_space_set_timing(ct_space *space, int32_t enable);
 ct_status ct_space_build_stats(const ct_space *space, ct_build_stats *stats);

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <cmath>
@@ -857,9 +858,14 @@ ct_status ct_unpack_keys(const ct_space* s, const uint64_t* keys, int64_t n, int
 
 ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_out) {
     if (!s) { set_error("space is NULL"); return CT_ERR_INVALID_ARG; }
+    using clk = std::chrono::steady_clock;
+    const auto ms_since = [](clk::time_point a) { return std::chrono::duration<float, std::milli>(clk::now() - a).count(); };
+    const auto t0 = clk::now();
     cudaStream_t st = (cudaStream_t)stream;
     CT_TRY(ensure_device(s));
     CT_TRY(ensure_tables(s, st));
+    const float setup_ms = ms_since(t0);
+    const auto t1 = clk::now();
     const DevSpace& h = s->h;
     const uint64_t* parents = nullptr;
     uint64_t F = 1;
@@ -867,6 +873,7 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
     s->occ_ready = false;
     memset(&s->stats, 0, sizeof s->stats);
     s->stats.timed = s->timing;
+    s->stats.host_setup_ms = setup_ms;
     if (s->timing && s->events.empty()) {
         s->events.resize(4 * (size_t)h.n_blocks);
         for (auto& e : s->events) CT_TRY_CUDA(cudaEventCreate(&e));
@@ -924,7 +931,11 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
     s->n_valid = F;
     s->built = true;
     if (n_valid_out) *n_valid_out = F;
+    s->stats.host_levels_ms = ms_since(t1);
+    const auto t2 = clk::now();
     if (F) CT_TRY(ensure_balls(s, wanted_radius(s)));
+    s->stats.host_balls_ms = ms_since(t2);
+    s->stats.host_total_ms = ms_since(t0);
     if (F == 0) { set_error("no configuration satisfies the constraints"); return CT_ERR_EMPTY_SPACE; }
     return CT_OK;
 }
