@@ -45,6 +45,14 @@ CONFIG = {"workload": "large: 16 int params, 51,609,600,000 Cartesian points, 12
 HOST_WARM_S = 1.0   # seconds of continuous host work before a timed region
 
 
+def host_warm(seconds=HOST_WARM_S):
+    """Busy host for `seconds`: the GPU machines' virtual CPUs slow down while idle (see the
+    warm-up note in run_ours), and host-bound timings must not start on a cold CPU."""
+    t = time.perf_counter()
+    while time.perf_counter() - t < seconds:
+        pass
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -508,6 +516,7 @@ def plain_runs(torch, ct, W, dev, gens=500, chunk=50):
     res, total = {}, 0.0
     for kind in ("de", "pso", "firefly", "ga"):
         torch.cuda.synchronize()
+        host_warm()
         t0 = time.perf_counter()
         o = ct.Opt(sp, kind, 128, seed=0, target=tgt)
         o.run_graph(0, 1)
@@ -560,6 +569,7 @@ def batched_runs(torch, ct, W, dev, n_runs=4096, gens=100, plain_sample=48):
     hits = res["hit_evals"][res["hit_evals"] >= 0]
     # the same runs, one at a time (plain path: per-generation kernels, graph replay per run)
     torch.cuda.synchronize()
+    host_warm()
     t0 = time.perf_counter()
     for r in range(plain_sample):
         si, kind, pop, seed, tgt = runs[r]
