@@ -38,7 +38,7 @@ UNIT = "valid configs/s"
 L2_BYTES = 126 * 2 ** 20
 POP = 256
 CONFIG = {"workload": "large: 16 int params, 51,609,600,000 Cartesian points, 12 constraints, 695,228,960 valid; "
-                      "step = build_valid_space + one DE generation (pop 256)",
+                      "step = build_valid_space + DE generations 0 (initial sample) and 1 (pop 256)",
           "pop": POP, "l2": "working set 5.6 GB of keys > 126 MB L2 (no flush needed)"}
 
 
