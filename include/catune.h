@@ -259,10 +259,12 @@ typedef struct {
 
 #define CT_PENALTY 1e20f
 
-/* Fills *p with the Table IV values and target = -inf. */
+/* Fills *p with the Table IV values, target = -inf, the Hamming repair (repair_rule 0), the
+ * constraint-aware methods, and best1bin / single-point operators. */
 void ct_opt_params_default(ct_opt_params *p);
 
-/* Creates one run: population `pop` (3..CT_MAX_POP; DE needs >= 3), counter-based
+/* Creates one run: population `pop` (3..CT_MAX_POP; DE needs one more than the random
+ * members its mutation draws), counter-based
  * RNG seed `seed`.  Allocates the run's device state (population, positions,
  * memo bitmap of |V| bits) on the space's device.  Requires a built space with a
  * fitness table.  The space must outlive the run. */

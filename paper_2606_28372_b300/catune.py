@@ -394,7 +394,11 @@ def default_params(**over):
 
 
 class Opt:
-    """ct_opt: one constraint-aware optimizer run on a built space with a fitness table."""
+    """ct_opt: one optimizer run on a built space with a fitness table.
+
+    params: any field of ct_opt_params (F, CR, ..., repair_rule, constraint_aware, and the
+    operators by name: de_mutation in DE_MUTATIONS, de_crossover in DE_CROSSOVERS, ga_crossover
+    in GA_CROSSOVERS)."""
 
     def __init__(self, space, kind, pop, seed, **params):
         self.space = space
@@ -478,7 +482,8 @@ class ct_batch_run(C.Structure):
 class Batch:
     """ct_batch: many independent runs over several spaces, one persistent launch per generation.
 
-    runs: list of (space_index, kind, pop, seed, target)."""
+    runs: list of (space_index, kind, pop, seed, target); params: shared ct_opt_params fields as
+    for Opt (repair_rule must stay 0)."""
 
     def __init__(self, spaces, runs, **params):
         self.spaces = list(spaces)
