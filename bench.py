@@ -389,6 +389,7 @@ def run_ours(args):
     sub.update(plain_runs(torch, ct, W, dev))
     sub.update(batched_runs(torch, ct, W, dev))
     sub.update(surrogate_vs_plain(torch, ct, W, dev))
+    sub.update(surrogate_large(torch, ct, sp, table, dev))
     sub.update(aware_vs_unaware(torch, ct, W, dev))
     sub.update(operator_variants(torch, ct, W, dev))
     del opt, table
@@ -704,6 +705,34 @@ def run_scan(args):
     print(json.dumps({"mode": "scan", "workload": args.workload, "n_valid": nv, "peak_GBps": hbm,
                       "peak_kind": kind, "results": res}))
     return 0
+
+
+def surrogate_large(torch, ct, sp, table, dev, gens=10):
+    """The surrogate at the large size: DE pop 256 on the large space, milliseconds per
+    generation for the plain run, for a run whose judge decides (the lognormal table holds
+    nothing to learn, so it mostly stays off), and for one forced to screen every generation
+    (a pool of 16 x 256 = 4,096 repaired candidates, all predicted, plus 8 training steps)."""
+    logt = torch.log(table)
+    out = {}
+    for mode in ("plain", "judged", "forced"):
+        o = ct.Opt(sp, "de", POP, seed=11)
+        if mode == "judged":
+            o.set_surrogate(logt)
+        elif mode == "forced":
+            o.set_surrogate(logt, warmup_mult=0, mae_ratio=1e30)
+        o.step(0)
+        torch.cuda.synchronize()
+        host_warm()
+        screened = 0
+        t0 = time.perf_counter()
+        for g in range(1, gens + 1):
+            o.step(g)
+            if mode != "plain":
+                screened += o.surrogate_info()["screened"]
+        torch.cuda.synchronize()
+        out[mode] = {"ms_per_generation": 1000 * (time.perf_counter() - t0) / gens, "screened_generations": screened}
+        del o
+    return {"surrogate_large_de_pop256": out}
 
 
 def surrogate_vs_plain(torch, ct, W, dev, seeds=16, gens=150):

@@ -68,3 +68,47 @@ def test_batched_full_size(oracle_mod, tmp_path):
         b.run_state(r, k)
         assert np.array_equal(from_dev_u64(k), E["popk"][-1]), r
         assert int(res["n_unique"][r]) == int(E["n_unique"][-1]) and int(res["hit_evals"][r]) == int(E["hit"][1]), r
+
+
+def test_surrogate_on_the_large_space():
+    """The surrogate at the large size (pop 256, a pool of 4,096 repaired candidates per screened
+    generation).  A generation the judge does not screen proposes exactly what the plain run
+    proposes, so up to the first screened generation the two trajectories are equal; a forced
+    screen must then choose every slot's key from its own pool of repaired candidates."""
+    from paper_2606_28372_b300 import catune as ct
+    dev = torch.device("cuda", 0)
+    sd = W.large_space()
+    sp = ct.Space.from_def(sd)
+    nv = sp.build()
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    table = torch.exp(torch.randn(nv, generator=g, device=dev, dtype=torch.float32))
+    sp.set_fitness(table)
+    logt = torch.log(table)
+    P, G = 256, 10
+    plain = ct.Opt(sp, "de", P, 3)
+    surr = ct.Opt(sp, "de", P, 3)
+    surr.set_surrogate(logt)
+    kp, ks = (torch.empty(P, dtype=torch.int64, device=dev) for _ in range(2))
+    opened = None
+    for gen in range(G + 1):
+        plain.step(gen)
+        surr.step(gen)
+        info = surr.surrogate_info()
+        if info["screened"] and opened is None:
+            opened = gen
+        if opened is None:
+            plain.state(kp)
+            surr.state(ks)
+            assert torch.equal(kp, ks), gen
+            assert plain.best() == surr.best(), gen
+    forced = ct.Opt(sp, "de", P, 4)
+    forced.set_surrogate(logt, warmup_mult=0, mae_ratio=1e30)
+    rep = torch.empty(P, dtype=torch.int64, device=dev)
+    rank = torch.empty(P, dtype=torch.int64, device=dev)
+    for gen in range(4):
+        forced.step(gen)
+        forced.last_generation(None, rep)
+        sp.lookup(rep, rank)
+        assert bool((rank >= 0).all()), gen                    # chosen candidates are repaired
+    assert forced.surrogate_info()["screened"]
