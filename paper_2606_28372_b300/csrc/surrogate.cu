@@ -109,55 +109,51 @@ __global__ void k_mlp_l1(const float* __restrict__ p, MlpOff o, int D, int H, in
 
 // Ordered product C[m][n] = sum_{k ascending} A(m,k) * Bv(n,k), one fused multiply-add per
 // term starting from 0, A(m,k) = A[m*sam + k*sak], Bv(n,k) = B[n*sbn + k*sbk] (optionally
-// bf16-rounded).  Tiles of 32 x 32 outputs, k in chunks of 32 through shared memory.
+// bf16-rounded).  One output per thread in tiles of OG_T x OG_T outputs (256 CTAs for a
+// 256 x 256 product, more than the SMs), k in chunks of OG_K through shared memory.
 // EPI 0: z = acc + bias[n] -> out (z) and out2 (ReLU);  EPI 1: out = zmask > 0 ? acc : 0;
 // EPI 2: out = acc;  EPI 3: out = acc + bias[n].
+constexpr int OG_T = 16, OG_K = 32;
+
 template <int EPI, bool BF16>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(OG_T * OG_T)
 k_ogemm(int M, int Nn, int K, const float* __restrict__ A, long sam, long sak, const float* __restrict__ Bm, long sbn,
         long sbk, const float* __restrict__ bias, const float* __restrict__ zmask, float* __restrict__ out,
         float* __restrict__ out2, long ldc) {
-    __shared__ float As[32][33], Bs[32][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 rows of 4 outputs
-    const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int k0 = 0; k0 < K; k0 += 32) {
-        const int kmax = min(32, K - k0);
-        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
-            const int r = e >> 5, c = e & 31;
+    __shared__ float As[OG_T][OG_K + 1], Bs[OG_T][OG_K + 1];
+    const int tx = threadIdx.x % OG_T, ty = threadIdx.x / OG_T;
+    const int m0 = blockIdx.y * OG_T, n0 = blockIdx.x * OG_T;
+    float acc = 0.0f;
+    for (int k0 = 0; k0 < K; k0 += OG_K) {
+        const int kmax = min(OG_K, K - k0);
+        for (int e = threadIdx.x; e < OG_T * OG_K; e += OG_T * OG_T) {
+            const int r = e / OG_K, c = e % OG_K;
             const int m = m0 + r, n = n0 + r, k = k0 + c;
             As[r][c] = (m < M && c < kmax) ? A[m * sam + k * sak] : 0.0f;
-            float bv = (n < Nn && c < kmax) ? Bm[n * sbn + k * sbk] : 0.0f;
+            const float bv = (n < Nn && c < kmax) ? Bm[n * sbn + k * sbk] : 0.0f;
             Bs[r][c] = BF16 ? bf16r(bv) : bv;
         }
         __syncthreads();
-        for (int kk = 0; kk < kmax; ++kk) {
-            const float bv = Bs[tx][kk];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[r] = __fmaf_rn(As[ty * 4 + r][kk], bv, acc[r]);
-        }
+        for (int kk = 0; kk < kmax; ++kk) acc = __fmaf_rn(As[ty][kk], Bs[tx][kk], acc);
         __syncthreads();
     }
-    const int n = n0 + tx;
-    if (n >= Nn) return;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int m = m0 + ty * 4 + r;
-        if (m >= M) continue;
-        const long idx = m * ldc + n;
-        if (EPI == 0) {
-            const float z = __fadd_rn(acc[r], bias[n]);
-            out[idx] = z;
-            out2[idx] = z > 0.0f ? z : 0.0f;
-        } else if (EPI == 1) {
-            out[idx] = zmask[idx] > 0.0f ? acc[r] : 0.0f;
-        } else if (EPI == 2) {
-            out[idx] = acc[r];
-        } else {
-            out[idx] = __fadd_rn(acc[r], bias[n]);
-        }
+    const int m = m0 + ty, n = n0 + tx;
+    if (m >= M || n >= Nn) return;
+    const long idx = m * ldc + n;
+    if (EPI == 0) {
+        const float z = __fadd_rn(acc, bias[n]);
+        out[idx] = z;
+        out2[idx] = z > 0.0f ? z : 0.0f;
+    } else if (EPI == 1) {
+        out[idx] = zmask[idx] > 0.0f ? acc : 0.0f;
+    } else if (EPI == 2) {
+        out[idx] = acc;
+    } else {
+        out[idx] = __fadd_rn(acc, bias[n]);
     }
 }
+
+static dim3 og_grid(int M, int Nn) { return dim3((Nn + OG_T - 1) / OG_T, (M + OG_T - 1) / OG_T); }
 
 // output gradient and the last hidden layer's delta
 __global__ void k_mlp_gout(const float* __restrict__ pred, const float* __restrict__ y, int B, float scale,
@@ -176,12 +172,20 @@ __global__ void k_mlp_d3(const float* __restrict__ p, MlpOff o, int H, int B, co
 }
 
 // column sums over the batch in ascending sample order (bias gradients)
-__global__ void k_colsum(const float* __restrict__ d, int B, int H, float* __restrict__ out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= H) return;
+struct ColSums {                       // up to four column sums in one launch
+    const float* d[4];
+    int cols[4];
+    float* out[4];
+};
+
+__global__ void k_colsums(const __grid_constant__ ColSums cs, int B) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int q = 0, j = t;
+    while (q < 4 && j >= cs.cols[q]) { j -= cs.cols[q]; ++q; }
+    if (q == 4) return;
     float acc = 0.0f;
-    for (int b = 0; b < B; ++b) acc = __fadd_rn(acc, d[(size_t)b * H + j]);
-    out[j] = acc;
+    for (int b = 0; b < B; ++b) acc = __fadd_rn(acc, cs.d[q][(size_t)b * cs.cols[q] + j]);
+    cs.out[q][j] = acc;
 }
 
 // gradient of the one-hot layer: for each (j, feature f), the sum over samples (ascending)
@@ -232,10 +236,11 @@ static ct_status mlp_forward_impl(const float* p, int D, int H, int N, const int
                                   const MlpWork& w, cudaStream_t st) {
     const MlpOff o = mlp_off(D, H);
     k_mlp_l1<<<grid_for((size_t)B * H), 256, 0, st>>>(p, o, D, H, N, feats, B, w.z1, w.h1);
-    const dim3 g((H + 31) / 32, (B + 31) / 32);
-    k_ogemm<0, true><<<g, 256, 0, st>>>(B, H, H, w.h1, H, 1, p + o.W2, H, 1, p + o.b2, nullptr, w.z2, w.h2, H);
-    k_ogemm<0, true><<<g, 256, 0, st>>>(B, H, H, w.h2, H, 1, p + o.W3, H, 1, p + o.b3, nullptr, w.z3, w.h3, H);
-    k_ogemm<3, true><<<dim3(1, (B + 31) / 32), 256, 0, st>>>(B, 1, H, w.h3, H, 1, p + o.W4, 0, 1, p + o.b4, nullptr,
+    const dim3 g = og_grid(B, H);
+    const int OT = OG_T * OG_T;
+    k_ogemm<0, true><<<g, OT, 0, st>>>(B, H, H, w.h1, H, 1, p + o.W2, H, 1, p + o.b2, nullptr, w.z2, w.h2, H);
+    k_ogemm<0, true><<<g, OT, 0, st>>>(B, H, H, w.h2, H, 1, p + o.W3, H, 1, p + o.b3, nullptr, w.z3, w.h3, H);
+    k_ogemm<3, true><<<og_grid(B, 1), OT, 0, st>>>(B, 1, H, w.h3, H, 1, p + o.W4, 0, 1, p + o.b4, nullptr,
                                                             pred, nullptr, 1);
     count_launch(4);
     CT_TRY_CUDA(cudaGetLastError());
@@ -249,22 +254,26 @@ static ct_status mlp_grad_impl(const float* p, int D, int H, int N, const int32_
     const float scale = 2.0f / (float)B;
     k_mlp_gout<<<(B + 255) / 256, 256, 0, st>>>(pred, y, B, scale, w.gout);
     k_mlp_d3<<<grid_for((size_t)B * H), 256, 0, st>>>(p, o, H, B, w.gout, w.z3, w.d3);
-    const dim3 gb((H + 31) / 32, (B + 31) / 32);
+    const dim3 gb = og_grid(B, H);
+    const int OT = OG_T * OG_T;
     // deltas through W3 and W2 (transposed: B(n=i, k=j) = W[j*H + i])
-    k_ogemm<1, true><<<gb, 256, 0, st>>>(B, H, H, w.d3, H, 1, p + o.W3, 1, H, nullptr, w.z2, w.d2, nullptr, H);
-    k_ogemm<1, true><<<gb, 256, 0, st>>>(B, H, H, w.d2, H, 1, p + o.W2, 1, H, nullptr, w.z1, w.d1, nullptr, H);
+    k_ogemm<1, true><<<gb, OT, 0, st>>>(B, H, H, w.d3, H, 1, p + o.W3, 1, H, nullptr, w.z2, w.d2, nullptr, H);
+    k_ogemm<1, true><<<gb, OT, 0, st>>>(B, H, H, w.d2, H, 1, p + o.W2, 1, H, nullptr, w.z1, w.d1, nullptr, H);
     // weight gradients: sum over samples, ascending
-    const dim3 gw((H + 31) / 32, (H + 31) / 32);
-    k_ogemm<2, false><<<gw, 256, 0, st>>>(H, H, B, w.d3, 1, H, w.h2, 1, H, nullptr, nullptr, grad + o.W3, nullptr, H);
-    k_ogemm<2, false><<<gw, 256, 0, st>>>(H, H, B, w.d2, 1, H, w.h1, 1, H, nullptr, nullptr, grad + o.W2, nullptr, H);
-    k_ogemm<2, false><<<dim3((H + 31) / 32, 1), 256, 0, st>>>(1, H, B, w.gout, 0, 1, w.h3, 1, H, nullptr, nullptr,
+    const dim3 gw = og_grid(H, H);
+    k_ogemm<2, false><<<gw, OT, 0, st>>>(H, H, B, w.d3, 1, H, w.h2, 1, H, nullptr, nullptr, grad + o.W3, nullptr, H);
+    k_ogemm<2, false><<<gw, OT, 0, st>>>(H, H, B, w.d2, 1, H, w.h1, 1, H, nullptr, nullptr, grad + o.W2, nullptr, H);
+    k_ogemm<2, false><<<og_grid(1, H), OT, 0, st>>>(1, H, B, w.gout, 0, 1, w.h3, 1, H, nullptr, nullptr,
                                                              grad + o.W4, nullptr, H);
-    k_colsum<<<1, 32, 0, st>>>(w.gout, B, 1, grad + o.b4);
-    k_colsum<<<(H + 255) / 256, 256, 0, st>>>(w.d3, B, H, grad + o.b3);
-    k_colsum<<<(H + 255) / 256, 256, 0, st>>>(w.d2, B, H, grad + o.b2);
-    k_colsum<<<(H + 255) / 256, 256, 0, st>>>(w.d1, B, H, grad + o.b1);
-    k_mlp_w1grad<<<grid_for((size_t)H * D), 256, 0, st>>>(w.d1, feats, param_of, B, N, D, H, grad + o.W1);
-    count_launch(12);
+    ColSums cs;
+    cs.d[0] = w.gout; cs.cols[0] = 1; cs.out[0] = grad + o.b4;
+    cs.d[1] = w.d3; cs.cols[1] = H; cs.out[1] = grad + o.b3;
+    cs.d[2] = w.d2; cs.cols[2] = H; cs.out[2] = grad + o.b2;
+    cs.d[3] = w.d1; cs.cols[3] = H; cs.out[3] = grad + o.b1;
+    k_colsums<<<(1 + 3 * H + 127) / 128, 128, 0, st>>>(cs, B);
+    // one sequential sum per output: small CTAs spread the H x D outputs over every SM
+    k_mlp_w1grad<<<grid_for((size_t)H * D, 64), 64, 0, st>>>(w.d1, feats, param_of, B, N, D, H, grad + o.W1);
+    count_launch(9);
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -343,29 +352,40 @@ __global__ void k_surr_choose(int P, int pool, const float* __restrict__ pred, c
 }
 
 // judge (error of the predictions made before learning) and append new evaluations
-__global__ void k_surr_judge(const uint64_t* __restrict__ keys, int64_t nv, const float* __restrict__ logt,
-                             const uint64_t* __restrict__ evk, const float* __restrict__ pred, int P, int warm_mult,
-                             float mae_ratio, int screened, uint32_t* __restrict__ in_e, uint64_t* __restrict__ ek,
-                             float* __restrict__ ey, float* __restrict__ scratch, SurrDev* sd) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+constexpr int JUDGE_THREADS = 256;
+
+__global__ void __launch_bounds__(JUDGE_THREADS)
+k_surr_judge(const uint64_t* __restrict__ keys, int64_t nv, const float* __restrict__ logt,
+             const uint64_t* __restrict__ evk, const float* __restrict__ pred, int P, int warm_mult,
+             float mae_ratio, int screened, uint32_t* __restrict__ in_e, uint64_t* __restrict__ ek,
+             float* __restrict__ ey, float* __restrict__ scratch, SurrDev* sd) {
+    __shared__ int64_t rks[CT_MAX_POP];
+    // the rank lookups (binary searches over the valid keys) in parallel ...
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int64_t rk = rank_of(keys, nv, evk[i]);
+        rks[i] = rk;
+        scratch[i] = logt[rk];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    // ... and the fp32 sums in ascending i, one thread
     float sa = 0.0f, sy = 0.0f, s_dev = 0.0f;
     for (int i = 0; i < P; ++i) {
-        const float y = logt[rank_of(keys, nv, evk[i])];
+        const float y = scratch[i];
         sa = __fadd_rn(sa, fabsf(__fsub_rn(pred[i], y)));
         sy = __fadd_rn(sy, y);
-        scratch[i] = y;
     }
     const float mae = __fdiv_rn(sa, (float)P), ybar = __fdiv_rn(sy, (float)P);
     for (int i = 0; i < P; ++i) s_dev = __fadd_rn(s_dev, fabsf(__fsub_rn(scratch[i], ybar)));
     const float tau = __fmul_rn(mae_ratio, __fdiv_rn(s_dev, (float)P));
     unsigned long long n = sd->n_e;
-    for (int i = 0; i < P; ++i) {
-        const int64_t rk = rank_of(keys, nv, evk[i]);
+    for (int i = 0; i < P; ++i) {   // append first evaluations to the training set, in order
+        const int64_t rk = rks[i];
         const uint32_t bit = 1u << (rk & 31);
         if (in_e[rk >> 5] & bit) continue;
         in_e[rk >> 5] |= bit;
         ek[n] = evk[i];
-        ey[n] = logt[rk];
+        ey[n] = scratch[i];
         ++n;
     }
     sd->n_e = n;
@@ -446,7 +466,7 @@ ct_status surrogate_step(ct_opt* o, uint32_t gen, cudaStream_t st) {
     }
     CT_TRY(evaluate_impl(s, o->memo.p, &o->st.p->n_unique, &o->st.p->cost, evk, P, o->fit.p, nullptr, st));
     CT_TRY(predict_keys(o, evk, P, g->pred.p, st));
-    k_surr_judge<<<1, 32, 0, st>>>(s->keys.p, (int64_t)s->n_valid, g->logt, evk, g->pred.p, P, g->cfg.warmup_mult,
+    k_surr_judge<<<1, JUDGE_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, g->logt, evk, g->pred.p, P, g->cfg.warmup_mult,
                                    g->cfg.mae_ratio, screened ? 1 : 0, g->in_e.p, g->ek.p, g->ey.p, g->by.p, g->sd.p);
     count_launch();
     const int B = g->cfg.batch, H = g->cfg.hidden;
