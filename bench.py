@@ -390,6 +390,7 @@ def run_ours(args):
     sub.update(batched_runs(torch, ct, W, dev))
     sub.update(surrogate_vs_plain(torch, ct, W, dev))
     sub.update(surrogate_large(torch, ct, sp, table, dev))
+    sub.update(surrogate_gain_large(torch, ct, W, sp, sd, dev))
     sub.update(aware_vs_unaware(torch, ct, W, dev))
     sub.update(operator_variants(torch, ct, W, dev))
     del opt, table
@@ -652,6 +653,18 @@ def run_batched(args):
     return 0
 
 
+def run_surrogate(args):
+    import torch
+    from paper_2606_28372_b300 import catune as ct
+    from paper_2606_28372_b300 import workloads as W
+    dev = torch.device("cuda", 0)
+    sd = W.large_space()
+    sp = ct.Space.from_def(sd)
+    sp.build()
+    print(json.dumps(surrogate_gain_large(torch, ct, W, sp, sd, dev)))
+    return 0
+
+
 def run_rules(args):
     import torch
     from paper_2606_28372_b300 import catune as ct
@@ -733,6 +746,54 @@ def surrogate_large(torch, ct, sp, table, dev, gens=10):
         out[mode] = {"ms_per_generation": 1000 * (time.perf_counter() - t0) / gens, "screened_generations": screened}
         del o
     return {"surrogate_large_de_pop256": out}
+
+
+def surrogate_gain_large(torch, ct, W, sp, sd, dev, seeds=8, gens=300, chunk=1 << 25):
+    """Surrogate against the plain optimizer on the large space with a learnable table: the smooth
+    bowl of the medium workload over all 695M valid configurations, built on the device from
+    their value indices (ct_unpack_keys_device, 32M keys at a time).  DE and GA at pop 256, 16x
+    pool, `seeds` seeds, `gens` generations: median unique evaluations to come within 2 / 5 / 10 %
+    of the table's optimum, and the best after 2,000 unique evaluations."""
+    keys = sp.keys()
+    nv = keys.numel()
+    n = len(sd.params)
+    table = torch.empty(nv, dtype=torch.float32, device=dev)
+    idx = torch.empty(min(chunk, nv) * n, dtype=torch.int32, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(20240)
+    for s0 in range(0, nv, chunk):
+        k = keys[s0:s0 + chunk]
+        part = idx[: k.numel() * n].view(k.numel(), n)
+        sp.unpack_device(k, part)
+        table[s0:s0 + k.numel()] = W.smooth_table_device(sd, part, seed=0, generator=gen)
+    del idx
+    sp.set_fitness(table)
+    logt = torch.log(table)
+    opt = float(table.min())
+    out = {}
+    for kind in ("de", "ga"):
+        for mode in ("plain", "surrogate"):
+            curves = []
+            for seed in range(seeds):
+                o = ct.Opt(sp, kind, POP, seed)
+                if mode == "surrogate":
+                    o.set_surrogate(logt)
+                cu = []
+                for g in range(gens + 1):
+                    o.step(g)
+                    b = o.best()
+                    cu.append((b["n_unique"], b["best_fit"] / opt))
+                curves.append(cu)
+                del o
+            rec = {}
+            for pct in (2, 5, 10):
+                first = [next((m for m, f in cu if f <= 1 + pct / 100), None) for cu in curves]
+                hit = [x for x in first if x is not None]
+                rec[f"evals_to_{pct}pct_median"] = float(np.median(hit)) if len(hit) * 2 > len(first) else None
+                rec[f"reached_{pct}pct"] = f"{len(hit)}/{len(first)}"
+            rec["best_rel_after_2000_evals"] = float(np.median([[f for m, f in cu if m <= 2000][-1] for cu in curves]))
+            out[f"surrogate_large_{kind}_{mode}"] = rec
+    return out
 
 
 def surrogate_vs_plain(torch, ct, W, dev, seeds=16, gens=150):
@@ -863,11 +924,12 @@ if __name__ == "__main__":
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--quick", action="store_true", help="headline step only (no e2e, no sub-metrics)")
-    ap.add_argument("--mode", default="step", choices=["step", "scan", "aware", "variants", "batched", "rules"],
+    ap.add_argument("--mode", default="step", choices=["step", "scan", "aware", "variants", "batched", "rules", "surrogate"],
                     help="scan: only the exhaustive repair scan (scan-only repair of 1, 2, 4 uniform candidates); "
                          "aware: only the constraint-aware vs non-aware comparison over the density ladder; "
                          "variants: only the DE/GA operator comparison; batched: only the batched-runs "
-                         "comparison; rules: only the paper's repair rules on --workload")
+                         "comparison; rules: only the paper's repair rules on --workload; surrogate: only the "
+                         "surrogate-vs-plain comparison on the large space")
     ap.add_argument("--workload", default="large", choices=["large", "large_slice"],
                     help="large_slice: the same kernels on a 146M-key slice, for hardware-counter captures")
     a = ap.parse_args()
@@ -879,6 +941,8 @@ if __name__ == "__main__":
         sys.exit(run_variants(a))
     if a.mode == "batched":
         sys.exit(run_batched(a))
+    if a.mode == "surrogate":
+        sys.exit(run_surrogate(a))
     if a.mode == "rules":
         sys.exit(run_rules(a))
     sys.exit(run_scan(a) if a.mode == "scan" else run_ours(a))

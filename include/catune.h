@@ -124,6 +124,10 @@ ct_status ct_space_info_get(const ct_space *space, ct_space_info *info);
  * rejects indices outside [0, r_k) with INVALID_ARG. */
 ct_status ct_pack_keys(const ct_space *space, const int32_t *idx, int64_t n, uint64_t *keys);
 ct_status ct_unpack_keys(const ct_space *space, const uint64_t *keys, int64_t n, int32_t *idx);
+/* Device form of ct_unpack_keys: d_idx[i * n_params + k] = value index of parameter k in
+ * d_keys[i] (device buffers, caller-owned; asynchronous on `stream`). */
+ct_status ct_unpack_keys_device(const ct_space *space, const uint64_t *d_keys, int64_t n, int32_t *d_idx,
+                                ct_stream stream);
 
 /* Resolves the whole valid space on the device (Section IV-A): decodes the
  * Cartesian points, evaluates the constraints and compacts the valid keys in

@@ -76,6 +76,7 @@ _SIGS = {
     "ct_space_info_get": [C.c_void_p, C.POINTER(ct_space_info)],
     "ct_pack_keys": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p],
     "ct_unpack_keys": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p],
+    "ct_unpack_keys_device": [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p],
     "ct_build_valid_space": [C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)],
     "ct_space_keys": [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_uint64)],
     "ct_set_fitness": [C.c_void_p, C.c_void_p, C.c_uint64],
@@ -302,6 +303,10 @@ class Space:
         out = np.zeros((len(keys), self.info().n_params), dtype=np.int32)
         check(lib().ct_unpack_keys(self.h, keys.ctypes.data_as(C.c_void_p), len(keys), out.ctypes.data_as(C.c_void_p)))
         return out
+
+    def unpack_device(self, keys, out, stream=None):
+        """Value indices of device keys into a device int32 tensor of shape [n, n_params]."""
+        check(lib().ct_unpack_keys_device(self.h, _ptr(keys), keys.numel(), _ptr(out), _stream(stream)))
 
     def build(self, stream=None, allow_empty=False):
         n = C.c_uint64()

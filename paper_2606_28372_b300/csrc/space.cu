@@ -121,6 +121,18 @@ constexpr uint64_t TABLE_WORDS_TOTAL = 1ull << 24;      // 64 MB
 // ---------------------------------------------------------------------------
 // table construction: one thread per (tabled constraint, row, point)
 // ---------------------------------------------------------------------------
+// value indices of keys, one (key, parameter) per thread
+__global__ void k_unpack(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, int64_t n,
+                         int32_t* __restrict__ idx) {
+    const int np = sp->n;
+    const int64_t total = n * np;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = g / np;
+        const int k = (int)(g - i * np);
+        idx[g] = field(sp, __ldg(keys + i), k);
+    }
+}
+
 __global__ void k_build_tables(const DevSpace* __restrict__ sp, const int32_t* __restrict__ tab_cons,
                                const uint64_t* __restrict__ tab_prefix, int n_tab, uint64_t total_words,
                                uint32_t* __restrict__ tables) {
@@ -853,6 +865,22 @@ ct_status ct_unpack_keys(const ct_space* s, const uint64_t* keys, int64_t n, int
     const int np = s->h.n;
     for (int64_t i = 0; i < n; ++i)
         for (int p = 0; p < np; ++p) idx[i * np + p] = (int32_t)((keys[i] & s->h.fmask[p]) >> s->h.off[p]);
+    return CT_OK;
+}
+
+ct_status ct_unpack_keys_device(const ct_space* s, const uint64_t* d_keys, int64_t n, int32_t* d_idx,
+                                ct_stream stream) {
+    if (!s || (n > 0 && (!d_idx || !d_keys)) || n < 0) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    if (n == 0) return CT_OK;
+    if (!s->d) { set_error("space not on the device yet (build it first)"); return CT_ERR_STATE; }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t total = n * s->h.n;
+    const unsigned g = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 16);
+    k_unpack<<<g, 256, 0, (cudaStream_t)stream>>>(s->d, d_keys, n, d_idx);
+    count_launch();
+    CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
 }
 

@@ -220,6 +220,27 @@ def smooth_table(space: SpaceDef, idx_tuples: np.ndarray, seed: int = 0,
     return (bowl * np.exp(noise * z)).astype(np.float32)
 
 
+def smooth_table_device(space: SpaceDef, idx_tuples, seed: int = 0, noise: float = 0.1, generator=None):
+    """Device form of smooth_table for spaces too large for host memory: the same bowl (a_k,
+    c_k drawn exactly as smooth_table draws them) over a torch int32 tensor of value indices
+    [n, N] on the device, times exp(noise * z) with z standard normal from ``generator`` (a
+    torch.Generator on that device, consumed in order; so the noise differs from smooth_table's
+    numpy draws).  Returns a float32 tensor of n entries."""
+    import torch
+    n = len(space.params)
+    g = np.random.Generator(np.random.Philox(key=0x5EED0000 + seed))
+    a = g.uniform(0.5, 2.0, size=n)
+    c = g.uniform(0.0, 1.0, size=n)
+    r = np.array(space.n_values, dtype=np.float64)
+    den = np.where(r > 1, r - 1, 1.0)
+    dev = idx_tuples.device
+    u = idx_tuples.to(torch.float64) / torch.tensor(den, dtype=torch.float64, device=dev)
+    bowl = 1.0 + ((u - torch.tensor(c, dtype=torch.float64, device=dev)) ** 2
+                  * torch.tensor(a, dtype=torch.float64, device=dev)).sum(dim=1)
+    z = torch.randn(len(idx_tuples), generator=generator, device=dev, dtype=torch.float64)
+    return (bowl * torch.exp(noise * z)).to(torch.float32)
+
+
 def eval_cost_table(table: np.ndarray, seed: int = 0, compile_s: float = 1.5, sigma: float = 0.25,
                     repeats: int = 7) -> np.ndarray:
     """Simulated time, in whole microseconds (uint32), of evaluating each valid configuration:

@@ -1,6 +1,7 @@
 """GPU parity: the valid space built by the CUDA path equals the oracle's, key for key."""
 import numpy as np
 import pytest
+import torch
 
 from paper_2606_28372_b300 import workloads as W
 from tests.helpers import Pair, from_dev_u64
@@ -86,3 +87,24 @@ def test_empty_space_status(oracle_mod):
         sp.build()
     assert e.value.status == ct.CT_ERR_EMPTY_SPACE
     assert sp.info().n_valid == 0 and sp.info().built
+
+
+def test_unpack_on_the_device(oracle_mod):
+    """ct_unpack_keys_device against the oracle's unpacking, and the device form of the smooth
+    table against the host form with the noise switched off (same bowl)."""
+    from paper_2606_28372_b300 import catune as ct
+    sd = W.medium_space()
+    osp = oracle_mod.from_def(sd)
+    ok = oracle_mod.valid_keys(osp)
+    sp = ct.Space.from_def(sd)
+    sp.build()
+    keys = sp.keys()
+    idx = torch.empty((keys.numel(), len(sd.params)), dtype=torch.int32, device="cuda")
+    sp.unpack_device(keys, idx)
+    exp = oracle_mod.unpack(osp, ok)
+    assert np.array_equal(idx.cpu().numpy(), exp)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    dev_t = W.smooth_table_device(sd, idx, seed=3, noise=0.0, generator=g).cpu().numpy()
+    host_t = W.smooth_table(sd, exp, seed=3, noise=0.0)
+    assert np.allclose(dev_t, host_t, rtol=1e-6, atol=0)
