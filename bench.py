@@ -464,7 +464,17 @@ def repair_rates(sp, sd, torch, ct, dev):
         ms = e0.elapsed_time(e1) / 5
         scan[f"q{q}"] = {"ms_per_pass": ms, "key_stream_GBps": 8 * keys.numel() / (ms / 1000.0) / 1e9}
     sp.set_repair_mode(0, 0)
+    # integer side of the scan: one population count per (key, candidate) on keys of <= 32 bits,
+    # two on wider keys; the population-count pipe bounds it, and the library's microbenchmark
+    # measures that pipe's rate
+    peak = ct.measure_int_peak()
+    per_pair = 2 if sp.info().key_bits > 32 else 1
+    for q, v in scan.items():
+        pairs = keys.numel() * int(q[1:]) / (v["ms_per_pass"] / 1000.0)
+        v["popc_pipe_frac"] = pairs * per_pair / peak
     res["scan_only_repair"] = scan
+    res["int_peak_popc_per_s"] = peak
+    res["scan_popc_per_pair"] = per_pair
     return res
 
 

@@ -469,6 +469,11 @@ ct_status ct_space_build_stats(const ct_space *space, ct_build_stats *stats);
  * driver. */
 void ct_trim_cache(void);
 
+/* Integer denominator of the key scans' roofline: runs a microbenchmark of independent 32-bit
+ * xor / population-count / add chains over every SM of the current device, bound like the scans
+ * by the population-count pipe, and writes population counts per second (synchronises). */
+ct_status ct_measure_int_peak(double *popc_per_s, ct_stream stream);
+
 /* Number of kernels this library has launched in this process (all devices). */
 uint64_t ct_launch_count(void);
 

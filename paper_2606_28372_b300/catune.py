@@ -131,6 +131,7 @@ _SIGS = {
     "ct_mlp_sgd": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float, C.c_void_p],
     "ct_space_set_timing": [C.c_void_p, C.c_int32],
     "ct_space_build_stats": [C.c_void_p, C.c_void_p],
+    "ct_measure_int_peak": [C.POINTER(C.c_double), C.c_void_p],
     "ct_launch_count": [],
     "ct_trim_cache": [],
     "ct_last_error": [],
@@ -385,6 +386,14 @@ class _CudaArray:
 
     def __init__(self, ptr, n):
         self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i8", "data": (ptr, False), "version": 3}
+
+
+def measure_int_peak(stream=None):
+    """Population counts per second of the library's integer microbenchmark (32-bit xor/popc/add
+    chains, bound by the population-count pipe like the key scans)."""
+    v = C.c_double()
+    check(lib().ct_measure_int_peak(C.byref(v), _stream(stream)))
+    return float(v.value)
 
 
 def default_params(**over):

@@ -1,0 +1,67 @@
+// Integer throughput microbenchmark: the denominator of the integer roofline of the key scans.
+//
+// Every thread runs eight independent accumulator chains of 32-bit operations; one step of a
+// chain is an exclusive or with a value that changes every iteration, a population count and
+// two additions -- the operations of the key scans.  The population count issues at a quarter of
+// the rate of the other integer operations, so this mix (like the scans, which spend one per
+// (key, candidate) on keys of at most 32 bits and two on wider keys) is bound by that pipe; the
+// rate reported is population counts per second, measured over every SM at full occupancy.
+#include <cuda_runtime.h>
+
+#include "internal.hpp"
+
+namespace ct {
+
+constexpr int IP_THREADS = 256, IP_ITERS = 4096, IP_CHAINS = 8;
+constexpr int IP_POPC_PER_STEP = 1;
+
+__global__ void __launch_bounds__(IP_THREADS) k_int_peak(uint32_t seed, uint32_t* __restrict__ sink) {
+    uint32_t a[IP_CHAINS];
+    const uint32_t w = seed * 0x9e3779b9u + blockIdx.x * IP_THREADS + threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < IP_CHAINS; ++c) a[c] = w * (2u * c + 1u);
+    for (int i = 0; i < IP_ITERS; ++i) {
+#pragma unroll
+        for (int c = 0; c < IP_CHAINS; ++c) {
+            const uint32_t x = a[c] ^ (uint32_t)i;
+            a[c] = x + (uint32_t)__popc(x) + (uint32_t)c;
+        }
+    }
+    uint32_t r = 0;
+#pragma unroll
+    for (int c = 0; c < IP_CHAINS; ++c) r ^= a[c];
+    if (r == 0x9e3779b9u) sink[0] = r;   // keeps the chains live; practically never written
+}
+
+}  // namespace ct
+
+using namespace ct;
+
+extern "C" ct_status ct_measure_int_peak(double* popc_per_s, ct_stream stream) {
+    if (!popc_per_s) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    int dev = 0, sms = 148;
+    CT_TRY_CUDA(cudaGetDevice(&dev));
+    CT_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    DevBuf<uint32_t> sink;
+    CT_TRY(sink.ensure(1));
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned grid = (unsigned)sms * 8 * 4;   // 8 resident CTAs of 256 per SM, four waves
+    cudaEvent_t e0, e1;
+    CT_TRY_CUDA(cudaEventCreate(&e0));
+    CT_TRY_CUDA(cudaEventCreate(&e1));
+    k_int_peak<<<grid, IP_THREADS, 0, st>>>(1u, sink.p);   // warm-up
+    cudaEventRecord(e0, st);
+    k_int_peak<<<grid, IP_THREADS, 0, st>>>(2u, sink.p);
+    cudaEventRecord(e1, st);
+    count_launch(2);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    sink.release();
+    if (err != cudaSuccess) { set_error("%s", cudaGetErrorString(err)); return CT_ERR_CUDA; }
+    const double popc = (double)grid * IP_THREADS * IP_ITERS * IP_CHAINS * IP_POPC_PER_STEP;
+    *popc_per_s = popc / (ms * 1e-3);
+    return CT_OK;
+}
