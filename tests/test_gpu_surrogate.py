@@ -52,9 +52,9 @@ def test_mlp_kernels_bit_exact(oracle_mod, D, H, N, B):
     assert np.array_equal(p.cpu().numpy(), p0) and np.array_equal(mom.cpu().numpy(), m0)
 
 
-def _gpu_surrogate_trace(pair, kind, pop, gens, seed, cfg, logt):
+def _gpu_surrogate_trace(pair, kind, pop, gens, seed, cfg, logt, **params):
     from paper_2606_28372_b300 import catune as ct
-    o = ct.Opt(pair.sp, kind, pop, seed)
+    o = ct.Opt(pair.sp, kind, pop, seed, **params)
     dl = torch.from_numpy(logt).cuda()
     o.set_surrogate(dl, **cfg)
     T = {k: [] for k in ("cand", "rep", "evalk", "fit", "popk", "n_unique", "best_key", "used", "mae", "tau", "ne")}
@@ -101,6 +101,24 @@ def test_surrogate_trajectory(oracle_mod, kind, space, pop, gens, cfg):
         a, b = T[f], E[e]
         assert np.array_equal(a.astype(b.dtype) if f in ("used", "ne") else a, b), f
     assert np.array_equal(T["params"], E["s_params"])
+
+
+@pytest.mark.parametrize("kind,ops", [("de", dict(de_mutation="rand2", de_crossover="exp")),
+                                      ("de", dict(de_mutation="currenttobest1")),
+                                      ("ga", dict(ga_crossover="disruptive_uniform"))])
+def test_surrogate_trajectory_with_operator_variants(oracle_mod, kind, ops):
+    """The pool proposals of a screened generation use the run's operators (streams offset by the
+    pool index), like the oracle's."""
+    p = Pair(W.medium_space(), oracle_mod)
+    logt = np.log(p.table.astype(np.float64)).astype(np.float32)
+    cfg = dict(pool=4, hidden=32, batch=64, steps=4, warmup_mult=1, mae_ratio=10.0)
+    ocfg = dict(pool=4, H=32, batch=64, steps=4, warm_mult=1, mae_ratio=10.0)
+    E = oracle_mod.run(kind, p.osp, p.okeys, p.table, pop=32, gens=6, seed=8, surrogate=ocfg, log_table=logt, **ops)
+    T = _gpu_surrogate_trace(p, kind, 32, 6, 8, cfg, logt, **ops)
+    assert T["used"][1:].any()
+    for f, e in (("cand", "cand"), ("evalk", "evalk"), ("popk", "popk"), ("n_unique", "n_unique"), ("used", "s_used")):
+        a, b = T[f], E[e]
+        assert np.array_equal(a.astype(b.dtype) if f == "used" else a, b), f
 
 
 def _curves(sp, kind, seeds, gens, logt=None):
