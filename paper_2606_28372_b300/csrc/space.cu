@@ -710,10 +710,11 @@ int wanted_radius(const ct_space* s) {
 
 // Enumerates and uploads the ball tables of radii balls.size()+1 .. dmax (subsets of the
 // parameters with r_k > 1, in lexicographic order, with prefix sums of their sizes).
-ct_status ensure_balls(ct_space* s, int dmax) {
+// Host part of the ball tables: enumerates radii balls.size()+1 .. dmax (subsets of the
+// parameters with r_k > 1, in lexicographic order, with prefix sums of their sizes).  No CUDA
+// call, so the build runs it while its last level is still being emitted.
+static void plan_balls(ct_space* s, int dmax) {
     dmax = std::min(dmax, s->ball_max);
-    if ((int)s->balls.size() >= dmax) return CT_OK;
-    CT_TRY(ensure_device(s));
     const DevSpace& h = s->h;
     std::vector<int> free_k;
     for (int k = 0; k < h.n; ++k) if (h.r[k] > 1) free_k.push_back(k);
@@ -738,13 +739,56 @@ ct_status ensure_balls(ct_space* s, int dmax) {
             ++idx[i];
             for (int t = i + 1; t < d; ++t) idx[t] = idx[t - 1] + 1;
         }
-        CT_TRY(br.d_masks.ensure(br.masks.size()));
-        CT_TRY(br.d_prefix.ensure(br.prefix.size()));
-        CT_TRY_CUDA(cudaMemcpy(br.d_masks.p, br.masks.data(), br.masks.size() * 4, cudaMemcpyHostToDevice));
-        CT_TRY_CUDA(cudaMemcpy(br.d_prefix.p, br.prefix.data(), br.prefix.size() * 8, cudaMemcpyHostToDevice));
         s->balls.push_back(std::move(br));
     }
+}
+
+// Pinned host staging shared by the uploads of small host tables: one copy into it, one
+// asynchronous copy per table, one synchronisation, instead of a synchronous copy per table.
+namespace {
+struct PinnedStage {
+    std::mutex mu;
+    char* p = nullptr;
+    size_t cap = 0;
+};
+PinnedStage g_stage;
+}  // namespace
+
+// Device part: uploads every planned radius that has no device tables yet.
+static ct_status upload_balls(ct_space* s, cudaStream_t st) {
+    size_t bytes = 0;
+    for (const BallRadius& br : s->balls)
+        if (!br.d_masks.p) bytes += br.masks.size() * 4 + 16 + br.prefix.size() * 8 + 16;
+    if (!bytes) return CT_OK;
+    CT_TRY(ensure_device(s));
+    std::lock_guard<std::mutex> lk(g_stage.mu);
+    if (g_stage.cap < bytes) {
+        if (g_stage.p) cudaFreeHost(g_stage.p);
+        g_stage.p = nullptr;
+        g_stage.cap = 0;
+        const size_t want = std::max<size_t>(bytes, 1 << 20);
+        CT_TRY_CUDA(cudaMallocHost(reinterpret_cast<void**>(&g_stage.p), want));
+        g_stage.cap = want;
+    }
+    size_t off = 0;
+    for (BallRadius& br : s->balls) {
+        if (br.d_masks.p) continue;
+        CT_TRY(br.d_masks.ensure(br.masks.size()));
+        CT_TRY(br.d_prefix.ensure(br.prefix.size()));
+        memcpy(g_stage.p + off, br.masks.data(), br.masks.size() * 4);
+        CT_TRY_CUDA(cudaMemcpyAsync(br.d_masks.p, g_stage.p + off, br.masks.size() * 4, cudaMemcpyHostToDevice, st));
+        off += (br.masks.size() * 4 + 15) & ~size_t(15);
+        memcpy(g_stage.p + off, br.prefix.data(), br.prefix.size() * 8);
+        CT_TRY_CUDA(cudaMemcpyAsync(br.d_prefix.p, g_stage.p + off, br.prefix.size() * 8, cudaMemcpyHostToDevice, st));
+        off += (br.prefix.size() * 8 + 15) & ~size_t(15);
+    }
+    CT_TRY_CUDA(cudaStreamSynchronize(st));   // the stage is reused by the next upload
     return CT_OK;
+}
+
+ct_status ensure_balls(ct_space* s, int dmax) {
+    plan_balls(s, dmax);
+    return upload_balls(s, nullptr);
 }
 
 static ct_status ensure_tables(ct_space* s, cudaStream_t st) {
@@ -948,6 +992,10 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
         parents = dst.p;
         F = Fn;
         if (F == 0) break;
+        if (j == h.n_blocks - 1) {   // the host plans the ball tables while the last level is emitted
+            s->n_valid = F;
+            plan_balls(s, wanted_radius(s));
+        }
     }
     CT_TRY_CUDA(cudaStreamSynchronize(st));
     if (s->timing)
@@ -961,7 +1009,7 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
     if (n_valid_out) *n_valid_out = F;
     s->stats.host_levels_ms = ms_since(t1);
     const auto t2 = clk::now();
-    if (F) CT_TRY(ensure_balls(s, wanted_radius(s)));
+    if (F) CT_TRY(upload_balls(s, st));
     s->stats.host_balls_ms = ms_since(t2);
     s->stats.host_total_ms = ms_since(t0);
     if (F == 0) { set_error("no configuration satisfies the constraints"); return CT_ERR_EMPTY_SPACE; }
