@@ -176,6 +176,13 @@ __device__ __forceinline__ bool vm_eval(const ct_instr* __restrict__ prog, int p
             case CT_OP_MOD:
                 if (p || b == 0) { rp = true; break; }
                 if (a == INT64_MIN && b == -1) { r = (op == CT_OP_DIV) ? INT64_MIN : 0; break; }
+                if (a == (int32_t)a && b == (int32_t)b && !(a == INT32_MIN && b == -1)) {
+                    // both operands fit in 32 bits: the same truncated quotient and remainder,
+                    // with the much cheaper 32-bit division
+                    const int32_t a32 = (int32_t)a, b32 = (int32_t)b;
+                    r = (op == CT_OP_DIV) ? (int64_t)(a32 / b32) : (int64_t)(a32 % b32);
+                    break;
+                }
                 r = (op == CT_OP_DIV) ? a / b : a % b;
                 break;
             case CT_OP_MIN: r = a < b ? a : b; rp = p; break;
