@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcatune.so")
-SOURCES = ["space.cu", "search.cu", "rules.cu", "optim.cu", "batch.cu", "surrogate.cu", "noalloc.cu", "measure.cu"]
+SOURCES = ["space.cu", "search.cu", "rules.cu", "optim.cu", "batch.cu", "surrogate.cu", "noalloc.cu", "measure.cu", "scan_lut.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

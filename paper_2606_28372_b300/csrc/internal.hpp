@@ -150,6 +150,8 @@ int wanted_radius(const ct_space* s);
 ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, int64_t n, uint64_t* d_out,
                       uint8_t* d_dist, cudaStream_t st);
 int auto_radius(const ct_space* s);
+ct_status scan_lut(const ct_space* s, const uint64_t* d_cand, const int32_t* pend, const uint32_t* count,
+                   unsigned long long* best, cudaStream_t st, bool* launched, int* lut_min);
 ct_status repair_reserve(RepairScratch& rs, int64_t n);
 ct_status rule_reserve(RuleScratch& r, int64_t n, int slices);
 int rule_slices_for(const ct_space* s);

@@ -12,7 +12,8 @@
 //     once per chunk of 32 candidates; per (key, candidate) the distance is a
 //     SWAR per-field non-zero test plus a population count, reduced as the packed
 //     minimum of (distance << 57 | rank) by warp shuffles, shared memory and one
-//     64-bit atomicMin per candidate and CTA.
+//     64-bit atomicMin per candidate and CTA.  On long key arrays, chunks of three or
+//     more candidates use per-candidate distance tables instead (scan_lut.cu).
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -233,9 +234,9 @@ k_scan(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_t hi
     }
 }
 
-// Few pending candidates (<= 4): one candidate set per CTA, high occupancy, four
-// independent 16-byte key loads in flight per thread.  CTAs whose chunk holds more
-// than four candidates leave it to k_scan_wide.
+// Few pending candidates (<= few_max, at most 4): one candidate set per CTA, high
+// occupancy, four independent 16-byte key loads in flight per thread.  A last chunk
+// with more candidates is left to k_scan_wide or to the distance-table scan.
 template <int Q, bool NARROW>
 __device__ __forceinline__ void scan_run4(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm,
                                           uint64_t highm, const uint64_t* cq, int nq,
@@ -310,14 +311,14 @@ __device__ __forceinline__ void scan_run4(const uint64_t* __restrict__ keys, int
 __global__ void __launch_bounds__(SCAN_THREADS, 4)
 k_scan_few(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_t highm,
            const uint64_t* __restrict__ cand, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
-           unsigned long long* __restrict__ best) {
+           unsigned long long* __restrict__ best, int few_max) {
     __shared__ uint64_t cq[SCAN_CHUNK];
     __shared__ unsigned long long red[SCAN_THREADS / 32][SCAN_CHUNK];
     const uint32_t cnt = *count;
     if (cnt == 0) return;
     const uint32_t q0 = (cnt - 1) / SCAN_CHUNK * SCAN_CHUNK;
     const int nq = (int)(cnt - q0);
-    if (nq > 4) return;
+    if (nq > few_max || nq > 4) return;
     if (threadIdx.x < SCAN_CHUNK) cq[threadIdx.x] = threadIdx.x < nq ? cand[pend[q0 + threadIdx.x]] : 0ull;
     __syncthreads();
     unsigned long long* bq = best + q0;
@@ -441,11 +442,17 @@ ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, in
     const int64_t need = ((int64_t)s->n_valid + SCAN_THREADS * 8 - 1) / (SCAN_THREADS * 8);
     const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 4));
     const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 2));
+    bool lut = false;   // long key arrays: per-candidate distance tables
+    int lut_min = 0;
+    CT_TRY(scan_lut(s, d_cand, pend[cur], cnt[cur], best[cur], st, &lut, &lut_min));
     k_scan_few<<<gf, SCAN_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, s->h.swar_low, s->h.swar_high, d_cand,
-                                            pend[cur], cnt[cur], best[cur]);
-    k_scan_wide<<<gw, SCAN_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, s->h.swar_low, s->h.swar_high, d_cand,
-                                             pend[cur], cnt[cur], best[cur]);
-    count_launch(2);
+                                            pend[cur], cnt[cur], best[cur], lut ? lut_min - 1 : 4);
+    count_launch();
+    if (!lut) {
+        k_scan_wide<<<gw, SCAN_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, s->h.swar_low, s->h.swar_high,
+                                                 d_cand, pend[cur], cnt[cur], best[cur]);
+        count_launch();
+    }
     k_scan_resolve<<<g1, 256, 0, st>>>(s->keys.p, pend[cur], cnt[cur], best[cur], d_out, d_dist);
     count_launch();
     CT_TRY_CUDA(cudaGetLastError());

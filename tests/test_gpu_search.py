@@ -136,7 +136,12 @@ def scan_spaces(oracle_mod):
     """Spaces with keys narrower and wider than 32 bits and with even and odd |V|."""
     from paper_2606_28372_b300 import catune as ct
     defs = [W.tiny_space(), W.batched_space(3),
-            W._space("wide33_odd", [(f"p{i}", range(1, 6)) for i in range(11)], ["(p0*p1 + p2*p3 + p4) % 17 == 2"])]
+            W._space("wide33_odd", [(f"p{i}", range(1, 6)) for i in range(11)], ["(p0*p1 + p2*p3 + p4) % 17 == 2"]),
+            # single-value parameters (fields of zero bits) between the others
+            W._space("zero_width", [("a", range(7)), ("z0", [3]), ("b", range(5)), ("c", range(6)), ("z1", [1]),
+                                    ("d", range(9)), ("e", range(3))], ["(a + 2*b + c*d + e) % 5 != 1", "a*e <= 8"]),
+            # a 9-bit parameter: no table plan, the SWAR scan runs either way
+            W._space("wide_field", [("a", range(300)), ("b", range(5)), ("c", range(4))], ["(a*b + c) % 7 == 3"])]
     out = []
     for sd in defs:
         osp = oracle_mod.from_def(sd)
@@ -148,9 +153,12 @@ def scan_spaces(oracle_mod):
     return out
 
 
-@pytest.mark.parametrize("count", [1, 2, 3, 4, 5, 9, 17, 33, 70])
-def test_scan_widths_and_odd_tail(oracle_mod, scan_spaces, count):
-    """Scan-only repair for every pending-candidate width."""
+@pytest.mark.parametrize("lut", [False, True])
+@pytest.mark.parametrize("count", [1, 2, 3, 4, 5, 9, 17, 33, 45, 70])
+def test_scan_widths_and_odd_tail(oracle_mod, scan_spaces, count, lut, monkeypatch):
+    """Scan-only repair for every pending-candidate width, with the SWAR distance and with the
+    per-candidate distance tables (forced on short key arrays)."""
+    monkeypatch.setenv("CATUNE_SCAN_LUT_MIN_KEYS", "0" if lut else str(1 << 62))
     for sd, osp, okeys, sp in scan_spaces:
         inv = np.setdiff1d(oracle_mod.pack(osp, W.uniform_tuples(sd, 4 * count + 40, seed=count)), okeys)[:count]
         assert len(inv) == count
@@ -162,3 +170,34 @@ def test_scan_widths_and_odd_tail(oracle_mod, scan_spaces, count):
         eo, ed = oracle_mod.repair(osp, okeys, inv)
         assert np.array_equal(from_dev_u64(out), eo), sd.name
         assert np.array_equal(dist.cpu().numpy(), ed), sd.name
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_large_repair_by_groups(oracle_mod, mode):
+    """Full-size large space in the bench's launch configuration (the scan over 695,228,960 keys
+    runs with the distance tables): no constraint spans the two parameter groups, so the Hamming
+    distance splits into the groups' distances and the nearest key, ties to the smallest key, is
+    the nearest group-A key above the nearest group-B key.  The oracle repairs each group over its
+    own valid keys."""
+    from paper_2606_28372_b300 import catune as ct
+    sd, sa, sb = W.large_space(), W.large_group_a(), W.large_group_b()
+    sp = ct.Space.from_def(sd)
+    sp.build()
+    osp, oa, ob = (oracle_mod.from_def(x) for x in (sd, sa, sb))
+    ka, kb = oracle_mod.valid_keys(oa), oracle_mod.valid_keys(ob)
+    bits_b = int(sum(max(0, int(r - 1).bit_length()) for r in sb.n_values))
+    keys = sp.keys()
+    base = sp.unpack(from_dev_u64(keys[torch.from_numpy(W.random_ranks(695_228_960, 40, seed=12)).cuda()]))
+    tup = np.concatenate([W.uniform_tuples(sd, 88 if mode == 0 else 24, seed=13), W.perturbed_tuples(sd, base, seed=13)])
+    cand = oracle_mod.pack(osp, tup)
+    sp.set_repair_mode(mode, 0)
+    out = torch.empty(len(cand), dtype=torch.int64, device="cuda")
+    dist = torch.empty(len(cand), dtype=torch.uint8, device="cuda")
+    sp.repair(to_dev_u64(cand), out, dist)
+    sp.set_repair_mode(0, 0)
+    na = len(sa.n_values)
+    ra, da = oracle_mod.repair(oa, ka, oracle_mod.pack(oa, tup[:, :na]))
+    rb, db = oracle_mod.repair(ob, kb, oracle_mod.pack(ob, tup[:, na:]))
+    want = (ra.astype(np.uint64) << np.uint64(bits_b)) | rb.astype(np.uint64)
+    assert np.array_equal(from_dev_u64(out), want)
+    assert np.array_equal(dist.cpu().numpy(), (da.astype(np.int64) + db).astype(np.uint8))
