@@ -313,7 +313,7 @@ k_expand_emit(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tabl
 // pattern mode: per-signature compacted inner-key lists, then broadcast-OR emission
 // ---------------------------------------------------------------------------
 constexpr int PAT_THREADS = 128;   // >= max words per block (4096 / 32)
-constexpr int PE_THREADS = 256;    // parents per tile of the pattern count/emit kernels
+constexpr int PE_THREADS = 256;    // threads of the pattern count/emit kernels (and most parents per tile)
 
 __global__ void __launch_bounds__(PAT_THREADS)
 k_build_patterns(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
@@ -382,11 +382,11 @@ __device__ __forceinline__ uint32_t sig_of(const PatArgs& pa, uint64_t parent) {
 }
 
 __global__ void __launch_bounds__(PE_THREADS)
-k_pcount(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents, uint64_t F,
+k_pcount(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents, uint64_t F, uint32_t pt,
          uint32_t* __restrict__ tile_counts) {
-    const uint64_t i = (uint64_t)blockIdx.x * PE_THREADS + threadIdx.x;
+    const uint64_t i = (uint64_t)blockIdx.x * pt + threadIdx.x;
     uint32_t c = 0;
-    if (i < F) c = __ldg(pa.cnt + sig_of(pa, parents ? __ldg(parents + i) : 0ull));
+    if (threadIdx.x < pt && i < F) c = __ldg(pa.cnt + sig_of(pa, parents ? __ldg(parents + i) : 0ull));
     __shared__ uint32_t ws[PE_THREADS / 32];
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
@@ -399,17 +399,17 @@ k_pcount(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parent
 }
 
 __global__ void __launch_bounds__(PE_THREADS)
-k_pemit(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents, uint64_t F,
+k_pemit(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents, uint64_t F, uint32_t pt,
         const unsigned long long* __restrict__ tile_base, uint64_t* __restrict__ out) {
     __shared__ uint32_t off_s[PE_THREADS], cnt_s[PE_THREADS], sig_s[PE_THREADS];
     __shared__ uint64_t par_s[PE_THREADS];
     __shared__ uint32_t wsum[PE_THREADS / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const uint64_t i0 = (uint64_t)blockIdx.x * PE_THREADS;
+    const uint64_t i0 = (uint64_t)blockIdx.x * pt;
     const uint64_t i = i0 + t;
     uint32_t c = 0, sg = 0;
     uint64_t parent = 0;
-    if (i < F) {
+    if (t < (int)pt && i < F) {
         parent = parents ? __ldg(parents + i) : 0ull;
         sg = sig_of(pa, parent);
         c = __ldg(pa.cnt + sg);
@@ -429,7 +429,7 @@ k_pemit(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents
     par_s[t] = parent;
     __syncthreads();
     const uint64_t tb = tile_base[blockIdx.x];
-    const int np = (int)min((uint64_t)PE_THREADS, F - i0);
+    const int np = (int)min((uint64_t)pt, F - i0);
     for (int p = warp; p < np; p += PE_THREADS / 32) {
         const uint32_t cp = cnt_s[p];
         const uint64_t par = par_s[p];
@@ -446,6 +446,17 @@ k_pemit(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents
         }
         for (; jj < cp; jj += 32) o[jj] = par | ((uint64_t)__ldg(lst + jj) << pa.key_shift);
     }
+}
+
+// Parents per CTA of the pattern count and emit kernels: all 256 threads' worth on long parent
+// lists, fewer on short ones so that the emit (one warp per parent) still fills every SM with
+// about eight CTAs -- with 256 per CTA a level of 6,032 parents ran on 24 CTAs.
+static uint64_t pattern_tile(uint64_t F) {
+    int sms = 148, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t pt = PE_THREADS;
+    while (pt > 8 && (F + pt - 1) / pt < (uint64_t)sms * 8) pt >>= 1;
+    return pt;
 }
 
 // ---------------------------------------------------------------------------
@@ -953,7 +964,7 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
     for (int j = 0; j < h.n_blocks; ++j) {
         const DevBlock& bl = h.blocks[j];
         const uint64_t items = bl.pattern ? F : F * (uint64_t)bl.W;
-        const uint64_t per_tile = bl.pattern ? PE_THREADS : EXP_TILE;
+        const uint64_t per_tile = bl.pattern ? pattern_tile(F) : EXP_TILE;
         const uint64_t tiles = (items + per_tile - 1) / per_tile;
         if (tiles > 0x7fffffffull) { set_error("level %d needs %llu tiles", j, (unsigned long long)tiles); return CT_ERR_LIMIT; }
         CT_TRY(s->tile_counts.ensure(tiles));
@@ -963,7 +974,7 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
         if (bl.pattern) pa = pat_args(s, j);
         if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j], st));
         if (bl.pattern)
-            k_pcount<<<(unsigned)tiles, PE_THREADS, 0, st>>>(pa, parents, F, s->tile_counts.p);
+            k_pcount<<<(unsigned)tiles, PE_THREADS, 0, st>>>(pa, parents, F, (uint32_t)per_tile, s->tile_counts.p);
         else
             k_expand_count<<<(unsigned)tiles, EXP_THREADS, 0, st>>>(s->d, s->tables.p, s->innerkey.p, j, parents,
                                                                    items, s->tile_counts.p);
@@ -978,7 +989,8 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
         if (Fn) {
             if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j + 2], st));
             if (bl.pattern)
-                k_pemit<<<(unsigned)tiles, PE_THREADS, 0, st>>>(pa, parents, F, s->tile_base.p, dst.p);
+                k_pemit<<<(unsigned)tiles, PE_THREADS, 0, st>>>(pa, parents, F, (uint32_t)per_tile, s->tile_base.p,
+                                                                dst.p);
             else
                 k_expand_emit<<<(unsigned)tiles, EXP_THREADS, EXP_THREADS * 32 * sizeof(uint64_t), st>>>(
                     s->d, s->tables.p, s->innerkey.p, j, parents, items, s->tile_base.p, dst.p);
