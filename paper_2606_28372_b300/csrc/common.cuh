@@ -26,7 +26,17 @@ struct DevCons {
     uint64_t table_off;       // word offset of row 0 in the table arena
     uint32_t rows;            // prod of outer value counts
     uint32_t scope;           // parameters the constraint reads (bit k: parameter k)
+    // compact truth table of a tabled constraint: one bit per combination of its own
+    // parameters, [row][cz_W words] with the in-block scope parameters in_k mixed-radix
+    // (stride in_stride, last fastest) inside a row; cz_off = CZ_NONE: the table bits
+    // are interpreted one by one instead
+    int32_t n_in;
+    int32_t in_k[MAXP];
+    int32_t in_stride[MAXP];
+    uint32_t cz_B, cz_W;      // combinations and words per row
+    uint64_t cz_off;          // word offset of row 0 in the compact arena
 };
+constexpr uint64_t CZ_NONE = ~0ull;
 
 // One enumeration block: consecutive parameters [s, e) whose Cartesian product
 // (B <= BLOCK_BITS_MAX points, W 32-bit words) is expanded per parent prefix.

@@ -103,6 +103,11 @@ struct ct_space {
     ct::DevBuf<uint32_t> tables;           // truth-mask arena
     ct::DevBuf<int32_t> d_tab_cons;
     ct::DevBuf<uint64_t> d_tab_prefix;
+    std::vector<int> cz_cons;              // tabled constraints with a compact truth table
+    std::vector<uint64_t> cz_prefix;       // cumulative compact words, size cz_cons.size() + 1
+    ct::DevBuf<uint32_t> compact;          // compact truth tables (input of the table build)
+    ct::DevBuf<int32_t> d_cz_cons;
+    ct::DevBuf<uint64_t> d_cz_prefix;
     ct::DevBuf<uint32_t> innerkey;         // per block: point -> key bits (shifted)
     bool tables_ready = false;
     std::vector<uint32_t> ik_host;         // innerkey tables before upload
@@ -144,7 +149,7 @@ struct ct_space {
 };
 
 namespace ct {
-ct_status ensure_device(ct_space* s);
+ct_status ensure_device(ct_space* s, cudaStream_t st = nullptr);
 ct_status ensure_balls(ct_space* s, int dmax);
 int wanted_radius(const ct_space* s);
 ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, int64_t n, uint64_t* d_out,

@@ -178,26 +178,32 @@ k_rule_scan(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, 
 
 // ------------------------------------------------------------------------------------
 // Table form of the scan for long key slices.  The key's fields are cut into groups of
-// adjacent fields (at most 8 bits, or one wider field of at most 12 bits); for each pending
-// candidate a CTA tabulates, per group and per bit pattern of the group, what the per-field
-// loop above computes for those fields, and a (key, candidate) pair then costs one table read
-// per group:
-//   rule 1: the group's index distance, four candidates to a 64-bit entry (16-bit lanes; the
-//           plan requires sum_k (r_k - 1) < 2^16, so lanes never carry);
+// adjacent fields (at most 8 bits, or one wider field of at most 12 bits; at most 8 groups;
+// keys of at most 59 bits); for each pending candidate a CTA tabulates, per group and per bit
+// pattern of the group, what the per-field loop above computes for those fields, and a
+// (key, candidate) pair then costs one table read per group:
+//   rule 1: the group's index distance, 16-bit lanes, eight candidates to a 16-byte entry (the
+//           plan requires sum_k (r_k - 1) < 2^15 - 1, so lanes never carry and a borrow test
+//           on 0x7fff + best - distance flags exactly the improving lanes);
 //   rules 2, 3: one byte per candidate: bit 0 "every field within +-1", bit 1 "every field
 //           unchanged or at its lower / higher occurring value", bits 2..7 the number of
-//           changed fields; groups combine by AND of the flags and a byte-wise sum of counts.
-// The minima, counts and (for set members) the fp32 Euclidean distance are those of the loop.
+//           changed fields; groups combine by AND of the flags and a byte-wise sum of counts,
+//           and only keys in some candidate's sets take the per-candidate work.
+// Groups are laid out widest first, so every group's first entry is a multiple of its size and
+// a key's byte offset into the tables is one shift, AND and OR per group.  The minima, counts
+// and (for set members) the fp32 Euclidean distance are those of the loop; a thread visits its
+// keys in increasing order and keeps strict improvements, so the first key wins ties.
 // ------------------------------------------------------------------------------------
-constexpr int LUT_MAX_GROUPS = 16;
+constexpr int LUT_MAX_GROUPS = 8;
 constexpr int LUT_MIN_SLICE = 32768;             // keys per CTA that amortise the tables
 constexpr size_t LUT_MAX_BYTES = 64 * 1024;
+constexpr size_t RULE2_MIN_BYTES = (size_t)3 * RQ * RT * sizeof(unsigned long long);
 
 struct LutPlan {
     int ng, entries;                             // groups; entries of one table set
     int shift[LUT_MAX_GROUPS];                   // lowest key bit of the group
     uint32_t mask[LUT_MAX_GROUPS];               // (1 << width) - 1
-    int base[LUT_MAX_GROUPS];                    // first entry of the group
+    int base[LUT_MAX_GROUPS];                    // first entry of the group (a multiple of mask + 1)
     int k0[LUT_MAX_GROUPS], k1[LUT_MAX_GROUPS];  // parameters k0..k1 of the group
 };
 
@@ -206,37 +212,125 @@ static bool lut_plan(const ct_space* s, int rule, int64_t slice, LutPlan& pl) {
     if (const char* env = getenv("CATUNE_RULE_LUT_MIN_SLICE")) min_slice = strtoll(env, nullptr, 10);
     if (slice < min_slice) return false;
     const DevSpace& h = s->h;
+    if (h.key_bits > 59) return false;
     int64_t sum_r = 0;
     for (int k = 0; k < h.n; ++k) sum_r += h.r[k] - 1;
-    if (rule == 1 && sum_r >= 65536) return false;
+    if (rule == 1 && sum_r >= 32767) return false;   // 16-bit lanes with a borrow guard bit
     pl.ng = 0;
-    pl.entries = 0;
+    int width[LUT_MAX_GROUPS];
     int k = h.n - 1;                             // the last parameter holds the lowest bits
     while (k >= 0) {
         if (pl.ng == LUT_MAX_GROUPS) return false;
         const int g = pl.ng++;
         pl.k1[g] = k;
         pl.shift[g] = h.off[k];
-        int width = h.w[k];
-        if (width > 12) return false;
+        int w = h.w[k];
+        if (w > 12) return false;
         --k;
-        while (k >= 0 && width <= 8 && width + h.w[k] <= 8) width += h.w[k--];
+        while (k >= 0 && w <= 8 && w + h.w[k] <= 8) w += h.w[k--];
         pl.k0[g] = k + 1;
-        pl.mask[g] = (1u << width) - 1u;
-        pl.base[g] = pl.entries;
-        pl.entries += 1 << width;
+        pl.mask[g] = (1u << w) - 1u;
+        width[g] = w;
     }
-    const size_t bytes = (size_t)pl.entries * 8 * (rule == 1 ? 2 : 1);
+    pl.entries = 0;
+    for (int w = 12; w >= 0; --w)                // widest first: bases stay aligned
+        for (int g = 0; g < pl.ng; ++g)
+            if (width[g] == w) { pl.base[g] = pl.entries; pl.entries += 1 << w; }
+    const size_t bytes = (size_t)pl.entries * (rule == 1 ? 16 : 8);
     return bytes <= LUT_MAX_BYTES;
 }
 
+// per-thread scan state of one chunk of RQ candidates
 template <int RULE>
+struct RuleScan {
+    uint32_t v[4];                    // rule 1: 0x7fff + best distance, two 16-bit lanes per word
+    int64_t bi[RQ];                   // rule 1: rank of the best key
+    unsigned long long* b;            // rule 2: packed (distance bits, rank) of (candidate q, set t)
+                                      // at b[(3 q + t) * RT] (shared memory: set members are rare)
+    uint32_t c3[RQ][3];               // rule 3: set sizes
+};
+
+template <int RULE, int NG>
+__device__ __forceinline__ void rule_visit(const DevSpace* __restrict__ sp, uint64_t v, int64_t i, int nq, int N,
+                                           float eps, const float (*xs)[MAXP], const char* __restrict__ tab,
+                                           const uint32_t (&rs)[NG], const uint32_t (&mk)[NG],
+                                           const uint32_t (&bb)[NG], RuleScan<RULE>& S) {
+    const uint64_t kx = v << 5;
+    uint32_t a[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) a[g] = ((uint32_t)(kx >> rs[g]) & mk[g]) | bb[g];
+    if (RULE == 1) {
+        uint32_t d[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const uint4 w = *reinterpret_cast<const uint4*>(tab + a[g]);
+            d[0] += w.x; d[1] += w.y; d[2] += w.z; d[3] += w.w;
+        }
+        uint32_t m[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m[j] = (S.v[j] - d[j]) & 0x80008000u;
+        if (m[0] | m[1] | m[2] | m[3]) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t f = (m[j] >> 15) * 0xffffu;
+                S.v[j] = (S.v[j] & ~f) | ((d[j] + 0x7fff7fffu) & f);
+                if (m[j] & 0x8000u) S.bi[2 * j] = i;
+                if (m[j] & 0x80000000u) S.bi[2 * j + 1] = i;
+            }
+        }
+    } else {
+        uint32_t f0 = ~0u, f1 = ~0u, n0 = 0, n1 = 0;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const uint2 w = *reinterpret_cast<const uint2*>(tab + a[g]);
+            f0 &= w.x; f1 &= w.y;
+            n0 += (w.x >> 2) & 0x3f3f3f3fu;
+            n1 += (w.y >> 2) & 0x3f3f3f3fu;
+        }
+        // the key matters to some candidate only if it is in one of its sets: an adjacency flag,
+        // or exactly one changed parameter (a zero byte of n ^ 0x01..; the borrow test is exact
+        // about whether any byte is zero)
+        const uint32_t x0 = n0 ^ 0x01010101u, x1 = n1 ^ 0x01010101u;
+        const uint32_t one = ((x0 - 0x01010101u) & ~x0) | ((x1 - 0x01010101u) & ~x1);
+        if (!(((f0 | f1) & 0x03030303u) | (one & 0x80808080u))) return;
+        const unsigned long long fl = ((unsigned long long)f1 << 32) | f0;
+        const unsigned long long nd = ((unsigned long long)n1 << 32) | n0;
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+            if (q >= nq) break;
+            const uint32_t n = (uint32_t)((nd >> (8 * q)) & 0xffu);
+            if (n == 0) continue;
+            const uint32_t f = (uint32_t)((fl >> (8 * q)) & 3u);
+            const uint32_t mm = f | (n == 1 ? 4u : 0u);
+            if (RULE == 3) {
+#pragma unroll
+                for (int t = 0; t < 3; ++t) S.c3[q][t] += (mm >> t) & 1u;
+            } else if (mm) {
+                float sum = 0.0f;
+                for (int k = 0; k < N; ++k) {
+                    const float dd = __fsub_rn(__fmul_rn((float)field(sp, v, k), eps), xs[q][k]);
+                    sum = __fadd_rn(sum, __fmul_rn(dd, dd));
+                }
+                const unsigned long long p = ((unsigned long long)__float_as_uint(sum) << 32) | (unsigned long long)i;
+#pragma unroll
+                for (int t = 0; t < 3; ++t)
+                    if ((mm >> t) & 1u) {
+                        unsigned long long& bt = S.b[(3 * q + t) * RT];
+                        bt = p < bt ? p : bt;
+                    }
+            }
+        }
+    }
+}
+
+template <int RULE, int NG>
 __global__ void __launch_bounds__(RT)
 k_rule_scan_lut(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, int64_t nv, int64_t slice,
                 const RuleCand* __restrict__ rc, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
                 const float* __restrict__ pos, float eps, unsigned long long* __restrict__ best,
                 uint32_t* __restrict__ cnt, const __grid_constant__ LutPlan pl) {
-    extern __shared__ unsigned long long tab[];  // rule 1: [2][entries]; rules 2, 3: [entries]
+    // rule 1: [entries][2]; rules 2, 3: [entries]; rule 2 then the per-thread minima [3 RQ][RT]
+    extern __shared__ __align__(16) unsigned long long tab[];
     __shared__ RuleCand cs[RQ];
     __shared__ float xs[RQ][MAXP];
     __shared__ unsigned long long red[RT / 32][RQ][3];
@@ -251,7 +345,7 @@ k_rule_scan_lut(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ ke
     __syncthreads();
     for (int e = threadIdx.x; e < pl.entries; e += RT) {
         int g = 0;
-        while (g + 1 < pl.ng && pl.base[g + 1] <= e) ++g;
+        while (g + 1 < pl.ng && !(e >= pl.base[g] && e <= pl.base[g] + (int)pl.mask[g])) ++g;
         const uint32_t local = (uint32_t)(e - pl.base[g]);
         unsigned long long t0 = 0, t1 = 0;
         for (int q = 0; q < nq; ++q) {
@@ -276,77 +370,64 @@ k_rule_scan_lut(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ ke
                 t0 |= byte << (8 * q);
             }
         }
-        tab[e] = t0;
-        if (RULE == 1) tab[pl.entries + e] = t1;
+        if (RULE == 1) { tab[2 * e] = t0; tab[2 * e + 1] = t1; }
+        else tab[e] = t0;
     }
     __syncthreads();
-    const int64_t lo = (int64_t)blockIdx.x * slice, hi = min(nv, lo + slice);
-    unsigned long long b[RQ][3];
-    uint32_t c3[RQ][3], bl[RQ];
-    int64_t bi[RQ];
+    constexpr int LGE = RULE == 1 ? 4 : 3;       // log2 of the entry size
+    uint32_t rs[NG], mk[NG], bb[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        rs[g] = (uint32_t)(pl.shift[g] + 5 - LGE);
+        mk[g] = pl.mask[g] << LGE;
+        bb[g] = (uint32_t)pl.base[g] << LGE;
+    }
+    RuleScan<RULE> S;
+    S.b = tab + (size_t)pl.entries + threadIdx.x;   // rule 2 only (the region exists then)
+    if (RULE == 2)
+#pragma unroll
+        for (int e = 0; e < 3 * RQ; ++e) S.b[e * RT] = ~0ull;
 #pragma unroll
     for (int q = 0; q < RQ; ++q) {
-        b[q][0] = b[q][1] = b[q][2] = ~0ull;
-        c3[q][0] = c3[q][1] = c3[q][2] = 0;
-        bl[q] = ~0u;
-        bi[q] = 0;
+        S.c3[q][0] = S.c3[q][1] = S.c3[q][2] = 0;
+        S.bi[q] = 0;
     }
-    for (int64_t i = lo + threadIdx.x; i < hi; i += RT) {
-        const uint64_t v = __ldg(keys + i);
-        if (RULE == 1) {
-            unsigned long long a0 = 0, a1 = 0;
-            for (int g = 0; g < pl.ng; ++g) {
-                const int e = pl.base[g] + (int)((v >> pl.shift[g]) & pl.mask[g]);
-                a0 += tab[e];
-                a1 += tab[pl.entries + e];
-            }
+    unsigned long long b1[RQ];   // rule 1: packed (distance, rank) after the scan
 #pragma unroll
-            for (int q = 0; q < RQ; ++q) {   // first key of the thread's stride wins ties
-                const uint32_t l = (uint32_t)(((q < 4 ? a0 : a1) >> (16 * (q & 3))) & 0xffffu);
-                if (l < bl[q]) { bl[q] = l; bi[q] = i; }
-            }
-        } else {
-            unsigned long long fl = ~0ull, nd = 0;
-            for (int g = 0; g < pl.ng; ++g) {
-                const unsigned long long t = tab[pl.base[g] + (int)((v >> pl.shift[g]) & pl.mask[g])];
-                fl &= t;
-                nd += (t >> 2) & 0x3f3f3f3f3f3f3f3full;
-            }
+    for (int q = 0; q < RQ; ++q) b1[q] = ~0ull;
 #pragma unroll
-            for (int q = 0; q < RQ; ++q) {
-                if (q >= nq) break;
-                const uint32_t n = (uint32_t)((nd >> (8 * q)) & 0xffu);
-                if (n == 0) continue;
-                const uint32_t f = (uint32_t)((fl >> (8 * q)) & 3u);
-                const uint32_t m = f | (n == 1 ? 4u : 0u);
-                if (RULE == 3) {
-#pragma unroll
-                    for (int t = 0; t < 3; ++t) c3[q][t] += (m >> t) & 1u;
-                } else if (m) {
-                    float s = 0.0f;
-                    for (int k = 0; k < N; ++k) {
-                        const float dd = __fsub_rn(__fmul_rn((float)field(sp, v, k), eps), xs[q][k]);
-                        s = __fadd_rn(s, __fmul_rn(dd, dd));
-                    }
-                    const unsigned long long p = ((unsigned long long)__float_as_uint(s) << 32) | (unsigned long long)i;
-#pragma unroll
-                    for (int t = 0; t < 3; ++t)
-                        if ((m >> t) & 1u) b[q][t] = p < b[q][t] ? p : b[q][t];
-                }
-            }
-        }
+    for (int j = 0; j < 4; ++j)   // lanes past the chunk start at 0x7fff and never improve
+        S.v[j] = (2 * j < nq ? 0xfffeu : 0x7fffu) | ((2 * j + 1 < nq ? 0xfffeu : 0x7fffu) << 16);
+    const char* tb = reinterpret_cast<const char*>(tab);
+    const int64_t lo = (int64_t)blockIdx.x * slice, hi = min(nv, lo + slice);   // slice is even
+    int64_t i = lo + 2 * threadIdx.x;
+    for (; i + 2 * RT + 1 < hi; i += 4 * RT) {   // two key pairs in flight per thread
+        const ulonglong2 k0 = __ldg(reinterpret_cast<const ulonglong2*>(keys + i));
+        const ulonglong2 k1 = __ldg(reinterpret_cast<const ulonglong2*>(keys + i + 2 * RT));
+        rule_visit<RULE, NG>(sp, k0.x, i, nq, N, eps, xs, tb, rs, mk, bb, S);
+        rule_visit<RULE, NG>(sp, k0.y, i + 1, nq, N, eps, xs, tb, rs, mk, bb, S);
+        rule_visit<RULE, NG>(sp, k1.x, i + 2 * RT, nq, N, eps, xs, tb, rs, mk, bb, S);
+        rule_visit<RULE, NG>(sp, k1.y, i + 2 * RT + 1, nq, N, eps, xs, tb, rs, mk, bb, S);
+    }
+    for (; i < hi; i += 2 * RT) {
+        rule_visit<RULE, NG>(sp, __ldg(keys + i), i, nq, N, eps, xs, tb, rs, mk, bb, S);
+        if (i + 1 < hi) rule_visit<RULE, NG>(sp, __ldg(keys + i + 1), i + 1, nq, N, eps, xs, tb, rs, mk, bb, S);
     }
     if (RULE == 1) {
 #pragma unroll
-        for (int q = 0; q < RQ; ++q)
-            if (bl[q] != ~0u) b[q][0] = ((unsigned long long)bl[q] << 32) | (unsigned long long)bi[q];
+        for (int q = 0; q < RQ; ++q) {
+            const uint32_t lv = (S.v[q >> 1] >> (16 * (q & 1))) & 0xffffu;
+            if (q < nq && lv < 0xfffeu)   // the lane improved at least once
+                b1[q] = ((unsigned long long)(lv - 0x7fffu) << 32) | (unsigned long long)S.bi[q];
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < RQ; ++q)
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
-            unsigned long long v = RULE == 3 ? (unsigned long long)c3[q][t] : b[q][t];
+            unsigned long long v = RULE == 3 ? (unsigned long long)S.c3[q][t]
+                                   : RULE == 2 ? S.b[(3 * q + t) * RT] : (t == 0 ? b1[q] : ~0ull);
             for (int o = 16; o; o >>= 1) {
                 const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
                 v = RULE == 3 ? v + w : (w < v ? w : v);
@@ -364,6 +445,35 @@ k_rule_scan_lut(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ ke
         if (RULE == 3) cnt[((size_t)(q0 + q) * 3 + t) * gridDim.x + blockIdx.x] = (uint32_t)v;
         else if (RULE == 1 && t == 0) atomicMin(best + (size_t)(q0 + q) * 3, v);
         else if (RULE == 2) atomicMin(best + (size_t)(q0 + q) * 3 + t, v);
+    }
+}
+
+template <int RULE, int NG>
+static void launch_lut_ng(dim3 grid, size_t bytes, cudaStream_t st, const ct_space* s, int64_t slice,
+                          const RuleCand* rc, const RuleScratch& r, const float* d_pos, float eps,
+                          unsigned long long* best, uint32_t* cnt, const LutPlan& pl) {
+    static std::once_flag once;   // allow the largest table set (and rule 2's minima) as dynamic shared memory
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_rule_scan_lut<RULE, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(LUT_MAX_BYTES + (RULE == 2 ? RULE2_MIN_BYTES : 0)));
+    });
+    k_rule_scan_lut<RULE, NG><<<grid, RT, bytes, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p,
+                                                      r.count.p, d_pos, eps, best, cnt, pl);
+}
+
+template <int RULE>
+static void launch_lut(dim3 grid, size_t bytes, cudaStream_t st, const ct_space* s, int64_t slice, const RuleCand* rc,
+                       const RuleScratch& r, const float* d_pos, float eps, unsigned long long* best, uint32_t* cnt,
+                       const LutPlan& pl) {
+    switch (pl.ng) {
+        case 1: launch_lut_ng<RULE, 1>(grid, bytes, st, s, slice, rc, r, d_pos, eps, best, cnt, pl); break;
+        case 2: launch_lut_ng<RULE, 2>(grid, bytes, st, s, slice, rc, r, d_pos, eps, best, cnt, pl); break;
+        case 3: launch_lut_ng<RULE, 3>(grid, bytes, st, s, slice, rc, r, d_pos, eps, best, cnt, pl); break;
+        case 4: launch_lut_ng<RULE, 4>(grid, bytes, st, s, slice, rc, r, d_pos, eps, best, cnt, pl); break;
+        case 5: launch_lut_ng<RULE, 5>(grid, bytes, st, s, slice, rc, r, d_pos, eps, best, cnt, pl); break;
+        case 6: launch_lut_ng<RULE, 6>(grid, bytes, st, s, slice, rc, r, d_pos, eps, best, cnt, pl); break;
+        case 7: launch_lut_ng<RULE, 7>(grid, bytes, st, s, slice, rc, r, d_pos, eps, best, cnt, pl); break;
+        default: launch_lut_ng<RULE, 8>(grid, bytes, st, s, slice, rc, r, d_pos, eps, best, cnt, pl); break;
     }
 }
 
@@ -494,40 +604,30 @@ ct_status repair_rule_impl(ct_space* s, RuleScratch& r, int rule, const uint64_t
     const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 8);
     k_rule_prep<<<g1, 256, 0, st>>>(s->d, s->tables.p, rule == 1 ? nullptr : s->occ.p, d_cand, n, d_out, r.pend.p,
                                     r.count.p, (RuleCand*)r.rc.p);
-    const int64_t slice = ((int64_t)s->n_valid + slices - 1) / slices;
+    int64_t slice = ((int64_t)s->n_valid + slices - 1) / slices;
+    slice += slice & 1;   // even: the table scan reads key pairs
     const dim3 grid(slices, (unsigned)((n + RQ - 1) / RQ));
     RuleCand* rc = (RuleCand*)r.rc.p;
     LutPlan pl;
     const bool lut = lut_plan(s, rule, slice, pl);
-    const size_t lut_bytes = lut ? (size_t)pl.entries * 8 * (rule == 1 ? 2 : 1) : 0;
-    if (lut) {
-        static std::once_flag once;   // allow the largest table set as dynamic shared memory
-        std::call_once(once, [] {
-            cudaFuncSetAttribute(k_rule_scan_lut<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LUT_MAX_BYTES);
-            cudaFuncSetAttribute(k_rule_scan_lut<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LUT_MAX_BYTES);
-            cudaFuncSetAttribute(k_rule_scan_lut<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LUT_MAX_BYTES);
-        });
-    }
+    const size_t lut_bytes = lut ? (size_t)pl.entries * (rule == 1 ? 16 : 8) + (rule == 2 ? RULE2_MIN_BYTES : 0) : 0;
     if (rule == 1) {
         if (lut)
-            k_rule_scan_lut<1><<<grid, RT, lut_bytes, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p,
-                                                            r.count.p, nullptr, 0.0f, r.best.p, nullptr, pl);
+            launch_lut<1>(grid, lut_bytes, st, s, slice, rc, r, nullptr, 0.0f, r.best.p, nullptr, pl);
         else
             k_rule_scan<1><<<grid, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p,
                                                 nullptr, 0.0f, r.best.p, nullptr);
         k_rule_finish<<<g1, 256, 0, st>>>(s->keys.p, r.pend.p, r.count.p, r.best.p, d_out);
     } else if (rule == 2) {
         if (lut)
-            k_rule_scan_lut<2><<<grid, RT, lut_bytes, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p,
-                                                            r.count.p, d_pos, eps, r.best.p, nullptr, pl);
+            launch_lut<2>(grid, lut_bytes, st, s, slice, rc, r, d_pos, eps, r.best.p, nullptr, pl);
         else
             k_rule_scan<2><<<grid, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p,
                                                 d_pos, eps, r.best.p, nullptr);
         k_rule_finish<<<g1, 256, 0, st>>>(s->keys.p, r.pend.p, r.count.p, r.best.p, d_out);
     } else {
         if (lut)
-            k_rule_scan_lut<3><<<grid, RT, lut_bytes, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p,
-                                                            r.count.p, nullptr, 0.0f, nullptr, r.cnt.p, pl);
+            launch_lut<3>(grid, lut_bytes, st, s, slice, rc, r, nullptr, 0.0f, nullptr, r.cnt.p, pl);
         else
             k_rule_scan<3><<<grid, RT, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, slice, rc, r.pend.p, r.count.p,
                                                 nullptr, 0.0f, nullptr, r.cnt.p);

@@ -133,9 +133,50 @@ __global__ void k_unpack(const DevSpace* __restrict__ sp, const uint64_t* __rest
     }
 }
 
+// Compact truth tables: bit (row, c) = the constraint at the outer values of `row` and the
+// in-block scope values of combination c (one interpreted evaluation per combination).
+__global__ void k_build_compact(const DevSpace* __restrict__ sp, const int32_t* __restrict__ cz_cons,
+                                const uint64_t* __restrict__ cz_prefix, int n_cz, uint64_t total_words,
+                                uint32_t* __restrict__ compact) {
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t gw = gid >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= total_words) return;   // whole warps share gw
+    int lo = 0, hi = n_cz - 1;       // last i with cz_prefix[i] <= gw
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (cz_prefix[mid] <= gw) lo = mid; else hi = mid - 1;
+    }
+    const DevCons& cs = sp->cons[cz_cons[lo]];
+    const uint64_t lw = gw - cz_prefix[lo];
+    const uint32_t row = (uint32_t)(lw / cs.cz_W), wd = (uint32_t)(lw % cs.cz_W);
+    const uint32_t c = wd * 32 + lane;
+    bool bit = false;
+    if (c < cs.cz_B) {
+        int64_t pv[MAXP];            // only the scope's parameters are set: the program reads no other
+        uint32_t o = row;
+        for (int q = cs.n_outer - 1; q >= 0; --q) {
+            const int k = cs.outer_k[q];
+            const int32_t ik = (int32_t)(o % sp->r[k]);
+            o /= sp->r[k];
+            pv[k] = sp->values[sp->vstart[k] + ik];
+        }
+        uint32_t t = c;
+        for (int q = 0; q < cs.n_in; ++q) {   // in_k runs from the last parameter backwards
+            const int k = cs.in_k[q];
+            const int32_t ik = (int32_t)(t % sp->r[k]);
+            t /= sp->r[k];
+            pv[k] = sp->values[sp->vstart[k] + ik];
+        }
+        bit = vm_eval(sp->prog, cs.pc, cs.len, pv);
+    }
+    const uint32_t word = __ballot_sync(0xffffffffu, bit);
+    if (lane == 0) compact[gw] = word;
+}
+
 __global__ void k_build_tables(const DevSpace* __restrict__ sp, const int32_t* __restrict__ tab_cons,
                                const uint64_t* __restrict__ tab_prefix, int n_tab, uint64_t total_words,
-                               uint32_t* __restrict__ tables) {
+                               const uint32_t* __restrict__ compact, uint32_t* __restrict__ tables) {
     const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t gw = gid >> 5;
     const int lane = threadIdx.x & 31;
@@ -151,7 +192,14 @@ __global__ void k_build_tables(const DevSpace* __restrict__ sp, const int32_t* _
     const uint32_t row = (uint32_t)(lw / bl.W), wd = (uint32_t)(lw % bl.W);
     const int p = wd * 32 + lane;
     bool bit = false;
-    if (p < bl.B) {
+    if (p < bl.B && cs.cz_off != CZ_NONE) {   // gather from the compact table
+        uint32_t c = 0;
+        for (int q = 0; q < cs.n_in; ++q) {
+            const int k = cs.in_k[q];
+            c += (uint32_t)((p / bl.pstride[k - bl.s]) % sp->r[k]) * (uint32_t)cs.in_stride[q];
+        }
+        bit = (__ldg(compact + cs.cz_off + (uint64_t)row * cs.cz_W + (c >> 5)) >> (c & 31)) & 1u;
+    } else if (p < bl.B) {
         int64_t pv[MAXP];
         for (int k = 0; k < sp->n; ++k) pv[k] = 0;
         uint32_t o = row;
@@ -587,6 +635,9 @@ static ct_status lower(ct_space* s, int32_t n, const int32_t* nv, const int64_t*
     if (const char* env = getenv("CATUNE_TABLE_WORDS")) per_cons = total_cap = strtoull(env, nullptr, 10);
     s->tab_cons.clear();
     s->tab_prefix.assign(1, 0);
+    s->cz_cons.clear();
+    s->cz_prefix.assign(1, 0);
+    uint64_t cz_words = 0;
     for (int j = 0; j < h.n_blocks; ++j) { h.blocks[j].cons_begin = h.blocks[j].cons_end = 0; h.blocks[j].has_vm = 0; }
     for (int ci = 0; ci < h.n_cons; ++ci) {
         const Raw& rc = raw[order[ci]];
@@ -602,6 +653,7 @@ static ct_status lower(ct_space* s, int32_t n, const int32_t* nv, const int64_t*
         uint64_t stride = 1;
         for (int q = cs.n_outer - 1; q >= 0; --q) { cs.outer_stride[q] = (int32_t)stride; stride *= h.r[cs.outer_k[q]]; }
         const uint64_t tw = rows * (uint64_t)bl.W;
+        cs.cz_off = CZ_NONE;
         if (rows < (1ull << 31) && tw <= per_cons && words + tw <= total_cap) {
             cs.tabled = 1;
             cs.rows = (uint32_t)rows;
@@ -609,6 +661,21 @@ static ct_status lower(ct_space* s, int32_t n, const int32_t* nv, const int64_t*
             words += tw;
             s->tab_cons.push_back(ci);
             s->tab_prefix.push_back(words);
+            // the table repeats each combination of the constraint's own parameters B / Bc
+            // times: evaluate every combination once when that at least halves the work
+            uint64_t bc = 1;
+            cs.n_in = 0;
+            for (int k = bl.e - 1; k >= bl.s; --k)
+                if (rc.scope >> k & 1) { cs.in_k[cs.n_in] = k; cs.in_stride[cs.n_in++] = (int32_t)bc; bc *= (uint64_t)h.r[k]; }
+            const uint64_t czw = rows * ((bc + 31) / 32);
+            if (2 * bc <= (uint64_t)bl.B) {
+                cs.cz_B = (uint32_t)bc;
+                cs.cz_W = (uint32_t)((bc + 31) / 32);
+                cs.cz_off = cz_words;
+                cz_words += czw;
+                s->cz_cons.push_back(ci);
+                s->cz_prefix.push_back(cz_words);
+            }
         } else {
             cs.tabled = 0;
         }
@@ -654,8 +721,49 @@ static ct_status lower(ct_space* s, int32_t n, const int32_t* nv, const int64_t*
     return CT_OK;
 }
 
+// Pinned host staging shared by the uploads of small host tables: one copy into it, one
+// asynchronous copy per table, one synchronisation, instead of a synchronous copy per table.
+namespace {
+struct PinnedStage {
+    std::mutex mu;
+    char* p = nullptr;
+    size_t cap = 0;
+};
+PinnedStage g_stage;
+
+struct Upload {
+    void* dst;
+    const void* src;
+    size_t bytes;
+};
+
+ct_status stage_uploads(const std::vector<Upload>& ups, cudaStream_t st) {
+    size_t bytes = 0;
+    for (const Upload& u : ups) bytes += (u.bytes + 15) & ~size_t(15);
+    if (!bytes) return CT_OK;
+    std::lock_guard<std::mutex> lk(g_stage.mu);
+    if (g_stage.cap < bytes) {
+        if (g_stage.p) cudaFreeHost(g_stage.p);
+        g_stage.p = nullptr;
+        g_stage.cap = 0;
+        const size_t want = std::max<size_t>(bytes, 1 << 20);
+        CT_TRY_CUDA(cudaMallocHost(reinterpret_cast<void**>(&g_stage.p), want));
+        g_stage.cap = want;
+    }
+    size_t off = 0;
+    for (const Upload& u : ups) {
+        if (!u.bytes) continue;
+        memcpy(g_stage.p + off, u.src, u.bytes);
+        CT_TRY_CUDA(cudaMemcpyAsync(u.dst, g_stage.p + off, u.bytes, cudaMemcpyHostToDevice, st));
+        off += (u.bytes + 15) & ~size_t(15);
+    }
+    CT_TRY_CUDA(cudaStreamSynchronize(st));   // the stage is reused by the next upload
+    return CT_OK;
+}
+}  // namespace
+
 // first device use: descriptor, tables, ball plan and status word go to the current device
-ct_status ensure_device(ct_space* s) {
+ct_status ensure_device(ct_space* s, cudaStream_t st) {
     if (s->d) return CT_OK;
     const DevSpace& h = s->h;
     cudaGetDevice(&s->device);
@@ -664,20 +772,28 @@ ct_status ensure_device(ct_space* s) {
         s->d = static_cast<DevSpace*>(dev_alloc(sizeof(DevSpace), &e));
         if (!s->d) { set_error("device allocation failed: %s", cudaGetErrorString(e)); return CT_ERR_OOM; }
     }
-    CT_TRY_CUDA(cudaMemcpy(s->d, &h, sizeof(DevSpace), cudaMemcpyHostToDevice));
+    std::vector<Upload> ups;
+    ups.push_back({s->d, &h, sizeof(DevSpace)});
     CT_TRY(s->innerkey.ensure(s->ik_host.size()));
-    CT_TRY_CUDA(cudaMemcpy(s->innerkey.p, s->ik_host.data(), s->ik_host.size() * 4, cudaMemcpyHostToDevice));
+    ups.push_back({s->innerkey.p, s->ik_host.data(), s->ik_host.size() * 4});
     CT_TRY(s->tables.ensure(s->tab_prefix.back()));
     if (!s->tab_cons.empty()) {
         CT_TRY(s->d_tab_cons.ensure(s->tab_cons.size()));
         CT_TRY(s->d_tab_prefix.ensure(s->tab_prefix.size()));
-        CT_TRY_CUDA(cudaMemcpy(s->d_tab_cons.p, s->tab_cons.data(), s->tab_cons.size() * 4, cudaMemcpyHostToDevice));
-        CT_TRY_CUDA(cudaMemcpy(s->d_tab_prefix.p, s->tab_prefix.data(), s->tab_prefix.size() * 8, cudaMemcpyHostToDevice));
+        ups.push_back({s->d_tab_cons.p, s->tab_cons.data(), s->tab_cons.size() * 4});
+        ups.push_back({s->d_tab_prefix.p, s->tab_prefix.data(), s->tab_prefix.size() * 8});
+    }
+    if (!s->cz_cons.empty()) {
+        CT_TRY(s->d_cz_cons.ensure(s->cz_cons.size()));
+        CT_TRY(s->d_cz_prefix.ensure(s->cz_prefix.size()));
+        ups.push_back({s->d_cz_cons.p, s->cz_cons.data(), s->cz_cons.size() * 4});
+        ups.push_back({s->d_cz_prefix.p, s->cz_prefix.data(), s->cz_prefix.size() * 8});
     }
     CT_TRY(s->status.ensure(1));
-    CT_TRY_CUDA(cudaMemset(s->status.p, 0, 4));
+    CT_TRY_CUDA(cudaMemsetAsync(s->status.p, 0, 4, st));
     CT_TRY(s->pat_cnt.ensure(s->pat_cnt_words));
     CT_TRY(s->pat_list.ensure(s->pat_list_words));
+    CT_TRY(stage_uploads(ups, st));
     CT_TRY_CUDA(cudaFuncSetAttribute(k_expand_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      EXP_THREADS * 32 * (int)sizeof(uint64_t)));
     return CT_OK;
@@ -754,47 +870,19 @@ static void plan_balls(ct_space* s, int dmax) {
     }
 }
 
-// Pinned host staging shared by the uploads of small host tables: one copy into it, one
-// asynchronous copy per table, one synchronisation, instead of a synchronous copy per table.
-namespace {
-struct PinnedStage {
-    std::mutex mu;
-    char* p = nullptr;
-    size_t cap = 0;
-};
-PinnedStage g_stage;
-}  // namespace
 
 // Device part: uploads every planned radius that has no device tables yet.
 static ct_status upload_balls(ct_space* s, cudaStream_t st) {
-    size_t bytes = 0;
-    for (const BallRadius& br : s->balls)
-        if (!br.d_masks.p) bytes += br.masks.size() * 4 + 16 + br.prefix.size() * 8 + 16;
-    if (!bytes) return CT_OK;
-    CT_TRY(ensure_device(s));
-    std::lock_guard<std::mutex> lk(g_stage.mu);
-    if (g_stage.cap < bytes) {
-        if (g_stage.p) cudaFreeHost(g_stage.p);
-        g_stage.p = nullptr;
-        g_stage.cap = 0;
-        const size_t want = std::max<size_t>(bytes, 1 << 20);
-        CT_TRY_CUDA(cudaMallocHost(reinterpret_cast<void**>(&g_stage.p), want));
-        g_stage.cap = want;
-    }
-    size_t off = 0;
+    std::vector<Upload> ups;
     for (BallRadius& br : s->balls) {
         if (br.d_masks.p) continue;
+        if (ups.empty()) CT_TRY(ensure_device(s, st));
         CT_TRY(br.d_masks.ensure(br.masks.size()));
         CT_TRY(br.d_prefix.ensure(br.prefix.size()));
-        memcpy(g_stage.p + off, br.masks.data(), br.masks.size() * 4);
-        CT_TRY_CUDA(cudaMemcpyAsync(br.d_masks.p, g_stage.p + off, br.masks.size() * 4, cudaMemcpyHostToDevice, st));
-        off += (br.masks.size() * 4 + 15) & ~size_t(15);
-        memcpy(g_stage.p + off, br.prefix.data(), br.prefix.size() * 8);
-        CT_TRY_CUDA(cudaMemcpyAsync(br.d_prefix.p, g_stage.p + off, br.prefix.size() * 8, cudaMemcpyHostToDevice, st));
-        off += (br.prefix.size() * 8 + 15) & ~size_t(15);
+        ups.push_back({br.d_masks.p, br.masks.data(), br.masks.size() * 4});
+        ups.push_back({br.d_prefix.p, br.prefix.data(), br.prefix.size() * 8});
     }
-    CT_TRY_CUDA(cudaStreamSynchronize(st));   // the stage is reused by the next upload
-    return CT_OK;
+    return stage_uploads(ups, st);
 }
 
 ct_status ensure_balls(ct_space* s, int dmax) {
@@ -805,11 +893,19 @@ ct_status ensure_balls(ct_space* s, int dmax) {
 static ct_status ensure_tables(ct_space* s, cudaStream_t st) {
     if (s->tables_ready) return CT_OK;
     const uint64_t words = s->tab_prefix.back();
+    const uint64_t cz_words = s->cz_prefix.back();
+    if (cz_words) {
+        CT_TRY(s->compact.ensure(cz_words));
+        const unsigned grid = (unsigned)((cz_words * 32 + 255) / 256);
+        k_build_compact<<<grid, 256, 0, st>>>(s->d, s->d_cz_cons.p, s->d_cz_prefix.p, (int)s->cz_cons.size(), cz_words,
+                                              s->compact.p);
+        count_launch();
+    }
     if (words) {
         const uint64_t threads = words * 32;
         const unsigned grid = (unsigned)((threads + 255) / 256);
         k_build_tables<<<grid, 256, 0, st>>>(s->d, s->d_tab_cons.p, s->d_tab_prefix.p, (int)s->tab_cons.size(),
-                                             words, s->tables.p);
+                                             words, s->compact.p, s->tables.p);
         count_launch();
         CT_TRY_CUDA(cudaGetLastError());
     }
@@ -852,6 +948,7 @@ ct_space::~ct_space() {
     if (d) dev_free(d, sizeof(ct::DevSpace));
     pat_cnt.release(); pat_list.release();
     tables.release(); d_tab_cons.release(); d_tab_prefix.release(); innerkey.release();
+    compact.release(); d_cz_cons.release(); d_cz_prefix.release();
     keys.release(); tile_counts.release(); tile_base.release(); d_total.release(); status.release();
     for (auto& f : frontier) f.release();
     for (auto& b : balls) { b.d_masks.release(); b.d_prefix.release(); }
@@ -945,7 +1042,7 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
     const auto ms_since = [](clk::time_point a) { return std::chrono::duration<float, std::milli>(clk::now() - a).count(); };
     const auto t0 = clk::now();
     cudaStream_t st = (cudaStream_t)stream;
-    CT_TRY(ensure_device(s));
+    CT_TRY(ensure_device(s, st));
     CT_TRY(ensure_tables(s, st));
     const float setup_ms = ms_since(t0);
     const auto t1 = clk::now();
