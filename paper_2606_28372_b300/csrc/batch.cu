@@ -130,8 +130,10 @@ __device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t*
         const uint64_t* prefix = bs.prefix[d - 1];
         const int nsub = bs.n_subsets[d - 1];
         const uint64_t total = (uint64_t)np * pts;
-        for (uint64_t g = t; g < total; g += nt) {
-            const uint64_t q = g / pts, j = g - q * pts;
+        const uint64_t dq = (uint64_t)nt / pts, dj = (uint64_t)nt - dq * pts;
+        uint64_t q = (uint64_t)t / pts, j = (uint64_t)t - q * pts;   // (g / pts, g % pts), stepped with g
+        for (uint64_t g = t; g < total; g += nt, q += dq, j += dj) {
+            if (j >= pts) { j -= pts; ++q; }
             const uint64_t u = cand[rs.pend[q]];
             int lo = 0, hi = nsub - 1;
             while (lo < hi) {
@@ -146,13 +148,14 @@ __device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t*
             while (m) {
                 const int k = 31 - __clz(m);
                 m &= ~(1u << k);
-                const uint32_t alt = (uint32_t)sp->r[k] - 1u;
-                const uint32_t a = local % alt;
-                local /= alt;
+                uint32_t a;
+                local = div_alt(sp, k, local, &a);
                 const uint32_t uk = (uint32_t)field(sp, u, k);
                 key = (key & ~sp->fmask[k]) | ((uint64_t)(a < uk ? a : a + 1u) << sp->off[k]);
             }
-            if (valid_changed(sp, bs.tables, key, S)) atomicMin(&rs.best[q], (unsigned long long)key);
+            // the atomic only when the key beats the candidate's current best
+            if (key < *(volatile unsigned long long*)&rs.best[q] && valid_changed(sp, bs.tables, key, S))
+                atomicMin(&rs.best[q], (unsigned long long)key);
         }
         __syncthreads();
         if (t == 0) {

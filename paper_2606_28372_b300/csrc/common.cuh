@@ -65,6 +65,7 @@ struct DevSpace {
     int32_t n, key_bits, n_cons, n_blocks;
     int32_t r[MAXP], w[MAXP], off[MAXP], vstart[MAXP];
     uint64_t fmask[MAXP];     // field mask in place
+    uint32_t alt_rcp[MAXP];   // floor(2^32 / (r_k - 1)) + 1: quotients by r_k - 1 (see div_alt)
     uint64_t swar_low;        // every bit of every field except the field's top bit
     uint64_t swar_high;       // the top bit of every field of width >= 1
     uint64_t domain_bits;     // bits used by the key
@@ -131,6 +132,20 @@ __device__ __forceinline__ uint64_t uint64_below(uint32_t whi, uint32_t wlo, uin
 // ------------------------------------------------------------------------------
 __device__ __forceinline__ int32_t field(const DevSpace* sp, uint64_t key, int k) {
     return (int32_t)((key & sp->fmask[k]) >> sp->off[k]);
+}
+
+// t / (r_k - 1) and t % (r_k - 1) for any 32-bit t (r_k >= 2), by the reciprocal method of
+// Granlund and Montgomery: with M = floor(2^32 / a) + 1, umulhi(t, M) is floor(t / a) or one
+// more (M exceeds 2^32 / a by at most 1, so the error is below t / 2^32 < 1); one correction
+// step fixes the overshoot.
+__device__ __forceinline__ uint32_t div_alt(const DevSpace* __restrict__ sp, int k, uint32_t t, uint32_t* rem) {
+    const uint32_t a = (uint32_t)sp->r[k] - 1u;
+    if (a == 1u) { *rem = 0u; return t; }   // M = 2^32 + 1 does not fit
+    uint32_t q = __umulhi(t, sp->alt_rcp[k]);
+    int32_t r = (int32_t)(t - q * a);
+    if (r < 0) { --q; r += (int32_t)a; }
+    *rem = (uint32_t)r;
+    return q;
 }
 
 // 1 when every field is < r_k and no bit above the key is set.

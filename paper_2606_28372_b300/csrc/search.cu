@@ -91,8 +91,12 @@ k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, con
        const int32_t* __restrict__ pend, const uint32_t* __restrict__ count, unsigned long long* __restrict__ best,
        const uint64_t* __restrict__ fail) {
     const uint64_t total = (uint64_t)(*count) * points;
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t q = g / points, j = g - q * points;
+    const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t dq = G / points, dj = G - dq * points;
+    uint64_t q = g0 / points, j = g0 - q * points;   // (g / points, g % points), stepped with g
+    for (uint64_t g = g0; g < total; g += G, q += dq, j += dj) {
+        if (j >= points) { j -= points; ++q; }
         const uint64_t u = __ldg(cand + pend[q]);
         int lo = 0, hi = n_subsets - 1;   // last subset with prefix <= j
         while (lo < hi) {
@@ -107,14 +111,15 @@ k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, con
         while (m) {
             const int k = 31 - __clz(m);
             m &= ~(1u << k);
-            const uint32_t alt = (uint32_t)sp->r[k] - 1u;
-            const uint32_t a = local % alt;
-            local /= alt;
+            uint32_t a;
+            local = div_alt(sp, k, local, &a);
             const uint32_t uk = (uint32_t)field(sp, u, k);
             const uint32_t v = a < uk ? a : a + 1u;
             key = (key & ~sp->fmask[k]) | ((uint64_t)v << sp->off[k]);
         }
-        if (fail ? valid_changed(sp, tables, key, S) : valid_key(sp, tables, key))
+        // the atomic only when the key beats the candidate's current best (read from L2): a
+        // high-radius ball can hold 10^5 valid points of one candidate
+        if (key < __ldcg(best + q) && (fail ? valid_changed(sp, tables, key, S) : valid_key(sp, tables, key)))
             atomicMin(best + q, (unsigned long long)key);
     }
 }

@@ -547,6 +547,7 @@ static ct_status lower(ct_space* s, int32_t n, const int32_t* nv, const int64_t*
     h.swar_low = h.swar_high = 0;
     for (int k = 0; k < n; ++k) {
         h.fmask[k] = h.w[k] ? (((h.w[k] == 64) ? ~0ull : ((1ull << h.w[k]) - 1)) << h.off[k]) : 0ull;
+        h.alt_rcp[k] = h.r[k] > 2 ? (uint32_t)((1ull << 32) / (uint64_t)(h.r[k] - 1) + 1) : 0u;
         if (h.w[k]) {
             h.swar_high |= 1ull << (h.off[k] + h.w[k] - 1);
             h.swar_low |= h.fmask[k] & ~(1ull << (h.off[k] + h.w[k] - 1));
