@@ -69,6 +69,7 @@ struct DevSpace {
     uint64_t swar_low;        // every bit of every field except the field's top bit
     uint64_t swar_high;       // the top bit of every field of width >= 1
     uint64_t domain_bits;     // bits used by the key
+    const uint32_t* compact;  // compact truth tables of the tabled constraints (device arena)
     int64_t values[MAXV];
     DevCons cons[MAXC];
     DevBlock blocks[MAXP];
@@ -286,19 +287,31 @@ __device__ __forceinline__ bool fixes_possible(const DevSpace* __restrict__ sp, 
     return true;
 }
 
+// One constraint at an in-domain key from its compact truth table: only the constraint's own
+// parameters are read (the block tables need the key's whole block).
+__device__ __forceinline__ bool cons_holds_compact(const DevSpace* __restrict__ sp, const DevCons& cs, uint64_t key) {
+    uint32_t row = 0, c = 0;
+    for (int q = 0; q < cs.n_outer; ++q) row += (uint32_t)field(sp, key, cs.outer_k[q]) * (uint32_t)cs.outer_stride[q];
+    for (int q = 0; q < cs.n_in; ++q) c += (uint32_t)field(sp, key, cs.in_k[q]) * (uint32_t)cs.in_stride[q];
+    const uint32_t wv = __ldg(sp->compact + cs.cz_off + (uint64_t)row * cs.cz_W + (c >> 5));
+    return (wv >> (c & 31)) & 1u;
+}
+
 // ... and then it is valid iff the constraints reading a parameter of S hold at it.
 __device__ __forceinline__ bool valid_changed(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
                                               uint64_t key, uint32_t S) {
-    const int nb = sp->n_blocks;
-    for (int j = 0; j < nb; ++j) {
-        const DevBlock& bl = sp->blocks[j];
-        bool any = false;
-        for (int c = bl.cons_begin; c < bl.cons_end; ++c) any = any || (sp->cons[c].scope & S);
-        if (!any) continue;
+    const int nc = sp->n_cons;
+    for (int c = 0; c < nc; ++c) {
+        const DevCons& cs = sp->cons[c];
+        if (!(cs.scope & S)) continue;
+        if (cs.cz_off != CZ_NONE) {
+            if (!cons_holds_compact(sp, cs, key)) return false;
+            continue;
+        }
+        const DevBlock& bl = sp->blocks[cs.block];
         int32_t p = 0;
         for (int k = bl.s; k < bl.e; ++k) p += field(sp, key, k) * bl.pstride[k - bl.s];
-        for (int c = bl.cons_begin; c < bl.cons_end; ++c)
-            if ((sp->cons[c].scope & S) && !cons_holds(sp, tables, key, bl, c, p)) return false;
+        if (!cons_holds(sp, tables, key, bl, c, p)) return false;
     }
     return true;
 }

@@ -790,6 +790,8 @@ ct_status ensure_device(ct_space* s, cudaStream_t st) {
         ups.push_back({s->d_cz_cons.p, s->cz_cons.data(), s->cz_cons.size() * 4});
         ups.push_back({s->d_cz_prefix.p, s->cz_prefix.data(), s->cz_prefix.size() * 8});
     }
+    CT_TRY(s->compact.ensure(s->cz_prefix.back()));
+    s->h.compact = s->compact.p;   // before the descriptor's copy below is staged
     CT_TRY(s->status.ensure(1));
     CT_TRY_CUDA(cudaMemsetAsync(s->status.p, 0, 4, st));
     CT_TRY(s->pat_cnt.ensure(s->pat_cnt_words));
