@@ -356,47 +356,77 @@ static __device__ void propose_dev(const OptArgs& a, uint32_t gen, uint64_t* __r
     }
 }
 
-// GA mutation: with probability p_mut, a random valid Hamming neighbour
+// GA mutation: with probability p_mut, a random valid Hamming neighbour.  Aware runs: the child
+// is valid (it was repaired), so a neighbour that changes parameter k is valid iff the constraints
+// reading k hold at it.  A warp takes one child; its lanes test the neighbours in (parameter,
+// value) order 32 at a time, a count pass and a pick pass over the same order.
+__device__ __forceinline__ uint64_t ga_neighbour(const DevSpace* __restrict__ sp, uint64_t u, int N, uint32_t n,
+                                                 int* kout) {
+    int k = 0;
+    uint32_t acc = 0;
+    while (k < N - 1 && acc + (uint32_t)(sp->r[k] - 1) <= n) { acc += (uint32_t)(sp->r[k] - 1); ++k; }
+    const uint32_t idx = n - acc, uk = (uint32_t)field(sp, u, k);
+    const uint32_t v = idx < uk ? idx : idx + 1u;   // the other values of k, ascending
+    *kout = k;
+    return (u & ~sp->fmask[k]) | ((uint64_t)v << sp->off[k]);
+}
+
 static __device__ void post_repair_dev(const OptArgs& a, uint32_t gen, uint64_t* __restrict__ keys, int s = 0) {
     if (a.kind != CT_GA || gen == 0) return;
     const DevSpace* sp = a.sp;
-    for (int i = threadIdx.x; i < a.P; i += blockDim.x) {
-        uint32_t w[4];
-        rng_block(a.seed, (uint32_t)(i + s * a.P), gen, PU_GA_MUT, 0, w);
-        if (!(u01(w[0]) < a.prm.ga_pmut)) continue;
-        const uint64_t u = keys[i];
-        if (!a.prm.constraint_aware) {   // baseline: one random parameter takes another value
+    if (!a.prm.constraint_aware) {   // baseline: one random parameter takes another value
+        for (int i = threadIdx.x; i < a.P; i += blockDim.x) {
+            uint32_t w[4];
+            rng_block(a.seed, (uint32_t)(i + s * a.P), gen, PU_GA_MUT, 0, w);
+            if (!(u01(w[0]) < a.prm.ga_pmut)) continue;
+            const uint64_t u = keys[i];
             const int k = (int)uint_below(w[1], (uint32_t)a.N);
             if (sp->r[k] < 2) continue;
             const uint32_t v = uint_below(w[2], (uint32_t)(sp->r[k] - 1)), uk = (uint32_t)field(sp, u, k);
             keys[i] = (u & ~sp->fmask[k]) | ((uint64_t)(v < uk ? v : v + 1u) << sp->off[k]);
-            continue;
         }
+        return;
+    }
+    uint32_t total = 0;   // Hamming-1 neighbours of any point
+    for (int k = 0; k < a.N; ++k) total += (uint32_t)(sp->r[k] - 1);
+    const int lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    for (int i = (int)(threadIdx.x >> 5); i < a.P; i += nw) {
+        uint32_t w[4];
+        rng_block(a.seed, (uint32_t)(i + s * a.P), gen, PU_GA_MUT, 0, w);
+        if (!(u01(w[0]) < a.prm.ga_pmut)) continue;   // the same draw in every lane
+        const uint64_t u = keys[i];
         uint32_t cnt = 0;
-        for (int k = 0; k < a.N; ++k) {
-            const int uk = field(sp, u, k);
-            for (int v = 0; v < sp->r[k]; ++v) {
-                if (v == uk) continue;
-                const uint64_t kk = (u & ~sp->fmask[k]) | ((uint64_t)v << sp->off[k]);
-                cnt += valid_key(sp, a.tables, kk);
+        for (uint32_t base = 0; base < total; base += 32) {
+            bool ok = false;
+            if (base + lane < total) {
+                int k;
+                const uint64_t kk = ga_neighbour(sp, u, a.N, base + lane, &k);
+                ok = valid_changed(sp, a.tables, kk, 1u << k);
             }
+            cnt += (uint32_t)__popc(__ballot_sync(0xffffffffu, ok));
         }
         if (!cnt) continue;
         const uint32_t pick = uint_below(w[1], cnt);
         uint32_t seen = 0;
         uint64_t res = u;
-        for (int k = 0; k < a.N && res == u; ++k) {
-            const int uk = field(sp, u, k);
-            for (int v = 0; v < sp->r[k]; ++v) {
-                if (v == uk) continue;
-                const uint64_t kk = (u & ~sp->fmask[k]) | ((uint64_t)v << sp->off[k]);
-                if (valid_key(sp, a.tables, kk)) {
-                    if (seen == pick) { res = kk; break; }
-                    ++seen;
-                }
+        for (uint32_t base = 0; base < total; base += 32) {
+            bool ok = false;
+            uint64_t kk = u;
+            if (base + lane < total) {
+                int k;
+                kk = ga_neighbour(sp, u, a.N, base + lane, &k);
+                ok = valid_changed(sp, a.tables, kk, 1u << k);
             }
+            uint32_t bal = __ballot_sync(0xffffffffu, ok);
+            const uint32_t c = (uint32_t)__popc(bal);
+            if (pick < seen + c) {   // the (pick - seen)-th valid neighbour of this group
+                for (uint32_t t = 0; t < pick - seen; ++t) bal &= bal - 1u;
+                res = __shfl_sync(0xffffffffu, kk, __ffs(bal) - 1);
+                break;
+            }
+            seen += c;
         }
-        keys[i] = res;
+        if (lane == 0) keys[i] = res;
     }
 }
 
