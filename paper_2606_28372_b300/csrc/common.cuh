@@ -70,6 +70,7 @@ struct DevSpace {
     uint64_t swar_high;       // the top bit of every field of width >= 1
     uint64_t domain_bits;     // bits used by the key
     const uint32_t* compact;  // compact truth tables of the tabled constraints (device arena)
+    uint64_t pcons[MAXP];     // constraints reading parameter k (bit c: constraint c)
     int64_t values[MAXV];
     DevCons cons[MAXC];
     DevBlock blocks[MAXP];
@@ -246,6 +247,27 @@ __device__ __forceinline__ bool cons_holds(const DevSpace* __restrict__ sp, cons
     return vm_eval(sp->prog, cs.pc, cs.len, pv);
 }
 
+// One constraint at an in-domain key from its compact truth table: only the constraint's own
+// parameters are read (the block tables need the key's whole block).
+__device__ __forceinline__ bool cons_holds_compact(const DevSpace* __restrict__ sp, const DevCons& cs, uint64_t key) {
+    uint32_t row = 0, c = 0;
+    for (int q = 0; q < cs.n_outer; ++q) row += (uint32_t)field(sp, key, cs.outer_k[q]) * (uint32_t)cs.outer_stride[q];
+    for (int q = 0; q < cs.n_in; ++q) c += (uint32_t)field(sp, key, cs.in_k[q]) * (uint32_t)cs.in_stride[q];
+    const uint32_t wv = __ldg(sp->compact + cs.cz_off + (uint64_t)row * cs.cz_W + (c >> 5));
+    return (wv >> (c & 31)) & 1u;
+}
+
+// One constraint at an in-domain key, from its compact table when it has one.
+__device__ __forceinline__ bool cons_at(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
+                                       uint64_t key, int c) {
+    const DevCons& cs = sp->cons[c];
+    if (cs.cz_off != CZ_NONE) return cons_holds_compact(sp, cs, key);
+    const DevBlock& bl = sp->blocks[cs.block];
+    int32_t p = 0;
+    for (int k = bl.s; k < bl.e; ++k) p += field(sp, key, k) * bl.pstride[k - bl.s];
+    return cons_holds(sp, tables, key, bl, c, p);
+}
+
 // Full-tuple constraint test of an in-domain key: AND over every constraint.
 __device__ __forceinline__ bool valid_key(const DevSpace* __restrict__ sp,
                                           const uint32_t* __restrict__ tables, uint64_t key) {
@@ -287,16 +309,6 @@ __device__ __forceinline__ bool fixes_possible(const DevSpace* __restrict__ sp, 
     return true;
 }
 
-// One constraint at an in-domain key from its compact truth table: only the constraint's own
-// parameters are read (the block tables need the key's whole block).
-__device__ __forceinline__ bool cons_holds_compact(const DevSpace* __restrict__ sp, const DevCons& cs, uint64_t key) {
-    uint32_t row = 0, c = 0;
-    for (int q = 0; q < cs.n_outer; ++q) row += (uint32_t)field(sp, key, cs.outer_k[q]) * (uint32_t)cs.outer_stride[q];
-    for (int q = 0; q < cs.n_in; ++q) c += (uint32_t)field(sp, key, cs.in_k[q]) * (uint32_t)cs.in_stride[q];
-    const uint32_t wv = __ldg(sp->compact + cs.cz_off + (uint64_t)row * cs.cz_W + (c >> 5));
-    return (wv >> (c & 31)) & 1u;
-}
-
 // ... and then it is valid iff the constraints reading a parameter of S hold at it.
 __device__ __forceinline__ bool valid_changed(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
                                               uint64_t key, uint32_t S) {
@@ -314,6 +326,99 @@ __device__ __forceinline__ bool valid_changed(const DevSpace* __restrict__ sp, c
         if (!cons_holds(sp, tables, key, bl, c, p)) return false;
     }
     return true;
+}
+
+// Single-parameter filtering of the Hamming balls.  A point that changes exactly the parameters S
+// of a candidate u can be valid only if, for every k in S and every constraint c whose scope meets
+// S in k alone, c holds at u with k set to the point's value of k: c reads no other changed
+// parameter.  Parameters with more than 64 values are not filtered.
+
+// position of the n-th (from 0) set bit of m; m has more than n set bits
+__device__ __forceinline__ int nth_bit(uint64_t m, uint32_t n) {
+    for (uint32_t t = 0; t < n; ++t) m &= m - 1;
+    return __ffsll((long long)m) - 1;
+}
+
+// The constraints (bit c) a point must still be tested on.
+__device__ __forceinline__ bool valid_rest(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
+                                           uint64_t key, uint64_t rest) {
+    while (rest) {
+        const int c = __ffsll((long long)rest) - 1;
+        rest &= rest - 1;
+        if (!cons_at(sp, tables, key, c)) return false;
+    }
+    return true;
+}
+
+// Enumeration plan of one (candidate, subset), built by a whole warp (every lane returns the same
+// plan): per parameter of S (highest first, the fastest digit) its allowed values (mask; 0 for an
+// unfiltered parameter, whose values are all but u_k) and their count, and the constraints still
+// to test at each point (those reading a parameter of S that the masks do not settle).  The lanes
+// test the values of a parameter in parallel and a ballot forms each constraint's mask.  Returns
+// the number of points (0: none).
+struct BallPlan {
+    uint64_t al[MAX_RADIUS];
+    uint32_t cnt[MAX_RADIUS], uk[MAX_RADIUS];
+    int k[MAX_RADIUS];
+    int d;
+    uint64_t rest;
+};
+
+__device__ __forceinline__ uint64_t ball_plan_warp(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
+                                                   uint64_t u, uint32_t S, int lane, BallPlan& bp) {
+    uint64_t size = 1, touched = 0, cov = 0;
+    bp.d = 0;
+    uint32_t m = S;
+#pragma unroll
+    for (int e = 0; e < MAX_RADIUS; ++e) {
+        if (!m) break;
+        const int k = 31 - __clz(m);
+        m &= ~(1u << k);
+        const int r = sp->r[k];
+        const uint32_t uk = (uint32_t)field(sp, u, k);
+        const uint64_t pc = sp->pcons[k];
+        touched |= pc;
+        uint64_t a = 0;
+        uint32_t cnt = (uint32_t)r - 1u;
+        if (r <= 64) {
+            a = (r == 64 ? ~0ull : ((1ull << r) - 1ull)) & ~(1ull << uk);
+            for (uint64_t cm = pc; cm && a; cm &= cm - 1) {
+                const int c = __ffsll((long long)cm) - 1;
+                if ((sp->cons[c].scope & S) != (1u << k)) continue;
+                uint64_t mk = 0;
+                for (int v0 = 0; v0 < r; v0 += 32) {
+                    const int v = v0 + lane;
+                    bool ok = false;
+                    if (v < r && ((a >> v) & 1ull))
+                        ok = cons_at(sp, tables, (u & ~sp->fmask[k]) | ((uint64_t)v << sp->off[k]), c);
+                    mk |= (uint64_t)__ballot_sync(0xffffffffu, ok) << v0;
+                }
+                a &= mk;
+                cov |= 1ull << c;
+            }
+            cnt = (uint32_t)__popcll(a);
+        }
+        bp.al[e] = a; bp.cnt[e] = cnt; bp.uk[e] = uk; bp.k[e] = k;
+        bp.d = e + 1;
+        size *= cnt;
+    }
+    bp.rest = touched & ~cov;
+    return size;
+}
+
+// The idx-th point of a plan.
+__device__ __forceinline__ uint64_t ball_point(const DevSpace* __restrict__ sp, uint64_t u, const BallPlan& bp,
+                                               uint64_t idx) {
+    uint64_t key = u;
+#pragma unroll
+    for (int e = 0; e < MAX_RADIUS; ++e) {
+        if (e >= bp.d) break;
+        const uint32_t dg = (uint32_t)(idx % bp.cnt[e]);
+        idx /= bp.cnt[e];
+        const uint32_t v = bp.al[e] ? (uint32_t)nth_bit(bp.al[e], dg) : (dg < bp.uk[e] ? dg : dg + 1u);
+        key = (key & ~sp->fmask[bp.k[e]]) | ((uint64_t)v << sp->off[bp.k[e]]);
+    }
+    return key;
 }
 
 // lower_bound over the sorted keys: first position with keys[pos] >= x.

@@ -124,6 +124,44 @@ k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, con
     }
 }
 
+// Radii whose subsets hold at least this many points on average take the filtered search (a warp
+// per (candidate, subset) pays for its plan only on large subsets; smaller ones keep a thread per
+// point).  On the large space that is radius 5 and above.
+constexpr uint64_t BALL_FS_MIN_AVG = 512;
+
+// The ball search with single-parameter filtering: a warp per (pending candidate, subset); the
+// lanes take the subset's allowed points 32 at a time, test the constraints the masks do not
+// settle, and the warp minimum goes to the candidate's best with at most one atomicMin.
+__global__ void __launch_bounds__(256)
+k_ball_fs(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, const uint32_t* __restrict__ masks,
+          int n_subsets, const uint64_t* __restrict__ cand, const int32_t* __restrict__ pend,
+          const uint32_t* __restrict__ count, unsigned long long* __restrict__ best, const uint64_t* __restrict__ fail) {
+    const uint64_t total = (uint64_t)(*count) * (uint64_t)n_subsets;
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nwarps) {
+        const uint64_t q = w / (uint64_t)n_subsets;
+        const int si = (int)(w - q * (uint64_t)n_subsets);
+        const int32_t i = pend[q];
+        const uint32_t S = __ldg(masks + si);
+        if (!fixes_possible(sp, __ldg(fail + i), S)) continue;   // the same in every lane
+        const uint64_t u = __ldg(cand + i);
+        BallPlan bp;
+        const uint64_t size = ball_plan_warp(sp, tables, u, S, lane, bp);
+        unsigned long long bl = ~0ull;
+        for (uint64_t idx = (uint64_t)lane; idx < size; idx += 32) {
+            const uint64_t key = ball_point(sp, u, bp, idx);
+            if (key < bl && valid_rest(sp, tables, key, bp.rest)) bl = key;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, bl, o);
+            bl = y < bl ? y : bl;
+        }
+        if (lane == 0 && bl != ~0ull && bl < __ldcg(best + q)) atomicMin(best + q, bl);
+    }
+}
+
 // settle candidates whose ball held a valid point; requeue the rest
 __global__ void k_ball_resolve(int d, const int32_t* __restrict__ pend_in, const uint32_t* __restrict__ count_in,
                                const unsigned long long* __restrict__ best_in, uint64_t* __restrict__ out,
@@ -431,10 +469,19 @@ ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, in
     int cur = 0;
     for (int d = 1; d <= dmax; ++d) {
         const BallRadius& br = s->balls[d - 1];
-        const uint64_t work = (uint64_t)n * br.total;
-        const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 4);   // one wave
-        k_ball<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
-                                   d_cand, pend[cur], cnt[cur], best[cur], rs.fail.p);
+        if (br.total >= BALL_FS_MIN_AVG * br.masks.size()) {
+            // large subsets: a warp per (candidate, subset) over the filtered points
+            const uint64_t work = (uint64_t)n * br.masks.size() * 32;
+            const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 4);   // one wave
+            k_ball_fs<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, (int)br.masks.size(), d_cand, pend[cur],
+                                          cnt[cur], best[cur], rs.fail.p);
+        } else {
+            // small subsets: a thread per point
+            const uint64_t work = (uint64_t)n * br.total;
+            const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 4);   // one wave
+            k_ball<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
+                                       d_cand, pend[cur], cnt[cur], best[cur], rs.fail.p);
+        }
         count_launch();
         CT_TRY_CUDA(cudaMemsetAsync(cnt[cur ^ 1], 0, 4, st));
         k_ball_resolve<<<g1, 256, 0, st>>>(d, pend[cur], cnt[cur], best[cur], d_out, d_dist, pend[cur ^ 1],

@@ -689,6 +689,13 @@ static ct_status lower(ct_space* s, int32_t n, const int32_t* nv, const int64_t*
     }
     for (int j = 0; j < h.n_blocks; ++j) if (h.blocks[j].cons_end == 0) h.blocks[j].cons_begin = 0;
 
+    for (int k = 0; k < h.n; ++k) {
+        h.pcons[k] = 0;
+        for (int ci = 0; ci < h.n_cons; ++ci)
+            if (h.cons[ci].scope >> k & 1) h.pcons[k] |= 1ull << ci;
+    }
+
+
     // pattern plan: U = parameters before the block read by its constraints
     const uint64_t PAT_SIG_MAX = 1ull << 22, PAT_LIST_WORDS_MAX = 1ull << 26;   // 256 MB of lists
     s->pat_cnt_words = s->pat_list_words = 0;
