@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <cstdlib>
 
 #include "internal.hpp"
 
@@ -466,10 +467,12 @@ ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, in
     count_launch();
     const int dmax = wanted_radius(s);
     CT_TRY(ensure_balls(s, dmax));   // normally planned already (after the build, at run creation)
+    uint64_t fs_min_avg = BALL_FS_MIN_AVG;   // CATUNE_BALL_FS_MIN_AVG overrides it (tests)
+    if (const char* env = getenv("CATUNE_BALL_FS_MIN_AVG")) fs_min_avg = strtoull(env, nullptr, 10);
     int cur = 0;
     for (int d = 1; d <= dmax; ++d) {
         const BallRadius& br = s->balls[d - 1];
-        if (br.total >= BALL_FS_MIN_AVG * br.masks.size()) {
+        if (br.total >= fs_min_avg * br.masks.size()) {
             // large subsets: a warp per (candidate, subset) over the filtered points
             const uint64_t work = (uint64_t)n * br.masks.size() * 32;
             const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 4);   // one wave

@@ -35,9 +35,16 @@ def test_lookup(pairs, name):
     assert np.array_equal(rank.cpu().numpy(), p.O.lookup(p.okeys, c))
 
 
+@pytest.mark.parametrize("filtered", [False, True])
 @pytest.mark.parametrize("name", ["tiny", "medium"])
 @pytest.mark.parametrize("mode,radius", [(0, 0), (1, 0), (2, 1), (2, 2), (2, 3)])
-def test_repair(pairs, name, mode, radius):
+def test_repair(pairs, name, mode, radius, filtered, monkeypatch):
+    """Every repair mode against the oracle, with the ball search per point and with the filtered
+    warp-per-subset search forced on every radius."""
+    if filtered:
+        if mode == 1:
+            pytest.skip("no ball search")
+        monkeypatch.setenv("CATUNE_BALL_FS_MIN_AVG", "0")
     p = pairs[name]
     c = _cands(p, 5 + mode + radius)
     p.sp.set_repair_mode(mode, radius)
@@ -173,7 +180,7 @@ def test_scan_widths_and_odd_tail(oracle_mod, scan_spaces, count, lut, monkeypat
 
 
 @pytest.mark.parametrize("mode", [0, 1])
-def test_large_repair_by_groups(oracle_mod, mode):
+def test_large_repair_by_groups(oracle_mod, mode):   # mode 0 runs the filtered search at radii 5, 6
     """Full-size large space in the bench's launch configuration (the scan over 695,228,960 keys
     runs with the distance tables): no constraint spans the two parameter groups, so the Hamming
     distance splits into the groups' distances and the nearest key, ties to the smallest key, is
@@ -201,3 +208,21 @@ def test_large_repair_by_groups(oracle_mod, mode):
     want = (ra.astype(np.uint64) << np.uint64(bits_b)) | rb.astype(np.uint64)
     assert np.array_equal(from_dev_u64(out), want)
     assert np.array_equal(dist.cpu().numpy(), (da.astype(np.int64) + db).astype(np.uint8))
+
+
+@pytest.mark.parametrize("filtered", [False, True])
+def test_ball_search_spaces(oracle_mod, scan_spaces, filtered, monkeypatch):
+    """Ball search up to radius 3 on spaces with single-value parameters, keys wider than 32 bits
+    and a 300-value parameter (not filtered: more than 64 values), per point and filtered."""
+    if filtered:
+        monkeypatch.setenv("CATUNE_BALL_FS_MIN_AVG", "0")
+    for sd, osp, okeys, sp in scan_spaces:
+        cand = oracle_mod.pack(osp, W.uniform_tuples(sd, 96, seed=7))
+        sp.set_repair_mode(2, 3)
+        out = torch.empty(len(cand), dtype=torch.int64, device="cuda")
+        dist = torch.empty(len(cand), dtype=torch.uint8, device="cuda")
+        sp.repair(to_dev_u64(cand), out, dist)
+        sp.set_repair_mode(0, 0)
+        eo, ed = oracle_mod.repair(osp, okeys, cand)
+        assert np.array_equal(from_dev_u64(out), eo), sd.name
+        assert np.array_equal(dist.cpu().numpy(), ed), sd.name
