@@ -782,6 +782,51 @@ def run_scan(args):
     return 0
 
 
+def run_repair(args):
+    """Repair alone on --workload: calls of 256 uniform random tuples and 256 DE-like perturbations
+    of valid keys, per radius cap of the ball search (--radius; the cost-model radius by default),
+    milliseconds per call (CUDA events on the launching stream)."""
+    import torch
+    from paper_2606_28372_b300 import build as B
+    B.build()
+    from paper_2606_28372_b300 import catune as ct
+    from paper_2606_28372_b300 import workloads as W
+    dev = torch.device("cuda", 0)
+    sd = W.SPACES[args.workload]()
+    sp = ct.Space.from_def(sd)
+    nv = sp.build()
+    keys = sp.keys()
+    kinds = [args.kind] if args.kind != "both" else ["perturbed", "uniform"]
+    res = {}
+    for kind in kinds:
+        if kind == "uniform":
+            t = W.uniform_tuples(sd, 256, seed=100)
+        else:
+            ranks = torch.from_numpy(W.random_ranks(nv, 256, seed=200)).to(dev)
+            t = W.perturbed_tuples(sd, sp.unpack(keys[ranks].cpu().numpy().view(np.uint64)), seed=300)
+        c = torch.from_numpy(sp.pack(t).view(np.int64)).to(dev)
+        out = torch.empty(256, dtype=torch.int64, device=dev)
+        dist = torch.empty(256, dtype=torch.uint8, device=dev)
+        res[kind] = {}
+        for r in (args.radius or [0]):
+            sp.set_repair_mode(2 if r else 0, r)
+            for _ in range(args.warmup):
+                sp.repair(c, out, dist)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                sp.repair(c, out, dist)
+            e1.record()
+            torch.cuda.synchronize()
+            res[kind][f"radius_{r}" if r else "auto"] = {
+                "ms_per_call": e0.elapsed_time(e1) / max(1, args.steps),
+                "distance_hist": np.bincount(dist.cpu().numpy(), minlength=8)[:8].tolist()}
+        sp.set_repair_mode(0, 0)
+    print(json.dumps({"mode": "repair", "workload": args.workload, "n_valid": nv, "results": res}))
+    return 0
+
+
 def surrogate_large(torch, ct, sp, table, dev, gens=10):
     """The surrogate at the large size: DE pop 256 on the large space, milliseconds per
     generation for the plain run, for a run whose judge decides (the lognormal table holds
@@ -986,14 +1031,20 @@ if __name__ == "__main__":
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--quick", action="store_true", help="headline step only (no e2e, no sub-metrics)")
-    ap.add_argument("--mode", default="step", choices=["step", "scan", "aware", "variants", "batched", "rules", "surrogate"],
-                    help="scan: only the exhaustive repair scan (scan-only repair of 1, 2, 4 uniform candidates); "
+    ap.add_argument("--mode", default="step",
+                    choices=["step", "scan", "repair", "aware", "variants", "batched", "rules", "surrogate"],
+                    help="scan: only the exhaustive repair scan (scan-only repair of 1 to 32 uniform candidates); "
+                         "repair: only repair calls of 256 candidates on --workload (--kind, --radius); "
                          "aware: only the constraint-aware vs non-aware comparison over the density ladder; "
                          "variants: only the DE/GA operator comparison; batched: only the batched-runs "
                          "comparison; rules: only the paper's repair rules on --workload; surrogate: only the "
                          "surrogate-vs-plain comparison on the large space")
     ap.add_argument("--workload", default="large", choices=["large", "large_slice"],
                     help="large_slice: the same kernels on a 146M-key slice, for hardware-counter captures")
+    ap.add_argument("--kind", default="both", choices=["both", "perturbed", "uniform"],
+                    help="repair mode: the candidates")
+    ap.add_argument("--radius", type=int, nargs="*", default=None,
+                    help="repair mode: ball radius caps to time (default: the cost-model radius)")
     a = ap.parse_args()
     if a.impl == "reference":
         sys.exit(run_reference(a))
@@ -1007,4 +1058,6 @@ if __name__ == "__main__":
         sys.exit(run_surrogate(a))
     if a.mode == "rules":
         sys.exit(run_rules(a))
+    if a.mode == "repair":
+        sys.exit(run_repair(a))
     sys.exit(run_scan(a) if a.mode == "scan" else run_ours(a))
