@@ -437,6 +437,25 @@ __device__ __forceinline__ int64_t rank_of(const uint64_t* __restrict__ keys, in
     return (p < n && __ldg(keys + p) == x) ? p : -1;
 }
 
+// rank_of by a whole warp (every lane returns the result): a 32-ary search, each round narrowing
+// the range to one of 32 chunks with one probe per lane (the last key of each chunk), so about
+// log32 |V| rounds of independent loads instead of log2 |V| dependent ones.
+__device__ __forceinline__ int64_t rank_of_warp(const uint64_t* __restrict__ keys, int64_t n, uint64_t x, int lane) {
+    int64_t lo = 0, len = n;   // the first key >= x lies in [lo, lo + len]
+    while (len > 32) {
+        const int64_t step = (len + 31) / 32;
+        const int64_t pos = lo + (int64_t)(lane + 1) * step - 1;
+        const bool below = pos < lo + len && __ldg(keys + pos) < x;
+        const int c = __popc(__ballot_sync(0xffffffffu, below));   // chunks entirely below x
+        const int64_t nlo = lo + (int64_t)c * step;
+        len = min(step, lo + len - nlo);
+        lo = nlo;
+    }
+    const bool below = lane < len && __ldg(keys + lo + lane) < x;
+    const int64_t p = lo + __popc(__ballot_sync(0xffffffffu, below));
+    return (p < n && __ldg(keys + p) == x) ? p : -1;
+}
+
 // Status bits recorded by kernels into the space's device status word.
 constexpr uint32_t ST_BAD_CANDIDATE = 1u;
 

@@ -100,8 +100,9 @@ extern "C" ct_status ct_repair_noalloc(ct_space* s, const uint64_t* d_cand, int6
     unsigned long long* best[2] = {sc->best[0], sc->best[1]};
     uint32_t* cnt[2] = {&sc->count[0], &sc->count[1]};
     const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+    const unsigned gw = (unsigned)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sms * 8);   // a warp per candidate
     CT_TRY_CUDA(cudaMemsetAsync(sc->count, 0, sizeof sc->count, st));   // the counters must start at zero
-    k_repair_init<<<g1, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, pend[0], cnt[0], best[0],
+    k_repair_init<<<gw, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, pend[0], cnt[0], best[0],
                                       s->status.p, nullptr);   // no failing-constraint masks: full tests
     count_launch();
     // ball radii already enumerated (the build plans the ones the repair path uses); any

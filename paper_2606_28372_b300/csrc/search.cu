@@ -27,22 +27,30 @@ constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_CHUNK = 32;        // candidates per CTA of the scan
 constexpr unsigned long long NONE = ~0ull;
 
+// a warp per candidate (the warp's 32-ary rank search)
 __global__ void k_lookup(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, int64_t nv,
                          const uint64_t* __restrict__ cand, int64_t n, int64_t* __restrict__ rank) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
         const uint64_t c = cand[i];
-        rank[i] = in_domain(sp, c) ? rank_of(keys, nv, c) : -1;
+        const int64_t r = in_domain(sp, c) ? rank_of_warp(keys, nv, c, lane) : -1;
+        if (lane == 0) rank[i] = r;
     }
 }
 
+// a warp per candidate: the warp's rank search, then lane 0 does the lookups and the memo
 __global__ void k_evaluate(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, int64_t nv,
                            const float* __restrict__ table, const uint64_t* __restrict__ cand, int64_t n,
                            float* __restrict__ fit, int64_t* __restrict__ rank_out, uint32_t* __restrict__ memo,
                            unsigned long long* __restrict__ unique, const uint32_t* __restrict__ cost,
                            unsigned long long* __restrict__ cost_acc, float invalid_fit) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
         const uint64_t c = cand[i];
-        const int64_t r = in_domain(sp, c) ? rank_of(keys, nv, c) : -1;
+        const int64_t r = in_domain(sp, c) ? rank_of_warp(keys, nv, c, lane) : -1;
+        if (lane) continue;
         if (fit) fit[i] = r >= 0 ? __ldg(table + r) : invalid_fit;
         if (rank_out) rank_out[i] = r;
         if (memo && r >= 0) {
@@ -56,21 +64,30 @@ __global__ void k_evaluate(const DevSpace* __restrict__ sp, const uint64_t* __re
     }
 }
 
-// valid candidates map to themselves; the others are queued for the search
+// a warp per candidate: lane c tests constraint c (and c + 32), a ballot gives the failing mask;
+// lane 0 settles valid and out-of-domain candidates and queues the others
 __global__ void k_repair_init(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
                               const uint64_t* __restrict__ cand, int64_t n, uint64_t* __restrict__ out,
                               uint8_t* __restrict__ dist, int32_t* __restrict__ pend, uint32_t* __restrict__ count,
                               unsigned long long* __restrict__ best, uint32_t* __restrict__ status,
                               uint64_t* __restrict__ fail) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nc = sp->n_cons;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
         const uint64_t c = cand[i];
-        if (!in_domain(sp, c)) {
-            out[i] = c;
-            if (dist) dist[i] = 255;
-            atomicOr(status, ST_BAD_CANDIDATE);
+        if (!in_domain(sp, c)) {   // the same in every lane
+            if (lane == 0) {
+                out[i] = c;
+                if (dist) dist[i] = 255;
+                atomicOr(status, ST_BAD_CANDIDATE);
+            }
             continue;
         }
-        const uint64_t f = fail ? failing_mask(sp, tables, c) : (valid_key(sp, tables, c) ? 0ull : 1ull);
+        const bool f0 = lane < nc && !cons_at(sp, tables, c, lane);
+        const bool f1 = lane + 32 < nc && !cons_at(sp, tables, c, lane + 32);
+        const uint64_t f = (uint64_t)__ballot_sync(0xffffffffu, f0) | ((uint64_t)__ballot_sync(0xffffffffu, f1) << 32);
+        if (lane) continue;
         if (!f) {
             out[i] = c;
             if (dist) dist[i] = 0;
@@ -461,8 +478,9 @@ ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, in
     uint32_t* cnt[2] = {rs.counts.p, rs.counts.p + 1};
     const int sms = sm_count();
     const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+    const unsigned gi = (unsigned)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sms * 8);   // a warp per candidate
     CT_TRY_CUDA(cudaMemsetAsync(rs.counts.p, 0, 8, st));
-    k_repair_init<<<g1, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, pend[0], cnt[0], best[0], s->status.p,
+    k_repair_init<<<gi, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, pend[0], cnt[0], best[0], s->status.p,
                                       rs.fail.p);
     count_launch();
     const int dmax = wanted_radius(s);
@@ -524,7 +542,7 @@ ct_status ct_lookup(const ct_space* s, const uint64_t* d_cand, int64_t n, int64_
     if (!s || n < 0 || (n > 0 && (!d_cand || !d_rank))) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
     if (!s->built) { set_error("space not built"); return CT_ERR_STATE; }
     if (n == 0) return CT_OK;
-    const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+    const unsigned g = (unsigned)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sm_count() * 8);   // a warp per key
     k_lookup<<<g, 256, 0, (cudaStream_t)stream>>>(s->d, s->keys.p, (int64_t)s->n_valid, d_cand, n, d_rank);
     count_launch();
     CT_TRY_CUDA(cudaGetLastError());
@@ -553,7 +571,7 @@ ct_status evaluate_impl(ct_space* s, uint32_t* memo, unsigned long long* unique,
                         const uint64_t* d_keys, int64_t n, float* d_fit, int64_t* d_rank, cudaStream_t st,
                         float invalid_fit) {
     if (n == 0) return CT_OK;
-    const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+    const unsigned g = (unsigned)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sm_count() * 8);   // a warp per key
     k_evaluate<<<g, 256, 0, st>>>(s->d, s->keys.p, (int64_t)s->n_valid, s->fit, d_keys, n, d_fit, d_rank, memo, unique,
                                   memo && cost_acc ? s->cost : nullptr, cost_acc, invalid_fit);
     count_launch();
