@@ -149,7 +149,7 @@ struct ct_space {
 };
 
 namespace ct {
-ct_status ensure_device(ct_space* s, cudaStream_t st = nullptr);
+ct_status ensure_device(ct_space* s, cudaStream_t st = nullptr, bool sync = true);   // sync: wait for the uploads
 ct_status ensure_balls(ct_space* s, int dmax);
 int wanted_radius(const ct_space* s);
 ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, int64_t n, uint64_t* d_out,

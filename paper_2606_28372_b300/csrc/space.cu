@@ -730,12 +730,16 @@ static ct_status lower(ct_space* s, int32_t n, const int32_t* nv, const int64_t*
 }
 
 // Pinned host staging shared by the uploads of small host tables: one copy into it, one
-// asynchronous copy per table, one synchronisation, instead of a synchronous copy per table.
+// asynchronous copy per table, instead of a synchronous copy per table.  An event recorded after
+// the copies guards the stage: the next upload waits for it before overwriting the stage.  With
+// sync, the call also waits for its own copies (callers whose data other streams may read next).
 namespace {
 struct PinnedStage {
     std::mutex mu;
     char* p = nullptr;
     size_t cap = 0;
+    cudaEvent_t done = nullptr;   // the copies of the last upload
+    bool pending = false;
 };
 PinnedStage g_stage;
 
@@ -745,11 +749,16 @@ struct Upload {
     size_t bytes;
 };
 
-ct_status stage_uploads(const std::vector<Upload>& ups, cudaStream_t st) {
+ct_status stage_uploads(const std::vector<Upload>& ups, cudaStream_t st, bool sync) {
     size_t bytes = 0;
     for (const Upload& u : ups) bytes += (u.bytes + 15) & ~size_t(15);
     if (!bytes) return CT_OK;
     std::lock_guard<std::mutex> lk(g_stage.mu);
+    if (!g_stage.done) CT_TRY_CUDA(cudaEventCreateWithFlags(&g_stage.done, cudaEventDisableTiming));
+    if (g_stage.pending) {   // the previous upload's copies may still read the stage
+        CT_TRY_CUDA(cudaEventSynchronize(g_stage.done));
+        g_stage.pending = false;
+    }
     if (g_stage.cap < bytes) {
         if (g_stage.p) cudaFreeHost(g_stage.p);
         g_stage.p = nullptr;
@@ -765,13 +774,18 @@ ct_status stage_uploads(const std::vector<Upload>& ups, cudaStream_t st) {
         CT_TRY_CUDA(cudaMemcpyAsync(u.dst, g_stage.p + off, u.bytes, cudaMemcpyHostToDevice, st));
         off += (u.bytes + 15) & ~size_t(15);
     }
-    CT_TRY_CUDA(cudaStreamSynchronize(st));   // the stage is reused by the next upload
+    if (sync) {
+        CT_TRY_CUDA(cudaStreamSynchronize(st));
+    } else {
+        CT_TRY_CUDA(cudaEventRecord(g_stage.done, st));
+        g_stage.pending = true;
+    }
     return CT_OK;
 }
 }  // namespace
 
 // first device use: descriptor, tables, ball plan and status word go to the current device
-ct_status ensure_device(ct_space* s, cudaStream_t st) {
+ct_status ensure_device(ct_space* s, cudaStream_t st, bool sync) {
     if (s->d) return CT_OK;
     const DevSpace& h = s->h;
     cudaGetDevice(&s->device);
@@ -803,7 +817,7 @@ ct_status ensure_device(ct_space* s, cudaStream_t st) {
     CT_TRY_CUDA(cudaMemsetAsync(s->status.p, 0, 4, st));
     CT_TRY(s->pat_cnt.ensure(s->pat_cnt_words));
     CT_TRY(s->pat_list.ensure(s->pat_list_words));
-    CT_TRY(stage_uploads(ups, st));
+    CT_TRY(stage_uploads(ups, st, sync));
     CT_TRY_CUDA(cudaFuncSetAttribute(k_expand_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      EXP_THREADS * 32 * (int)sizeof(uint64_t)));
     return CT_OK;
@@ -881,23 +895,24 @@ static void plan_balls(ct_space* s, int dmax) {
 }
 
 
-// Device part: uploads every planned radius that has no device tables yet.
-static ct_status upload_balls(ct_space* s, cudaStream_t st) {
+// Device part: uploads every planned radius that has no device tables yet.  sync = false only
+// inside the build, whose final synchronisation then covers the copies.
+static ct_status upload_balls(ct_space* s, cudaStream_t st, bool sync) {
     std::vector<Upload> ups;
     for (BallRadius& br : s->balls) {
         if (br.d_masks.p) continue;
-        if (ups.empty()) CT_TRY(ensure_device(s, st));
+        if (ups.empty()) CT_TRY(ensure_device(s, st, sync));
         CT_TRY(br.d_masks.ensure(br.masks.size()));
         CT_TRY(br.d_prefix.ensure(br.prefix.size()));
         ups.push_back({br.d_masks.p, br.masks.data(), br.masks.size() * 4});
         ups.push_back({br.d_prefix.p, br.prefix.data(), br.prefix.size() * 8});
     }
-    return stage_uploads(ups, st);
+    return stage_uploads(ups, st, sync);
 }
 
 ct_status ensure_balls(ct_space* s, int dmax) {
     plan_balls(s, dmax);
-    return upload_balls(s, nullptr);
+    return upload_balls(s, nullptr, true);
 }
 
 static ct_status ensure_tables(ct_space* s, cudaStream_t st) {
@@ -1052,7 +1067,7 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
     const auto ms_since = [](clk::time_point a) { return std::chrono::duration<float, std::milli>(clk::now() - a).count(); };
     const auto t0 = clk::now();
     cudaStream_t st = (cudaStream_t)stream;
-    CT_TRY(ensure_device(s, st));
+    CT_TRY(ensure_device(s, st, false));   // the build synchronises st before it returns
     CT_TRY(ensure_tables(s, st));
     const float setup_ms = ms_since(t0);
     const auto t1 = clk::now();
@@ -1114,6 +1129,7 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
         if (j == h.n_blocks - 1) {   // the host plans the ball tables while the last level is emitted
             s->n_valid = F;
             plan_balls(s, wanted_radius(s));
+            CT_TRY(upload_balls(s, st, false));   // queued behind the emit; the sync below covers it
         }
     }
     CT_TRY_CUDA(cudaStreamSynchronize(st));
@@ -1128,7 +1144,7 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
     if (n_valid_out) *n_valid_out = F;
     s->stats.host_levels_ms = ms_since(t1);
     const auto t2 = clk::now();
-    if (F) CT_TRY(upload_balls(s, st));
+    if (F) CT_TRY(upload_balls(s, st, true));   // nothing left to upload, unless the last level was empty
     s->stats.host_balls_ms = ms_since(t2);
     s->stats.host_total_ms = ms_since(t0);
     if (F == 0) { set_error("no configuration satisfies the constraints"); return CT_ERR_EMPTY_SPACE; }
