@@ -739,6 +739,7 @@ struct PinnedStage {
     char* p = nullptr;
     size_t cap = 0;
     cudaEvent_t done = nullptr;   // the copies of the last upload
+    int done_dev = -1;            // the device the event belongs to
     bool pending = false;
 };
 PinnedStage g_stage;
@@ -754,10 +755,19 @@ ct_status stage_uploads(const std::vector<Upload>& ups, cudaStream_t st, bool sy
     for (const Upload& u : ups) bytes += (u.bytes + 15) & ~size_t(15);
     if (!bytes) return CT_OK;
     std::lock_guard<std::mutex> lk(g_stage.mu);
-    if (!g_stage.done) CT_TRY_CUDA(cudaEventCreateWithFlags(&g_stage.done, cudaEventDisableTiming));
     if (g_stage.pending) {   // the previous upload's copies may still read the stage
         CT_TRY_CUDA(cudaEventSynchronize(g_stage.done));
         g_stage.pending = false;
+    }
+    int dev = 0;
+    CT_TRY_CUDA(cudaGetDevice(&dev));
+    if (g_stage.done && g_stage.done_dev != dev) {   // an event is recorded on its own device's streams
+        cudaEventDestroy(g_stage.done);
+        g_stage.done = nullptr;
+    }
+    if (!g_stage.done) {
+        CT_TRY_CUDA(cudaEventCreateWithFlags(&g_stage.done, cudaEventDisableTiming));
+        g_stage.done_dev = dev;
     }
     if (g_stage.cap < bytes) {
         if (g_stage.p) cudaFreeHost(g_stage.p);
