@@ -30,6 +30,8 @@ namespace ct {
 
 constexpr int BATCH_MAX_POP = 256;
 constexpr int BATCH_MAX_THREADS = 256;
+constexpr int BATCH_LUT_GROUPS = 8;
+constexpr int BATCH_LUT_CHUNK = 32;   // candidates per pass of the table scan (four sets of eight)
 
 struct BatchSpace {
     const DevSpace* sp;
@@ -47,6 +49,12 @@ struct BatchSpace {
     uint64_t swar_low, swar_high;
     float eps;
     int32_t N;
+    // distance tables of the in-CTA scan: groups of adjacent fields of at most 8 bits, group g's
+    // entries at 256 g (0 groups: the SWAR scan)
+    int32_t lut_ng;
+    int32_t lut_shift[BATCH_LUT_GROUPS];
+    uint32_t lut_mask[BATCH_LUT_GROUPS];
+    int32_t lut_k0[BATCH_LUT_GROUPS], lut_k1[BATCH_LUT_GROUPS];
 };
 
 struct BatchRun {
@@ -85,6 +93,7 @@ struct BatchArgs {
     int32_t* ev_idx;
     unsigned long long* ev_clock;
     float* ev_fit;
+    uint32_t* scan_tags;                // table scan: best keys' ranks, [CTA][candidate][thread]
 };
 
 // Per-evaluation bookkeeping for the event log: whether the memo bit was first set by this
@@ -102,8 +111,117 @@ struct RepairSmem {
     int npend;
 };
 
+// The in-CTA exhaustive scan with per-candidate distance tables (as the repair's table scan):
+// for every group value, how many of the group's fields differ from each candidate, eight
+// candidates to a 64-bit entry; a key's eight distances are the lane sums of one entry per group,
+// and a borrow test on 127 + best - distance flags the lanes it improves.  A thread visits its
+// keys in increasing rank and keeps strict improvements; the packed (distance, rank) minimum over
+// the threads keeps the smallest rank among the nearest keys.
+template <int S>
+__device__ void cta_scan_pass(const BatchSpace& bs, const unsigned long long* __restrict__ tab, int nq,
+                              uint32_t* __restrict__ tags, unsigned long long* best) {
+    const int t = threadIdx.x, nt = blockDim.x, ng = bs.lut_ng;
+    uint32_t vl[S], vh[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        uint32_t il = 0, ih = 0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {   // lanes past the chunk never improve
+            il |= (8 * s + l < nq ? 254u : 127u) << (8 * l);
+            ih |= (8 * s + 4 + l < nq ? 254u : 127u) << (8 * l);
+        }
+        vl[s] = il;
+        vh[s] = ih;
+    }
+    uint32_t* tg = tags + t;
+    for (int64_t i = t; i < bs.nv; i += nt) {
+        const uint64_t key = __ldg(bs.keys + i);
+        uint32_t dl[S], dh[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) dl[s] = dh[s] = 0;
+#pragma unroll
+        for (int g = 0; g < BATCH_LUT_GROUPS; ++g) {
+            if (g >= ng) break;
+            const uint32_t e = ((uint32_t)(key >> bs.lut_shift[g]) & bs.lut_mask[g]) + 256u * (uint32_t)g;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+                const unsigned long long w = tab[(size_t)e * S + s];
+                dl[s] += (uint32_t)w;
+                dh[s] += (uint32_t)(w >> 32);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const uint32_t ml = (vl[s] - dl[s]) & 0x80808080u, mh = (vh[s] - dh[s]) & 0x80808080u;
+            if (ml | mh) {
+                const uint32_t fl = (ml >> 7) * 0xFFu, fh = (mh >> 7) * 0xFFu;
+                vl[s] = (vl[s] & ~fl) | ((dl[s] + 0x7F7F7F7Fu) & fl);
+                vh[s] = (vh[s] & ~fh) | ((dh[s] + 0x7F7F7F7Fu) & fh);
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    if ((ml >> (8 * l + 7)) & 1u) tg[(8 * s + l) * nt] = (uint32_t)i;
+                    if ((mh >> (8 * l + 7)) & 1u) tg[(8 * s + 4 + l) * nt] = (uint32_t)i;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+            unsigned long long x = ~0ull;
+            const uint32_t lv = ((l < 4 ? vl[s] : vh[s]) >> (8 * (l & 3))) & 0xFFu;
+            if (8 * s + l < nq && lv < 254u)   // the lane improved at least once
+                x = ((unsigned long long)(lv - 127u) << 57) | (unsigned long long)tg[(8 * s + l) * nt];
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+                x = y < x ? y : x;
+            }
+            if ((t & 31) == 0 && x != ~0ull) atomicMin(best + 8 * s + l, x);
+        }
+    }
+}
+
+__device__ void cta_scan_lut(const BatchSpace& bs, const uint64_t* cand, uint64_t* rep, RepairSmem& rs,
+                             unsigned long long* tab, uint32_t* __restrict__ tags) {
+    const DevSpace* sp = bs.sp;
+    const int t = threadIdx.x, nt = blockDim.x, np = rs.npend;
+    for (int q0 = 0; q0 < np; q0 += BATCH_LUT_CHUNK) {
+        const int nq = min(BATCH_LUT_CHUNK, np - q0);
+        const int S = nq <= 8 ? 1 : nq <= 16 ? 2 : 4;
+        for (int q = t; q < nq; q += nt) rs.best[q0 + q] = ~0ull;
+        for (int e = t; e < 256 * bs.lut_ng; e += nt) {
+            const int g = e >> 8;
+            const uint32_t x = (uint32_t)e & 255u;
+            if (x > bs.lut_mask[g]) continue;   // never read
+            const uint64_t local = (uint64_t)x << bs.lut_shift[g];
+            for (int s = 0; s < S; ++s) {
+                unsigned long long word = 0;
+                for (int l = 0; l < 8; ++l) {
+                    const int q = 8 * s + l;
+                    if (q >= nq) break;
+                    const uint64_t d = local ^ cand[rs.pend[q0 + q]];
+                    uint32_t cnt = 0;
+                    for (int k = bs.lut_k0[g]; k <= bs.lut_k1[g]; ++k) cnt += (d & sp->fmask[k]) != 0;
+                    word |= (unsigned long long)cnt << (8 * l);
+                }
+                tab[(size_t)e * S + s] = word;
+            }
+        }
+        __syncthreads();
+        if (S == 1) cta_scan_pass<1>(bs, tab, nq, tags, rs.best + q0);
+        else if (S == 2) cta_scan_pass<2>(bs, tab, nq, tags, rs.best + q0);
+        else cta_scan_pass<4>(bs, tab, nq, tags, rs.best + q0);
+        __syncthreads();
+        for (int q = t; q < nq; q += nt) rep[rs.pend[q0 + q]] = __ldg(bs.keys + (rs.best[q0 + q] & ((1ull << 57) - 1)));
+        __syncthreads();
+    }
+}
+
 // exact nearest valid key (Hamming on value indices, ties to the smallest key) for P candidates
-__device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t* rep, int P, RepairSmem& rs) {
+__device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t* rep, int P, RepairSmem& rs,
+                           unsigned long long* lut_tab, uint32_t* scan_tags) {
     const DevSpace* sp = bs.sp;
     const int t = threadIdx.x, nt = blockDim.x;
     if (t == 0) rs.npend = 0;
@@ -172,7 +290,11 @@ __device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t*
         }
         __syncthreads();
     }
-    // exhaustive scan for the rest, eight candidates per pass over the keys
+    if (bs.lut_ng) {   // exhaustive scan for the rest: distance tables, up to 32 candidates per pass
+        cta_scan_lut(bs, cand, rep, rs, lut_tab, scan_tags);
+        return;
+    }
+    // exhaustive scan for the rest (SWAR distances), eight candidates per pass over the keys
     const int np = rs.npend;
     for (int q0 = 0; q0 < np; q0 += 8) {
         const int nq = min(8, np - q0);
@@ -199,6 +321,7 @@ __device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t*
 }
 
 __global__ void __launch_bounds__(BATCH_MAX_THREADS, 2) k_batch_gen(const __grid_constant__ BatchArgs ba) {
+    extern __shared__ __align__(16) unsigned long long lut_tab[];   // the table scan's tables
     __shared__ uint64_t cand[BATCH_MAX_POP], rep[BATCH_MAX_POP];
     __shared__ float fit[BATCH_MAX_POP];
     __shared__ int order[BATCH_MAX_POP];
@@ -225,7 +348,8 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 2) k_batch_gen(const __grid
         const int P = run.P;
         propose_dev(a, gen, cand, order);
         __syncthreads();
-        if (a.prm.constraint_aware) cta_repair(bs, cand, rep, P, rsm);
+        if (a.prm.constraint_aware)
+            cta_repair(bs, cand, rep, P, rsm, lut_tab, ba.scan_tags + (size_t)blockIdx.x * BATCH_LUT_CHUNK * blockDim.x);
         else for (int i = threadIdx.x; i < P; i += blockDim.x) rep[i] = cand[i];
         __syncthreads();
         post_repair_dev(a, gen, rep);
@@ -321,6 +445,8 @@ struct ct_batch {
     DevBuf<uint64_t> X;
     DevBuf<float> FX, pos, vel, pb, fpb, gb, ynew;
     DevBuf<uint32_t> memo, ctr;   // ctr[0] = generation, ctr[1] = work counter
+    DevBuf<uint32_t> scan_tags;   // table scan: per CTA of the largest grid, BATCH_LUT_CHUNK x threads
+    size_t lut_bytes = 0;         // dynamic shared memory of the table scan (largest plan, four sets)
     DevBuf<float> tr_fit;
     DevBuf<unsigned long long> tr_cost, tr_unique;
     uint32_t tr_gens = 0;
@@ -349,6 +475,7 @@ struct ct_batch {
         a.tr_fit = tr_fit.p; a.tr_cost = tr_cost.p; a.tr_unique = tr_unique.p; a.tr_gens = tr_gens;
         a.ev_cap = ev_cap; a.ev_count = ev_count.p; a.ev_gen = ev_gen.p; a.ev_idx = ev_idx.p;
         a.ev_clock = ev_clock.p; a.ev_fit = ev_fit.p;
+        a.scan_tags = scan_tags.p;
         return a;
     }
     int grid() const {
@@ -364,7 +491,7 @@ static ct_status batch_launch(ct_batch* b, cudaStream_t st) {
         cudaFuncSetAttribute(k_batch_gen, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     });
-    k_batch_gen<<<b->grid(), b->threads, 0, st>>>(b->args());
+    k_batch_gen<<<b->grid(), b->threads, b->lut_bytes, st>>>(b->args());
     k_batch_advance<<<1, 1, 0, st>>>(b->ctr.p, b->ctr.p + 1);
     count_launch(2);
     CT_TRY_CUDA(cudaGetLastError());
@@ -405,14 +532,39 @@ static ct_status batch_reset(ct_batch* b) {
 }
 }  // namespace ct
 
+// Groups of the in-CTA table scan: adjacent fields (lowest key bits first) of at most 8 bits
+// together; no plan (the SWAR scan) when a field is wider, more than 8 groups are needed or the
+// space has 2^32 valid keys or more.
+static void batch_lut_plan(const ct_space* s, BatchSpace& b) {
+    const DevSpace& h = s->h;
+    b.lut_ng = 0;
+    if (s->n_valid >= (1ull << 32)) return;   // ranks are kept in 32 bits
+    int ng = 0, k = h.n - 1;
+    while (k >= 0 && h.w[k] == 0) --k;
+    while (k >= 0) {
+        if (ng == BATCH_LUT_GROUPS || h.w[k] > 8) return;
+        b.lut_k1[ng] = k;
+        b.lut_shift[ng] = h.off[k];
+        int width = h.w[k];
+        --k;
+        while (k >= 0 && width + h.w[k] <= 8) width += h.w[k--];
+        b.lut_k0[ng] = k + 1;
+        b.lut_mask[ng] = (1u << width) - 1u;
+        ++ng;
+        while (k >= 0 && h.w[k] == 0) --k;
+    }
+    b.lut_ng = ng;
+}
+
 // Ball radius of the in-CTA repair: the ball is cut where its cumulative size passes |V| / 8,
 // never below radius 1; an explicit ct_set_repair_mode on the space takes precedence.  With the
 // failing-constraint pruning a ball point is cheap, and on the 4096-run batched workload the
 // cut at |V| / 4 .. |V| / 16 is flat (2.84-2.88 ms per generation) against 3.19 at |V| / 32 and
 // 3.26 at |V| / 1.
+constexpr double BATCH_BALL_DIV = 8.0;   // |V| / 4 .. |V| / 8 measured flat, |V| / 32 5 % slower
 static int batch_radius(const ct_space* sp) {
     if (sp->repair_mode != 0) return wanted_radius(sp);
-    return std::max(auto_radius(sp), std::min(1, sp->ball_max));
+    return std::max(auto_radius(sp, BATCH_BALL_DIV), std::min(1, sp->ball_max));
 }
 
 extern "C" {
@@ -443,6 +595,7 @@ ct_status ct_batch_create(ct_space* const* spaces, int32_t n_spaces, const ct_ba
         for (int k = 0; k < sp->h.n; ++k) rmax = std::max(rmax, (int)sp->h.r[k]);
         b.eps = rmax > 1 ? 1.0f / (float)(rmax - 1) : 1.0f;
         b.N = sp->h.n;
+        batch_lut_plan(sp, b);
     }
     if (params && params->repair_rule) { set_error("batches use the Hamming repair (repair_rule 0)"); return CT_ERR_INVALID_ARG; }
     ct_batch* bt = new (std::nothrow) ct_batch();
@@ -497,6 +650,31 @@ ct_status ct_batch_create(ct_space* const* spaces, int32_t n_spaces, const ct_ba
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&bt->sms, cudaDevAttrMultiProcessorCount, dev);
+    {   // the table scan: tables of the largest plan with four candidate sets, and the best-rank
+        // tags of every CTA of the largest grid (16 CTAs per SM)
+        int ng_max = 0;
+        for (const BatchSpace& b : bsp) ng_max = std::max(ng_max, (int)b.lut_ng);
+        bt->lut_bytes = (size_t)ng_max * 256 * 4 * sizeof(unsigned long long);
+        const uint64_t ctas = (uint64_t)std::min(n_runs, bt->sms * 16);
+        if (ng_max && bt->scan_tags.ensure(ctas * BATCH_LUT_CHUNK * BATCH_MAX_THREADS) != CT_OK) {
+            delete bt;
+            return CT_ERR_OOM;
+        }
+        // the kernel's dynamic shared-memory limit only grows (batches share the kernel); set here,
+        // never under a graph capture
+        static std::mutex mu;
+        static size_t granted = 0;
+        std::lock_guard<std::mutex> lk(mu);
+        if (bt->lut_bytes > granted) {
+            if (cudaFuncSetAttribute(k_batch_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->lut_bytes) !=
+                cudaSuccess) {
+                delete bt;
+                set_error("shared memory for the in-CTA table scan (%zu bytes)", bt->lut_bytes);
+                return CT_ERR_CUDA;
+            }
+            granted = bt->lut_bytes;
+        }
+    }
     *out = bt;
     return CT_OK;
 }

@@ -154,7 +154,7 @@ ct_status ensure_balls(ct_space* s, int dmax);
 int wanted_radius(const ct_space* s);
 ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, int64_t n, uint64_t* d_out,
                       uint8_t* d_dist, cudaStream_t st);
-int auto_radius(const ct_space* s);
+int auto_radius(const ct_space* s, double div = 8.0);   // div: the scan pass's cost, in ball points
 ct_status scan_lut(const ct_space* s, const uint64_t* d_cand, const int32_t* pend, const uint32_t* count,
                    unsigned long long* best, cudaStream_t st, bool* launched, int* lut_min);
 ct_status repair_reserve(RepairScratch& rs, int64_t n);

@@ -447,8 +447,8 @@ static int sm_count() {
 
 // Largest radius whose cumulative ball is cheaper than one scan pass per candidate:
 // a ball point costs a table test (~8x a scanned key's SWAR distance).
-int auto_radius(const ct_space* s) {
-    const double budget = (double)s->n_valid / 8.0;
+int auto_radius(const ct_space* s, double div) {
+    const double budget = (double)s->n_valid / div;
     double cum = 0;
     int d = 0;
     for (int r = 1; r <= s->ball_max; ++r) {
