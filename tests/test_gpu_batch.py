@@ -101,3 +101,30 @@ def test_batch_launch_shapes_and_autotune(spaces, tmp_path):
     for _ in range(6):
         b.step()
     assert np.array_equal(b.results()["best_key"], outs[0]["best_key"])
+
+
+@pytest.mark.parametrize("mode,radius", [(1, 0), (2, 1)])
+def test_batch_scan_paths_equal_oracle(oracle_mod, spaces, mode, radius):
+    """Scan-only repair and a radius-1 ball: most pending candidates reach the in-CTA exhaustive
+    scan (distance tables, chunks of 32, 16 and 8 candidates), against the oracle."""
+    from paper_2606_28372_b300 import catune as ct
+    runs = [(1, "de", 128, 17, -np.inf), (3, "ga", 96, 18, -np.inf), (2, "pso", 40, 19, -np.inf),
+            (0, "de", 9, 20, -np.inf)]
+    for p in spaces:
+        p.sp.set_repair_mode(mode, radius)
+    try:
+        b = ct.Batch([p.sp for p in spaces], runs)
+        gens = 6
+        for _ in range(gens):
+            b.step()
+        res = b.results()
+    finally:
+        for p in spaces:
+            p.sp.set_repair_mode(0, 0)
+    for r, (si, kind, pop, seed, _) in enumerate(runs):
+        p = spaces[si]
+        E = oracle_mod.run(kind, p.osp, p.okeys, p.table, pop=pop, gens=gens - 1, seed=seed)
+        k = torch.empty(pop, dtype=torch.int64, device="cuda")
+        b.run_state(r, k)
+        assert np.array_equal(from_dev_u64(k), E["popk"][-1]), (kind, mode)
+        assert int(res["n_unique"][r]) == int(E["n_unique"][-1]), (kind, mode)
