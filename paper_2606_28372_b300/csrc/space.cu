@@ -613,11 +613,16 @@ static ct_status lower(ct_space* s, int32_t n, const int32_t* nv, const int64_t*
         bl.W = (int32_t)((B + 31) / 32);
         bl.key_shift = h.off[bl.e - 1];
         bl.innerkey_off = (uint32_t)ik_all.size();
+        ik_all.reserve(ik_all.size() + (size_t)B);
+        int32_t dg[MAXP] = {};   // mixed-radix digits of point p, the last parameter fastest
+        uint64_t key = 0;
         for (int64_t p = 0; p < B; ++p) {
-            uint64_t key = 0;
-            int64_t t = p;
-            for (int k = bl.e - 1; k >= bl.s; --k) { key |= (uint64_t)(t % h.r[k]) << h.off[k]; t /= h.r[k]; }
             ik_all.push_back((uint32_t)(key >> bl.key_shift));
+            for (int k = bl.e - 1; k >= bl.s; --k) {   // next point: an odometer step
+                if (++dg[k] < h.r[k]) { key += 1ull << h.off[k]; break; }
+                key -= (uint64_t)(h.r[k] - 1) << h.off[k];
+                dg[k] = 0;
+            }
         }
     }
     // attach constraints to blocks, sorted by block (stable)
