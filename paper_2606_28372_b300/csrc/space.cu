@@ -363,12 +363,22 @@ k_expand_emit(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tabl
 constexpr int PAT_THREADS = 128;   // >= max words per block (4096 / 32)
 constexpr int PE_THREADS = 256;    // threads of the pattern count/emit kernels (and most parents per tile)
 
+// The pattern blocks of one launch: CTA b builds signature b - first[i] of block blk[i], for the
+// last i with first[i] <= b.
+struct PatBlocks {
+    int32_t n;
+    int32_t blk[MAXP];
+    uint32_t first[MAXP];
+};
+
 __global__ void __launch_bounds__(PAT_THREADS)
 k_build_patterns(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
-                 const uint32_t* __restrict__ innerkey, int j, uint32_t* __restrict__ pat_cnt,
-                 uint32_t* __restrict__ pat_list) {
-    const DevBlock& bl = sp->blocks[j];
-    const uint32_t sig = blockIdx.x;
+                 const uint32_t* __restrict__ innerkey, const __grid_constant__ PatBlocks pb,
+                 uint32_t* __restrict__ pat_cnt, uint32_t* __restrict__ pat_list) {
+    int i = 0;
+    while (i + 1 < pb.n && pb.first[i + 1] <= blockIdx.x) ++i;
+    const DevBlock& bl = sp->blocks[pb.blk[i]];
+    const uint32_t sig = blockIdx.x - pb.first[i];
     __shared__ int32_t fidx[MAXP];
     __shared__ uint32_t wsum[PAT_THREADS / 32];
     if (threadIdx.x == 0) {
@@ -949,11 +959,21 @@ static ct_status ensure_tables(ct_space* s, cudaStream_t st) {
         count_launch();
         CT_TRY_CUDA(cudaGetLastError());
     }
+    PatBlocks pb;   // every pattern block in one launch: the blocks are independent
+    memset(&pb, 0, sizeof pb);
+    uint64_t ctas = 0;
     for (int j = 0; j < s->h.n_blocks; ++j) {
         const DevBlock& bl = s->h.blocks[j];
         if (!bl.pattern) continue;
-        k_build_patterns<<<bl.n_sig, PAT_THREADS, 0, st>>>(s->d, s->tables.p, s->innerkey.p, j, s->pat_cnt.p,
-                                                           s->pat_list.p);
+        pb.blk[pb.n] = j;
+        pb.first[pb.n] = (uint32_t)ctas;
+        ++pb.n;
+        ctas += bl.n_sig;
+    }
+    if (ctas > 0x7fffffffull) { set_error("%llu pattern signatures", (unsigned long long)ctas); return CT_ERR_LIMIT; }
+    if (pb.n) {
+        k_build_patterns<<<(unsigned)ctas, PAT_THREADS, 0, st>>>(s->d, s->tables.p, s->innerkey.p, pb, s->pat_cnt.p,
+                                                                 s->pat_list.p);
         count_launch();
     }
     CT_TRY_CUDA(cudaGetLastError());
