@@ -167,14 +167,39 @@ __device__ void sl_pass(const uint64_t* __restrict__ keys, int64_t nv, const Sca
     const int64_t start = ((int64_t)blockIdx.x * SL_THREADS + threadIdx.x) * 2;
     uint32_t it = 0;
     int64_t i = start;
-    for (; i + (U - 1) * stride + 1 < nv; i += U * stride, it += U) {
+    if (S == 1) {   // one set: no prefetch, the registers keep 4 CTAs per SM
+        for (; i + (U - 1) * stride + 1 < nv; i += U * stride, it += U) {
+            ulonglong2 kk[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) kk[u] = __ldg(reinterpret_cast<const ulonglong2*>(keys + i + u * stride));
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                sl_visit<NG, S>(kk[u].x, (it + u) << 1, rs, mk, tab, vl, vh, tg);
+                sl_visit<NG, S>(kk[u].y, ((it + u) << 1) | 1u, rs, mk, tab, vl, vh, tg);
+            }
+        }
+    } else if (i + (U - 1) * stride + 1 < nv) {   // the next group of pairs is loaded while this one is visited
         ulonglong2 kk[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) kk[u] = __ldg(reinterpret_cast<const ulonglong2*>(keys + i + u * stride));
+        for (;;) {
+            const int64_t in = i + U * stride;
+            const bool more = in + (U - 1) * stride + 1 < nv;
+            ulonglong2 kn[U];
+            if (more) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            sl_visit<NG, S>(kk[u].x, (it + u) << 1, rs, mk, tab, vl, vh, tg);
-            sl_visit<NG, S>(kk[u].y, ((it + u) << 1) | 1u, rs, mk, tab, vl, vh, tg);
+                for (int u = 0; u < U; ++u) kn[u] = __ldg(reinterpret_cast<const ulonglong2*>(keys + in + u * stride));
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                sl_visit<NG, S>(kk[u].x, (it + u) << 1, rs, mk, tab, vl, vh, tg);
+                sl_visit<NG, S>(kk[u].y, ((it + u) << 1) | 1u, rs, mk, tab, vl, vh, tg);
+            }
+            i = in;
+            it += U;
+            if (!more) break;
+#pragma unroll
+            for (int u = 0; u < U; ++u) kk[u] = kn[u];
         }
     }
     for (; i < nv; i += stride, ++it) {
