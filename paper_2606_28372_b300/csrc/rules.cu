@@ -185,10 +185,11 @@ k_rule_scan(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, 
 //   rule 1: the group's index distance, 16-bit lanes, eight candidates to a 16-byte entry (the
 //           plan requires sum_k (r_k - 1) < 2^15 - 1, so lanes never carry and a borrow test
 //           on 0x7fff + best - distance flags exactly the improving lanes);
-//   rules 2, 3: one byte per candidate: bit 0 "every field within +-1", bit 1 "every field
-//           unchanged or at its lower / higher occurring value", bits 2..7 the number of
-//           changed fields; groups combine by AND of the flags and a byte-wise sum of counts,
-//           and only keys in some candidate's sets take the per-candidate work.
+//   rules 2, 3: a 16-byte entry of a flag byte per candidate (bit 0 "every field within +-1",
+//           bit 1 "every field unchanged or at its lower / higher occurring value") and a count
+//           byte per candidate (the number of changed fields); groups combine by AND of the flags
+//           and a byte-wise sum of the counts, and only keys in some candidate's sets take the
+//           per-candidate work.
 // Groups are laid out widest first, so every group's first entry is a multiple of its size and
 // a key's byte offset into the tables is one shift, AND and OR per group.  The minima, counts
 // and (for set members) the fp32 Euclidean distance are those of the loop; a thread visits its
@@ -236,7 +237,7 @@ static bool lut_plan(const ct_space* s, int rule, int64_t slice, LutPlan& pl) {
     for (int w = 12; w >= 0; --w)                // widest first: bases stay aligned
         for (int g = 0; g < pl.ng; ++g)
             if (width[g] == w) { pl.base[g] = pl.entries; pl.entries += 1 << w; }
-    const size_t bytes = (size_t)pl.entries * (rule == 1 ? 16 : 8);
+    const size_t bytes = (size_t)pl.entries * 16;
     return bytes <= LUT_MAX_BYTES;
 }
 
@@ -281,11 +282,10 @@ __device__ __forceinline__ void rule_visit(const DevSpace* __restrict__ sp, uint
     } else {
         uint32_t f0 = ~0u, f1 = ~0u, n0 = 0, n1 = 0;
 #pragma unroll
-        for (int g = 0; g < NG; ++g) {
-            const uint2 w = *reinterpret_cast<const uint2*>(tab + a[g]);
+        for (int g = 0; g < NG; ++g) {   // flag bytes AND, count bytes add
+            const uint4 w = *reinterpret_cast<const uint4*>(tab + a[g]);
             f0 &= w.x; f1 &= w.y;
-            n0 += (w.x >> 2) & 0x3f3f3f3fu;
-            n1 += (w.y >> 2) & 0x3f3f3f3fu;
+            n0 += w.z; n1 += w.w;
         }
         // the key matters to some candidate only if it is in one of its sets: an adjacency flag,
         // or exactly one changed parameter (a zero byte of n ^ 0x01..; the borrow test is exact
@@ -329,7 +329,8 @@ k_rule_scan_lut(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ ke
                 const RuleCand* __restrict__ rc, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
                 const float* __restrict__ pos, float eps, unsigned long long* __restrict__ best,
                 uint32_t* __restrict__ cnt, const __grid_constant__ LutPlan pl) {
-    // rule 1: [entries][2]; rules 2, 3: [entries]; rule 2 then the per-thread minima [3 RQ][RT]
+    // [entries][2] (rule 1: two words of 16-bit distances; rules 2, 3: flag bytes, count bytes);
+    // rule 2 then the per-thread minima [3 RQ][RT]
     extern __shared__ __align__(16) unsigned long long tab[];
     __shared__ RuleCand cs[RQ];
     __shared__ float xs[RQ][MAXP];
@@ -365,16 +366,16 @@ k_rule_scan_lut(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ ke
             if (RULE == 1) {
                 if (q < 4) t0 |= (unsigned long long)l1 << (16 * q);
                 else t1 |= (unsigned long long)l1 << (16 * (q - 4));
-            } else {
-                const unsigned long long byte = (sa ? 1ull : 0ull) | (adj ? 2ull : 0ull) | ((unsigned long long)nd << 2);
-                t0 |= byte << (8 * q);
+            } else {   // a flag byte and a count byte per candidate
+                t0 |= ((sa ? 1ull : 0ull) | (adj ? 2ull : 0ull)) << (8 * q);
+                t1 |= (unsigned long long)nd << (8 * q);
             }
         }
-        if (RULE == 1) { tab[2 * e] = t0; tab[2 * e + 1] = t1; }
-        else tab[e] = t0;
+        tab[2 * e] = t0;
+        tab[2 * e + 1] = t1;
     }
     __syncthreads();
-    constexpr int LGE = RULE == 1 ? 4 : 3;       // log2 of the entry size
+    constexpr int LGE = 4;                       // log2 of the entry size (16 bytes)
     uint32_t rs[NG], mk[NG], bb[NG];
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
@@ -383,7 +384,7 @@ k_rule_scan_lut(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ ke
         bb[g] = (uint32_t)pl.base[g] << LGE;
     }
     RuleScan<RULE> S;
-    S.b = tab + (size_t)pl.entries + threadIdx.x;   // rule 2 only (the region exists then)
+    S.b = tab + 2 * (size_t)pl.entries + threadIdx.x;   // rule 2 only (the region exists then)
     if (RULE == 2)
 #pragma unroll
         for (int e = 0; e < 3 * RQ; ++e) S.b[e * RT] = ~0ull;
@@ -610,7 +611,7 @@ ct_status repair_rule_impl(ct_space* s, RuleScratch& r, int rule, const uint64_t
     RuleCand* rc = (RuleCand*)r.rc.p;
     LutPlan pl;
     const bool lut = lut_plan(s, rule, slice, pl);
-    const size_t lut_bytes = lut ? (size_t)pl.entries * (rule == 1 ? 16 : 8) + (rule == 2 ? RULE2_MIN_BYTES : 0) : 0;
+    const size_t lut_bytes = lut ? (size_t)pl.entries * 16 + (rule == 2 ? RULE2_MIN_BYTES : 0) : 0;
     if (rule == 1) {
         if (lut)
             launch_lut<1>(grid, lut_bytes, st, s, slice, rc, r, nullptr, 0.0f, r.best.p, nullptr, pl);
