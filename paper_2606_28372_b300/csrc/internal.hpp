@@ -76,6 +76,19 @@ struct RepairScratch {
     DevBuf<uint32_t> counts;           // [0]: pending a, [1]: pending b
     DevBuf<unsigned long long> best;   // per pending slot: best key / packed (dist, rank)
     DevBuf<uint64_t> fail;             // per candidate: the constraints it fails
+    DevBuf<uint32_t> done;             // ball kernels: CTAs finished (the last one resolves the radius)
+};
+
+// The resolve step of one ball radius, done by the ball kernel's last CTA (see search.cu);
+// done = null: the caller resolves with k_ball_resolve.
+struct BallNext {
+    uint32_t* done;                 // CTAs finished (zero before the launch; the last CTA resets it)
+    int d;                          // the radius
+    uint64_t* out;                  // settled candidates: the repaired key
+    uint8_t* dist;                  // ... and its distance (may be null)
+    int32_t* pend_out;              // the rest, for the next radius
+    uint32_t* count_out;
+    unsigned long long* best_out;
 };
 
 // Scratch of the paper's repair rules (candidates, adjacency bounds, per-set minima,

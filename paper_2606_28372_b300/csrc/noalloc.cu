@@ -32,7 +32,7 @@ __global__ void k_repair_init(const DevSpace* sp, const uint32_t* tables, const 
                               unsigned long long* best, uint32_t* status, uint64_t* fail);
 __global__ void k_ball(const DevSpace* sp, const uint32_t* tables, const uint32_t* masks, const uint64_t* prefix,
                        int n_subsets, uint64_t points, const uint64_t* cand, const int32_t* pend,
-                       const uint32_t* count, unsigned long long* best, const uint64_t* fail);
+                       const uint32_t* count, unsigned long long* best, const uint64_t* fail, const BallNext nx);
 __global__ void k_ball_resolve(int d, const int32_t* pend_in, const uint32_t* count_in,
                                const unsigned long long* best_in, uint64_t* out, uint8_t* dist, int32_t* pend_out,
                                uint32_t* count_out, unsigned long long* best_out);
@@ -114,7 +114,7 @@ extern "C" ct_status ct_repair_noalloc(ct_space* s, const uint64_t* d_cand, int6
         const uint64_t work = (uint64_t)n * br.total;
         const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 16);
         k_ball<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
-                                   d_cand, pend[cur], cnt[cur], best[cur], nullptr);
+                                   d_cand, pend[cur], cnt[cur], best[cur], nullptr, BallNext{});   // resolved below
         CT_TRY_CUDA(cudaMemsetAsync(cnt[cur ^ 1], 0, sizeof(uint32_t), st));
         k_ball_resolve<<<g1, 256, 0, st>>>(d, pend[cur], cnt[cur], best[cur], d_out, d_dist, pend[cur ^ 1],
                                            cnt[cur ^ 1], best[cur ^ 1]);

@@ -100,6 +100,41 @@ __global__ void k_repair_init(const DevSpace* __restrict__ sp, const uint32_t* _
     }
 }
 
+// The resolve step of one radius, run by the last CTA of the ball kernel to finish (an atomic
+// ticket after a fence; nothing waits): candidates whose ball held a valid point are settled, the
+// others are queued for the next radius.  A null ticket counter leaves the resolve to
+// k_ball_resolve (the fixed-scratch repair).
+__device__ __forceinline__ void ball_resolve_last(const BallNext& nx, const int32_t* __restrict__ pend_in,
+                                                  const uint32_t* __restrict__ count_in,
+                                                  const unsigned long long* __restrict__ best_in) {
+    if (!nx.done) return;
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();   // this CTA's atomics on best_in before its ticket
+        last = atomicAdd(nx.done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) *nx.count_out = 0;
+    __syncthreads();
+    const uint32_t cnt = *count_in;
+    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const unsigned long long b = __ldcg(best_in + q);
+        const int32_t i = pend_in[q];
+        if (b != NONE) {
+            nx.out[i] = b;
+            if (nx.dist) nx.dist[i] = (uint8_t)nx.d;
+        } else {
+            const uint32_t slot = atomicAdd(nx.count_out, 1u);
+            nx.pend_out[slot] = i;
+            nx.best_out[slot] = NONE;
+        }
+    }
+    if (threadIdx.x == 0) *nx.done = 0;   // for the next launch
+}
+
 // every point at Hamming distance exactly d of each pending candidate; with the candidates'
 // failing-constraint masks, subsets that cannot fix them are skipped and only the constraints
 // reading a changed parameter are tested
@@ -107,7 +142,7 @@ __global__ void __launch_bounds__(256)
 k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, const uint32_t* __restrict__ masks,
        const uint64_t* __restrict__ prefix, int n_subsets, uint64_t points, const uint64_t* __restrict__ cand,
        const int32_t* __restrict__ pend, const uint32_t* __restrict__ count, unsigned long long* __restrict__ best,
-       const uint64_t* __restrict__ fail) {
+       const uint64_t* __restrict__ fail, const BallNext nx) {
     const uint64_t total = (uint64_t)(*count) * points;
     const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -140,6 +175,7 @@ k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, con
         if (key < __ldcg(best + q) && (fail ? valid_changed(sp, tables, key, S) : valid_key(sp, tables, key)))
             atomicMin(best + q, (unsigned long long)key);
     }
+    ball_resolve_last(nx, pend, count, best);
 }
 
 // Radii whose subsets hold at least this many points on average take the filtered search (a warp
@@ -153,7 +189,8 @@ constexpr uint64_t BALL_FS_MIN_AVG = 512;
 __global__ void __launch_bounds__(256)
 k_ball_fs(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, const uint32_t* __restrict__ masks,
           int n_subsets, const uint64_t* __restrict__ cand, const int32_t* __restrict__ pend,
-          const uint32_t* __restrict__ count, unsigned long long* __restrict__ best, const uint64_t* __restrict__ fail) {
+          const uint32_t* __restrict__ count, unsigned long long* __restrict__ best, const uint64_t* __restrict__ fail,
+          const BallNext nx) {
     const uint64_t total = (uint64_t)(*count) * (uint64_t)n_subsets;
     const int lane = threadIdx.x & 31;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -178,6 +215,7 @@ k_ball_fs(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, 
         }
         if (lane == 0 && bl != ~0ull && bl < __ldcg(best + q)) atomicMin(best + q, bl);
     }
+    ball_resolve_last(nx, pend, count, best);
 }
 
 // settle candidates whose ball held a valid point; requeue the rest
@@ -460,6 +498,10 @@ int auto_radius(const ct_space* s, double div) {
 }
 
 ct_status repair_reserve(RepairScratch& rs, int64_t n) {
+    if (!rs.done.p) {   // the ball kernels' ticket counter: zero between launches
+        CT_TRY(rs.done.ensure(1));
+        CT_TRY_CUDA(cudaMemset(rs.done.p, 0, sizeof(uint32_t)));
+    }
     CT_TRY(rs.pend_a.ensure(n));
     CT_TRY(rs.pend_b.ensure(n));
     CT_TRY(rs.counts.ensure(2));
@@ -490,23 +532,21 @@ ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, in
     int cur = 0;
     for (int d = 1; d <= dmax; ++d) {
         const BallRadius& br = s->balls[d - 1];
+        // the kernel's last CTA resolves this radius: settles, and queues the rest for the next
+        const BallNext nx{rs.done.p, d, d_out, d_dist, pend[cur ^ 1], cnt[cur ^ 1], best[cur ^ 1]};
         if (br.total >= fs_min_avg * br.masks.size()) {
             // large subsets: a warp per (candidate, subset) over the filtered points
             const uint64_t work = (uint64_t)n * br.masks.size() * 32;
             const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 4);   // one wave
             k_ball_fs<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, (int)br.masks.size(), d_cand, pend[cur],
-                                          cnt[cur], best[cur], rs.fail.p);
+                                          cnt[cur], best[cur], rs.fail.p, nx);
         } else {
             // small subsets: a thread per point
             const uint64_t work = (uint64_t)n * br.total;
             const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 4);   // one wave
             k_ball<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
-                                       d_cand, pend[cur], cnt[cur], best[cur], rs.fail.p);
+                                       d_cand, pend[cur], cnt[cur], best[cur], rs.fail.p, nx);
         }
-        count_launch();
-        CT_TRY_CUDA(cudaMemsetAsync(cnt[cur ^ 1], 0, 4, st));
-        k_ball_resolve<<<g1, 256, 0, st>>>(d, pend[cur], cnt[cur], best[cur], d_out, d_dist, pend[cur ^ 1],
-                                           cnt[cur ^ 1], best[cur ^ 1]);
         count_launch();
         cur ^= 1;
     }
