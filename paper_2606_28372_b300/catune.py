@@ -48,7 +48,7 @@ class ct_build_stats(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("timed", C.c_int32), ("parents", C.c_uint64 * MAX_PARAMS),
                 ("children", C.c_uint64 * MAX_PARAMS), ("count_ms", C.c_float * MAX_PARAMS),
                 ("emit_ms", C.c_float * MAX_PARAMS), ("host_setup_ms", C.c_float), ("host_levels_ms", C.c_float),
-                ("host_balls_ms", C.c_float), ("host_total_ms", C.c_float)]
+                ("host_balls_ms", C.c_float), ("host_total_ms", C.c_float), ("hinted", C.c_int32)]
 
 
 class ct_surrogate_params(C.Structure):
@@ -374,7 +374,7 @@ class Space:
         return dict(levels=n, timed=bool(st.timed), parents=list(st.parents[:n]), children=list(st.children[:n]),
                     count_ms=list(st.count_ms[:n]), emit_ms=list(st.emit_ms[:n]),
                     host_ms=dict(setup=st.host_setup_ms, levels=st.host_levels_ms, balls=st.host_balls_ms,
-                                 total=st.host_total_ms))
+                                 total=st.host_total_ms), hinted=bool(st.hinted))
 
 
 def launch_count():

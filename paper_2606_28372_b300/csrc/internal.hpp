@@ -134,8 +134,10 @@ struct ct_space {
     std::vector<ct::DevBuf<uint64_t>> frontier;
     ct::DevBuf<uint32_t> tile_counts;
     ct::DevBuf<unsigned long long> tile_base;
-    ct::DevBuf<unsigned long long> d_total;
+    ct::DevBuf<unsigned long long> d_total;   // per level: the level's size (written by its scan)
     unsigned long long h_total = 0;
+    std::vector<unsigned long long> h_totals;
+    std::vector<uint64_t> hint;            // level sizes of the last build (empty before the first)
 
     // repair
     std::vector<ct::BallRadius> balls;     // enumerated radii 1..balls.size() (planned on demand)

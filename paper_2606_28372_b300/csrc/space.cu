@@ -309,9 +309,11 @@ k_scan_tiles(const uint32_t* __restrict__ counts, uint64_t n, unsigned long long
 __global__ void __launch_bounds__(EXP_THREADS)
 k_expand_emit(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
               const uint32_t* __restrict__ innerkey, int j, const uint64_t* __restrict__ parents,
-              uint64_t n_items, const unsigned long long* __restrict__ tile_base, uint64_t* __restrict__ out) {
+              uint64_t n_items, const unsigned long long* __restrict__ tile_base,
+              const unsigned long long* __restrict__ total, unsigned long long expect, uint64_t* __restrict__ out) {
     extern __shared__ uint64_t stage[];                // EXP_THREADS * 32 keys
     __shared__ uint32_t wsum[EXP_THREADS / 32];
+    if (expect != ~0ull && *total != expect) return;   // launched for another level size: write nothing
     const DevBlock& bl = sp->blocks[j];
     const uint32_t* ik = innerkey + bl.innerkey_off;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -458,7 +460,8 @@ k_pcount(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parent
 
 __global__ void __launch_bounds__(PE_THREADS)
 k_pemit(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents, uint64_t F, uint32_t pt,
-        const unsigned long long* __restrict__ tile_base, uint64_t* __restrict__ out) {
+        const unsigned long long* __restrict__ tile_base, const unsigned long long* __restrict__ total,
+        unsigned long long expect, uint64_t* __restrict__ out) {
     __shared__ uint32_t off_s[PE_THREADS], cnt_s[PE_THREADS], sig_s[PE_THREADS];
     __shared__ uint64_t par_s[PE_THREADS];
     __shared__ uint32_t wsum[PE_THREADS / 32];
@@ -487,6 +490,7 @@ k_pemit(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents
     par_s[t] = parent;
     __syncthreads();
     const uint64_t tb = tile_base[blockIdx.x];
+    if (expect != ~0ull && *total != expect) return;   // launched for another level size: write nothing
     const int np = (int)min((uint64_t)pt, F - i0);
     for (int p = warp; p < np; p += PE_THREADS / 32) {
         const uint32_t cp = cnt_s[p];
@@ -1096,28 +1100,24 @@ ct_status ct_unpack_keys_device(const ct_space* s, const uint64_t* d_keys, int64
     return CT_OK;
 }
 
-ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_out) {
-    if (!s) { set_error("space is NULL"); return CT_ERR_INVALID_ARG; }
-    using clk = std::chrono::steady_clock;
-    const auto ms_since = [](clk::time_point a) { return std::chrono::duration<float, std::milli>(clk::now() - a).count(); };
-    const auto t0 = clk::now();
-    cudaStream_t st = (cudaStream_t)stream;
-    CT_TRY(ensure_device(s, st, false));   // the build synchronises st before it returns
-    CT_TRY(ensure_tables(s, st));
-    const float setup_ms = ms_since(t0);
-    const auto t1 = clk::now();
+// One pass over the levels: per level the count kernel, the scan of the tile counts (the level's
+// size into d_total[j]) and the emit.  The emit's grid and the next level's need the level's size
+// on the host.  Per-level mode reads it back after each scan.  Hinted mode takes it from the last
+// build of this space instead (a space's definition never changes, so its levels have the same
+// sizes every time) and launches every level without waiting; each emit compares the hint with
+// its level's total on the device and writes nothing if they differ, and the host checks all
+// totals once at the end (*ok = false: a size differed, the pass is void).
+static ct_status build_levels(ct_space* s, cudaStream_t st, bool hinted, bool* ok) {
     const DevSpace& h = s->h;
     const uint64_t* parents = nullptr;
     uint64_t F = 1;
-    s->built = false;
-    s->occ_ready = false;
+    *ok = true;
+    const float setup_ms = s->stats.host_setup_ms;
     memset(&s->stats, 0, sizeof s->stats);
     s->stats.timed = s->timing;
     s->stats.host_setup_ms = setup_ms;
-    if (s->timing && s->events.empty()) {
-        s->events.resize(4 * (size_t)h.n_blocks);
-        for (auto& e : s->events) CT_TRY_CUDA(cudaEventCreate(&e));
-    }
+    CT_TRY(s->d_total.ensure((size_t)h.n_blocks));
+    const int n_hint = (int)s->hint.size();
     for (int j = 0; j < h.n_blocks; ++j) {
         const DevBlock& bl = h.blocks[j];
         const uint64_t items = bl.pattern ? F : F * (uint64_t)bl.W;
@@ -1126,7 +1126,6 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
         if (tiles > 0x7fffffffull) { set_error("level %d needs %llu tiles", j, (unsigned long long)tiles); return CT_ERR_LIMIT; }
         CT_TRY(s->tile_counts.ensure(tiles));
         CT_TRY(s->tile_base.ensure(tiles));
-        CT_TRY(s->d_total.ensure(1));
         PatArgs pa;
         if (bl.pattern) pa = pat_args(s, j);
         if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j], st));
@@ -1136,21 +1135,28 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
             k_expand_count<<<(unsigned)tiles, EXP_THREADS, 0, st>>>(s->d, s->tables.p, s->innerkey.p, j, parents,
                                                                    items, s->tile_counts.p);
         if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j + 1], st));
-        k_scan_tiles<<<1, 1024, 0, st>>>(s->tile_counts.p, tiles, s->tile_base.p, s->d_total.p);
+        unsigned long long* total = s->d_total.p + j;
+        k_scan_tiles<<<1, 1024, 0, st>>>(s->tile_counts.p, tiles, s->tile_base.p, total);
         count_launch(2);
-        CT_TRY_CUDA(cudaMemcpyAsync(&s->h_total, s->d_total.p, 8, cudaMemcpyDeviceToHost, st));
-        CT_TRY_CUDA(cudaStreamSynchronize(st));
-        const uint64_t Fn = s->h_total;
+        uint64_t Fn;
+        if (hinted) {
+            Fn = j < n_hint ? s->hint[j] : 0;
+        } else {
+            CT_TRY_CUDA(cudaMemcpyAsync(&s->h_total, total, 8, cudaMemcpyDeviceToHost, st));
+            CT_TRY_CUDA(cudaStreamSynchronize(st));
+            Fn = s->h_total;
+        }
         DevBuf<uint64_t>& dst = (j == h.n_blocks - 1) ? s->keys : s->frontier[j];
         CT_TRY(dst.ensure(Fn));
         if (Fn) {
+            const unsigned long long expect = hinted ? (unsigned long long)Fn : ~0ull;
             if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j + 2], st));
             if (bl.pattern)
                 k_pemit<<<(unsigned)tiles, PE_THREADS, 0, st>>>(pa, parents, F, (uint32_t)per_tile, s->tile_base.p,
-                                                                dst.p);
+                                                                total, expect, dst.p);
             else
                 k_expand_emit<<<(unsigned)tiles, EXP_THREADS, EXP_THREADS * 32 * sizeof(uint64_t), st>>>(
-                    s->d, s->tables.p, s->innerkey.p, j, parents, items, s->tile_base.p, dst.p);
+                    s->d, s->tables.p, s->innerkey.p, j, parents, items, s->tile_base.p, total, expect, dst.p);
             if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j + 3], st));
             count_launch();
             CT_TRY_CUDA(cudaGetLastError());
@@ -1167,14 +1173,68 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
             CT_TRY(upload_balls(s, st, false));   // queued behind the emit; the sync below covers it
         }
     }
+    const int L = s->stats.n_levels;
+    if (hinted) {
+        s->h_totals.resize((size_t)L);
+        CT_TRY_CUDA(cudaMemcpyAsync(s->h_totals.data(), s->d_total.p, (size_t)L * 8, cudaMemcpyDeviceToHost, st));
+    }
     CT_TRY_CUDA(cudaStreamSynchronize(st));
+    if (hinted)
+        for (int j = 0; j < L; ++j)
+            if (s->h_totals[j] != (unsigned long long)s->stats.children[j]) *ok = false;
+    s->n_valid = F;
+    return CT_OK;
+}
+
+// Hinted builds are on unless CATUNE_BUILD_PIPELINE=0.  CATUNE_BUILD_HINT_SKEW=k (nonzero) adds k
+// to the hinted size of the last level, which makes the check fail: the emit writes nothing and
+// the build is redone level by level (used to test that path).
+static bool build_pipeline_enabled() {
+    const char* e = getenv("CATUNE_BUILD_PIPELINE");
+    return !(e && e[0] == '0');
+}
+static long long build_hint_skew() {
+    const char* e = getenv("CATUNE_BUILD_HINT_SKEW");
+    return e ? atoll(e) : 0;
+}
+
+ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_out) {
+    if (!s) { set_error("space is NULL"); return CT_ERR_INVALID_ARG; }
+    using clk = std::chrono::steady_clock;
+    const auto ms_since = [](clk::time_point a) { return std::chrono::duration<float, std::milli>(clk::now() - a).count(); };
+    const auto t0 = clk::now();
+    cudaStream_t st = (cudaStream_t)stream;
+    CT_TRY(ensure_device(s, st, false));   // the build synchronises st before it returns
+    CT_TRY(ensure_tables(s, st));
+    s->stats.host_setup_ms = ms_since(t0);
+    const auto t1 = clk::now();
+    const DevSpace& h = s->h;
+    s->built = false;
+    s->occ_ready = false;
+    if (s->timing && s->events.empty()) {
+        s->events.resize(4 * (size_t)h.n_blocks);
+        for (auto& e : s->events) CT_TRY_CUDA(cudaEventCreate(&e));
+    }
+    bool hinted = build_pipeline_enabled() && !s->hint.empty();
+    if (hinted) {
+        const long long skew = build_hint_skew();
+        if (skew && (int)s->hint.size() == h.n_blocks) s->hint.back() = (uint64_t)((long long)s->hint.back() + skew);
+    }
+    bool ok = true;
+    CT_TRY(build_levels(s, st, hinted, &ok));
+    if (!ok) {   // a level size differed from the hint: redo the build reading each size back
+        hinted = false;
+        CT_TRY(build_levels(s, st, false, &ok));
+    }
+    s->hint.assign(s->stats.children, s->stats.children + s->stats.n_levels);
+    s->stats.hinted = hinted ? 1 : 0;
     if (s->timing)
         for (int j = 0; j < s->stats.n_levels; ++j) {
             CT_TRY_CUDA(cudaEventElapsedTime(&s->stats.count_ms[j], s->events[4 * j], s->events[4 * j + 1]));
             if (s->stats.children[j])
                 CT_TRY_CUDA(cudaEventElapsedTime(&s->stats.emit_ms[j], s->events[4 * j + 2], s->events[4 * j + 3]));
         }
-    s->n_valid = F;
+    const uint64_t F = s->n_valid;
     s->built = true;
     if (n_valid_out) *n_valid_out = F;
     s->stats.host_levels_ms = ms_since(t1);

@@ -22,6 +22,36 @@ def test_batched_spaces_equal_oracle(oracle_mod, s):
     assert np.array_equal(p.gkeys(), p.okeys)
 
 
+@pytest.mark.parametrize("name", ["tiny", "medium", "large_a"])
+def test_rebuild_from_previous_sizes(oracle_mod, name, monkeypatch):
+    """A rebuild launches every level from the previous build's level sizes and writes the same
+    keys.  With the last level's size hint off by one either way, that level's emit writes
+    nothing, the end-of-build check fails and the level-by-level build writes the keys again.
+    The keys are zeroed before each rebuild, so each rebuild must write all of them itself."""
+    p = Pair(W.SPACES[name](), oracle_mod, table=None)
+    assert not p.sp.build_stats()["hinted"]
+    first = p.sp.build_stats()["children"]
+
+    def rebuild():
+        p.sp.keys().fill_(0)
+        torch.cuda.synchronize()
+        assert p.sp.build() == len(p.okeys)
+        st = p.sp.build_stats()
+        assert st["children"] == first
+        assert np.array_equal(p.gkeys(), p.okeys)
+        return st["hinted"]
+
+    assert rebuild()
+    for skew in ("1", "-1"):
+        monkeypatch.setenv("CATUNE_BUILD_HINT_SKEW", skew)
+        assert not rebuild()
+    monkeypatch.delenv("CATUNE_BUILD_HINT_SKEW")
+    monkeypatch.setenv("CATUNE_BUILD_PIPELINE", "0")
+    assert not rebuild()
+    monkeypatch.delenv("CATUNE_BUILD_PIPELINE")
+    assert rebuild()
+
+
 def test_large_full_size(oracle_mod):
     """51.6e9 Cartesian points: count = |V(A)|*|V(B)|, keys strictly increasing, and sampled
     Cartesian windows equal the oracle's brute force of the same windows."""
