@@ -534,10 +534,13 @@ static __device__ void select_dev(const OptArgs& a, uint32_t gen, const uint64_t
                 st->stag = 0;
             }
         } else {
+            // duplicate tests: plain ORs over the population, unrolled so that eight shared loads
+            // are in flight (no early exit; duplicates are rare)
             for (int i = t; i < P; i += nt) {
                 const uint64_t u = sm.us[i];
                 bool in_x = false;
-                for (int k = 0; k < P && !in_x; ++k) in_x = sm.xs[k] == u;
+#pragma unroll 8
+                for (int k = 0; k < P; ++k) in_x |= sm.xs[k] == u;
                 sm.pass[i] = fit[i] <= a.FX[i] && !in_x;
             }
             __syncthreads();
@@ -546,7 +549,12 @@ static __device__ void select_dev(const OptArgs& a, uint32_t gen, const uint64_t
             for (int i = t; i < P; i += nt) {
                 bool ok = sm.pass[i];
                 const uint64_t u = sm.us[i];
-                for (int k = 0; k < i && ok; ++k) ok = !(sm.pass[k] && sm.us[k] == u);
+                if (ok) {   // not an earlier passing trial with the same key
+                    bool dup = false;
+#pragma unroll 8
+                    for (int k = 0; k < i; ++k) dup |= sm.us[k] == u && sm.pass[k];
+                    ok = !dup;
+                }
                 sm.acc[i] = ok;
                 if (ok) {
                     a.X[i] = u;
