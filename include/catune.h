@@ -133,12 +133,13 @@ ct_status ct_unpack_keys_device(const ct_space *space, const uint64_t *d_keys, i
  * Cartesian points, evaluates the constraints and compacts the valid keys in
  * increasing key order into a library-owned device array.  Synchronises the
  * stream; writes |V| to *n_valid_out.  Rebuilding replaces the previous keys.
- * The first build reads each level's size back before launching the next level;
- * a rebuild of the same space (whose definition cannot change) launches every
- * level from the previous build's sizes, each emit checking its size against
- * this build's own count on the device and writing nothing on a mismatch, and
- * the host checks all sizes once at the end (a mismatch redoes the build level
- * by level).  CATUNE_BUILD_PIPELINE=0 in the environment turns the latter off.
+ * The first build reads each level's size back before launching the next level.
+ * A rebuild of the same space (whose definition cannot change), when its buffers
+ * already hold the previous build's sizes, launches every level from those sizes:
+ * each emit checks its size against this build's own count on the device and
+ * writes nothing on a mismatch, and the host checks all sizes once at the end (a
+ * mismatch redoes the build level by level).  CATUNE_BUILD_PIPELINE=0 in the
+ * environment turns rebuilds from the previous sizes off.
  * Errors: EMPTY_SPACE (|V| = 0; the space stays usable for queries), OOM, CUDA. */
 ct_status ct_build_valid_space(ct_space *space, ct_stream stream, uint64_t *n_valid_out);
 

@@ -1186,6 +1186,30 @@ static ct_status build_levels(ct_space* s, cudaStream_t st, bool hinted, bool* o
     return CT_OK;
 }
 
+// Whether every buffer a hinted pass writes already holds the hinted sizes: a hinted pass then
+// allocates and releases nothing (no block goes back to the cache while earlier work that may
+// read it is still queued).  Otherwise the build takes the level-by-level path, which grows
+// buffers only after a synchronisation.
+static bool hint_fits(const ct_space* s) {
+    const DevSpace& h = s->h;
+    const int L = (int)s->hint.size();
+    if (L == 0 || L > h.n_blocks || s->d_total.cap < (size_t)h.n_blocks) return false;
+    uint64_t F = 1;
+    for (int j = 0; j < L; ++j) {
+        const DevBlock& bl = h.blocks[j];
+        const uint64_t items = bl.pattern ? F : F * (uint64_t)bl.W;
+        const uint64_t per_tile = bl.pattern ? pattern_tile(F) : EXP_TILE;
+        const uint64_t tiles = (items + per_tile - 1) / per_tile;
+        if (tiles > s->tile_counts.cap || tiles > s->tile_base.cap) return false;
+        const uint64_t Fn = s->hint[j];
+        const DevBuf<uint64_t>& dst = (j == h.n_blocks - 1) ? s->keys : s->frontier[j];
+        if (!dst.p || Fn > dst.cap) return false;
+        F = Fn;
+        if (F == 0) break;
+    }
+    return true;
+}
+
 // Hinted builds are on unless CATUNE_BUILD_PIPELINE=0.  CATUNE_BUILD_HINT_SKEW=k (nonzero) adds k
 // to the hinted size of the last level, which makes the check fail: the emit writes nothing and
 // the build is redone level by level (used to test that path).
@@ -1219,6 +1243,7 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
     if (hinted) {
         const long long skew = build_hint_skew();
         if (skew && (int)s->hint.size() == h.n_blocks) s->hint.back() = (uint64_t)((long long)s->hint.back() + skew);
+        hinted = hint_fits(s);
     }
     bool ok = true;
     CT_TRY(build_levels(s, st, hinted, &ok));

@@ -25,9 +25,10 @@ def test_batched_spaces_equal_oracle(oracle_mod, s):
 @pytest.mark.parametrize("name", ["tiny", "medium", "large_a"])
 def test_rebuild_from_previous_sizes(oracle_mod, name, monkeypatch):
     """A rebuild launches every level from the previous build's level sizes and writes the same
-    keys.  With the last level's size hint off by one either way, that level's emit writes
-    nothing, the end-of-build check fails and the level-by-level build writes the keys again.
-    The keys are zeroed before each rebuild, so each rebuild must write all of them itself."""
+    keys.  With the last level's size hint one too small, that level's emit writes nothing, the
+    end-of-build check fails and the level-by-level build writes the keys again; one too large
+    does not fit the key buffer, so the rebuild goes level by level from the start.  The keys
+    are zeroed before each rebuild, so each rebuild must write all of them itself."""
     p = Pair(W.SPACES[name](), oracle_mod, table=None)
     assert not p.sp.build_stats()["hinted"]
     first = p.sp.build_stats()["children"]
