@@ -501,12 +501,14 @@ k_pemit(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents
         for (; jj + 96 < cp; jj += 128) {   // four independent 32-key rows per iteration
             const uint32_t a0 = __ldg(lst + jj), a1 = __ldg(lst + jj + 32), a2 = __ldg(lst + jj + 64),
                            a3 = __ldg(lst + jj + 96);
-            o[jj] = par | ((uint64_t)a0 << pa.key_shift);
-            o[jj + 32] = par | ((uint64_t)a1 << pa.key_shift);
-            o[jj + 64] = par | ((uint64_t)a2 << pa.key_shift);
-            o[jj + 96] = par | ((uint64_t)a3 << pa.key_shift);
+            // streaming stores: the keys are written once per build, the pattern lists stay in L2
+            __stcs(reinterpret_cast<unsigned long long*>(o + jj), par | ((uint64_t)a0 << pa.key_shift));
+            __stcs(reinterpret_cast<unsigned long long*>(o + jj + 32), par | ((uint64_t)a1 << pa.key_shift));
+            __stcs(reinterpret_cast<unsigned long long*>(o + jj + 64), par | ((uint64_t)a2 << pa.key_shift));
+            __stcs(reinterpret_cast<unsigned long long*>(o + jj + 96), par | ((uint64_t)a3 << pa.key_shift));
         }
-        for (; jj < cp; jj += 32) o[jj] = par | ((uint64_t)__ldg(lst + jj) << pa.key_shift);
+        for (; jj < cp; jj += 32)
+            __stcs(reinterpret_cast<unsigned long long*>(o + jj), par | ((uint64_t)__ldg(lst + jj) << pa.key_shift));
     }
 }
 
