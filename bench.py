@@ -2,17 +2,20 @@
 
 Workload (default): the large space — 16 integer parameters, 51,609,600,000 Cartesian points
 (int64 index), 12 constraints, 695,228,960 valid configurations as packed uint64 keys.  One step
-is the whole hot path on it: build_valid_space end to end (decode, predicates, compaction into
-the sorted key array), then one generation of constraint-aware DE at pop 256 (initial valid
-sample, mutation + crossover, validity lookup, exhaustive-equivalent Hamming repair, fitness
-lookup in a seeded lognormal table, greedy selection).
+is the whole hot path of a tuning session on it, from a fresh definition: define_space from the
+host value lists and constraints, the space's first build_valid_space (decode, predicates,
+compaction into the sorted key array), then generations 0 and 1 of constraint-aware DE at pop 256
+(initial valid sample, mutation + crossover, validity lookup, exhaustive-equivalent Hamming
+repair, fitness lookup in a seeded lognormal table, greedy selection).
 
 Headline `value`: valid configurations enumerated per second (all ranks' |V| per step / step
-time), inputs resident on the device.  `e2e`: the same metric through the public C-ABI with host
-inputs (space definition) and host outputs (|V|, repaired population, best) inside the timed
-region.  Sub-metrics: repaired candidates/s on the large space, plain and batched runs/s.
+time, CUDA events on the launching stream).  `e2e`: the same step through the public C-ABI with
+the population, fitness and best read back to pinned host buffers, host wall clock.  `also`: the
+metric's other parts (repaired candidates/s on the large space, batched runs/s and their ratio to
+the same runs done one at a time) and the rebuild of an already built space.  `--full` adds every
+sub-metric on an earlier stdout line; the headline is always the last line.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--full]
 Under torchrun each rank runs an independent replica (weak scaling).
 """
 from __future__ import annotations
@@ -38,9 +41,9 @@ UNIT = "valid configs/s"
 L2_BYTES = 126 * 2 ** 20
 POP = 256
 CONFIG = {"workload": "large: 16 int params, 51,609,600,000 Cartesian points, 12 constraints, 695,228,960 valid; "
-                      "step = build_valid_space (every level's count, scan and emit; a rebuild launches the levels "
-                      "from the previous build's sizes, checked on the device) + DE generations 0 (initial sample) "
-                      "and 1 (pop 256, one CUDA graph)",
+                      "step = first build: define_space from host lists + the space's first build_valid_space "
+                      "(tables, every level's count, scan, size read-back and emit) + DE generations 0 (initial "
+                      "sample) and 1 (pop 256) + destroy",
           "pop": POP, "l2": "working set 5.6 GB of keys > 126 MB L2 (no flush needed)"}
 
 
@@ -288,6 +291,56 @@ def kernel_source_hash(name):
     return hashlib.sha256(src[m.start():end].encode()).hexdigest()[:16]
 
 
+def first_build_step(ct, sd, table, rank, emit):
+    """One step of the headline: a tuning session's device work from a fresh definition.
+    ct_define_space from the host lists, the first ct_build_valid_space of that space (device
+    upload of the descriptor, the compact, truth-mask and pattern tables, every level's count,
+    scan and emit with its size read back), the fitness table attached, a DE run created and its
+    generations 0 (initial sample) and 1 (pop 256) launched, then both handles destroyed (their
+    blocks go back to the library's cache in stream order).  `emit` collects the last-level
+    emit's CUDA-event time and algorithmic bytes."""
+    s = ct.Space.from_def(sd)
+    s.set_timing(True)
+    s.build()
+    s.set_fitness(table)
+    o = ct.Opt(s, "de", POP, seed=rank)
+    o.step(0)
+    o.step(1)
+    st = s.build_stats()
+    last = st["levels"] - 1
+    emit.append((st["emit_ms"][last], 8 * st["children"][last] + 8 * st["parents"][last], st["children"][last]))
+    del o, s
+
+
+def timed_loop(torch, ct, step, steps, warmup, stream, dist):
+    """W warm-up steps (more until the host has been busy for HOST_WARM_S), then exactly `steps`
+    steps between CUDA events on the launching stream, a barrier and a synchronisation on both
+    sides.  Returns (device ms over the timed steps, wall t0, wall t1, the library's kernel
+    launches inside the timed region)."""
+    tw = time.perf_counter()
+    done = 0
+    while done < warmup or time.perf_counter() - tw < HOST_WARM_S:
+        step(False)
+        done += 1
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    l0 = ct.launch_count()
+    e0.record(stream)
+    for _ in range(steps):
+        step(True)
+    e1.record(stream)
+    launches = ct.launch_count() - l0
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if dist:
+        dist.barrier()
+    return e0.elapsed_time(e1), t0, t1, launches
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -304,81 +357,70 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     sd = W.SPACES[args.workload]()
 
-    # ---- setup (untimed): space, table, run ----
+    # ---- input synthesis (untimed): the fitness table over the valid ranks ----
     sp = ct.Space.from_def(sd)
-    sp.set_timing(True)
     nv = sp.build()
     g = torch.Generator(device=dev)
     g.manual_seed(1234 + rank)
     table = torch.exp(torch.randn(nv, generator=g, device=dev, dtype=torch.float32))
-    sp.set_fitness(table)
-    opt = ct.Opt(sp, "de", POP, seed=rank)
 
-    def step():
-        sp.build()
-        opt.run_graph(0, 2)   # DE generations 0 and 1, one CUDA graph (dropped if a build moves the keys)
-
-    # Warm-up: W steps, then more until the host has been busy for HOST_WARM_S.  The host CPUs of
-    # the GPU machines run several times slower after an idle spell and take about a second of
-    # continuous work to come back to speed; a timed region right after a pause would time the
-    # host's wake-up rather than the library.  The clock sampler starts first so that it is
-    # already sampling when the timed region begins.
+    # ---- headline: first builds of freshly defined spaces + DE generations 0 and 1 ----
+    # The host CPUs of the GPU machines run several times slower after an idle spell and take
+    # about a second of continuous work to come back to speed; the warm-up keeps the host busy
+    # for at least HOST_WARM_S so that the timed region does not time the host's wake-up.  The
+    # clock sampler starts first so that it is already sampling when the timed region begins.
     clocks = ClockSampler(local)
     clocks.start()
-    tw = time.perf_counter()
-    done = 0
-    while done < args.warmup or time.perf_counter() - tw < HOST_WARM_S:
-        step()
-        done += 1
-    torch.cuda.synchronize()
-    emit_ms, emit_bytes = [], []
-    hinted = 0   # timed builds launched from the previous build's level sizes
-    l0 = ct.launch_count()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.time()
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-        st = sp.build_stats()
-        last = st["levels"] - 1
-        emit_ms.append(st["emit_ms"][last])
-        emit_bytes.append(8 * st["children"][last] + 8 * st["parents"][last])
-        hinted += bool(st["hinted"])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t1 = time.time()
-    if dist:
-        dist.barrier()
-    launches = ct.launch_count() - l0
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    emit = []
+    ms, t0, t1, launches = timed_loop(torch, ct, lambda rec: first_build_step(ct, sd, table, rank, emit if rec else []),
+                                      args.steps, args.warmup, stream, dist)
+    ms = max_over_ranks(ms, dist, dev)
     time.sleep(0.2)
     clocks.stop()
     ms_step = ms / args.steps
     value = job_throughput(nv, world, args.steps, ms)
 
-    # ---- roofline of the dominant kernel (last-level expand/emit) ----
+    # ---- roofline of the dominant kernel (last-level pattern emit), from the timed steps ----
     hbm, peak_kind = peaks()
-    emit_avg_ms = float(np.mean(emit_ms))
-    achieved = float(np.mean(emit_bytes)) / (emit_avg_ms / 1000.0) / 1e9
+    emit_avg_ms = float(np.mean([e[0] for e in emit]))
+    emit_bytes = float(np.mean([e[1] for e in emit]))
+    achieved = emit_bytes / (emit_avg_ms / 1000.0) / 1e9
     tpk = traffic_from_profile()
-    st = sp.build_stats()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": (tpk * st["children"][-1]) if tpk else None,
-                "traffic_note": "ncu dram bytes per key on the 146M-key slice, scaled by keys written"
-                                if tpk else "no ncu capture for the current kernel source",
-                "kernel": "k_pemit (last-level expand/emit of build_valid_space)", "peak_kind": f"{peak_kind} copy bandwidth",
-                "algorithmic_bytes_per_launch": float(np.mean(emit_bytes)), "avg_launch_ms": emit_avg_ms,
+                "traffic": (tpk * emit[-1][2]) if tpk else None,
+                "traffic_source": "not measured in this run: ncu DRAM bytes per key of the same kernel source "
+                                  "(profiles/expand_emit_large.md, 146M-key slice) x keys written per launch"
+                                  if tpk else "null: no ncu capture of the current kernel source",
+                "kernel": "k_pemit, last level of a first build_valid_space",
+                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": emit_bytes, "avg_launch_ms": emit_avg_ms,
                 "share_of_step": emit_avg_ms / ms_step}
+
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                              "ms_per_step": ms_step, "roofline": roofline, "gpu_launches": launches,
+                              "clocks": clocks.summary(t0, t1), "quick": True}), flush=True)
+        return 0
+
+    # ---- rebuild of an already built space (labelled sub-metric, not the headline) ----
+    sp.set_fitness(table)
+    opt = ct.Opt(sp, "de", POP, seed=rank)
+
+    def rebuild_step(rec):
+        sp.build()
+        opt.run_graph(0, 2)   # DE generations 0 and 1, one CUDA graph (dropped if a build moves the keys)
+
+    rb_ms, _, _, _ = timed_loop(torch, ct, rebuild_step, args.steps, args.warmup, stream, dist)
+    rb_ms = max_over_ranks(rb_ms, dist, dev)
+    hinted = bool(sp.build_stats()["hinted"])
+    del opt
 
     # ---- end to end through the C-ABI with host buffers ----
     keys_h = torch.empty(POP, dtype=torch.int64, pin_memory=True)     # the caller's host result buffers
     fit_h = torch.empty(POP, dtype=torch.float32, pin_memory=True)
     kd = torch.empty(POP, dtype=torch.int64, device=dev)
     fd = torch.empty(POP, dtype=torch.float32, device=dev)
-
     phases = {k: [] for k in ("define", "build", "create", "generations", "read_back", "destroy")}
 
     def e2e_step(record=False):
@@ -405,13 +447,6 @@ def run_ours(args):
                 phases[k].append(1000 * (z - a))
         return n2, b
 
-    if args.quick:
-        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-               "ms_per_step": ms_step, "roofline": roofline, "gpu_launches": launches,
-               "builds_from_previous_sizes": hinted, "quick": True}
-        if rank == 0:
-            print(json.dumps(out))
-        return 0
     h2d = sum(8 * len(v) + 4 for v in sd.values) + 16 * sum(len(c) for c in sd.constraints)
     d2h = 8 + POP * 12 + 8 + 4 + 8 + 16
     tw = time.perf_counter()                    # untimed: at least one step, host back to speed
@@ -426,49 +461,66 @@ def run_ours(args):
         e2e_step(record=True)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - ta) / e2e_steps
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
     e2e = {"value": world * nv / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "ms_per_step": 1000 * e2e_s,
-           "note": "define_space from host lists + build (5.6 GB key array from the library's block cache) + "
-                   "DE generations 0 and 1 + population and best read back to pinned host buffers, per step",
-           "phase_ms_median": {k: float(np.median(v)) for k, v in phases.items()}}
+           "note": "host wall clock: the headline step plus population, fitness and best read back to pinned host buffers",
+           "phase_ms_median": {k: round(float(np.median(v)), 4) for k, v in phases.items()}}
 
-    # ---- sub-metrics ----
-    sub = {"valid_configs_per_s": value, "cartesian_points_covered_per_s": world * sd.cartesian_size * args.steps / (ms / 1000.0),
-           "timed_builds_from_previous_sizes": hinted}
-    sub.update(repair_rates(sp, sd, torch, ct, dev))
-    sub.update(repair_paper_rates(sp, sd, torch, ct, dev, "large"))
-    med_sd = W.medium_space()
-    med = ct.Space.from_def(med_sd)
-    med.build()
-    sub.update(repair_paper_rates(med, med_sd, torch, ct, dev, "medium", n=256))
-    del med
-    sub.update(plain_runs(torch, ct, W, dev))
-    sub.update(batched_runs(torch, ct, W, dev))
-    sub.update(surrogate_vs_plain(torch, ct, W, dev))
-    sub.update(surrogate_large(torch, ct, sp, table, dev))
-    sub.update(surrogate_gain_large(torch, ct, W, sp, sd, dev))
-    sub.update(aware_vs_unaware(torch, ct, W, dev))
-    sub.update(operator_variants(torch, ct, W, dev))
-    del opt, table
+    # ---- the metric's other two parts, compact ----
+    also = {"rebuild_ms_per_step": rb_ms / args.steps, "rebuild_valid_configs_per_s": job_throughput(nv, world, args.steps, rb_ms),
+            "rebuild_note": "build of an already built space (levels launched from its previous sizes) + DE gens 0-1 as one graph",
+            "rebuild_hinted": hinted}
+    rr = repair_rates(sp, sd, torch, ct, dev, scan=args.full)
+    also.update({k: rr[k] for k in ("repaired_candidates_per_s_perturbed", "repaired_candidates_per_s_uniform")})
+    br = batched_runs(torch, ct, W, dev)
+    also.update({k: br[k] for k in ("batched_runs_per_s", "plain_runs_per_s_same_runs", "batched_vs_plain")})
+
+    sub = None
+    if args.full:
+        sub = {"valid_configs_per_s": value,
+               "cartesian_points_covered_per_s": world * sd.cartesian_size * args.steps / (ms / 1000.0)}
+        sub.update(rr)
+        sub.update(br)
+        sub.update(repair_paper_rates(sp, sd, torch, ct, dev, "large"))
+        med_sd = W.medium_space()
+        med = ct.Space.from_def(med_sd)
+        med.build()
+        sub.update(repair_paper_rates(med, med_sd, torch, ct, dev, "medium", n=256))
+        del med
+        sub.update(plain_runs(torch, ct, W, dev))
+        sub.update(surrogate_vs_plain(torch, ct, W, dev))
+        sub.update(surrogate_large(torch, ct, sp, table, dev))
+        sub.update(surrogate_gain_large(torch, ct, W, sp, sd, dev))
+        sub.update(aware_vs_unaware(torch, ct, W, dev))
+        sub.update(operator_variants(torch, ct, W, dev))
+    del table
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
            "config": dict(CONFIG, parallelism=f"replicas x{world}"),
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
-           "clocks": clocks.summary(t0, t1), "submetrics": sub}
+           "clocks": clocks.summary(t0, t1), "also": also}
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:
-        print(json.dumps(out))
+        if sub is not None:
+            blob = json.dumps({"submetrics": sub})
+            if args.submetrics_out:
+                with open(args.submetrics_out, "w") as f:
+                    f.write(blob + "\n")
+            print(blob, flush=True)
+        print(json.dumps(out), flush=True)   # the headline: always the last line on stdout
     if dist:
         dist.destroy_process_group()
     return 0
 
 
-def repair_rates(sp, sd, torch, ct, dev):
+def repair_rates(sp, sd, torch, ct, dev, scan=True):
     """Repaired candidates per second on the large space: batches of 256 DE-like perturbations
-    of valid keys, and batches of 256 uniform random tuples (worst case)."""
+    of valid keys, and batches of 256 uniform random tuples (worst case); with `scan`, also the
+    exhaustive scan alone for 1 to 32 pending candidates."""
     from paper_2606_28372_b300 import workloads as W
     keys = sp.keys()
     res = {}
@@ -503,6 +555,8 @@ def repair_rates(sp, sd, torch, ct, dev):
         d = np.concatenate(ds)
         res[f"repaired_candidates_per_s_{kind}"] = reps * len(batches) * 256 / (ms / 1000.0)
         res[f"repair_distance_hist_{kind}"] = np.bincount(d, minlength=8)[:8].tolist()
+    if not scan:
+        return res
     # exhaustive scan alone (scan-only mode): one pass over the 5.56 GB of keys per call
     unif = torch.from_numpy(sp.pack(W.uniform_tuples(sd, 64, seed=999)).view(np.int64)).to(dev)
     sp.set_repair_mode(1, 0)
@@ -520,17 +574,11 @@ def repair_rates(sp, sd, torch, ct, dev):
         ms = e0.elapsed_time(e1) / 5
         scan[f"q{q}"] = {"ms_per_pass": ms, "key_stream_GBps": 8 * keys.numel() / (ms / 1000.0) / 1e9}
     sp.set_repair_mode(0, 0)
-    # integer side of the scan: one population count per (key, candidate) on keys of <= 32 bits,
-    # two on wider keys; the population-count pipe bounds it, and the library's microbenchmark
-    # measures that pipe's rate
-    peak = ct.measure_int_peak()
-    per_pair = 2 if sp.info().key_bits > 32 else 1
+    hbm, _ = peaks()
     for q, v in scan.items():
-        pairs = keys.numel() * int(q[1:]) / (v["ms_per_pass"] / 1000.0)
-        v["popc_pipe_frac"] = pairs * per_pair / peak
+        v["pairs_per_s"] = keys.numel() * int(q[1:]) / (v["ms_per_pass"] / 1000.0)
+        v["key_stream_frac_of_copy_peak"] = v["key_stream_GBps"] / hbm
     res["scan_only_repair"] = scan
-    res["int_peak_popc_per_s"] = peak
-    res["scan_popc_per_pair"] = per_pair
     return res
 
 
@@ -1035,7 +1083,11 @@ if __name__ == "__main__":
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
-    ap.add_argument("--quick", action="store_true", help="headline step only (no e2e, no sub-metrics)")
+    ap.add_argument("--quick", action="store_true", help="headline step only (no rebuild, e2e, other parts or CPU leg)")
+    ap.add_argument("--full", action="store_true",
+                    help="also every sub-metric (repair rules, plain runs, surrogate, aware vs unaware, operator "
+                         "variants; minutes), printed as one JSON line before the headline")
+    ap.add_argument("--submetrics-out", default=None, help="with --full: also write the sub-metrics line to this file")
     ap.add_argument("--mode", default="step",
                     choices=["step", "scan", "repair", "aware", "variants", "batched", "rules", "surrogate"],
                     help="scan: only the exhaustive repair scan (scan-only repair of 1 to 32 uniform candidates); "

@@ -77,6 +77,9 @@ struct RepairScratch {
     DevBuf<unsigned long long> best;   // per pending slot: best key / packed (dist, rank)
     DevBuf<uint64_t> fail;             // per candidate: the constraints it fails
     DevBuf<uint32_t> done;             // ball kernels: CTAs finished (the last one resolves the radius)
+    void release_all() {
+        pend_a.release(); pend_b.release(); counts.release(); best.release(); fail.release(); done.release();
+    }
 };
 
 // The resolve step of one ball radius, done by the ball kernel's last CTA (see search.cu);

@@ -666,7 +666,7 @@ struct ct_opt {
         for (auto& g : graphs) cudaGraphExecDestroy(g.second);
         st.release(); X.release(); cand.release(); rep.release(); FX.release(); pos.release(); vel.release();
         pb.release(); fpb.release(); gb.release(); ynew.release(); fit.release(); memo.release();
-        rs.pend_a.release(); rs.pend_b.release(); rs.counts.release(); rs.best.release();
+        rs.release_all();
     }
     OptArgs args() const {
         OptArgs a;

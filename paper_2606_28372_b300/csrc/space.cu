@@ -1020,7 +1020,7 @@ ct_space::~ct_space() {
     keys.release(); tile_counts.release(); tile_base.release(); d_total.release(); status.release();
     for (auto& f : frontier) f.release();
     for (auto& b : balls) { b.d_masks.release(); b.d_prefix.release(); }
-    rs.pend_a.release(); rs.pend_b.release(); rs.counts.release(); rs.best.release();
+    rs.release_all();
     rules.release_all();
     occ.release();
 }

@@ -310,7 +310,7 @@ void surrogate_free(SurrogateState* g) {
     g->params.release(); g->mom.release(); g->grad.release(); g->work.release(); g->pred.release(); g->by.release();
     g->feats.release(); g->param_of.release(); g->cand.release(); g->rep.release(); g->evk.release(); g->ek.release();
     g->evk_chosen.release(); g->ey.release(); g->in_e.release(); g->sd.release();
-    g->rs.pend_a.release(); g->rs.pend_b.release(); g->rs.counts.release(); g->rs.best.release();
+    g->rs.release_all();
     if (g->h_sd) cudaFreeHost(g->h_sd);
     if (g->h_od) cudaFreeHost(g->h_od);
     delete g;
