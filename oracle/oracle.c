@@ -22,8 +22,11 @@
  * Pins (tests/test_oracle_*.py): hand-counted tiny space, closed-form large
  * space, brute-force medium count, Philox known-answer vectors, exp error bound,
  * exhaustive repair invariants, optimizer reduction cases and rerun determinism.
- * Optimizer trajectories themselves are "parity unpinned" by the paper (it
- * prints no trace); they are pinned by the reduction cases only.
+ * The paper prints no optimizer trace, so each update rule is pinned on its own
+ * (tests/test_oracle_moves.py): the PSO velocity carry and its cognitive and
+ * social terms, the Firefly attraction and noise, each isolated at
+ * hyper-parameters where the other terms vanish, and DE's acceptance and best
+ * update replayed from the trace of whole runs.
  */
 #include <math.h>
 #include <stdint.h>
