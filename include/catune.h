@@ -173,17 +173,22 @@ ct_status ct_repair(ct_space *space, const uint64_t *d_cand, int64_t n, uint64_t
                     uint8_t *d_dist, ct_stream stream);
 
 /* Repair that allocates nothing (the paper has no counterpart to this call).
- * Same arguments and result as ct_repair, for callers that must not allocate
- * device memory: host applications that reserve device memory through their own
- * allocator and forbid allocations from libraries, and latency-sensitive loops in
- * which cudaFree's implicit device-wide synchronisation would stall other streams.
- * Scratch comes from a fixed array compiled into the library (one ~384 KB copy on
- * every device that loads it, held until the process exits), so n may not exceed
- * CT_REPAIR_NOALLOC_MAX (larger n returns CT_ERR_LIMIT; split the batch).  The
- * first call on each device looks up the array's device address once; make that
- * call before capturing any stream.  All calls share the array: calls whose
- * execution overlaps on the GPU race on it, so the caller must order them (one
- * stream, or explicit synchronisation).  The space must already be built. */
+ * Same arguments and result as ct_repair, by the same kernels, for callers that
+ * must not allocate device memory: host applications that reserve device memory
+ * through their own allocator and forbid allocations from libraries, and
+ * latency-sensitive loops in which an allocation, or cudaFree's implicit
+ * device-wide synchronisation, would stall other streams.  Scratch comes from a
+ * fixed array compiled into the library (one ~512 KB copy on every device that
+ * loads it, held until the process exits), so n may not exceed
+ * CT_REPAIR_NOALLOC_MAX (larger n returns CT_ERR_LIMIT; split the batch).  It
+ * searches only the Hamming-ball radii whose tables are already on the device
+ * (the build uploads every radius ct_repair uses) and scans exhaustively for the
+ * rest, so the result is always exact.  The first call on each device looks up
+ * the array's device address once; make that call before capturing any stream.
+ * A cudaDeviceReset invalidates that address, as it does every handle and
+ * buffer of this library.  All calls share the array: calls whose execution
+ * overlaps on the GPU race on it, so the caller must order them (one stream, or
+ * explicit synchronisation).  The space must already be built. */
 #define CT_REPAIR_NOALLOC_MAX 16384
 ct_status ct_repair_noalloc(ct_space *space, const uint64_t *d_cand, int64_t n, uint64_t *d_out,
                             uint8_t *d_dist, ct_stream stream);
@@ -485,6 +490,10 @@ ct_status ct_measure_int_peak(double *popc_per_s, ct_stream stream);
 
 /* Number of kernels this library has launched in this process (all devices). */
 uint64_t ct_launch_count(void);
+
+/* Number of device blocks this library has taken in this process (all devices), whether
+ * from its cache or from the driver: a call that leaves it unchanged allocated nothing. */
+uint64_t ct_alloc_count(void);
 
 /* ------------------------------------------------------------------------- */
 /* misc                                                                      */

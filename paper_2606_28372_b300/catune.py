@@ -133,6 +133,7 @@ _SIGS = {
     "ct_space_build_stats": [C.c_void_p, C.c_void_p],
     "ct_measure_int_peak": [C.POINTER(C.c_double), C.c_void_p],
     "ct_launch_count": [],
+    "ct_alloc_count": [],
     "ct_trim_cache": [],
     "ct_last_error": [],
     "ct_version": [],
@@ -160,6 +161,7 @@ def lib():
         L.ct_mlp_workspace_bytes.restype = C.c_size_t
         L.ct_opt_params_default.restype = None
         L.ct_launch_count.restype = C.c_uint64
+        L.ct_alloc_count.restype = C.c_uint64
         L.ct_trim_cache.restype = None
         _lib = L
     return _lib
@@ -379,6 +381,11 @@ class Space:
 
 def launch_count():
     return int(lib().ct_launch_count())
+
+
+def alloc_count():
+    """Device blocks the library has taken so far (from its cache or the driver)."""
+    return int(lib().ct_alloc_count())
 
 
 class _CudaArray:

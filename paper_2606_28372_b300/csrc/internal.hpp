@@ -82,8 +82,7 @@ struct RepairScratch {
     }
 };
 
-// The resolve step of one ball radius, done by the ball kernel's last CTA (see search.cu);
-// done = null: the caller resolves with k_ball_resolve.
+// The resolve step of one ball radius, done by the ball kernel's last CTA (see search.cu).
 struct BallNext {
     uint32_t* done;                 // CTAs finished (zero before the launch; the last CTA resets it)
     int d;                          // the radius
@@ -172,6 +171,22 @@ ct_status ensure_balls(ct_space* s, int dmax);
 int wanted_radius(const ct_space* s);
 ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, int64_t n, uint64_t* d_out,
                       uint8_t* d_dist, cudaStream_t st);
+// Device scratch of one repair call: pending lists, their counters and argmin words (ping-pong
+// between radii), the failing-constraint word of each candidate, and the ball kernels' CTA
+// ticket.  The counters must be zero when the call starts, and so must the ticket (the ball
+// kernels leave it at zero).
+struct RepairPtrs {
+    int32_t* pend[2];
+    uint32_t* cnt[2];
+    unsigned long long* best[2];
+    uint64_t* fail;
+    uint32_t* done;
+};
+// The launches of one repair (table test, Hamming balls of radii 1..dmax whose tables are on
+// the device, exhaustive scan of whatever is left, resolve), on caller-provided scratch for n
+// candidates; allocates nothing.
+ct_status repair_launch(const ct_space* s, const RepairPtrs& p, int dmax, const uint64_t* d_cand, int64_t n,
+                        uint64_t* d_out, uint8_t* d_dist, cudaStream_t st);
 int auto_radius(const ct_space* s, double div = 8.0);   // div: the scan pass's cost, in ball points
 ct_status scan_lut(const ct_space* s, const uint64_t* d_cand, const int32_t* pend, const uint32_t* count,
                    unsigned long long* best, cudaStream_t st, bool* launched, int* lut_min);

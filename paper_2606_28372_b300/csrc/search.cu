@@ -102,8 +102,7 @@ __global__ void k_repair_init(const DevSpace* __restrict__ sp, const uint32_t* _
 
 // The resolve step of one radius, run by the last CTA of the ball kernel to finish (an atomic
 // ticket after a fence; nothing waits): candidates whose ball held a valid point are settled, the
-// others are queued for the next radius.  A null ticket counter leaves the resolve to
-// k_ball_resolve (the fixed-scratch repair).
+// others are queued for the next radius.
 __device__ __forceinline__ void ball_resolve_last(const BallNext& nx, const int32_t* __restrict__ pend_in,
                                                   const uint32_t* __restrict__ count_in,
                                                   const unsigned long long* __restrict__ best_in) {
@@ -218,26 +217,6 @@ k_ball_fs(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, 
     ball_resolve_last(nx, pend, count, best);
 }
 
-// settle candidates whose ball held a valid point; requeue the rest
-__global__ void k_ball_resolve(int d, const int32_t* __restrict__ pend_in, const uint32_t* __restrict__ count_in,
-                               const unsigned long long* __restrict__ best_in, uint64_t* __restrict__ out,
-                               uint8_t* __restrict__ dist, int32_t* __restrict__ pend_out, uint32_t* __restrict__ count_out,
-                               unsigned long long* __restrict__ best_out) {
-    const uint32_t cnt = *count_in;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
-        const unsigned long long b = best_in[q];
-        const int32_t i = pend_in[q];
-        if (b != NONE) {
-            out[i] = b;
-            if (dist) dist[i] = (uint8_t)d;
-        } else {
-            const uint32_t slot = atomicAdd(count_out, 1u);
-            pend_out[slot] = i;
-            best_out[slot] = NONE;
-        }
-    }
-}
-
 // Exhaustive streaming argmin of (distance, rank) for up to 32 candidates per CTA.
 // Each thread reads two keys per 16-byte load and keeps, per candidate, the packed
 // minimum (distance << 26 | iteration << 1 | which); keys ascend within a thread, so
@@ -300,36 +279,6 @@ __device__ __forceinline__ void scan_run(const uint64_t* __restrict__ keys, int6
         unsigned long long v = ~0ull;
         for (int w = 0; w < SCAN_THREADS / 32; ++w) v = red[w][threadIdx.x] < v ? red[w][threadIdx.x] : v;
         atomicMin(best + threadIdx.x, v);
-    }
-}
-
-__global__ void __launch_bounds__(SCAN_THREADS)
-k_scan(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_t highm,
-       const uint64_t* __restrict__ cand, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
-       unsigned long long* __restrict__ best) {
-    __shared__ uint64_t cq[SCAN_CHUNK];
-    __shared__ unsigned long long red[SCAN_THREADS / 32][SCAN_CHUNK];
-    const uint32_t cnt = *count;
-    const uint32_t q0 = blockIdx.y * SCAN_CHUNK;
-    if (q0 >= cnt) return;
-    const int nq = min((uint32_t)SCAN_CHUNK, cnt - q0);
-    if (threadIdx.x < SCAN_CHUNK) cq[threadIdx.x] = threadIdx.x < nq ? cand[pend[q0 + threadIdx.x]] : 0ull;
-    __syncthreads();
-    unsigned long long* bq = best + q0;
-    if ((highm >> 32) == 0) {
-        if (nq <= 1) scan_run<1, true>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else if (nq <= 2) scan_run<2, true>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else if (nq <= 4) scan_run<4, true>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else if (nq <= 8) scan_run<8, true>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else if (nq <= 16) scan_run<16, true>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else scan_run<32, true>(keys, nv, lowm, highm, cq, nq, bq, red);
-    } else {
-        if (nq <= 1) scan_run<1, false>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else if (nq <= 2) scan_run<2, false>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else if (nq <= 4) scan_run<4, false>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else if (nq <= 8) scan_run<8, false>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else if (nq <= 16) scan_run<16, false>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else scan_run<32, false>(keys, nv, lowm, highm, cq, nq, bq, red);
     }
 }
 
@@ -510,42 +459,33 @@ ct_status repair_reserve(RepairScratch& rs, int64_t n) {
     return CT_OK;
 }
 
-ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, int64_t n, uint64_t* d_out,
-                      uint8_t* d_dist, cudaStream_t st) {
-    if (n == 0) return CT_OK;
-    if (n > 0x7fffffffLL) { set_error("n too large"); return CT_ERR_LIMIT; }
-    CT_TRY(repair_reserve(rs, n));
-    unsigned long long* best[2] = {rs.best.p, rs.best.p + n};
-    int32_t* pend[2] = {rs.pend_a.p, rs.pend_b.p};
-    uint32_t* cnt[2] = {rs.counts.p, rs.counts.p + 1};
+ct_status repair_launch(const ct_space* s, const RepairPtrs& p, int dmax, const uint64_t* d_cand, int64_t n,
+                        uint64_t* d_out, uint8_t* d_dist, cudaStream_t st) {
     const int sms = sm_count();
     const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
     const unsigned gi = (unsigned)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sms * 8);   // a warp per candidate
-    CT_TRY_CUDA(cudaMemsetAsync(rs.counts.p, 0, 8, st));
-    k_repair_init<<<gi, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, pend[0], cnt[0], best[0], s->status.p,
-                                      rs.fail.p);
+    k_repair_init<<<gi, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, p.pend[0], p.cnt[0], p.best[0],
+                                      s->status.p, p.fail);
     count_launch();
-    const int dmax = wanted_radius(s);
-    CT_TRY(ensure_balls(s, dmax));   // normally planned already (after the build, at run creation)
     uint64_t fs_min_avg = BALL_FS_MIN_AVG;   // CATUNE_BALL_FS_MIN_AVG overrides it (tests)
     if (const char* env = getenv("CATUNE_BALL_FS_MIN_AVG")) fs_min_avg = strtoull(env, nullptr, 10);
     int cur = 0;
     for (int d = 1; d <= dmax; ++d) {
         const BallRadius& br = s->balls[d - 1];
         // the kernel's last CTA resolves this radius: settles, and queues the rest for the next
-        const BallNext nx{rs.done.p, d, d_out, d_dist, pend[cur ^ 1], cnt[cur ^ 1], best[cur ^ 1]};
+        const BallNext nx{p.done, d, d_out, d_dist, p.pend[cur ^ 1], p.cnt[cur ^ 1], p.best[cur ^ 1]};
         if (br.total >= fs_min_avg * br.masks.size()) {
             // large subsets: a warp per (candidate, subset) over the filtered points
             const uint64_t work = (uint64_t)n * br.masks.size() * 32;
             const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 4);   // one wave
-            k_ball_fs<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, (int)br.masks.size(), d_cand, pend[cur],
-                                          cnt[cur], best[cur], rs.fail.p, nx);
+            k_ball_fs<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, (int)br.masks.size(), d_cand, p.pend[cur],
+                                          p.cnt[cur], p.best[cur], p.fail, nx);
         } else {
             // small subsets: a thread per point
             const uint64_t work = (uint64_t)n * br.total;
             const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 4);   // one wave
             k_ball<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
-                                       d_cand, pend[cur], cnt[cur], best[cur], rs.fail.p, nx);
+                                       d_cand, p.pend[cur], p.cnt[cur], p.best[cur], p.fail, nx);
         }
         count_launch();
         cur ^= 1;
@@ -557,19 +497,32 @@ ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, in
     const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 2));
     bool lut = false;   // long key arrays: per-candidate distance tables
     int lut_min = 0;
-    CT_TRY(scan_lut(s, d_cand, pend[cur], cnt[cur], best[cur], st, &lut, &lut_min));
+    CT_TRY(scan_lut(s, d_cand, p.pend[cur], p.cnt[cur], p.best[cur], st, &lut, &lut_min));
     k_scan_few<<<gf, SCAN_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, s->h.swar_low, s->h.swar_high, d_cand,
-                                            pend[cur], cnt[cur], best[cur], lut ? lut_min - 1 : 4);
+                                            p.pend[cur], p.cnt[cur], p.best[cur], lut ? lut_min - 1 : 4);
     count_launch();
     if (!lut) {
         k_scan_wide<<<gw, SCAN_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, s->h.swar_low, s->h.swar_high,
-                                                 d_cand, pend[cur], cnt[cur], best[cur]);
+                                                 d_cand, p.pend[cur], p.cnt[cur], p.best[cur]);
         count_launch();
     }
-    k_scan_resolve<<<g1, 256, 0, st>>>(s->keys.p, pend[cur], cnt[cur], best[cur], d_out, d_dist);
+    k_scan_resolve<<<g1, 256, 0, st>>>(s->keys.p, p.pend[cur], p.cnt[cur], p.best[cur], d_out, d_dist);
     count_launch();
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
+}
+
+ct_status repair_impl(ct_space* s, RepairScratch& rs, const uint64_t* d_cand, int64_t n, uint64_t* d_out,
+                      uint8_t* d_dist, cudaStream_t st) {
+    if (n == 0) return CT_OK;
+    if (n > 0x7fffffffLL) { set_error("n too large"); return CT_ERR_LIMIT; }
+    CT_TRY(repair_reserve(rs, n));
+    const int dmax = wanted_radius(s);
+    CT_TRY(ensure_balls(s, dmax));   // normally planned already (after the build, at run creation)
+    CT_TRY_CUDA(cudaMemsetAsync(rs.counts.p, 0, 8, st));
+    const RepairPtrs p{{rs.pend_a.p, rs.pend_b.p}, {rs.counts.p, rs.counts.p + 1}, {rs.best.p, rs.best.p + n},
+                       rs.fail.p, rs.done.p};
+    return repair_launch(s, p, dmax, d_cand, n, d_out, d_dist, st);
 }
 
 }  // namespace ct

@@ -47,6 +47,7 @@ void set_error(const char* fmt, ...) {
 const char* last_error() { return g_err.c_str(); }
 
 static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint64_t> g_allocs{0};
 
 // ---- device block cache ----
 namespace {
@@ -73,6 +74,7 @@ void flush_device(BlockCache& c, int d) {
 }  // namespace
 
 void* dev_alloc(size_t bytes, cudaError_t* err) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     BlockCache& c = cache();
     const int d = current_device();
     {
@@ -892,8 +894,6 @@ int wanted_radius(const ct_space* s) {
     return auto_radius(s);
 }
 
-// Enumerates and uploads the ball tables of radii balls.size()+1 .. dmax (subsets of the
-// parameters with r_k > 1, in lexicographic order, with prefix sums of their sizes).
 // Host part of the ball tables: enumerates radii balls.size()+1 .. dmax (subsets of the
 // parameters with r_k > 1, in lexicographic order, with prefix sums of their sizes).  No CUDA
 // call, so the build runs it while its last level is still being emitted.
@@ -1288,6 +1288,7 @@ ct_status ct_space_build_stats(const ct_space* s, ct_build_stats* out) {
 }
 
 uint64_t ct_launch_count(void) { return g_launches.load(); }
+uint64_t ct_alloc_count(void) { return g_allocs.load(); }
 
 void ct_trim_cache(void) {
     BlockCache& c = cache();

@@ -91,6 +91,39 @@ def test_large_full_size(oracle_mod):
     del keys
 
 
+def _large_expected_on_device(oracle_mod):
+    """All 695,228,960 keys of the large space from the oracle: it is group A x group B with no
+    constraint across them and A's parameters in the high bits, so its sorted keys are
+    (key_A << bits_B) | key_B over the oracle's valid keys of each group, A outer."""
+    ka = oracle_mod.valid_keys(oracle_mod.from_def(W.large_group_a()))
+    kb = oracle_mod.valid_keys(oracle_mod.from_def(W.large_group_b()))
+    osp = oracle_mod.from_def(W.large_space())
+    unit = np.zeros((1, 16), np.int64)
+    unit[0, 7] = 1                      # index 1 in A's lowest parameter: the key 1 << bits_B
+    bits_b = int(oracle_mod.pack(osp, unit)[0]).bit_length() - 1
+    a = torch.from_numpy(ka.astype(np.int64)).cuda()
+    b = torch.from_numpy(kb.astype(np.int64)).cuda()
+    return ((a[:, None] << bits_b) | b[None, :]).reshape(-1)
+
+
+def test_large_key_for_key(oracle_mod):
+    """The large space's first build and a rebuild into a zeroed key buffer (levels launched from
+    the first build's sizes) both equal the oracle's keys, every one of the 695,228,960."""
+    from paper_2606_28372_b300 import catune as ct
+    expected = _large_expected_on_device(oracle_mod)
+    assert expected.numel() == 695_228_960
+    sp = ct.Space.from_def(W.large_space())
+    assert sp.build() == expected.numel()
+    assert not sp.build_stats()["hinted"]
+    assert torch.equal(sp.keys(), expected)
+    sp.keys().fill_(0)
+    torch.cuda.synchronize()
+    assert sp.build() == expected.numel()
+    assert sp.build_stats()["hinted"]
+    assert torch.equal(sp.keys(), expected)
+    del expected
+
+
 def test_edge_spaces(oracle_mod):
     from paper_2606_28372_b300 import catune as ct
     cases = [
