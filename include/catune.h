@@ -131,15 +131,19 @@ ct_status ct_unpack_keys_device(const ct_space *space, const uint64_t *d_keys, i
 
 /* Resolves the whole valid space on the device (Section IV-A): decodes the
  * Cartesian points, evaluates the constraints and compacts the valid keys in
- * increasing key order into a library-owned device array.  Synchronises the
- * stream; writes |V| to *n_valid_out.  Rebuilding replaces the previous keys.
- * The first build reads each level's size back before launching the next level.
+ * increasing key order into a library-owned device array.  Writes |V| to
+ * *n_valid_out.  Rebuilding replaces the previous keys.  The first build reads
+ * each level's size back (synchronising the stream) before launching the next
+ * level, and returns as soon as the last level's size is known: the last level's
+ * keys are still being written, and every later call on the stream (or any work
+ * ordered after it) sees them complete.
  * A rebuild of the same space (whose definition cannot change), when its buffers
  * already hold the previous build's sizes, launches every level from those sizes:
  * each emit checks its size against this build's own count on the device and
- * writes nothing on a mismatch, and the host checks all sizes once at the end (a
- * mismatch redoes the build level by level).  CATUNE_BUILD_PIPELINE=0 in the
- * environment turns rebuilds from the previous sizes off.
+ * writes nothing on a mismatch, and the host checks all sizes once at the end,
+ * synchronising the stream (a mismatch redoes the build level by level).
+ * CATUNE_BUILD_PIPELINE=0 in the environment turns rebuilds from the previous
+ * sizes off.
  * Errors: EMPTY_SPACE (|V| = 0; the space stays usable for queries), OOM, CUDA. */
 ct_status ct_build_valid_space(ct_space *space, ct_stream stream, uint64_t *n_valid_out);
 
@@ -282,8 +286,11 @@ void ct_opt_params_default(ct_opt_params *p);
 /* Creates one run: population `pop` (3..CT_MAX_POP; DE needs one more than the random
  * members its mutation draws), counter-based
  * RNG seed `seed`.  Allocates the run's device state (population, positions,
- * memo bitmap of |V| bits) on the space's device.  Requires a built space with a
- * fitness table.  The space must outlive the run. */
+ * memo bitmap of |V| bits) on the space's device and initialises it
+ * asynchronously on the legacy default stream, behind the work already queued
+ * there (the space's build may still be writing its last keys); the run's first
+ * use on any other stream waits for that initialisation.  Requires a built space
+ * with a fitness table.  The space must outlive the run. */
 ct_status ct_opt_create(ct_space *space, ct_opt_kind kind, const ct_opt_params *params, int32_t pop,
                         uint64_t seed, ct_opt **out);
 void ct_opt_destroy(ct_opt *opt);
@@ -307,7 +314,9 @@ ct_status ct_opt_select(ct_opt *opt, uint32_t generation, const uint64_t *d_keys
 /* The whole generation with run-owned buffers. */
 ct_status ct_opt_step(ct_opt *opt, uint32_t generation, ct_stream stream);
 /* Runs generations [first, first + count) as one CUDA graph (captured on the
- * first call for this count, replayed afterwards). */
+ * first call for this count, replayed afterwards).  Generation 0, when included,
+ * runs eagerly before the graph: its sample is valid by construction, so it
+ * skips the repair launches. */
 ct_status ct_opt_run_graph(ct_opt *opt, uint32_t first, uint32_t count, ct_stream stream);
 
 /* Run summary (synchronises): best key and fitness so far, unique evaluations,
@@ -474,6 +483,7 @@ typedef struct {
     int32_t hinted;
 } ct_build_stats;
 ct_status ct_space_set_timing(ct_space *space, int32_t enable);
+/* With timing on, waits for the build's last timed kernel before it reads the times. */
 ct_status ct_space_build_stats(const ct_space *space, ct_build_stats *stats);
 
 /* Device memory released by the library (destroyed spaces and runs, shrunk

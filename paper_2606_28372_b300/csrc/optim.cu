@@ -41,6 +41,16 @@ __global__ void __launch_bounds__(OPT_THREADS) k_select(OptArgs a, uint32_t gen_
 
 __global__ void k_set_gen(OptDev* st, uint32_t g) { st->gen = g; }
 
+// A new run's device state: the initial run record, and zeroed positions, velocities and bests.
+__global__ void k_opt_init(OptDev* __restrict__ st, const OptDev init, float* __restrict__ pos,
+                           float* __restrict__ vel, float* __restrict__ pb, float* __restrict__ ynew, size_t PN,
+                           float* __restrict__ gb, int N) {
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
+    if (t0 == 0) *st = init;
+    for (size_t i = t0; i < PN; i += nt) { pos[i] = 0.0f; vel[i] = 0.0f; pb[i] = 0.0f; ynew[i] = 0.0f; }
+    for (size_t i = t0; i < (size_t)N; i += nt) gb[i] = 0.0f;
+}
+
 }  // namespace ct
 
 using namespace ct;
@@ -75,7 +85,12 @@ static ct_status step_impl(ct_opt* o, uint32_t gen, int use_dev, cudaStream_t st
     const OptArgs a = o->args();
     k_propose<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->cand.p);
     count_launch();
-    CT_TRY(repair_step(o, a, gen, use_dev, st));
+    if (!use_dev && gen == 0 && o->prm.constraint_aware) {
+        // the initial sample draws valid ranks, so repair is the identity: skip its launches
+        CT_TRY_CUDA(cudaMemcpyAsync(o->rep.p, o->cand.p, (size_t)o->P * 8, cudaMemcpyDeviceToDevice, st));
+    } else {
+        CT_TRY(repair_step(o, a, gen, use_dev, st));
+    }
     k_post_repair<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->rep.p);
     count_launch();
     CT_TRY(evaluate_impl(o->s, o->memo.p, &o->st.p->n_unique, &o->st.p->cost, o->rep.p, o->P, o->fit.p, nullptr, st,
@@ -145,11 +160,16 @@ ct_status ct_opt_create(ct_space* s, ct_opt_kind kind, const ct_opt_params* para
     init.best_fit = __builtin_inff();
     init.hit_gen = -1;
     init.hit_evals = -1;
-    if (cudaMemcpy(o->st.p, &init, sizeof init, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(o->memo.p, 0, o->memo_words * 4) != cudaSuccess ||
-        cudaMemset(o->pos.p, 0, PN * 4) != cudaSuccess || cudaMemset(o->vel.p, 0, PN * 4) != cudaSuccess ||
-        cudaMemset(o->pb.p, 0, PN * 4) != cudaSuccess || cudaMemset(o->gb.p, 0, o->N * 4) != cudaSuccess ||
-        cudaMemset(o->ynew.p, 0, PN * 4) != cudaSuccess) {
+    // Asynchronous on the legacy default stream, after everything queued before (a space's build
+    // may still be writing its last keys); the run's first use on another stream waits for the
+    // event recorded behind it.
+    const unsigned gi = (unsigned)std::min<size_t>((PN + 255) / 256 + 1, 1024);
+    k_opt_init<<<gi, 256, 0, cudaStreamLegacy>>>(o->st.p, init, o->pos.p, o->vel.p, o->pb.p, o->ynew.p, PN, o->gb.p, o->N);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemsetAsync(o->memo.p, 0, o->memo_words * 4, cudaStreamLegacy) != cudaSuccess ||
+        cudaEventCreateWithFlags(&o->ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(o->ready, cudaStreamLegacy) != cudaSuccess) {
         set_error("initialising run state failed");
         delete o;
         return CT_ERR_CUDA;
@@ -162,6 +182,7 @@ void ct_opt_destroy(ct_opt* o) { delete o; }
 
 ct_status ct_propose_population(ct_opt* o, uint32_t gen, uint64_t* d_cand, ct_stream stream) {
     if (!o || !d_cand) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    CT_TRY(o->wait_ready((cudaStream_t)stream));
     k_propose<<<1, OPT_THREADS, 0, (cudaStream_t)stream>>>(o->args(), gen, 0, d_cand);
     count_launch();
     CT_TRY_CUDA(cudaGetLastError());
@@ -170,6 +191,7 @@ ct_status ct_propose_population(ct_opt* o, uint32_t gen, uint64_t* d_cand, ct_st
 
 ct_status ct_opt_post_repair(ct_opt* o, uint32_t gen, uint64_t* d_keys, ct_stream stream) {
     if (!o || !d_keys) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    CT_TRY(o->wait_ready((cudaStream_t)stream));
     k_post_repair<<<1, OPT_THREADS, 0, (cudaStream_t)stream>>>(o->args(), gen, 0, d_keys);
     count_launch();
     CT_TRY_CUDA(cudaGetLastError());
@@ -178,6 +200,7 @@ ct_status ct_opt_post_repair(ct_opt* o, uint32_t gen, uint64_t* d_keys, ct_strea
 
 ct_status ct_opt_select(ct_opt* o, uint32_t gen, const uint64_t* d_keys, const float* d_fit, ct_stream stream) {
     if (!o || !d_keys || !d_fit) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    CT_TRY(o->wait_ready((cudaStream_t)stream));
     k_select<<<1, OPT_THREADS, 0, (cudaStream_t)stream>>>(o->args(), gen, 0, d_keys, d_fit);
     count_launch();
     CT_TRY_CUDA(cudaGetLastError());
@@ -190,12 +213,14 @@ ct_status ct_evaluate(ct_space* s, ct_opt* o, const uint64_t* d_keys, int64_t n,
     if (!s->built) { set_error("space not built"); return CT_ERR_STATE; }
     if (!s->fit && d_fit) { set_error("no fitness table"); return CT_ERR_STATE; }
     if (o && o->s != s) { set_error("run belongs to another space"); return CT_ERR_INVALID_ARG; }
+    if (o) CT_TRY(o->wait_ready((cudaStream_t)stream));
     return evaluate_impl(s, o ? o->memo.p : nullptr, o ? &o->st.p->n_unique : nullptr, o ? &o->st.p->cost : nullptr,
                          d_keys, n, d_fit, d_rank, (cudaStream_t)stream);
 }
 
 ct_status ct_opt_step(ct_opt* o, uint32_t gen, ct_stream stream) {
     if (!o) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    CT_TRY(o->wait_ready((cudaStream_t)stream));
     if (o->sg) return surrogate_step(o, gen, (cudaStream_t)stream);
     return step_impl(o, gen, 0, (cudaStream_t)stream);
 }
@@ -204,6 +229,12 @@ ct_status ct_opt_run_graph(ct_opt* o, uint32_t first, uint32_t count, ct_stream 
     if (!o || count == 0) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
     if (o->sg) { set_error("runs with a surrogate advance with ct_opt_step"); return CT_ERR_STATE; }
     cudaStream_t st = (cudaStream_t)stream;
+    CT_TRY(o->wait_ready(st));
+    if (first == 0) {   // the initial generation runs eagerly (it skips the repair launches)
+        CT_TRY(step_impl(o, 0, 0, st));
+        if (--count == 0) return CT_OK;
+        first = 1;
+    }
     if (o->graph_keys != (const void*)o->s->keys.p) {   // the space was rebuilt into a new buffer
         for (auto& gx : o->graphs) cudaGraphExecDestroy(gx.second);
         o->graphs.clear();
@@ -248,6 +279,7 @@ ct_status ct_opt_best(ct_opt* o, uint64_t* best_key, float* best_fit, uint64_t* 
     if (!o) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
     OptDev h;
     cudaStream_t st = (cudaStream_t)stream;
+    CT_TRY(o->wait_ready(st));
     CT_TRY_CUDA(cudaMemcpyAsync(&h, o->st.p, sizeof h, cudaMemcpyDeviceToHost, st));
     CT_TRY_CUDA(cudaStreamSynchronize(st));
     if (best_key) *best_key = h.best_key;
@@ -262,6 +294,7 @@ ct_status ct_opt_cost(ct_opt* o, uint64_t* cost, ct_stream stream) {
     if (!o || !cost) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long h = 0;
+    CT_TRY(o->wait_ready(st));
     CT_TRY_CUDA(cudaMemcpyAsync(&h, &o->st.p->cost, sizeof h, cudaMemcpyDeviceToHost, st));
     CT_TRY_CUDA(cudaStreamSynchronize(st));
     *cost = h;
@@ -271,6 +304,7 @@ ct_status ct_opt_cost(ct_opt* o, uint64_t* cost, ct_stream stream) {
 ct_status ct_opt_state(const ct_opt* o, uint64_t* d_keys, float* d_fit, float* d_pos, ct_stream stream) {
     if (!o) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
+    CT_TRY(o->wait_ready(st));
     if (d_keys) CT_TRY_CUDA(cudaMemcpyAsync(d_keys, o->X.p, o->P * 8, cudaMemcpyDeviceToDevice, st));
     if (d_fit) CT_TRY_CUDA(cudaMemcpyAsync(d_fit, o->FX.p, o->P * 4, cudaMemcpyDeviceToDevice, st));
     if (d_pos) CT_TRY_CUDA(cudaMemcpyAsync(d_pos, o->pos.p, (size_t)o->P * o->N * 4, cudaMemcpyDeviceToDevice, st));
@@ -287,6 +321,7 @@ ct_status ct_opt_save(const ct_opt* o, void* buf, size_t* len, ct_stream stream)
     if (!buf) { *len = need; return CT_OK; }
     if (*len < need) { set_error("buffer too small (%zu < %zu)", *len, need); return CT_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
+    CT_TRY(o->wait_ready(st));
     char* p = (char*)buf;
     CkptHeader hd{0x43545054u, 1u, o->kind, o->P, o->N, 0u, o->seed, o->memo_words};
     memcpy(p, &hd, sizeof hd); p += sizeof hd;
@@ -312,6 +347,7 @@ ct_status ct_opt_load(ct_opt* o, const void* buf, size_t len, ct_stream stream) 
         return CT_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    CT_TRY(o->wait_ready(st));
     const char* p = (const char*)buf + sizeof hd;
     struct { void* dst; size_t bytes; } parts[] = {
         {o->st.p, sizeof(OptDev)}, {o->X.p, (size_t)o->P * 8}, {o->FX.p, (size_t)o->P * 4}, {o->fpb.p, (size_t)o->P * 4},

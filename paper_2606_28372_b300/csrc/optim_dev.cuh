@@ -660,13 +660,30 @@ struct ct_opt {
     RepairScratch rs;                             // run-owned repair scratch (fixed size: pop)
     ct::RuleScratch rules;                        // paper's repair rules (repair_rule = 1)
     ct::SurrogateState* sg = nullptr;             // MLP surrogate screening (DE, GA), or none
+    // The device state is initialised asynchronously on the legacy default stream at creation;
+    // `ready` is recorded after it, and the first use on another stream waits for it.
+    cudaEvent_t ready = nullptr;
+    mutable cudaStream_t ready_on = nullptr;      // the stream that last waited for `ready`
+    mutable bool ready_seen = false;
     ~ct_opt() {
+        if (ready) cudaEventDestroy(ready);
         ct::surrogate_free(sg);
         rules.release_all();
         for (auto& g : graphs) cudaGraphExecDestroy(g.second);
         st.release(); X.release(); cand.release(); rep.release(); FX.release(); pos.release(); vel.release();
         pb.release(); fpb.release(); gb.release(); ynew.release(); fit.release(); memo.release();
         rs.release_all();
+    }
+    // Orders stream st after the run's initialisation (a no-op once st has waited).
+    ct_status wait_ready(cudaStream_t st) const {
+        if (ready_seen && ready_on == st) return CT_OK;
+        if (cudaStreamWaitEvent(st, ready, 0) != cudaSuccess) {
+            ct::set_error("waiting for the run's initialisation failed");
+            return CT_ERR_CUDA;
+        }
+        ready_seen = true;
+        ready_on = st;
+        return CT_OK;
     }
     OptArgs args() const {
         OptArgs a;

@@ -259,8 +259,9 @@ __device__ __forceinline__ uint32_t block_word(const DevSpace* __restrict__ sp, 
 __global__ void __launch_bounds__(EXP_THREADS)
 k_expand_count(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
                const uint32_t* __restrict__ innerkey, int j, const uint64_t* __restrict__ parents,
-               uint64_t n_items, uint32_t* __restrict__ tile_counts) {
+               uint64_t n_items, const unsigned long long* __restrict__ Fd, uint32_t* __restrict__ tile_counts) {
     const DevBlock& bl = sp->blocks[j];
+    if (Fd) n_items = *Fd * (uint64_t)bl.W;   // launched for an upper bound: the level's own size
     const uint32_t* ik = innerkey + bl.innerkey_off;
     const uint64_t t0 = (uint64_t)blockIdx.x * EXP_TILE;
     uint32_t cnt = 0;
@@ -283,40 +284,76 @@ k_expand_count(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tab
     }
 }
 
-// exclusive scan of n tile counts into bases (one CTA; contiguous segments per thread)
-__global__ void __launch_bounds__(1024)
+// Exclusive scan of n tile counts into bases, and their sum into *total (one CTA of 1024
+// threads).  Chunks of 8K counts are staged in shared memory with coalesced loads; each thread
+// sums 8 contiguous counts, the thread sums are scanned with warp shuffles, and the bases go
+// back through shared memory with coalesced stores; the running total carries between chunks.
+constexpr int SCAN_T = 1024, SCAN_PER = 8, SCAN_CH = SCAN_T * SCAN_PER;
+__global__ void __launch_bounds__(SCAN_T)
 k_scan_tiles(const uint32_t* __restrict__ counts, uint64_t n, unsigned long long* __restrict__ base,
              unsigned long long* __restrict__ total) {
-    __shared__ unsigned long long part[1024];
-    const uint64_t seg = (n + 1023) / 1024;
-    const uint64_t b = threadIdx.x * seg, e = min(n, b + seg);
-    unsigned long long s = 0;
-    for (uint64_t i = b; i < e; ++i) s += counts[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {   // Hillis-Steele inclusive scan of the 1024 sums
-        unsigned long long v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0ull;
+    __shared__ __align__(16) uint32_t cs[SCAN_CH + SCAN_CH / 32];   // padded: a thread's 8 counts in distinct banks
+    __shared__ unsigned long long wsum[SCAN_T / 32];
+    __shared__ unsigned long long carry_s;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    auto at = [](int i) { return i + (i >> 5); };
+    unsigned long long carry = 0;
+    for (uint64_t c0 = 0; c0 < n; c0 += SCAN_CH) {
+        const int m = (int)min((uint64_t)SCAN_CH, n - c0);
+        for (int i = t; i < SCAN_CH; i += SCAN_T) cs[at(i)] = i < m ? __ldg(counts + c0 + i) : 0u;
         __syncthreads();
-        part[threadIdx.x] += v;
+        uint32_t v[SCAN_PER];
+        unsigned long long sum = 0;
+#pragma unroll
+        for (int q = 0; q < SCAN_PER; ++q) { v[q] = cs[at(t * SCAN_PER + q)]; sum += v[q]; }
+        unsigned long long inc = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) wsum[warp] = inc;
         __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = wsum[lane], wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long u = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += u;
+            }
+            wsum[lane] = wi - w;   // exclusive warp bases
+            if (lane == 31) carry_s = wi;
+        }
+        __syncthreads();
+        unsigned long long run = carry + wsum[warp] + inc - sum;
+        // bases back into shared memory (as 64-bit, in two halves of the chunk), then out coalesced
+        unsigned long long* bs = reinterpret_cast<unsigned long long*>(cs);
+        __syncthreads();
+        for (int h = 0; h < 2; ++h) {
+            const int lo = h * (SCAN_CH / 2);
+            if (t * SCAN_PER >= lo && t * SCAN_PER < lo + SCAN_CH / 2) {
+#pragma unroll
+                for (int q = 0; q < SCAN_PER; ++q) { bs[t * SCAN_PER + q - lo] = run; run += v[q]; }
+            }
+            __syncthreads();
+            for (int i = t; i < SCAN_CH / 2; i += SCAN_T)
+                if (lo + i < m) base[c0 + lo + i] = bs[i];
+            __syncthreads();
+        }
+        carry += carry_s;
     }
-    unsigned long long run = part[threadIdx.x] - s;
-    for (uint64_t i = b; i < e; ++i) {
-        base[i] = run;
-        run += counts[i];
-    }
-    if (threadIdx.x == 1023) *total = part[1023];
+    if (t == 0) *total = carry;
 }
 
 __global__ void __launch_bounds__(EXP_THREADS)
 k_expand_emit(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
               const uint32_t* __restrict__ innerkey, int j, const uint64_t* __restrict__ parents,
-              uint64_t n_items, const unsigned long long* __restrict__ tile_base,
-              const unsigned long long* __restrict__ total, unsigned long long expect, uint64_t* __restrict__ out) {
+              uint64_t n_items, const unsigned long long* __restrict__ Fd,
+              const unsigned long long* __restrict__ tile_base, const unsigned long long* __restrict__ total,
+              unsigned long long expect, uint64_t* __restrict__ out) {
     extern __shared__ uint64_t stage[];                // EXP_THREADS * 32 keys
     __shared__ uint32_t wsum[EXP_THREADS / 32];
     if (expect != ~0ull && *total != expect) return;   // launched for another level size: write nothing
     const DevBlock& bl = sp->blocks[j];
+    if (Fd) n_items = *Fd * (uint64_t)bl.W;             // launched for an upper bound: the level's own size
     const uint32_t* ik = innerkey + bl.innerkey_off;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t base = tile_base[blockIdx.x];
@@ -443,32 +480,47 @@ __device__ __forceinline__ uint32_t sig_of(const PatArgs& pa, uint64_t parent) {
     return sg;
 }
 
+// Counts of the pattern emit's tiles: a CTA covers PE_THREADS consecutive parents, which are
+// PE_THREADS / pt tiles of pt parents (pt a power of two from 8 to PE_THREADS).
 __global__ void __launch_bounds__(PE_THREADS)
-k_pcount(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents, uint64_t F, uint32_t pt,
-         uint32_t* __restrict__ tile_counts) {
-    const uint64_t i = (uint64_t)blockIdx.x * pt + threadIdx.x;
+k_pcount(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents, uint64_t F,
+         const unsigned long long* __restrict__ Fd, uint32_t pt, uint32_t* __restrict__ tile_counts) {
+    if (Fd) F = *Fd;   // launched for an upper bound: the level's own size
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint64_t i = (uint64_t)blockIdx.x * PE_THREADS + t;
     uint32_t c = 0;
-    if (threadIdx.x < pt && i < F) c = __ldg(pa.cnt + sig_of(pa, parents ? __ldg(parents + i) : 0ull));
+    if (i < F) c = __ldg(pa.cnt + sig_of(pa, parents ? __ldg(parents + i) : 0ull));
+    const uint64_t tile0 = (uint64_t)blockIdx.x * (PE_THREADS / pt);
+    if (pt <= 32) {   // a tile is pt aligned lanes of one warp
+        for (uint32_t o = 1; o < pt; o <<= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if ((lane & (pt - 1)) == 0) tile_counts[tile0 + t / pt] = c;
+        return;
+    }
     __shared__ uint32_t ws[PE_THREADS / 32];
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    if (lane == 0) ws[warp] = c;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t s = 0;
-        for (int w = 0; w < PE_THREADS / 32; ++w) s += ws[w];
-        tile_counts[blockIdx.x] = s;
+    const int wpt = (int)(pt / 32);   // warps per tile
+    if (t < PE_THREADS / (int)pt) {
+        uint32_t sum = 0;
+        for (int w = 0; w < wpt; ++w) sum += ws[t * wpt + w];
+        tile_counts[tile0 + t] = sum;
     }
 }
 
 __global__ void __launch_bounds__(PE_THREADS)
-k_pemit(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents, uint64_t F, uint32_t pt,
-        const unsigned long long* __restrict__ tile_base, const unsigned long long* __restrict__ total,
-        unsigned long long expect, uint64_t* __restrict__ out) {
+k_pemit(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents, uint64_t F,
+        const unsigned long long* __restrict__ Fd, uint32_t pt, const unsigned long long* __restrict__ tile_base,
+        const unsigned long long* __restrict__ total, unsigned long long expect, uint64_t* __restrict__ out) {
     __shared__ uint32_t off_s[PE_THREADS], cnt_s[PE_THREADS], sig_s[PE_THREADS];
     __shared__ uint64_t par_s[PE_THREADS];
     __shared__ uint32_t wsum[PE_THREADS / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint64_t i0 = (uint64_t)blockIdx.x * pt;
+    if (Fd) {   // launched for an upper bound: the level's own size
+        F = *Fd;
+        if (i0 >= F) return;
+    }
     const uint64_t i = i0 + t;
     uint32_t c = 0, sg = 0;
     uint64_t parent = 0;
@@ -1104,89 +1156,124 @@ ct_status ct_unpack_keys_device(const ct_space* s, const uint64_t* d_keys, int64
     return CT_OK;
 }
 
+// Largest upper bound of a level's size (in keys) for which a first build allocates the level's
+// frontier by that bound and launches the level without reading its size back.
+constexpr uint64_t FRONTIER_BOUND_MAX = 1ull << 25;   // 256 MB of keys
+
 // One pass over the levels: per level the count kernel, the scan of the tile counts (the level's
 // size into d_total[j]) and the emit.  The emit's grid and the next level's need the level's size
-// on the host.  Per-level mode reads it back after each scan.  Hinted mode takes it from the last
-// build of this space instead (a space's definition never changes, so its levels have the same
-// sizes every time) and launches every level without waiting; each emit compares the hint with
-// its level's total on the device and writes nothing if they differ, and the host checks all
-// totals once at the end (*ok = false: a size differed, the pass is void).
+// on the host.
+// - Hinted mode takes the sizes from the last build of this space (a space's definition never
+//   changes, so its levels have the same sizes every time) and launches every level without
+//   waiting; each emit compares the hint with its level's total on the device and writes nothing
+//   if they differ, and the host checks all totals once at the end (*ok = false: a size
+//   differed, the pass is void).
+// - A first build reads a level's size back only where the host needs it: before the last level
+//   (whose grids are sized by its exact parent count) and after it (|V|), or where a level's
+//   Cartesian upper bound exceeds FRONTIER_BOUND_MAX.  Other levels run on that upper bound:
+//   their frontier buffer and grids are sized by it and their kernels read the exact parent count
+//   from the previous level's total on the device.
 static ct_status build_levels(ct_space* s, cudaStream_t st, bool hinted, bool* ok) {
     const DevSpace& h = s->h;
     const uint64_t* parents = nullptr;
-    uint64_t F = 1;
+    uint64_t F = 1;          // parents of the level: exact when `known`, else an upper bound
+    bool known = true;
     *ok = true;
     const float setup_ms = s->stats.host_setup_ms;
     memset(&s->stats, 0, sizeof s->stats);
     s->stats.timed = s->timing;
     s->stats.host_setup_ms = setup_ms;
     CT_TRY(s->d_total.ensure((size_t)h.n_blocks));
+    s->h_totals.resize((size_t)h.n_blocks);
     const int n_hint = (int)s->hint.size();
+    int L = h.n_blocks;      // levels launched
     for (int j = 0; j < h.n_blocks; ++j) {
         const DevBlock& bl = h.blocks[j];
+        const bool last = j == h.n_blocks - 1;
         const uint64_t items = bl.pattern ? F : F * (uint64_t)bl.W;
         const uint64_t per_tile = bl.pattern ? pattern_tile(F) : EXP_TILE;
         const uint64_t tiles = (items + per_tile - 1) / per_tile;
-        if (tiles > 0x7fffffffull) { set_error("level %d needs %llu tiles", j, (unsigned long long)tiles); return CT_ERR_LIMIT; }
-        CT_TRY(s->tile_counts.ensure(tiles));
+        const uint64_t count_ctas = bl.pattern ? (F + PE_THREADS - 1) / PE_THREADS : tiles;
+        if (tiles > 0x7fffffffull || count_ctas > 0x7fffffffull) {
+            set_error("level %d needs %llu tiles", j, (unsigned long long)tiles);
+            return CT_ERR_LIMIT;
+        }
+        CT_TRY(s->tile_counts.ensure(bl.pattern ? count_ctas * (PE_THREADS / per_tile) : tiles));
         CT_TRY(s->tile_base.ensure(tiles));
+        const unsigned long long* Fd = known ? nullptr : s->d_total.p + (j - 1);
         PatArgs pa;
         if (bl.pattern) pa = pat_args(s, j);
         if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j], st));
         if (bl.pattern)
-            k_pcount<<<(unsigned)tiles, PE_THREADS, 0, st>>>(pa, parents, F, (uint32_t)per_tile, s->tile_counts.p);
+            k_pcount<<<(unsigned)count_ctas, PE_THREADS, 0, st>>>(pa, parents, F, Fd, (uint32_t)per_tile,
+                                                                  s->tile_counts.p);
         else
             k_expand_count<<<(unsigned)tiles, EXP_THREADS, 0, st>>>(s->d, s->tables.p, s->innerkey.p, j, parents,
-                                                                   items, s->tile_counts.p);
+                                                                   items, Fd, s->tile_counts.p);
         if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j + 1], st));
         unsigned long long* total = s->d_total.p + j;
-        k_scan_tiles<<<1, 1024, 0, st>>>(s->tile_counts.p, tiles, s->tile_base.p, total);
+        k_scan_tiles<<<1, SCAN_T, 0, st>>>(s->tile_counts.p, tiles, s->tile_base.p, total);
         count_launch(2);
         uint64_t Fn;
+        bool known_next = true;
+        const uint64_t bound = F * (uint64_t)bl.B;   // Cartesian bound of the level's size
         if (hinted) {
             Fn = j < n_hint ? s->hint[j] : 0;
-        } else {
-            CT_TRY_CUDA(cudaMemcpyAsync(&s->h_total, total, 8, cudaMemcpyDeviceToHost, st));
+        } else if (last || j + 1 == h.n_blocks - 1 || bound > FRONTIER_BOUND_MAX || bound / (uint64_t)bl.B != F) {
+            // every total so far in one read (the unread levels' sizes for the statistics)
+            CT_TRY_CUDA(cudaMemcpyAsync(s->h_totals.data(), s->d_total.p, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, st));
             CT_TRY_CUDA(cudaStreamSynchronize(st));
-            Fn = s->h_total;
+            Fn = s->h_totals[j];
+        } else {
+            Fn = bound;
+            known_next = false;
         }
-        DevBuf<uint64_t>& dst = (j == h.n_blocks - 1) ? s->keys : s->frontier[j];
+        DevBuf<uint64_t>& dst = last ? s->keys : s->frontier[j];
         CT_TRY(dst.ensure(Fn));
         if (Fn) {
             const unsigned long long expect = hinted ? (unsigned long long)Fn : ~0ull;
             if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j + 2], st));
             if (bl.pattern)
-                k_pemit<<<(unsigned)tiles, PE_THREADS, 0, st>>>(pa, parents, F, (uint32_t)per_tile, s->tile_base.p,
+                k_pemit<<<(unsigned)tiles, PE_THREADS, 0, st>>>(pa, parents, F, Fd, (uint32_t)per_tile, s->tile_base.p,
                                                                 total, expect, dst.p);
             else
                 k_expand_emit<<<(unsigned)tiles, EXP_THREADS, EXP_THREADS * 32 * sizeof(uint64_t), st>>>(
-                    s->d, s->tables.p, s->innerkey.p, j, parents, items, s->tile_base.p, total, expect, dst.p);
+                    s->d, s->tables.p, s->innerkey.p, j, parents, items, Fd, s->tile_base.p, total, expect, dst.p);
             if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j + 3], st));
             count_launch();
             CT_TRY_CUDA(cudaGetLastError());
         }
-        s->stats.n_levels = j + 1;
         s->stats.parents[j] = F;
         s->stats.children[j] = Fn;
         parents = dst.p;
         F = Fn;
-        if (F == 0) break;
-        if (j == h.n_blocks - 1) {   // the host plans the ball tables while the last level is emitted
+        known = known_next;
+        if (known && F == 0) { L = j + 1; break; }
+        if (last) {   // the host plans the ball tables while the last level is emitted
             s->n_valid = F;
             plan_balls(s, wanted_radius(s));
-            CT_TRY(upload_balls(s, st, false));   // queued behind the emit; the sync below covers it
+            CT_TRY(upload_balls(s, st, false));   // queued behind the emit
         }
     }
-    const int L = s->stats.n_levels;
-    if (hinted) {
-        s->h_totals.resize((size_t)L);
+    if (hinted) {   // the levels ran on the hints: read every level's own size back and compare
         CT_TRY_CUDA(cudaMemcpyAsync(s->h_totals.data(), s->d_total.p, (size_t)L * 8, cudaMemcpyDeviceToHost, st));
-    }
-    CT_TRY_CUDA(cudaStreamSynchronize(st));
-    if (hinted)
+        CT_TRY_CUDA(cudaStreamSynchronize(st));
         for (int j = 0; j < L; ++j)
             if (s->h_totals[j] != (unsigned long long)s->stats.children[j]) *ok = false;
-    s->n_valid = F;
+    } else {
+        // levels launched on bounds: their exact sizes came back with the last read.  A level that
+        // came out empty ends the statistics there (the levels after it ran on no parents).
+        for (int j = 0; j < L; ++j) {
+            s->stats.children[j] = s->h_totals[j];
+            s->stats.parents[j] = j ? s->h_totals[j - 1] : 1;
+            if (s->h_totals[j] == 0) { L = j + 1; break; }
+        }
+    }
+    s->stats.n_levels = L;
+    // Level by level, every size was read back before it was needed: nothing is left to check, so
+    // the call returns while the last level's emit (and the ball-table upload behind it) still
+    // run; every later use of the keys is ordered after them on the stream.
+    s->n_valid = s->stats.children[L - 1];
     return CT_OK;
 }
 
@@ -1204,7 +1291,8 @@ static bool hint_fits(const ct_space* s) {
         const uint64_t items = bl.pattern ? F : F * (uint64_t)bl.W;
         const uint64_t per_tile = bl.pattern ? pattern_tile(F) : EXP_TILE;
         const uint64_t tiles = (items + per_tile - 1) / per_tile;
-        if (tiles > s->tile_counts.cap || tiles > s->tile_base.cap) return false;
+        const uint64_t counts = bl.pattern ? (F + PE_THREADS - 1) / PE_THREADS * (PE_THREADS / per_tile) : tiles;
+        if (counts > s->tile_counts.cap || tiles > s->tile_base.cap) return false;
         const uint64_t Fn = s->hint[j];
         const DevBuf<uint64_t>& dst = (j == h.n_blocks - 1) ? s->keys : s->frontier[j];
         if (!dst.p || Fn > dst.cap) return false;
@@ -1257,12 +1345,6 @@ ct_status ct_build_valid_space(ct_space* s, ct_stream stream, uint64_t* n_valid_
     }
     s->hint.assign(s->stats.children, s->stats.children + s->stats.n_levels);
     s->stats.hinted = hinted ? 1 : 0;
-    if (s->timing)
-        for (int j = 0; j < s->stats.n_levels; ++j) {
-            CT_TRY_CUDA(cudaEventElapsedTime(&s->stats.count_ms[j], s->events[4 * j], s->events[4 * j + 1]));
-            if (s->stats.children[j])
-                CT_TRY_CUDA(cudaEventElapsedTime(&s->stats.emit_ms[j], s->events[4 * j + 2], s->events[4 * j + 3]));
-        }
     const uint64_t F = s->n_valid;
     s->built = true;
     if (n_valid_out) *n_valid_out = F;
@@ -1284,6 +1366,15 @@ ct_status ct_space_set_timing(ct_space* s, int32_t enable) {
 ct_status ct_space_build_stats(const ct_space* s, ct_build_stats* out) {
     if (!s || !out) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
     *out = s->stats;
+    if (s->stats.timed && s->built) {   // the kernel times, once the build's last event has completed
+        const int L = s->stats.n_levels;
+        CT_TRY_CUDA(cudaEventSynchronize(s->events[4 * (L - 1) + (s->stats.children[L - 1] ? 3 : 1)]));
+        for (int j = 0; j < L; ++j) {
+            CT_TRY_CUDA(cudaEventElapsedTime(&out->count_ms[j], s->events[4 * j], s->events[4 * j + 1]));
+            if (s->stats.children[j])
+                CT_TRY_CUDA(cudaEventElapsedTime(&out->emit_ms[j], s->events[4 * j + 2], s->events[4 * j + 3]));
+        }
+    }
     return CT_OK;
 }
 

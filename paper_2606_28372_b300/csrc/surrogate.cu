@@ -622,6 +622,7 @@ ct_status ct_opt_last_generation(const ct_opt* o, uint64_t* d_cand, uint64_t* d_
                                  ct_stream stream) {
     if (!o) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
+    CT_TRY(o->wait_ready(st));
     const size_t P = o->P;
     const uint64_t* ev = o->sg ? o->sg->evk_chosen.p : o->rep.p;
     if (d_cand) CT_TRY_CUDA(cudaMemcpyAsync(d_cand, o->cand.p, P * 8, cudaMemcpyDeviceToDevice, st));
