@@ -311,12 +311,16 @@ ct_status ct_opt_post_repair(ct_opt *opt, uint32_t generation, uint64_t *d_keys,
  * the run's best (minimum (fitness, key) over everything evaluated). */
 ct_status ct_opt_select(ct_opt *opt, uint32_t generation, const uint64_t *d_keys, const float *d_fit,
                         ct_stream stream);
-/* The whole generation with run-owned buffers. */
+/* The whole generation with run-owned buffers.  The first two calls of a run
+ * launch kernel by kernel; later ones (generation > 0, on a stream that is not
+ * being captured) replay a cached one-generation CUDA graph, with the same
+ * result and far fewer launches. */
 ct_status ct_opt_step(ct_opt *opt, uint32_t generation, ct_stream stream);
 /* Runs generations [first, first + count) as one CUDA graph (captured on the
  * first call for this count, replayed afterwards).  Generation 0, when included,
  * runs eagerly before the graph: its sample is valid by construction, so it
- * skips the repair launches. */
+ * skips the repair launches.  A run's graphs are captured again when the space's
+ * keys, fitness or cost table, or repair strategy change. */
 ct_status ct_opt_run_graph(ct_opt *opt, uint32_t first, uint32_t count, ct_stream stream);
 
 /* Run summary (synchronises): best key and fitness so far, unique evaluations,

@@ -7,8 +7,9 @@
 // then a scan of the space's keys for what is left), GA mutation, memoised
 // evaluation and selection.  The per-run arithmetic is the same device code as
 // the single-run kernels, so every batched run equals the same run done alone.
-// A generation is two launches (the persistent kernel and a one-thread advance
-// of the generation counter), so G generations replay as one CUDA graph.
+// A generation is one launch: the kernel's last CTA to finish advances the
+// generation counter and resets the work list, so G generations replay as one
+// CUDA graph of G kernel nodes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -82,7 +83,8 @@ struct BatchArgs {
     float* ynew;
     uint32_t* memo;
     uint32_t* work;
-    const uint32_t* gen;
+    uint32_t* gen;                      // the generation (advanced by the launch's last CTA)
+    uint32_t* done;                     // CTAs finished in this launch (the last one resets it)
     float* tr_fit;                      // per-generation trace [run][generation], or null
     unsigned long long* tr_cost;
     unsigned long long* tr_unique;
@@ -423,12 +425,21 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 2) k_batch_gen(const __grid
             }
         }
     }
+    // The last CTA to finish advances the generation and resets the work list for the next
+    // launch: every CTA has read the generation at its start and left the work loop by then.
+    __shared__ bool last_s;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last_s = atomicAdd(ba.done, 1u) == gridDim.x - 1;
+        if (last_s) {
+            *ba.gen = gen + 1;
+            *ba.work = 0;
+            *ba.done = 0;
+            __threadfence();
+        }
+    }
 }
 
-__global__ void k_batch_advance(uint32_t* gen, uint32_t* work) {
-    *gen += 1;
-    *work = 0;
-}
 
 }  // namespace ct
 
@@ -444,7 +455,7 @@ struct ct_batch {
     DevBuf<OptDev> st;
     DevBuf<uint64_t> X;
     DevBuf<float> FX, pos, vel, pb, fpb, gb, ynew;
-    DevBuf<uint32_t> memo, ctr;   // ctr[0] = generation, ctr[1] = work counter
+    DevBuf<uint32_t> memo, ctr;   // ctr[0] = generation, ctr[1] = work counter, ctr[2] = CTAs done
     DevBuf<uint32_t> scan_tags;   // table scan: per CTA of the largest grid, BATCH_LUT_CHUNK x threads
     size_t lut_bytes = 0;         // dynamic shared memory of the table scan (largest plan, four sets)
     DevBuf<float> tr_fit;
@@ -471,7 +482,7 @@ struct ct_batch {
         BatchArgs a;
         a.spaces = d_spaces.p; a.runs = d_runs.p; a.order = d_order.p; a.n_runs = (int)runs_h.size(); a.prm = prm;
         a.st = st.p; a.X = X.p; a.FX = FX.p; a.pos = pos.p; a.vel = vel.p; a.pb = pb.p; a.fpb = fpb.p; a.gb = gb.p;
-        a.ynew = ynew.p; a.memo = memo.p; a.work = ctr.p + 1; a.gen = ctr.p;
+        a.ynew = ynew.p; a.memo = memo.p; a.work = ctr.p + 1; a.gen = ctr.p; a.done = ctr.p + 2;
         a.tr_fit = tr_fit.p; a.tr_cost = tr_cost.p; a.tr_unique = tr_unique.p; a.tr_gens = tr_gens;
         a.ev_cap = ev_cap; a.ev_count = ev_count.p; a.ev_gen = ev_gen.p; a.ev_idx = ev_idx.p;
         a.ev_clock = ev_clock.p; a.ev_fit = ev_fit.p;
@@ -492,8 +503,7 @@ static ct_status batch_launch(ct_batch* b, cudaStream_t st) {
                              (int)cudaSharedmemCarveoutMaxShared);
     });
     k_batch_gen<<<b->grid(), b->threads, b->lut_bytes, st>>>(b->args());
-    k_batch_advance<<<1, 1, 0, st>>>(b->ctr.p, b->ctr.p + 1);
-    count_launch(2);
+    count_launch();
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -518,7 +528,7 @@ static ct_status batch_reset(ct_batch* b) {
     CT_TRY_CUDA(cudaMemset(b->pb.p, 0, b->n_pn * 4));
     CT_TRY_CUDA(cudaMemset(b->ynew.p, 0, b->n_pn * 4));
     CT_TRY_CUDA(cudaMemset(b->gb.p, 0, b->n_n * 4));
-    CT_TRY_CUDA(cudaMemset(b->ctr.p, 0, 8));
+    CT_TRY_CUDA(cudaMemset(b->ctr.p, 0, 12));
     if (b->tr_gens) {
         const size_t n = R * b->tr_gens;
         std::vector<float> inf(n, __builtin_inff());
@@ -637,7 +647,7 @@ ct_status ct_batch_create(ct_space* const* spaces, int32_t n_spaces, const ct_ba
 #define ALLOC(b, n) if (e == CT_OK) e = bt->b.ensure(n)
     ALLOC(d_spaces, n_spaces); ALLOC(d_runs, n_runs); ALLOC(d_order, n_runs); ALLOC(st, n_runs);
     ALLOC(X, bt->n_pop); ALLOC(FX, bt->n_pop); ALLOC(fpb, bt->n_pop); ALLOC(pos, bt->n_pn); ALLOC(vel, bt->n_pn);
-    ALLOC(pb, bt->n_pn); ALLOC(ynew, bt->n_pn); ALLOC(gb, bt->n_n); ALLOC(memo, bt->n_memo); ALLOC(ctr, 2);
+    ALLOC(pb, bt->n_pn); ALLOC(ynew, bt->n_pn); ALLOC(gb, bt->n_n); ALLOC(memo, bt->n_memo); ALLOC(ctr, 3);
 #undef ALLOC
     if (e == CT_OK && (cudaMemcpy(bt->d_spaces.p, bsp.data(), n_spaces * sizeof(BatchSpace), cudaMemcpyHostToDevice) != cudaSuccess ||
                        cudaMemcpy(bt->d_runs.p, bt->brun.data(), n_runs * sizeof(BatchRun), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -728,7 +738,7 @@ ct_status ct_batch_run_graph(ct_batch* b, uint32_t count, ct_stream stream) {
         it = b->graphs.emplace(count, ex).first;
     }
     CT_TRY_CUDA(cudaGraphLaunch(it->second, st));
-    count_launch(2ull * count);
+    count_launch(count);
     b->generation += count;
     return CT_OK;
 }

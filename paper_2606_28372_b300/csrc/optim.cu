@@ -91,13 +91,16 @@ static ct_status step_impl(ct_opt* o, uint32_t gen, int use_dev, cudaStream_t st
     } else {
         CT_TRY(repair_step(o, a, gen, use_dev, st));
     }
-    k_post_repair<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->rep.p);
-    count_launch();
+    if (o->kind == CT_GA && (use_dev || gen > 0)) {   // GA mutation; a no-op for the other kinds
+        k_post_repair<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->rep.p);
+        count_launch();
+    }
     CT_TRY(evaluate_impl(o->s, o->memo.p, &o->st.p->n_unique, &o->st.p->cost, o->rep.p, o->P, o->fit.p, nullptr, st,
                          CT_PENALTY));
     k_select<<<1, OPT_THREADS, 0, st>>>(a, gen, use_dev, o->rep.p, o->fit.p);
     count_launch();
     CT_TRY_CUDA(cudaGetLastError());
+    if (!use_dev) o->dev_gen = gen + 1;   // select advances the device's generation
     return CT_OK;
 }
 }  // namespace ct
@@ -204,6 +207,7 @@ ct_status ct_opt_select(ct_opt* o, uint32_t gen, const uint64_t* d_keys, const f
     k_select<<<1, OPT_THREADS, 0, (cudaStream_t)stream>>>(o->args(), gen, 0, d_keys, d_fit);
     count_launch();
     CT_TRY_CUDA(cudaGetLastError());
+    o->dev_gen = gen + 1;
     return CT_OK;
 }
 
@@ -218,31 +222,26 @@ ct_status ct_evaluate(ct_space* s, ct_opt* o, const uint64_t* d_keys, int64_t n,
                          d_keys, n, d_fit, d_rank, (cudaStream_t)stream);
 }
 
-ct_status ct_opt_step(ct_opt* o, uint32_t gen, ct_stream stream) {
-    if (!o) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
-    CT_TRY(o->wait_ready((cudaStream_t)stream));
-    if (o->sg) return surrogate_step(o, gen, (cudaStream_t)stream);
-    return step_impl(o, gen, 0, (cudaStream_t)stream);
-}
-
-ct_status ct_opt_run_graph(ct_opt* o, uint32_t first, uint32_t count, ct_stream stream) {
-    if (!o || count == 0) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
-    if (o->sg) { set_error("runs with a surrogate advance with ct_opt_step"); return CT_ERR_STATE; }
-    cudaStream_t st = (cudaStream_t)stream;
-    CT_TRY(o->wait_ready(st));
+// Generations [first, first + count) as one cached CUDA graph (generation read on the device).
+static ct_status run_graph_impl(ct_opt* o, uint32_t first, uint32_t count, cudaStream_t st) {
     if (first == 0) {   // the initial generation runs eagerly (it skips the repair launches)
         CT_TRY(step_impl(o, 0, 0, st));
         if (--count == 0) return CT_OK;
         first = 1;
     }
-    if (o->graph_keys != (const void*)o->s->keys.p) {   // the space was rebuilt into a new buffer
+    const ct_space* s = o->s;
+    ct_opt::GraphSig sig;
+    sig.keys = s->keys.p; sig.fit = s->fit; sig.cost = s->cost; sig.nv = s->n_valid;
+    sig.mode = s->repair_mode; sig.max_radius = s->repair_max_radius; sig.dmax = wanted_radius(s);
+    if (!(o->graph_sig == sig)) {   // the space changed under the graphs: capture again
         for (auto& gx : o->graphs) cudaGraphExecDestroy(gx.second);
         o->graphs.clear();
         o->graph_kernels.clear();
-        o->graph_keys = o->s->keys.p;
+        o->graph_sig = sig;
     }
     auto it = o->graphs.find(count);
     if (it == o->graphs.end()) {
+        CT_TRY(ensure_balls(o->s, sig.dmax));   // the ball tables the captured repair reads
         cudaStream_t cap;
         CT_TRY_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t g;
@@ -267,11 +266,39 @@ ct_status ct_opt_run_graph(ct_opt* o, uint32_t first, uint32_t count, ct_stream 
         if (ce != cudaSuccess) { set_error("instantiate failed: %s", cudaGetErrorString(ce)); return CT_ERR_CUDA; }
         it = o->graphs.emplace(count, ex).first;
     }
-    k_set_gen<<<1, 1, 0, st>>>(o->st.p, first);
-    count_launch();
+    if (o->dev_gen != first) {   // the graph reads the generation on the device
+        k_set_gen<<<1, 1, 0, st>>>(o->st.p, first);
+        count_launch();
+    }
     CT_TRY_CUDA(cudaGraphLaunch(it->second, st));
     count_launch(o->graph_kernels[count]);
+    o->dev_gen = first + count;
     return CT_OK;
+}
+
+// Eager steps after which ct_opt_step replays a cached one-generation graph instead of launching
+// kernel by kernel (a run that is stepped repeatedly; a short session captures nothing).
+constexpr uint32_t STEP_GRAPH_AFTER = 2;
+
+ct_status ct_opt_step(ct_opt* o, uint32_t gen, ct_stream stream) {
+    if (!o) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    CT_TRY(o->wait_ready(st));
+    if (o->sg) return surrogate_step(o, gen, st);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CT_TRY_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (gen > 0 && o->eager_steps >= STEP_GRAPH_AFTER && cs == cudaStreamCaptureStatusNone)
+        return run_graph_impl(o, gen, 1, st);
+    ++o->eager_steps;
+    return step_impl(o, gen, 0, st);
+}
+
+ct_status ct_opt_run_graph(ct_opt* o, uint32_t first, uint32_t count, ct_stream stream) {
+    if (!o || count == 0) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
+    if (o->sg) { set_error("runs with a surrogate advance with ct_opt_step"); return CT_ERR_STATE; }
+    cudaStream_t st = (cudaStream_t)stream;
+    CT_TRY(o->wait_ready(st));
+    return run_graph_impl(o, first, count, st);
 }
 
 ct_status ct_opt_best(ct_opt* o, uint64_t* best_key, float* best_fit, uint64_t* n_unique, int64_t* hit_generation,
@@ -356,6 +383,7 @@ ct_status ct_opt_load(ct_opt* o, const void* buf, size_t len, ct_stream stream) 
     for (auto& pt : parts) { CT_TRY_CUDA(cudaMemcpyAsync(pt.dst, p, pt.bytes, cudaMemcpyHostToDevice, st)); p += pt.bytes; }
     CT_TRY_CUDA(cudaStreamSynchronize(st));
     o->seed = hd.seed;
+    o->dev_gen = ~0u;   // the loaded state carries its own generation
     return CT_OK;
 }
 

@@ -656,7 +656,21 @@ struct ct_opt {
     size_t memo_words = 0;
     std::map<uint32_t, cudaGraphExec_t> graphs;
     std::map<uint32_t, uint64_t> graph_kernels;   // kernels per replay of each graph
-    const void* graph_keys = nullptr;             // space key buffer the graphs were captured with
+    // What the graphs captured from the space: key buffer, fitness and cost tables, |V| and the
+    // repair strategy (its ball radii).  Any change drops them.
+    struct GraphSig {
+        const void* keys = nullptr;
+        const void* fit = nullptr;
+        const void* cost = nullptr;
+        uint64_t nv = 0;
+        int mode = -1, max_radius = -1, dmax = -1;
+        bool operator==(const GraphSig& o) const {
+            return keys == o.keys && fit == o.fit && cost == o.cost && nv == o.nv && mode == o.mode &&
+                   max_radius == o.max_radius && dmax == o.dmax;
+        }
+    } graph_sig;
+    uint32_t eager_steps = 0;                     // ct_opt_step calls that launched kernel by kernel
+    uint32_t dev_gen = ~0u;                       // the generation the device state holds next (~0: unknown)
     RepairScratch rs;                             // run-owned repair scratch (fixed size: pop)
     ct::RuleScratch rules;                        // paper's repair rules (repair_rule = 1)
     ct::SurrogateState* sg = nullptr;             // MLP surrogate screening (DE, GA), or none

@@ -65,7 +65,12 @@ static bool scan_lut_plan(const ct_space* s, ScanLutPlan& pl) {
 }
 
 // Tables of one chunk: entry 256 g + x, lane l of set s = number of group g's fields in which the
-// group value x differs from candidate 8 s + l (0 for lanes past the chunk).  Stored as [entry][S].
+// group value x differs from candidate 8 s + l (0 for lanes past the chunk).  One set: [entry].
+// Two or four sets: planes of 16-byte entries (sets 2p and 2p + 1 in plane p), so that the
+// 16-byte reads of one plane by a warp spread over all eight 16-byte bank groups.
+__device__ __forceinline__ size_t sl_index(int S, int ng, int e, int s) {
+    return S == 1 ? (size_t)e : (size_t)(s >> 1) * 512 * ng + (size_t)e * 2 + (s & 1);
+}
 __device__ void sl_tables(const DevSpace* __restrict__ sp, const ScanLutPlan& pl, const uint64_t* cq, int nq,
                           int S, unsigned long long* tab) {
     for (int e = threadIdx.x; e < 256 * pl.ng; e += SL_THREADS) {
@@ -83,34 +88,30 @@ __device__ void sl_tables(const DevSpace* __restrict__ sp, const ScanLutPlan& pl
                 for (int k = pl.k0[g]; k <= pl.k1[g]; ++k) nd += (d & sp->fmask[k]) != 0;
                 word |= (unsigned long long)nd << (8 * l);
             }
-            tab[(size_t)e * S + s] = word;
+            tab[sl_index(S, pl.ng, e, s)] = word;
         }
     }
 }
 
-// Lane states and best tags of one set of eight candidates, as two 32-bit halves: the lanes never
-// carry or borrow into each other, so the halves are summed and tested independently.
-template <int NG, int S>
-__device__ __forceinline__ void sl_visit(uint64_t key, uint32_t tag, const uint32_t (&rs)[NG],
-                                         const uint32_t (&mk)[NG], const char* __restrict__ tab, uint32_t (&vl)[S],
-                                         uint32_t (&vh)[S], uint32_t* __restrict__ tg) {
-    const uint64_t kx = key << 5;
-    uint32_t a[NG];   // byte offset of the group's entry: (256 g + x) * 8 S
+// Adds the table entries of groups [G0, G1) of one key (shifted left by 5) to the sums of each
+// set of eight candidates, kept as two 32-bit halves: the lanes never carry or borrow into each
+// other, so the halves are summed and tested independently.
+template <int G0, int G1, int NG, int S>
+__device__ __forceinline__ void sl_add(uint64_t kx, const uint32_t (&rs)[NG], const uint32_t (&mk)[NG],
+                                       const char* __restrict__ tab, uint32_t (&dl)[S], uint32_t (&dh)[S]) {
+    constexpr int LGE = S == 1 ? 3 : 4;             // bytes per entry of a plane: 8 or 16
+    constexpr uint32_t PLANE = 256u * NG << LGE;    // bytes per plane
 #pragma unroll
-    for (int g = 0; g < NG; ++g) a[g] = ((uint32_t)(kx >> rs[g]) & mk[g]) | ((uint32_t)g << (11 + (S == 1 ? 0 : S == 2 ? 1 : 2)));
-    uint32_t dl[S], dh[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) dl[s] = dh[s] = 0;
-#pragma unroll
-    for (int g = 0; g < NG; ++g) {
+    for (int g = G0; g < G1; ++g) {
+        const uint32_t a = ((uint32_t)(kx >> rs[g]) & mk[g]) | ((uint32_t)g << (8 + LGE));
         if (S == 1) {
-            const uint2 w = *reinterpret_cast<const uint2*>(tab + a[g]);
+            const uint2 w = *reinterpret_cast<const uint2*>(tab + a);
             dl[0] += w.x;
             dh[0] += w.y;
         } else {
 #pragma unroll
             for (int p = 0; p < S / 2; ++p) {
-                const uint4 w = *reinterpret_cast<const uint4*>(tab + a[g] + 16 * p);
+                const uint4 w = *reinterpret_cast<const uint4*>(tab + a + p * PLANE);
                 dl[2 * p] += w.x;
                 dh[2 * p] += w.y;
                 dl[2 * p + 1] += w.z;
@@ -118,10 +119,16 @@ __device__ __forceinline__ void sl_visit(uint64_t key, uint32_t tag, const uint3
             }
         }
     }
+}
+
+// The borrow test of one key against the chunk's sets: d = the key's distances (as 8-bit lanes
+// in two 32-bit halves per set).  Lane l of v - d is 127 + best_l - d_l, in [63, 254]: no borrow
+// between lanes, and its bit 7 is set exactly when d_l < best_l; only improved lanes are updated.
+template <int S>
+__device__ __forceinline__ void sl_test(uint32_t tag, const uint32_t (&dl)[S], const uint32_t (&dh)[S],
+                                        uint32_t (&vl)[S], uint32_t (&vh)[S], uint32_t* __restrict__ tg) {
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        // lane l of v - D is 127 + best_l - D_l, in [63, 254]: no borrow between lanes, and its
-        // bit 7 is set exactly when D_l < best_l
         const uint32_t ml = (vl[s] - dl[s]) & SL_H32, mh = (vh[s] - dh[s]) & SL_H32;
         if (ml | mh) {
             const uint32_t fl = (ml >> 7) * 0xFFu, fh = (mh >> 7) * 0xFFu;
@@ -136,21 +143,52 @@ __device__ __forceinline__ void sl_visit(uint64_t key, uint32_t tag, const uint3
     }
 }
 
+// The distances of a key: the sums of its upper groups (ul, uh, refreshed when the key's upper
+// bits changed; sorted keys keep them for runs of hundreds to thousands of keys) plus its NL low
+// groups' entries.
+template <int NL, int NG, int S>
+__device__ __forceinline__ void sl_dist(uint64_t key, int ushift, uint64_t& ucur, const uint32_t (&rs)[NG],
+                                        const uint32_t (&mk)[NG], const char* __restrict__ tab, uint32_t (&ul)[S],
+                                        uint32_t (&uh)[S], uint32_t (&dl)[S], uint32_t (&dh)[S]) {
+    if (NL < NG) {
+        const uint64_t u = key >> ushift;
+        if (u != ucur) {
+            ucur = u;
+#pragma unroll
+            for (int s = 0; s < S; ++s) ul[s] = uh[s] = 0;
+            sl_add<NL, NG, NG, S>(key << 5, rs, mk, tab, ul, uh);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) { dl[s] = ul[s]; dh[s] = uh[s]; }
+    sl_add<0, NL, NG, S>(key << 5, rs, mk, tab, dl, dh);
+}
+
+// The pass over the keys for one chunk.  Each warp takes contiguous segments of SL_SEG keys
+// (segment w, w + warps, ...) as rows of 32 keys, one key per lane: a warp's loads are
+// contiguous 256-byte rows, each lane visits its keys in increasing order, and the lanes of a
+// row share their upper fields.  Only the NL lowest groups are looked up per key; within a row
+// group 1 mostly has one or two values, so its reads are mostly broadcasts.
 // tags: [8 S candidates][SL_THREADS] key tags of each thread's best keys (shared memory; written
-// only when a key improves a lane)
+// only when a key improves a lane): tag = segment iteration * rows + row.
+constexpr int SL_SEG = 2048;   // keys per warp segment (64 rows of 32)
+constexpr int SL_NL = 2;       // groups looked up for every key
 template <int NG, int S>
 __device__ void sl_pass(const uint64_t* __restrict__ keys, int64_t nv, const ScanLutPlan& pl,
                         const char* __restrict__ tab, uint32_t* __restrict__ tags, int nq,
                         unsigned long long* __restrict__ best, unsigned long long (*red)[SL_CHUNK]) {
-    constexpr int LGS = S == 1 ? 0 : S == 2 ? 1 : 2;
-    constexpr int U = S == 1 ? 4 : 2;   // key pairs in flight per thread
+    constexpr int LGE = S == 1 ? 3 : 4;
+    constexpr int NL = NG < SL_NL ? NG : SL_NL;
+    constexpr int ROWS = SL_SEG / 32;
+    constexpr int U = S == 4 ? 2 : 4;   // rows per step (their distances first, then their tests); the next
+                                        // step's rows are loaded while this one is computed
     uint32_t rs[NG], mk[NG];
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
-        rs[g] = (uint32_t)(pl.shift[g] + 2 - LGS);
-        mk[g] = pl.mask[g] << (3 + LGS);
+        rs[g] = (uint32_t)(pl.shift[g] + 5 - LGE);
+        mk[g] = pl.mask[g] << LGE;
     }
-    uint32_t vl[S], vh[S];
+    uint32_t vl[S], vh[S], ul[S], uh[S];
     uint32_t* tg = tags + threadIdx.x;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -162,51 +200,46 @@ __device__ void sl_pass(const uint64_t* __restrict__ keys, int64_t nv, const Sca
         }
         vl[s] = il;
         vh[s] = ih;
-    }
-    const int64_t stride = (int64_t)gridDim.x * SL_THREADS * 2;
-    const int64_t start = ((int64_t)blockIdx.x * SL_THREADS + threadIdx.x) * 2;
-    uint32_t it = 0;
-    int64_t i = start;
-    if (S == 1) {   // one set: no prefetch, the registers keep 4 CTAs per SM
-        for (; i + (U - 1) * stride + 1 < nv; i += U * stride, it += U) {
-            ulonglong2 kk[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) kk[u] = __ldg(reinterpret_cast<const ulonglong2*>(keys + i + u * stride));
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                sl_visit<NG, S>(kk[u].x, (it + u) << 1, rs, mk, tab, vl, vh, tg);
-                sl_visit<NG, S>(kk[u].y, ((it + u) << 1) | 1u, rs, mk, tab, vl, vh, tg);
-            }
-        }
-    } else if (i + (U - 1) * stride + 1 < nv) {   // the next group of pairs is loaded while this one is visited
-        ulonglong2 kk[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) kk[u] = __ldg(reinterpret_cast<const ulonglong2*>(keys + i + u * stride));
-        for (;;) {
-            const int64_t in = i + U * stride;
-            const bool more = in + (U - 1) * stride + 1 < nv;
-            ulonglong2 kn[U];
-            if (more) {
-#pragma unroll
-                for (int u = 0; u < U; ++u) kn[u] = __ldg(reinterpret_cast<const ulonglong2*>(keys + in + u * stride));
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                sl_visit<NG, S>(kk[u].x, (it + u) << 1, rs, mk, tab, vl, vh, tg);
-                sl_visit<NG, S>(kk[u].y, ((it + u) << 1) | 1u, rs, mk, tab, vl, vh, tg);
-            }
-            i = in;
-            it += U;
-            if (!more) break;
-#pragma unroll
-            for (int u = 0; u < U; ++u) kk[u] = kn[u];
-        }
-    }
-    for (; i < nv; i += stride, ++it) {
-        sl_visit<NG, S>(__ldg(keys + i), it << 1, rs, mk, tab, vl, vh, tg);
-        if (i + 1 < nv) sl_visit<NG, S>(__ldg(keys + i + 1), (it << 1) | 1u, rs, mk, tab, vl, vh, tg);
+        ul[s] = uh[s] = 0;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * (SL_THREADS / 32);
+    const int64_t gw = (int64_t)blockIdx.x * (SL_THREADS / 32) + warp;
+    const int ushift = NL < NG ? pl.shift[NL] : 0;
+    uint64_t ucur = ~0ull;
+    uint32_t m = 0;
+    for (int64_t s0 = gw * SL_SEG; s0 < nv; s0 += nw * SL_SEG, ++m) {
+        const int64_t base = s0 + lane;
+        if (s0 + SL_SEG <= nv) {   // a whole segment (the same for every lane of the warp)
+            uint64_t kn[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) kn[u] = __ldg(keys + base + (int64_t)u * 32);
+#pragma unroll 1
+            for (int j = 0; j < ROWS; j += U) {
+                uint64_t kk[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) kk[u] = kn[u];
+                if (j + U < ROWS) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) kn[u] = __ldg(keys + base + (int64_t)(j + U + u) * 32);
+                }
+                uint32_t dl[U][S], dh[U][S];
+#pragma unroll
+                for (int u = 0; u < U; ++u) sl_dist<NL, NG, S>(kk[u], ushift, ucur, rs, mk, tab, ul, uh, dl[u], dh[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) sl_test<S>(m * ROWS + (uint32_t)(j + u), dl[u], dh[u], vl, vh, tg);
+            }
+        } else {                   // the last, partial segment
+            for (int j = 0; j < ROWS; ++j) {
+                const int64_t i = base + (int64_t)j * 32;
+                if (i < nv) {
+                    uint32_t dl[S], dh[S];
+                    sl_dist<NL, NG, S>(__ldg(keys + i), ushift, ucur, rs, mk, tab, ul, uh, dl, dh);
+                    sl_test<S>(m * ROWS + (uint32_t)j, dl, dh, vl, vh, tg);
+                }
+            }
+        }
+    }
 #pragma unroll
     for (int s = 0; s < S; ++s) {
 #pragma unroll
@@ -216,7 +249,7 @@ __device__ void sl_pass(const uint64_t* __restrict__ keys, int64_t nv, const Sca
             if (8 * s + l < nq && lv < 254u) {   // the lane improved at least once: its tag is set
                 const uint64_t d = lv - 127u;
                 const uint32_t t = tg[(8 * s + l) * SL_THREADS];
-                const int64_t idx = start + (int64_t)(t >> 1) * stride + (t & 1u);
+                const int64_t idx = (gw + (int64_t)(t / ROWS) * nw) * SL_SEG + (int64_t)(t % ROWS) * 32 + lane;
                 x = (d << 57) | (unsigned long long)idx;
             }
 #pragma unroll

@@ -26,6 +26,7 @@ namespace ct {
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_CHUNK = 32;        // candidates per CTA of the scan
 constexpr unsigned long long NONE = ~0ull;
+constexpr int64_t SCAN_FOLD_MAX = 4096;   // repairs of up to this many candidates resolve in the last scan CTA
 
 // a warp per candidate (the warp's 32-ary rank search)
 __global__ void k_lookup(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, int64_t nv,
@@ -282,6 +283,40 @@ __device__ __forceinline__ void scan_run(const uint64_t* __restrict__ keys, int6
     }
 }
 
+// The resolve step of the exhaustive scan, run by the last CTA of the last scan kernel to finish
+// (an atomic ticket after a fence; nothing waits): each pending candidate takes the key of its
+// packed (distance << 57 | rank) minimum.  done = null: k_scan_resolve does it instead (many
+// pending candidates, which one CTA would resolve slowly).
+struct ScanNext {
+    uint32_t* done;                 // CTAs finished (zero before the launch; the last CTA resets it)
+    const uint64_t* keys;
+    uint64_t* out;
+    uint8_t* dist;
+};
+
+__device__ __forceinline__ void scan_resolve_last(const ScanNext& nx, const int32_t* __restrict__ pend,
+                                                  const uint32_t* __restrict__ count,
+                                                  const unsigned long long* __restrict__ best) {
+    if (!nx.done) return;
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();   // this CTA's atomics on best before its ticket
+        last = atomicAdd(nx.done, 1u) == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const uint32_t cnt = *count;
+    for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const unsigned long long b = __ldcg(best + q);
+        const int32_t i = pend[q];
+        nx.out[i] = __ldg(nx.keys + (b & ((1ull << 57) - 1)));
+        if (nx.dist) nx.dist[i] = (uint8_t)(b >> 57);
+    }
+    if (threadIdx.x == 0) *nx.done = 0;   // for the next launch
+}
+
 // Few pending candidates (<= few_max, at most 4): one candidate set per CTA, high
 // occupancy, four independent 16-byte key loads in flight per thread.  A last chunk
 // with more candidates is left to k_scan_wide or to the distance-table scan.
@@ -359,26 +394,27 @@ __device__ __forceinline__ void scan_run4(const uint64_t* __restrict__ keys, int
 __global__ void __launch_bounds__(SCAN_THREADS, 4)
 k_scan_few(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_t highm,
            const uint64_t* __restrict__ cand, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
-           unsigned long long* __restrict__ best, int few_max) {
+           unsigned long long* __restrict__ best, int few_max, const ScanNext nx) {
     __shared__ uint64_t cq[SCAN_CHUNK];
     __shared__ unsigned long long red[SCAN_THREADS / 32][SCAN_CHUNK];
     const uint32_t cnt = *count;
-    if (cnt == 0) return;
-    const uint32_t q0 = (cnt - 1) / SCAN_CHUNK * SCAN_CHUNK;
+    const uint32_t q0 = cnt ? (cnt - 1) / SCAN_CHUNK * SCAN_CHUNK : 0;
     const int nq = (int)(cnt - q0);
-    if (nq > few_max || nq > 4) return;
-    if (threadIdx.x < SCAN_CHUNK) cq[threadIdx.x] = threadIdx.x < nq ? cand[pend[q0 + threadIdx.x]] : 0ull;
-    __syncthreads();
-    unsigned long long* bq = best + q0;
-    if ((highm >> 32) == 0) {
-        if (nq <= 1) scan_run4<1, true>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else if (nq <= 2) scan_run4<2, true>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else scan_run4<4, true>(keys, nv, lowm, highm, cq, nq, bq, red);
-    } else {
-        if (nq <= 1) scan_run4<1, false>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else if (nq <= 2) scan_run4<2, false>(keys, nv, lowm, highm, cq, nq, bq, red);
-        else scan_run4<4, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+    if (cnt && nq <= few_max && nq <= 4) {
+        if (threadIdx.x < SCAN_CHUNK) cq[threadIdx.x] = threadIdx.x < nq ? cand[pend[q0 + threadIdx.x]] : 0ull;
+        __syncthreads();
+        unsigned long long* bq = best + q0;
+        if ((highm >> 32) == 0) {
+            if (nq <= 1) scan_run4<1, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+            else if (nq <= 2) scan_run4<2, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+            else scan_run4<4, true>(keys, nv, lowm, highm, cq, nq, bq, red);
+        } else {
+            if (nq <= 1) scan_run4<1, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+            else if (nq <= 2) scan_run4<2, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+            else scan_run4<4, false>(keys, nv, lowm, highm, cq, nq, bq, red);
+        }
     }
+    scan_resolve_last(nx, pend, count, best);
 }
 
 // Every chunk with more than four pending candidates.  One wave of CTAs; each CTA
@@ -386,7 +422,7 @@ k_scan_few(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_
 __global__ void __launch_bounds__(SCAN_THREADS)
 k_scan_wide(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64_t highm,
             const uint64_t* __restrict__ cand, const int32_t* __restrict__ pend, const uint32_t* __restrict__ count,
-            unsigned long long* __restrict__ best) {
+            unsigned long long* __restrict__ best, const ScanNext nx) {
     __shared__ uint64_t cq[SCAN_CHUNK];
     __shared__ unsigned long long red[SCAN_THREADS / 32][SCAN_CHUNK];
     const uint32_t cnt = *count;
@@ -407,6 +443,7 @@ k_scan_wide(const uint64_t* __restrict__ keys, int64_t nv, uint64_t lowm, uint64
             else scan_run<32, false>(keys, nv, lowm, highm, cq, nq, bq, red);
         }
     }
+    scan_resolve_last(nx, pend, count, best);
 }
 
 __global__ void k_scan_resolve(const uint64_t* __restrict__ keys, const int32_t* __restrict__ pend,
@@ -498,16 +535,22 @@ ct_status repair_launch(const ct_space* s, const RepairPtrs& p, int dmax, const 
     bool lut = false;   // long key arrays: per-candidate distance tables
     int lut_min = 0;
     CT_TRY(scan_lut(s, d_cand, p.pend[cur], p.cnt[cur], p.best[cur], st, &lut, &lut_min));
+    // the last scan kernel's last CTA resolves, unless many candidates could be pending
+    const bool fold = n <= SCAN_FOLD_MAX;
+    const ScanNext nx = fold ? ScanNext{p.done, s->keys.p, d_out, d_dist} : ScanNext{};
     k_scan_few<<<gf, SCAN_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, s->h.swar_low, s->h.swar_high, d_cand,
-                                            p.pend[cur], p.cnt[cur], p.best[cur], lut ? lut_min - 1 : 4);
+                                            p.pend[cur], p.cnt[cur], p.best[cur], lut ? lut_min - 1 : 4,
+                                            lut ? nx : ScanNext{});
     count_launch();
     if (!lut) {
         k_scan_wide<<<gw, SCAN_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, s->h.swar_low, s->h.swar_high,
-                                                 d_cand, p.pend[cur], p.cnt[cur], p.best[cur]);
+                                                 d_cand, p.pend[cur], p.cnt[cur], p.best[cur], nx);
         count_launch();
     }
-    k_scan_resolve<<<g1, 256, 0, st>>>(s->keys.p, p.pend[cur], p.cnt[cur], p.best[cur], d_out, d_dist);
-    count_launch();
+    if (!fold) {
+        k_scan_resolve<<<g1, 256, 0, st>>>(s->keys.p, p.pend[cur], p.cnt[cur], p.best[cur], d_out, d_dist);
+        count_launch();
+    }
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
 }
