@@ -767,6 +767,40 @@ def run_batched(args):
     return 0
 
 
+def run_surrogate_step(args):
+    """Milliseconds per generation of DE at pop 256 on the large space: plain, and forced to screen
+    a pool of 16 x 256 candidates every generation (--steps generations after generation 0)."""
+    import torch
+    from paper_2606_28372_b300 import build as B
+    B.build()
+    from paper_2606_28372_b300 import catune as ct
+    from paper_2606_28372_b300 import workloads as W
+    dev = torch.device("cuda", 0)
+    sd = W.SPACES[args.workload]()
+    sp = ct.Space.from_def(sd)
+    nv = sp.build()
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234)
+    table = torch.exp(torch.randn(nv, generator=g, device=dev, dtype=torch.float32))
+    sp.set_fitness(table)
+    out = surrogate_large(torch, ct, sp, table, dev, gens=args.steps)
+    # fixed-order fp32 work of a screened generation (CUDA cores, two operations per fused
+    # multiply-add): forward passes of the 16 x P pool and of the P evaluated configurations, then
+    # 8 training steps of 256 (forward and backward)
+    N, H, P, pool, steps, bt = len(sd.params), 256, POP, 16, 8, 256
+    fwd = H * N + H + 2 * (2 * H * H + H) + 2 * H + 1
+    bwd = H + 2 * (2 * H * H) + 2 * (2 * H * H) + 2 * H + (3 * H + 1) + N * H
+    flop = (pool * P + P) * fwd + steps * bt * (fwd + bwd)
+    peak = ct.measure_fp32_peak()
+    ms = out["surrogate_large_de_pop256"]["forced"]["ms_per_generation"]
+    out["forced_fp32_flop_per_generation"] = flop
+    out["forced_fp32_tflops"] = flop / (ms / 1000.0) / 1e12
+    out["fp32_peak_tflops_measured"] = peak / 1e12
+    out["forced_frac_of_fp32_peak"] = flop / (ms / 1000.0) / peak
+    print(json.dumps({"mode": "surrogate_step", "workload": args.workload, **out}))
+    return 0
+
+
 def run_surrogate(args):
     import torch
     from paper_2606_28372_b300 import catune as ct
@@ -1089,13 +1123,15 @@ if __name__ == "__main__":
                          "variants; minutes), printed as one JSON line before the headline")
     ap.add_argument("--submetrics-out", default=None, help="with --full: also write the sub-metrics line to this file")
     ap.add_argument("--mode", default="step",
-                    choices=["step", "scan", "repair", "aware", "variants", "batched", "rules", "surrogate"],
+                    choices=["step", "scan", "repair", "aware", "variants", "batched", "rules", "surrogate",
+                             "surrogate_step"],
                     help="scan: only the exhaustive repair scan (scan-only repair of 1 to 32 uniform candidates); "
                          "repair: only repair calls of 256 candidates on --workload (--kind, --radius); "
                          "aware: only the constraint-aware vs non-aware comparison over the density ladder; "
                          "variants: only the DE/GA operator comparison; batched: only the batched-runs "
                          "comparison; rules: only the paper's repair rules on --workload; surrogate: only the "
-                         "surrogate-vs-plain comparison on the large space")
+                         "surrogate-vs-plain comparison on the large space; surrogate_step: milliseconds per "
+                         "generation of plain, judged and forced-screening DE on --workload")
     ap.add_argument("--workload", default="large", choices=["large", "large_slice"],
                     help="large_slice: the same kernels on a 146M-key slice, for hardware-counter captures")
     ap.add_argument("--kind", default="both", choices=["both", "perturbed", "uniform"],
@@ -1113,6 +1149,8 @@ if __name__ == "__main__":
         sys.exit(run_batched(a))
     if a.mode == "surrogate":
         sys.exit(run_surrogate(a))
+    if a.mode == "surrogate_step":
+        sys.exit(run_surrogate_step(a))
     if a.mode == "rules":
         sys.exit(run_rules(a))
     if a.mode == "repair":

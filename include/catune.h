@@ -502,6 +502,11 @@ void ct_trim_cache(void);
  * by the population-count pipe, and writes population counts per second (synchronises). */
 ct_status ct_measure_int_peak(double *popc_per_s, ct_stream stream);
 
+/* Denominator of the surrogate's fixed-order fp32 products (CUDA cores, no tensor cores): runs
+ * independent fp32 fused multiply-add chains over every SM of the current device and writes
+ * floating-point operations per second, two per fused multiply-add (synchronises). */
+ct_status ct_measure_fp32_peak(double *flop_per_s, ct_stream stream);
+
 /* Number of kernels this library has launched in this process (all devices). */
 uint64_t ct_launch_count(void);
 

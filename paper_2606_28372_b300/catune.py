@@ -132,6 +132,7 @@ _SIGS = {
     "ct_space_set_timing": [C.c_void_p, C.c_int32],
     "ct_space_build_stats": [C.c_void_p, C.c_void_p],
     "ct_measure_int_peak": [C.POINTER(C.c_double), C.c_void_p],
+    "ct_measure_fp32_peak": [C.POINTER(C.c_double), C.c_void_p],
     "ct_launch_count": [],
     "ct_alloc_count": [],
     "ct_trim_cache": [],
@@ -400,6 +401,14 @@ def measure_int_peak(stream=None):
     chains, bound by the population-count pipe like the key scans)."""
     v = C.c_double()
     check(lib().ct_measure_int_peak(C.byref(v), _stream(stream)))
+    return float(v.value)
+
+
+def measure_fp32_peak(stream=None):
+    """fp32 operations per second of the library's fused multiply-add microbenchmark (the
+    denominator of the surrogate's CUDA-core products)."""
+    v = C.c_double()
+    check(lib().ct_measure_fp32_peak(C.byref(v), _stream(stream)))
     return float(v.value)
 
 

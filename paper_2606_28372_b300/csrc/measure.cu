@@ -6,6 +6,10 @@
 // the rate of the other integer operations, so this mix (like the scans, which spend one per
 // (key, candidate) on keys of at most 32 bits and two on wider keys) is bound by that pipe; the
 // rate reported is population counts per second, measured over every SM at full occupancy.
+//
+// A second microbenchmark gives the denominator of the surrogate's fixed-order fp32 products:
+// eight independent fused multiply-add chains per thread, every SM at full occupancy, reported
+// as floating-point operations (two per fused multiply-add) per second.
 #include <cuda_runtime.h>
 
 #include "internal.hpp"
@@ -33,9 +37,64 @@ __global__ void __launch_bounds__(IP_THREADS) k_int_peak(uint32_t seed, uint32_t
     if (r == 0x9e3779b9u) sink[0] = r;   // keeps the chains live; practically never written
 }
 
+constexpr int FP_ITERS = 4096, FP_CHAINS = 8;
+
+__global__ void __launch_bounds__(IP_THREADS) k_fp32_peak(float seed, float* __restrict__ sink) {
+    float a[FP_CHAINS];
+    const float x = seed + 1e-7f * (float)(blockIdx.x * IP_THREADS + threadIdx.x);
+#pragma unroll
+    for (int c = 0; c < FP_CHAINS; ++c) a[c] = x + (float)c;
+    for (int i = 0; i < FP_ITERS; ++i) {
+#pragma unroll
+        for (int c = 0; c < FP_CHAINS; ++c) a[c] = __fmaf_rn(a[c], 0.999999f, 1e-6f);
+    }
+    float r = 0.0f;
+#pragma unroll
+    for (int c = 0; c < FP_CHAINS; ++c) r += a[c];
+    if (r == 12345.678f) sink[0] = r;   // keeps the chains live; practically never written
+}
+
+// Times one launch of `k` over every SM (grid: 8 resident CTAs of 256 per SM, four waves) after
+// a warm-up launch; milliseconds into *ms.
+template <class Launch>
+static ct_status time_peak(Launch launch, cudaStream_t st, float* ms) {
+    cudaEvent_t e0, e1;
+    CT_TRY_CUDA(cudaEventCreate(&e0));
+    CT_TRY_CUDA(cudaEventCreate(&e1));
+    launch(1);   // warm-up
+    cudaEventRecord(e0, st);
+    launch(2);
+    cudaEventRecord(e1, st);
+    count_launch(2);
+    cudaError_t err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) { set_error("%s", cudaGetErrorString(err)); return CT_ERR_CUDA; }
+    return CT_OK;
+}
+
 }  // namespace ct
 
 using namespace ct;
+
+extern "C" ct_status ct_measure_fp32_peak(double* flop_per_s, ct_stream stream) {
+    if (!flop_per_s) { set_error("null argument"); return CT_ERR_INVALID_ARG; }
+    int dev = 0, sms = 148;
+    CT_TRY_CUDA(cudaGetDevice(&dev));
+    CT_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    DevBuf<float> sink;
+    CT_TRY(sink.ensure(1));
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned grid = (unsigned)sms * 8 * 4;
+    float ms = 0.0f;
+    const ct_status r = time_peak([&](int w) { k_fp32_peak<<<grid, IP_THREADS, 0, st>>>((float)w, sink.p); }, st, &ms);
+    sink.release();
+    CT_TRY(r);
+    const double flop = 2.0 * (double)grid * IP_THREADS * FP_ITERS * FP_CHAINS;
+    *flop_per_s = flop / (ms * 1e-3);
+    return CT_OK;
+}
 
 extern "C" ct_status ct_measure_int_peak(double* popc_per_s, ct_stream stream) {
     if (!popc_per_s) { set_error("null argument"); return CT_ERR_INVALID_ARG; }

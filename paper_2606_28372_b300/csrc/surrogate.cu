@@ -110,34 +110,70 @@ __global__ void k_mlp_l1(const float* __restrict__ p, MlpOff o, int D, int H, in
 // Ordered product C[m][n] = sum_{k ascending} A(m,k) * Bv(n,k), one fused multiply-add per
 // term starting from 0, A(m,k) = A[m*sam + k*sak], Bv(n,k) = B[n*sbn + k*sbk] (optionally
 // bf16-rounded).  One output per thread in tiles of OG_T x OG_T outputs (256 CTAs for a
-// 256 x 256 product, more than the SMs), k in chunks of OG_K through shared memory.
+// 256 x 256 product, more than the SMs: every output is one sequential chain of K terms, so the
+// products of the training steps are latency-bound and want many threads), k in chunks of OG_K
+// through shared memory; the next chunk's elements are loaded into registers while the current
+// chunk is multiplied.
 // EPI 0: z = acc + bias[n] -> out (z) and out2 (ReLU);  EPI 1: out = zmask > 0 ? acc : 0;
-// EPI 2: out = acc;  EPI 3: out = acc + bias[n].
-constexpr int OG_T = 16, OG_K = 32;
+// EPI 2: out = acc (and, with rowsum, rowsum[m] = sum_{k ascending} A(m,k), added from 0: the
+// bias gradients, by the threads of column 0);  EPI 3: out = acc + bias[n].
+constexpr int OG_T = 16, OG_K = 32, OG_THREADS = OG_T * OG_T, OG_PER = OG_T * OG_K / OG_THREADS;
 
 template <int EPI, bool BF16>
-__global__ void __launch_bounds__(OG_T * OG_T)
+__global__ void __launch_bounds__(OG_THREADS)
 k_ogemm(int M, int Nn, int K, const float* __restrict__ A, long sam, long sak, const float* __restrict__ Bm, long sbn,
         long sbk, const float* __restrict__ bias, const float* __restrict__ zmask, float* __restrict__ out,
-        float* __restrict__ out2, long ldc) {
+        float* __restrict__ out2, long ldc, float* __restrict__ rowsum) {
     __shared__ float As[OG_T][OG_K + 1], Bs[OG_T][OG_K + 1];
     const int tx = threadIdx.x % OG_T, ty = threadIdx.x / OG_T;
     const int m0 = blockIdx.y * OG_T, n0 = blockIdx.x * OG_T;
-    float acc = 0.0f;
+    const bool do_rs = EPI == 2 && rowsum && blockIdx.x == 0 && tx == 0;
+    // the elements this thread stages, e = threadIdx.x + q * OG_THREADS: consecutive threads run
+    // along the operand's unit stride (k for a row-major operand, the row otherwise), so that the
+    // loads are contiguous; the shared rows are padded, so either order stores without conflicts
+    const bool ak = sak == 1, bk = sbk == 1;
+    auto rc = [](bool along_k, int e, int& r, int& c) {
+        if (along_k) { r = e / OG_K; c = e % OG_K; } else { r = e % OG_T; c = e / OG_T; }
+    };
+    float pa[OG_PER], pb[OG_PER];
+    auto fetch = [&](int k0) {
+        const int kmax = min(OG_K, K - k0);
+#pragma unroll
+        for (int q = 0; q < OG_PER; ++q) {
+            const int e = threadIdx.x + q * OG_THREADS;
+            int r, c;
+            rc(ak, e, r, c);
+            const int m = m0 + r;
+            pa[q] = (m < M && c < kmax) ? A[m * sam + (k0 + c) * sak] : 0.0f;
+            rc(bk, e, r, c);
+            const int n = n0 + r;
+            const float bv = (n < Nn && c < kmax) ? Bm[n * sbn + (k0 + c) * sbk] : 0.0f;
+            pb[q] = BF16 ? bf16r(bv) : bv;
+        }
+    };
+    fetch(0);
+    float acc = 0.0f, rs = 0.0f;
     for (int k0 = 0; k0 < K; k0 += OG_K) {
         const int kmax = min(OG_K, K - k0);
-        for (int e = threadIdx.x; e < OG_T * OG_K; e += OG_T * OG_T) {
-            const int r = e / OG_K, c = e % OG_K;
-            const int m = m0 + r, n = n0 + r, k = k0 + c;
-            As[r][c] = (m < M && c < kmax) ? A[m * sam + k * sak] : 0.0f;
-            const float bv = (n < Nn && c < kmax) ? Bm[n * sbn + k * sbk] : 0.0f;
-            Bs[r][c] = BF16 ? bf16r(bv) : bv;
+#pragma unroll
+        for (int q = 0; q < OG_PER; ++q) {
+            const int e = threadIdx.x + q * OG_THREADS;
+            int r, c;
+            rc(ak, e, r, c);
+            As[r][c] = pa[q];
+            rc(bk, e, r, c);
+            Bs[r][c] = pb[q];
         }
         __syncthreads();
-        for (int kk = 0; kk < kmax; ++kk) acc = __fmaf_rn(As[ty][kk], Bs[tx][kk], acc);
+        if (k0 + OG_K < K) fetch(k0 + OG_K);   // in flight while this chunk is multiplied
+        for (int kk = 0; kk < kmax; ++kk) {
+            acc = __fmaf_rn(As[ty][kk], Bs[tx][kk], acc);
+            if (do_rs) rs = __fadd_rn(rs, As[ty][kk]);
+        }
         __syncthreads();
     }
     const int m = m0 + ty, n = n0 + tx;
+    if (do_rs && m < M) rowsum[m] = rs;
     if (m >= M || n >= Nn) return;
     const long idx = m * ldc + n;
     if (EPI == 0) {
@@ -150,6 +186,97 @@ k_ogemm(int M, int Nn, int K, const float* __restrict__ A, long sam, long sak, c
         out[idx] = acc;
     } else {
         out[idx] = __fadd_rn(acc, bias[n]);
+    }
+}
+
+// The same ordered product for tall products (the screening pool's forward pass): a CTA of 64
+// threads computes a 32 x 32 tile, 4 x 4 outputs per thread in registers, so each pair of
+// 16-byte shared loads feeds 16 fused multiply-adds; tiles are staged k-major (rows padded to
+// 36 floats, four consecutive rows per 16-byte store).  Each output still takes its terms one at
+// a time in ascending k from 0, so it equals k_ogemm's bit for bit.  EPI 0 and 3 as above.
+constexpr int O4_T = 32, O4_K = 32, O4_R = 4, O4_THREADS = (O4_T / O4_R) * (O4_T / O4_R), O4_LD = O4_T + 4;
+constexpr int O4_MIN_ROWS = 1024;   // forward passes of at least this many samples take k_ogemm4
+
+constexpr int O4_PER = O4_K * (O4_T / 4) / O4_THREADS;   // 16-byte groups a thread stages per operand
+
+// One operand's chunk into registers (all loads issued before any is used), then into shared
+// memory: group e = threadIdx.x + q * O4_THREADS holds X(r0 + 4 g .. + 3, k0 + c); the lanes run
+// along the operand's unit stride.
+__device__ __forceinline__ void o4_coords(long sk, int e, int& c, int& g) {
+    if (sk == 1) { c = e % O4_K; g = e / O4_K; } else { g = e % (O4_T / 4); c = e / (O4_T / 4); }
+}
+template <bool BF16>
+__device__ __forceinline__ void o4_load(float (&v)[O4_PER][4], const float* __restrict__ X, long sr, long sk, int rows,
+                                        int r0, int k0, int kmax) {
+#pragma unroll
+    for (int q = 0; q < O4_PER; ++q) {
+        int c, g;
+        o4_coords(sk, threadIdx.x + q * O4_THREADS, c, g);
+        const int r = r0 + 4 * g;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float x = (c < kmax && r + i < rows) ? X[(long)(r + i) * sr + (long)(k0 + c) * sk] : 0.0f;
+            v[q][i] = BF16 ? bf16r(x) : x;
+        }
+    }
+}
+__device__ __forceinline__ void o4_store(float (*S)[O4_LD], const float (&v)[O4_PER][4], long sk) {
+#pragma unroll
+    for (int q = 0; q < O4_PER; ++q) {
+        int c, g;
+        o4_coords(sk, threadIdx.x + q * O4_THREADS, c, g);
+        *reinterpret_cast<float4*>(&S[c][4 * g]) = make_float4(v[q][0], v[q][1], v[q][2], v[q][3]);
+    }
+}
+
+template <int EPI, bool BF16>
+__global__ void __launch_bounds__(O4_THREADS)
+k_ogemm4(int M, int Nn, int K, const float* __restrict__ A, long sam, long sak, const float* __restrict__ Bm, long sbn,
+         long sbk, const float* __restrict__ bias, float* __restrict__ out, float* __restrict__ out2, long ldc) {
+    __shared__ __align__(16) float As[O4_K][O4_LD], Bs[O4_K][O4_LD];
+    const int tx = threadIdx.x % (O4_T / O4_R), ty = threadIdx.x / (O4_T / O4_R);
+    const int m0 = blockIdx.y * O4_T, n0 = blockIdx.x * O4_T;
+    float acc[O4_R][O4_R];
+#pragma unroll
+    for (int i = 0; i < O4_R; ++i)
+#pragma unroll
+        for (int j = 0; j < O4_R; ++j) acc[i][j] = 0.0f;
+    float va[O4_PER][4], vb[O4_PER][4];
+    o4_load<false>(va, A, sam, sak, M, m0, 0, min(O4_K, K));
+    o4_load<BF16>(vb, Bm, sbn, sbk, Nn, n0, 0, min(O4_K, K));
+    for (int k0 = 0; k0 < K; k0 += O4_K) {
+        const int kmax = min(O4_K, K - k0);
+        o4_store(As, va, sak);
+        o4_store(Bs, vb, sbk);
+        __syncthreads();
+        if (k0 + O4_K < K) {   // the next chunk is in flight while this one is multiplied
+            o4_load<false>(va, A, sam, sak, M, m0, k0 + O4_K, min(O4_K, K - k0 - O4_K));
+            o4_load<BF16>(vb, Bm, sbn, sbk, Nn, n0, k0 + O4_K, min(O4_K, K - k0 - O4_K));
+        }
+        for (int kk = 0; kk < kmax; ++kk) {
+            const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * O4_R]);
+            const float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][tx * O4_R]);
+            const float av[O4_R] = {a4.x, a4.y, a4.z, a4.w}, bv[O4_R] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int i = 0; i < O4_R; ++i)
+#pragma unroll
+                for (int j = 0; j < O4_R; ++j) acc[i][j] = __fmaf_rn(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < O4_R; ++i) {
+        const int m = m0 + ty * O4_R + i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < O4_R; ++j) {
+            const int n = n0 + tx * O4_R + j;
+            if (n >= Nn) continue;
+            const long idx = m * ldc + n;
+            const float z = __fadd_rn(acc[i][j], bias[n]);
+            out[idx] = z;
+            if (EPI == 0) out2[idx] = z > 0.0f ? z : 0.0f;
+        }
     }
 }
 
@@ -171,27 +298,88 @@ __global__ void k_mlp_d3(const float* __restrict__ p, MlpOff o, int H, int B, co
     }
 }
 
-// column sums over the batch in ascending sample order (bias gradients)
-struct ColSums {                       // up to four column sums in one launch
-    const float* d[4];
-    int cols[4];
-    float* out[4];
-};
+// Gradient of the one-hot layer and of its bias.  A CTA takes JB hidden units; thread (jj, k)
+// owns the outputs gW1[j][base_k .. base_k + r_k) of parameter k's values (kept in shared memory,
+// no other thread writes them) and adds d1[b][j] to the one that sample b activates, in
+// ascending b; thread (jj, 0) also sums d1[b][j] over b for the bias.  Every output is thus its
+// plain ascending-sample sum from 0 (features never active stay 0).  Samples are staged through
+// shared memory in chunks of W1_CHUNK.
+constexpr int W1_CHUNK = 256;
 
-__global__ void k_colsums(const __grid_constant__ ColSums cs, int B) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int q = 0, j = t;
-    while (q < 4 && j >= cs.cols[q]) { j -= cs.cols[q]; ++q; }
-    if (q == 4) return;
-    float acc = 0.0f;
-    for (int b = 0; b < B; ++b) acc = __fadd_rn(acc, cs.d[q][(size_t)b * cs.cols[q] + j]);
-    cs.out[q][j] = acc;
+static __host__ __device__ size_t w1grad_ft_off(int JB, int D) {   // floats before the feature tile (16-byte aligned)
+    return ((size_t)JB * D + (size_t)W1_CHUNK * JB + 3) & ~(size_t)3;
+}
+static size_t w1grad_smem(int JB, int D, int N) {
+    return (w1grad_ft_off(JB, D) + (size_t)W1_CHUNK * N) * sizeof(float);
 }
 
-// gradient of the one-hot layer: for each (j, feature f), the sum over samples (ascending)
-// in which f is active of d1[b][j]; an owner index outside 0..N-1 means f is never active
-__global__ void k_mlp_w1grad(const float* __restrict__ d1, const int32_t* __restrict__ feats,
-                             const int32_t* __restrict__ param_of, int B, int N, int D, int H, float* __restrict__ gW1) {
+__global__ void k_mlp_w1grad(const float* __restrict__ d1, const int32_t* __restrict__ feats, int B, int N, int D,
+                             int H, int JB, float* __restrict__ gW1, float* __restrict__ gb1) {
+    extern __shared__ __align__(16) float w1s[];
+    float* outs = w1s;                                        // [JB][D]
+    float* dt = outs + (size_t)JB * D;                        // [W1_CHUNK][JB]
+    int32_t* ft = reinterpret_cast<int32_t*>(w1s + w1grad_ft_off(JB, D));   // [W1_CHUNK][N]
+    const int j0 = blockIdx.x * JB;
+    const int t = threadIdx.x, jj = t / N, k = t % N;
+    const bool mine = jj < JB && j0 + jj < H;
+    for (int e = t; e < JB * D; e += blockDim.x) outs[e] = 0.0f;
+    float bsum = 0.0f;
+    for (int b0 = 0; b0 < B; b0 += W1_CHUNK) {
+        const int nb = min(W1_CHUNK, B - b0);
+        __syncthreads();   // the previous chunk is done with dt and ft (and outs is zeroed)
+        // eight loads in flight per thread before their stores
+        for (int e0 = t; e0 < nb * JB; e0 += 8 * blockDim.x) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * blockDim.x, bb = e / JB, q = e % JB;
+                v[u] = (e < nb * JB && j0 + q < H) ? d1[(size_t)(b0 + bb) * H + j0 + q] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (e0 + u * (int)blockDim.x < nb * JB) dt[e0 + u * blockDim.x] = v[u];
+        }
+        if ((N & 3) == 0) {   // 16-byte loads of the sample rows
+            const int4* src = reinterpret_cast<const int4*>(feats + (size_t)b0 * N);
+            int4* dst = reinterpret_cast<int4*>(ft);
+            const int nv4 = nb * N / 4;
+            for (int e0 = t; e0 < nv4; e0 += 8 * blockDim.x) {
+                int4 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (e0 + u * (int)blockDim.x < nv4) v[u] = src[e0 + u * blockDim.x];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (e0 + u * (int)blockDim.x < nv4) dst[e0 + u * blockDim.x] = v[u];
+            }
+        } else {
+            for (int e = t; e < nb * N; e += blockDim.x) ft[e] = feats[(size_t)b0 * N + e];
+        }
+        __syncthreads();
+        if (mine) {
+            float* row = outs + (size_t)jj * D;
+            for (int bb = 0; bb < nb; ++bb) {
+                const float v = dt[bb * JB + jj];
+                const int f = ft[bb * N + k];
+                row[f] = __fadd_rn(row[f], v);
+                if (k == 0) bsum = __fadd_rn(bsum, v);
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < JB * D; e += blockDim.x) {
+        const int q = e / D, f = e % D;
+        if (j0 + q < H) gW1[(size_t)(j0 + q) * D + f] = outs[e];
+    }
+    if (mine && k == 0) gb1[j0 + jj] = bsum;
+}
+
+// The same gradient for inputs too wide for the shared-memory form: one thread per (j, feature f)
+// sums d1[b][j] over the samples (ascending) in which f is active; an owner index outside 0..N-1
+// means f is never active.  The bias is left to k_colsum.
+__global__ void k_mlp_w1grad_wide(const float* __restrict__ d1, const int32_t* __restrict__ feats,
+                                  const int32_t* __restrict__ param_of, int B, int N, int D, int H,
+                                  float* __restrict__ gW1) {
     const size_t total = (size_t)H * D;
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(g / D), f = (int)(g % D);
@@ -202,6 +390,15 @@ __global__ void k_mlp_w1grad(const float* __restrict__ d1, const int32_t* __rest
                 if (feats[(size_t)b * N + k] == f) acc = __fadd_rn(acc, d1[(size_t)b * H + j]);
         gW1[g] = acc;
     }
+}
+
+// column sums over the batch in ascending sample order
+__global__ void k_colsum(const float* __restrict__ d, int cols, int B, float* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols) return;
+    float acc = 0.0f;
+    for (int b = 0; b < B; ++b) acc = __fadd_rn(acc, d[(size_t)b * cols + j]);
+    out[j] = acc;
 }
 
 __global__ void k_mlp_sgd(float* __restrict__ p, float* __restrict__ mom, const float* __restrict__ g, size_t n, float lr,
@@ -236,12 +433,23 @@ static ct_status mlp_forward_impl(const float* p, int D, int H, int N, const int
                                   const MlpWork& w, cudaStream_t st) {
     const MlpOff o = mlp_off(D, H);
     k_mlp_l1<<<grid_for((size_t)B * H), 256, 0, st>>>(p, o, D, H, N, feats, B, w.z1, w.h1);
+    if (B >= O4_MIN_ROWS) {   // tall: register-blocked tiles
+        const dim3 g4((H + O4_T - 1) / O4_T, (B + O4_T - 1) / O4_T);
+        k_ogemm4<0, true><<<g4, O4_THREADS, 0, st>>>(B, H, H, w.h1, H, 1, p + o.W2, H, 1, p + o.b2, w.z2, w.h2, H);
+        k_ogemm4<0, true><<<g4, O4_THREADS, 0, st>>>(B, H, H, w.h2, H, 1, p + o.W3, H, 1, p + o.b3, w.z3, w.h3, H);
+        k_ogemm<3, true><<<og_grid(B, 1), OG_THREADS, 0, st>>>(B, 1, H, w.h3, H, 1, p + o.W4, 0, 1, p + o.b4, nullptr,
+                                                               pred, nullptr, 1, nullptr);
+        count_launch(4);
+        CT_TRY_CUDA(cudaGetLastError());
+        return CT_OK;
+    }
     const dim3 g = og_grid(B, H);
-    const int OT = OG_T * OG_T;
-    k_ogemm<0, true><<<g, OT, 0, st>>>(B, H, H, w.h1, H, 1, p + o.W2, H, 1, p + o.b2, nullptr, w.z2, w.h2, H);
-    k_ogemm<0, true><<<g, OT, 0, st>>>(B, H, H, w.h2, H, 1, p + o.W3, H, 1, p + o.b3, nullptr, w.z3, w.h3, H);
-    k_ogemm<3, true><<<og_grid(B, 1), OT, 0, st>>>(B, 1, H, w.h3, H, 1, p + o.W4, 0, 1, p + o.b4, nullptr,
-                                                            pred, nullptr, 1);
+    k_ogemm<0, true><<<g, OG_THREADS, 0, st>>>(B, H, H, w.h1, H, 1, p + o.W2, H, 1, p + o.b2, nullptr, w.z2, w.h2, H,
+                                               nullptr);
+    k_ogemm<0, true><<<g, OG_THREADS, 0, st>>>(B, H, H, w.h2, H, 1, p + o.W3, H, 1, p + o.b3, nullptr, w.z3, w.h3, H,
+                                               nullptr);
+    k_ogemm<3, true><<<og_grid(B, 1), OG_THREADS, 0, st>>>(B, 1, H, w.h3, H, 1, p + o.W4, 0, 1, p + o.b4, nullptr,
+                                                           pred, nullptr, 1, nullptr);
     count_launch(4);
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
@@ -255,25 +463,31 @@ static ct_status mlp_grad_impl(const float* p, int D, int H, int N, const int32_
     k_mlp_gout<<<(B + 255) / 256, 256, 0, st>>>(pred, y, B, scale, w.gout);
     k_mlp_d3<<<grid_for((size_t)B * H), 256, 0, st>>>(p, o, H, B, w.gout, w.z3, w.d3);
     const dim3 gb = og_grid(B, H);
-    const int OT = OG_T * OG_T;
     // deltas through W3 and W2 (transposed: B(n=i, k=j) = W[j*H + i])
-    k_ogemm<1, true><<<gb, OT, 0, st>>>(B, H, H, w.d3, H, 1, p + o.W3, 1, H, nullptr, w.z2, w.d2, nullptr, H);
-    k_ogemm<1, true><<<gb, OT, 0, st>>>(B, H, H, w.d2, H, 1, p + o.W2, 1, H, nullptr, w.z1, w.d1, nullptr, H);
-    // weight gradients: sum over samples, ascending
+    k_ogemm<1, true><<<gb, OG_THREADS, 0, st>>>(B, H, H, w.d3, H, 1, p + o.W3, 1, H, nullptr, w.z2, w.d2, nullptr, H,
+                                                nullptr);
+    k_ogemm<1, true><<<gb, OG_THREADS, 0, st>>>(B, H, H, w.d2, H, 1, p + o.W2, 1, H, nullptr, w.z1, w.d1, nullptr, H,
+                                                nullptr);
+    // weight gradients: sums over samples, ascending; the bias gradients are the same sums of the
+    // deltas alone (the row sums of A)
     const dim3 gw = og_grid(H, H);
-    k_ogemm<2, false><<<gw, OT, 0, st>>>(H, H, B, w.d3, 1, H, w.h2, 1, H, nullptr, nullptr, grad + o.W3, nullptr, H);
-    k_ogemm<2, false><<<gw, OT, 0, st>>>(H, H, B, w.d2, 1, H, w.h1, 1, H, nullptr, nullptr, grad + o.W2, nullptr, H);
-    k_ogemm<2, false><<<og_grid(1, H), OT, 0, st>>>(1, H, B, w.gout, 0, 1, w.h3, 1, H, nullptr, nullptr,
-                                                             grad + o.W4, nullptr, H);
-    ColSums cs;
-    cs.d[0] = w.gout; cs.cols[0] = 1; cs.out[0] = grad + o.b4;
-    cs.d[1] = w.d3; cs.cols[1] = H; cs.out[1] = grad + o.b3;
-    cs.d[2] = w.d2; cs.cols[2] = H; cs.out[2] = grad + o.b2;
-    cs.d[3] = w.d1; cs.cols[3] = H; cs.out[3] = grad + o.b1;
-    k_colsums<<<(1 + 3 * H + 127) / 128, 128, 0, st>>>(cs, B);
-    // one sequential sum per output: small CTAs spread the H x D outputs over every SM
-    k_mlp_w1grad<<<grid_for((size_t)H * D, 64), 64, 0, st>>>(w.d1, feats, param_of, B, N, D, H, grad + o.W1);
-    count_launch(9);
+    k_ogemm<2, false><<<gw, OG_THREADS, 0, st>>>(H, H, B, w.d3, 1, H, w.h2, 1, H, nullptr, nullptr, grad + o.W3, nullptr,
+                                                 H, grad + o.b3);
+    k_ogemm<2, false><<<gw, OG_THREADS, 0, st>>>(H, H, B, w.d2, 1, H, w.h1, 1, H, nullptr, nullptr, grad + o.W2, nullptr,
+                                                 H, grad + o.b2);
+    k_ogemm<2, false><<<og_grid(1, H), OG_THREADS, 0, st>>>(1, H, B, w.gout, 0, 1, w.h3, 1, H, nullptr, nullptr,
+                                                            grad + o.W4, nullptr, H, grad + o.b4);
+    int JB = 2;   // hidden units per CTA: few, so that the H / JB CTAs reach many SMs
+    while (JB > 1 && (JB * N > 1024 || w1grad_smem(JB, D, N) > 48 * 1024)) JB >>= 1;
+    if (JB * N <= 1024 && w1grad_smem(JB, D, N) <= 48 * 1024) {
+        k_mlp_w1grad<<<(H + JB - 1) / JB, JB * N, w1grad_smem(JB, D, N), st>>>(w.d1, feats, B, N, D, H, JB, grad + o.W1,
+                                                                           grad + o.b1);
+        count_launch(8);
+    } else {
+        k_mlp_w1grad_wide<<<grid_for((size_t)H * D, 64), 64, 0, st>>>(w.d1, feats, param_of, B, N, D, H, grad + o.W1);
+        k_colsum<<<(H + 127) / 128, 128, 0, st>>>(w.d1, H, B, grad + o.b1);
+        count_launch(9);
+    }
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
 }
@@ -358,36 +572,66 @@ __global__ void __launch_bounds__(JUDGE_THREADS)
 k_surr_judge(const uint64_t* __restrict__ keys, int64_t nv, const float* __restrict__ logt,
              const uint64_t* __restrict__ evk, const float* __restrict__ pred, int P, int warm_mult,
              float mae_ratio, int screened, uint32_t* __restrict__ in_e, uint64_t* __restrict__ ek,
-             float* __restrict__ ey, float* __restrict__ scratch, SurrDev* sd) {
+             float* __restrict__ ey, SurrDev* sd) {
     __shared__ int64_t rks[CT_MAX_POP];
-    // the rank lookups (binary searches over the valid keys) in parallel ...
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    __shared__ float ys[CT_MAX_POP], ps[CT_MAX_POP];
+    __shared__ uint32_t pos[CT_MAX_POP];
+    __shared__ uint32_t wsum[JUDGE_THREADS / 32];
+    __shared__ unsigned long long n0_s;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // the rank lookups (binary searches over the valid keys) and whether each configuration is
+    // new to the training set, in parallel ...
+    for (int i = t; i < P; i += blockDim.x) {
         const int64_t rk = rank_of(keys, nv, evk[i]);
         rks[i] = rk;
-        scratch[i] = logt[rk];
+        ys[i] = logt[rk];
+        ps[i] = pred[i];
     }
+    if (t == 0) n0_s = sd->n_e;
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    // ... and the fp32 sums in ascending i, one thread
+    // ... a configuration joins the training set at its first position in this generation, if no
+    // earlier generation added it; positions by an exclusive scan over population order
+    uint32_t carry = 0;
+    for (int c0 = 0; c0 < P; c0 += JUDGE_THREADS) {
+        const int i = c0 + t;
+        uint32_t fresh = 0;
+        if (i < P) {
+            const int64_t rk = rks[i];
+            fresh = !((in_e[rk >> 5] >> (rk & 31)) & 1u);
+            for (int q = 0; q < i && fresh; ++q) fresh = rks[q] != rk;
+        }
+        uint32_t inc = fresh;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        uint32_t wb = 0, tot = 0;
+        for (int w = 0; w < JUDGE_THREADS / 32; ++w) { wb += w < warp ? wsum[w] : 0u; tot += wsum[w]; }
+        if (i < P) pos[i] = fresh ? carry + wb + inc - 1u : ~0u;
+        carry += tot;
+        __syncthreads();
+    }
+    for (int i = t; i < P; i += blockDim.x) {
+        if (pos[i] == ~0u) continue;
+        const size_t n = (size_t)n0_s + pos[i];
+        ek[n] = evk[i];
+        ey[n] = ys[i];
+        atomicOr(in_e + (rks[i] >> 5), 1u << (rks[i] & 31));
+    }
+    if (t != 0) return;
+    // the fp32 sums in ascending i, one thread
     float sa = 0.0f, sy = 0.0f, s_dev = 0.0f;
     for (int i = 0; i < P; ++i) {
-        const float y = scratch[i];
-        sa = __fadd_rn(sa, fabsf(__fsub_rn(pred[i], y)));
+        const float y = ys[i];
+        sa = __fadd_rn(sa, fabsf(__fsub_rn(ps[i], y)));
         sy = __fadd_rn(sy, y);
     }
     const float mae = __fdiv_rn(sa, (float)P), ybar = __fdiv_rn(sy, (float)P);
-    for (int i = 0; i < P; ++i) s_dev = __fadd_rn(s_dev, fabsf(__fsub_rn(scratch[i], ybar)));
+    for (int i = 0; i < P; ++i) s_dev = __fadd_rn(s_dev, fabsf(__fsub_rn(ys[i], ybar)));
     const float tau = __fmul_rn(mae_ratio, __fdiv_rn(s_dev, (float)P));
-    unsigned long long n = sd->n_e;
-    for (int i = 0; i < P; ++i) {   // append first evaluations to the training set, in order
-        const int64_t rk = rks[i];
-        const uint32_t bit = 1u << (rk & 31);
-        if (in_e[rk >> 5] & bit) continue;
-        in_e[rk >> 5] |= bit;
-        ek[n] = evk[i];
-        ey[n] = scratch[i];
-        ++n;
-    }
+    const unsigned long long n = n0_s + carry;
     sd->n_e = n;
     sd->mae = mae;
     sd->tau = tau;
@@ -467,7 +711,7 @@ ct_status surrogate_step(ct_opt* o, uint32_t gen, cudaStream_t st) {
     CT_TRY(evaluate_impl(s, o->memo.p, &o->st.p->n_unique, &o->st.p->cost, evk, P, o->fit.p, nullptr, st));
     CT_TRY(predict_keys(o, evk, P, g->pred.p, st));
     k_surr_judge<<<1, JUDGE_THREADS, 0, st>>>(s->keys.p, (int64_t)s->n_valid, g->logt, evk, g->pred.p, P, g->cfg.warmup_mult,
-                                   g->cfg.mae_ratio, screened ? 1 : 0, g->in_e.p, g->ek.p, g->ey.p, g->by.p, g->sd.p);
+                                   g->cfg.mae_ratio, screened ? 1 : 0, g->in_e.p, g->ek.p, g->ey.p, g->sd.p);
     count_launch();
     const int B = g->cfg.batch, H = g->cfg.hidden;
     for (int t = 0; t < g->cfg.steps; ++t) {
