@@ -489,6 +489,7 @@ def run_ours(args):
         sub.update(repair_paper_rates(med, med_sd, torch, ct, dev, "medium", n=256))
         del med
         sub.update(plain_runs(torch, ct, W, dev))
+        sub.update(one_percent(torch, ct, W, dev))
         sub.update(surrogate_vs_plain(torch, ct, W, dev))
         sub.update(surrogate_large(torch, ct, sp, table, dev))
         sub.update(surrogate_gain_large(torch, ct, W, sp, sd, dev))
@@ -687,18 +688,31 @@ def batched_runs(torch, ct, W, dev, n_runs=4096, gens=100, plain_sample=48):
     torch.cuda.synchronize()
     host_warm()
     t0 = time.perf_counter()
+    plain_hits = []
     for r in range(plain_sample):
         si, kind, pop, seed, tgt = runs[r]
         o = ct.Opt(spaces[si], kind, pop, seed, target=tgt)
         o.run_graph(0, 1)
         o.run_graph(1, gens - 1)
-        del o
+        plain_hits.append(o)
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t0
+    plain_hits = [o.best()["hit_evals"] for o in plain_hits]   # read after the timed region
     del b
     batched = n_runs / (ms / 1000.0)
     plain = plain_sample / plain_s
+    same = res["hit_evals"][:plain_sample]
+
+    def med(h):
+        h = np.asarray(h, dtype=np.float64)
+        h = np.where(h >= 0, h, np.inf)
+        m = float(np.median(h))
+        return m if np.isfinite(m) else None
     return {"batched_runs_per_s": batched, "batched_ms_for_all_runs": ms, "batched_generations": gens,
+            "evals_to_1pct_same_runs": {"runs": plain_sample, "plain_median": med(plain_hits),
+                                        "batched_median": med(same),
+                                        "identical": bool(np.array_equal(np.asarray(plain_hits), np.asarray(same))),
+                                        "reached": f"{int((np.asarray(same) >= 0).sum())}/{plain_sample}"},
             "batched_runs": n_runs, "batched_launch": {"threads": th, "ctas_per_sm": cps},
             "batched_kernel_launches": batched_launches,
             "plain_runs_per_s_same_runs": plain, "plain_sample_runs": plain_sample,
@@ -1028,6 +1042,67 @@ def surrogate_vs_plain(torch, ct, W, dev, seeds=16, gens=150):
     return out
 
 
+def _median_hits(h):
+    """Median unique evaluations to the target over all runs (a run that never got there counts as
+    infinitely many); None when fewer than half got there."""
+    h = np.asarray(h, dtype=np.float64)
+    m = float(np.median(np.where(h >= 0, h, np.inf)))
+    return m if np.isfinite(m) else None
+
+
+def one_percent(torch, ct, W, dev, seeds=16):
+    """The 1 % criterion.  (1) Census of the smooth tables: how many configurations lie within
+    1 / 2 / 5 % of each table's optimum, and the second best's ratio to it.  (2) Plain against
+    surrogate-screened DE and GA: unique evaluations until the best is within 1 % of the optimum
+    (medians over `seeds` seeds, runs that never get there counted as infinitely many), on a batched
+    space of 22,386 valid configurations (pop 64, 200 generations) and on the medium space
+    (pop 128, 600 generations)."""
+    census, out = {}, {}
+    cases = [("medium", W.medium_space(), 0, 128, 600), ("batched_5", W.batched_space(5), 5, 64, 200),
+             ("batched_10", W.batched_space(10), 10, 64, 200)]
+    for name, sd, tseed, pop, gens in cases:
+        sp = ct.Space.from_def(sd)
+        sp.build()
+        keys = sp.keys().cpu().numpy().view(np.uint64)
+        t = W.smooth_table(sd, sp.unpack(keys), seed=tseed)
+        srt = np.sort(t)
+        census[name] = {"valid": int(len(t)), "second_best_rel": float(srt[1] / srt[0]),
+                        **{f"within_{p}pct": int((t <= np.float32((1 + p / 100) * srt[0])).sum()) for p in (1, 2, 5)}}
+        if name == "batched_10":
+            continue
+        dt = torch.from_numpy(t).to(dev)
+        sp.set_fitness(dt)
+        logt = torch.from_numpy(np.log(t.astype(np.float64)).astype(np.float32)).to(dev)
+        tgt = float(np.float32(1.01 * float(srt[0])))
+        for kind in ("de", "ga"):
+            for mode in ("plain", "surrogate"):
+                hits = []
+                for seed in range(seeds):
+                    o = ct.Opt(sp, kind, pop, seed, target=tgt)
+                    if mode == "surrogate":
+                        o.set_surrogate(logt)
+                    for g in range(gens + 1):
+                        o.step(g)
+                    hits.append(o.best()["hit_evals"])
+                    del o
+                reached = [h for h in hits if h >= 0]
+                out[f"{name}_{kind}_{mode}"] = {
+                    "evals_to_1pct_median": _median_hits(hits),
+                    "evals_to_1pct_median_of_reached": float(np.median(reached)) if reached else None,
+                    "reached": f"{len(reached)}/{seeds}", "pop": pop, "generations": gens}
+    return {"one_percent": {"census": census, "runs": out}}
+
+
+def run_one_percent(args):
+    import torch
+    from paper_2606_28372_b300 import build as B
+    B.build()
+    from paper_2606_28372_b300 import catune as ct
+    from paper_2606_28372_b300 import workloads as W
+    print(json.dumps(one_percent(torch, ct, W, torch.device("cuda", 0))))
+    return 0
+
+
 PAPER_POP = {"de": 160, "pso": 30, "firefly": 20, "ga": 20}   # Table IV (DE: 16 x 10 parameters)
 
 
@@ -1124,14 +1199,15 @@ if __name__ == "__main__":
     ap.add_argument("--submetrics-out", default=None, help="with --full: also write the sub-metrics line to this file")
     ap.add_argument("--mode", default="step",
                     choices=["step", "scan", "repair", "aware", "variants", "batched", "rules", "surrogate",
-                             "surrogate_step"],
+                             "surrogate_step", "onepct"],
                     help="scan: only the exhaustive repair scan (scan-only repair of 1 to 32 uniform candidates); "
                          "repair: only repair calls of 256 candidates on --workload (--kind, --radius); "
                          "aware: only the constraint-aware vs non-aware comparison over the density ladder; "
                          "variants: only the DE/GA operator comparison; batched: only the batched-runs "
                          "comparison; rules: only the paper's repair rules on --workload; surrogate: only the "
                          "surrogate-vs-plain comparison on the large space; surrogate_step: milliseconds per "
-                         "generation of plain, judged and forced-screening DE on --workload")
+                         "generation of plain, judged and forced-screening DE on --workload; onepct: the 1 %% "
+                         "criterion (table census, plain against surrogate-screened runs)")
     ap.add_argument("--workload", default="large", choices=["large", "large_slice"],
                     help="large_slice: the same kernels on a 146M-key slice, for hardware-counter captures")
     ap.add_argument("--kind", default="both", choices=["both", "perturbed", "uniform"],
@@ -1151,6 +1227,8 @@ if __name__ == "__main__":
         sys.exit(run_surrogate(a))
     if a.mode == "surrogate_step":
         sys.exit(run_surrogate_step(a))
+    if a.mode == "onepct":
+        sys.exit(run_one_percent(a))
     if a.mode == "rules":
         sys.exit(run_rules(a))
     if a.mode == "repair":

@@ -176,51 +176,102 @@ __global__ void k_build_compact(const DevSpace* __restrict__ sp, const int32_t* 
     if (lane == 0) compact[gw] = word;
 }
 
-__global__ void k_build_tables(const DevSpace* __restrict__ sp, const int32_t* __restrict__ tab_cons,
-                               const uint64_t* __restrict__ tab_prefix, int n_tab, uint64_t total_words,
-                               const uint32_t* __restrict__ compact, uint32_t* __restrict__ tables) {
-    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t gw = gid >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= total_words) return;   // whole warps share gw
-    int lo = 0, hi = n_tab - 1;      // last i with tab_prefix[i] <= gw
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (tab_prefix[mid] <= gw) lo = mid; else hi = mid - 1;
+// Block truth tables: each CTA builds TB_WORDS_PER_CTA consecutive words of one tabled
+// constraint's table (the constraints' words are split into such runs in order), a warp per
+// 32-point word.  The CTA's thread 0 finds its constraint and run, and the constraint's and
+// block's descriptors are copied to shared memory once.  A point's digits come from the block's
+// point -> key-bits table (one coalesced load per word) instead of divisions.
+constexpr int TB_WORDS_PER_CTA = 32;   // 8 warps x 4 words
+__global__ void __launch_bounds__(256)
+k_build_tables(const DevSpace* __restrict__ sp, const int32_t* __restrict__ tab_cons, int n_tab,
+               const uint64_t* __restrict__ tab_prefix, const uint32_t* __restrict__ compact,
+               const uint32_t* __restrict__ innerkey, uint32_t* __restrict__ tables) {
+    __shared__ DevCons cs;
+    __shared__ DevBlock bl;
+    __shared__ int32_t rk[MAXP], offk[MAXP];
+    __shared__ uint64_t run0_s, nw_s;
+    __shared__ int ti_s;
+    if (threadIdx.x < 32) {   // the constraint whose runs hold CTA blockIdx.x: warp 0, 32 constraints at a time
+        const int lane = threadIdx.x;
+        uint64_t first = 0;
+        int found = -1;
+        for (int c0 = 0; c0 < n_tab && found < 0; c0 += 32) {
+            const int ti = c0 + lane;
+            const uint64_t runs = ti < n_tab ? (tab_prefix[ti + 1] - tab_prefix[ti] + TB_WORDS_PER_CTA - 1) / TB_WORDS_PER_CTA : 0;
+            uint64_t inc = runs;   // inclusive prefix of the runs over the lanes
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            const unsigned hit = __ballot_sync(0xffffffffu, ti < n_tab && blockIdx.x < first + inc);
+            if (hit) {
+                const int l = __ffs(hit) - 1;
+                found = c0 + l;
+                const uint64_t before = first + __shfl_sync(0xffffffffu, inc - runs, l);
+                if (lane == 0) {
+                    ti_s = found;
+                    run0_s = (uint64_t)(blockIdx.x - before) * TB_WORDS_PER_CTA;
+                    nw_s = tab_prefix[found + 1] - tab_prefix[found];
+                }
+            } else {
+                first += __shfl_sync(0xffffffffu, inc, 31);
+            }
+        }
+        if (found < 0 && lane == 0) ti_s = n_tab;
     }
-    const DevCons& cs = sp->cons[tab_cons[lo]];
-    const DevBlock& bl = sp->blocks[cs.block];
-    const uint64_t lw = gw - tab_prefix[lo];
-    const uint32_t row = (uint32_t)(lw / bl.W), wd = (uint32_t)(lw % bl.W);
-    const int p = wd * 32 + lane;
-    bool bit = false;
-    if (p < bl.B && cs.cz_off != CZ_NONE) {   // gather from the compact table
-        uint32_t c = 0;
-        for (int q = 0; q < cs.n_in; ++q) {
-            const int k = cs.in_k[q];
-            c += (uint32_t)((p / bl.pstride[k - bl.s]) % sp->r[k]) * (uint32_t)cs.in_stride[q];
+    __syncthreads();
+    const int ti = ti_s;
+    if (ti >= n_tab) return;
+    {
+        const DevCons& gc = sp->cons[tab_cons[ti]];
+        const int32_t* src = reinterpret_cast<const int32_t*>(&gc);
+        int32_t* dst = reinterpret_cast<int32_t*>(&cs);
+        for (int e = threadIdx.x; e < (int)(sizeof(DevCons) / 4); e += blockDim.x) dst[e] = src[e];
+        const int32_t* srcb = reinterpret_cast<const int32_t*>(&sp->blocks[gc.block]);
+        int32_t* dstb = reinterpret_cast<int32_t*>(&bl);
+        for (int e = threadIdx.x; e < (int)(sizeof(DevBlock) / 4); e += blockDim.x) dstb[e] = srcb[e];
+        for (int e = threadIdx.x; e < MAXP; e += blockDim.x) {
+            rk[e] = e < sp->n ? sp->r[e] : 1;
+            offk[e] = e < sp->n ? sp->off[e] : 0;
         }
-        bit = (__ldg(compact + cs.cz_off + (uint64_t)row * cs.cz_W + (c >> 5)) >> (c & 31)) & 1u;
-    } else if (p < bl.B) {
-        int64_t pv[MAXP];
-        for (int k = 0; k < sp->n; ++k) pv[k] = 0;
-        uint32_t o = row;
-        for (int q = cs.n_outer - 1; q >= 0; --q) {
-            const int k = cs.outer_k[q];
-            const int32_t ik = (int32_t)(o % sp->r[k]);
-            o /= sp->r[k];
-            pv[k] = sp->values[sp->vstart[k] + ik];
-        }
-        int t = p;
-        for (int k = bl.e - 1; k >= bl.s; --k) {
-            const int32_t ik = t % sp->r[k];
-            t /= sp->r[k];
-            pv[k] = sp->values[sp->vstart[k] + ik];
-        }
-        bit = vm_eval(sp->prog, cs.pc, cs.len, pv);
     }
-    const uint32_t word = __ballot_sync(0xffffffffu, bit);
-    if (lane == 0) tables[cs.table_off + lw] = word;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t nw = nw_s, run0 = run0_s;
+    const uint32_t* ik = innerkey + bl.innerkey_off;
+    for (uint64_t lw = run0 + warp; lw < nw && lw < run0 + TB_WORDS_PER_CTA; lw += 8) {
+        const uint32_t row = (uint32_t)(lw / bl.W), wd = (uint32_t)(lw % bl.W);
+        const int p = wd * 32 + lane;
+        bool bit = false;
+        if (p < bl.B && cs.cz_off != CZ_NONE) {   // gather from the compact table
+            const uint64_t bits = (uint64_t)__ldg(ik + p) << bl.key_shift;   // the point's fields in place
+            uint32_t c = 0;
+            for (int q = 0; q < cs.n_in; ++q) {
+                const int k = cs.in_k[q];
+                c += (uint32_t)((bits & sp->fmask[k]) >> offk[k]) * (uint32_t)cs.in_stride[q];
+            }
+            bit = (__ldg(compact + cs.cz_off + (uint64_t)row * cs.cz_W + (c >> 5)) >> (c & 31)) & 1u;
+        } else if (p < bl.B) {
+            int64_t pv[MAXP];
+            for (int k = 0; k < sp->n; ++k) pv[k] = 0;
+            uint32_t o = row;
+            for (int q = cs.n_outer - 1; q >= 0; --q) {
+                const int k = cs.outer_k[q];
+                const int32_t ikk = (int32_t)(o % rk[k]);
+                o /= rk[k];
+                pv[k] = sp->values[sp->vstart[k] + ikk];
+            }
+            int t = p;
+            for (int k = bl.e - 1; k >= bl.s; --k) {
+                const int32_t ikk = t % rk[k];
+                t /= rk[k];
+                pv[k] = sp->values[sp->vstart[k] + ikk];
+            }
+            bit = vm_eval(sp->prog, cs.pc, cs.len, pv);
+        }
+        const uint32_t word = __ballot_sync(0xffffffffu, bit);
+        if (lane == 0) tables[cs.table_off + lw] = word;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1012,10 +1063,12 @@ static ct_status ensure_tables(ct_space* s, cudaStream_t st) {
         count_launch();
     }
     if (words) {
-        const uint64_t threads = words * 32;
-        const unsigned grid = (unsigned)((threads + 255) / 256);
-        k_build_tables<<<grid, 256, 0, st>>>(s->d, s->d_tab_cons.p, s->d_tab_prefix.p, (int)s->tab_cons.size(),
-                                             words, s->compact.p, s->tables.p);
+        uint64_t runs = 0;   // every constraint's words in runs of TB_WORDS_PER_CTA, one CTA each
+        for (size_t i = 0; i + 1 < s->tab_prefix.size(); ++i)
+            runs += (s->tab_prefix[i + 1] - s->tab_prefix[i] + TB_WORDS_PER_CTA - 1) / TB_WORDS_PER_CTA;
+        if (runs > 0x7fffffffull) { set_error("%llu table runs", (unsigned long long)runs); return CT_ERR_LIMIT; }
+        k_build_tables<<<(unsigned)runs, 256, 0, st>>>(s->d, s->d_tab_cons.p, (int)s->tab_cons.size(), s->d_tab_prefix.p,
+                                                       s->compact.p, s->innerkey.p, s->tables.p);
         count_launch();
         CT_TRY_CUDA(cudaGetLastError());
     }
