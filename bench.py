@@ -50,9 +50,10 @@ CONFIG = {"workload": "large: 16 int params, 51,609,600,000 Cartesian points, 12
 HOST_WARM_S = 1.0   # seconds of continuous host work before a timed region
 
 
-def host_warm(seconds=HOST_WARM_S):
+def host_warm(seconds=None):
     """Busy host for `seconds`: the GPU machines' virtual CPUs slow down while idle (see the
     warm-up note in run_ours), and host-bound timings must not start on a cold CPU."""
+    seconds = HOST_WARM_S if seconds is None else seconds
     t = time.perf_counter()
     while time.perf_counter() - t < seconds:
         pass
@@ -1197,6 +1198,9 @@ if __name__ == "__main__":
                     help="also every sub-metric (repair rules, plain runs, surrogate, aware vs unaware, operator "
                          "variants; minutes), printed as one JSON line before the headline")
     ap.add_argument("--submetrics-out", default=None, help="with --full: also write the sub-metrics line to this file")
+    ap.add_argument("--host-warm", type=float, default=HOST_WARM_S,
+                    help="seconds of continuous host work before each timed region (0 for profiler runs, whose "
+                         "numbers are never bench values)")
     ap.add_argument("--mode", default="step",
                     choices=["step", "scan", "repair", "aware", "variants", "batched", "rules", "surrogate",
                              "surrogate_step", "onepct"],
@@ -1215,6 +1219,7 @@ if __name__ == "__main__":
     ap.add_argument("--radius", type=int, nargs="*", default=None,
                     help="repair mode: ball radius caps to time (default: the cost-model radius)")
     a = ap.parse_args()
+    HOST_WARM_S = a.host_warm
     if a.impl == "reference":
         sys.exit(run_reference(a))
     if a.mode == "aware":

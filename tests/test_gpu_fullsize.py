@@ -25,6 +25,25 @@ def test_medium_full_size_trajectory(oracle_mod, kind):
             raise AssertionError(f"{f} differs first at {bad[0]} ({len(bad)} entries)")
 
 
+@pytest.mark.parametrize("kind", ["de", "pso", "firefly", "ga"])
+def test_medium_full_size_more_seeds(oracle_mod, kind):
+    """Seeds 1, 2 and 3 of the same workload at full length.  The oracle runs of the three seeds
+    go to threads (the oracle's C calls release the interpreter lock), the GPU runs one by one."""
+    from concurrent.futures import ThreadPoolExecutor
+    p = Pair(W.medium_space(), oracle_mod)
+    seeds = (1, 2, 3)
+    with ThreadPoolExecutor(len(seeds)) as ex:
+        futs = {s: ex.submit(oracle_mod.run, kind, p.osp, p.okeys, p.table, 128, 499, s) for s in seeds}
+        traces = {s: step_trace(p, kind, 128, 499, s) for s in seeds}
+        for s in seeds:
+            E, T = futs[s].result(), traces[s]
+            for f in ("cand", "evalk", "fit", "popk", "popf", "best_key", "best_fit", "n_unique"):
+                a, b = T[f], E[f].astype(T[f].dtype)
+                if not np.array_equal(a, b):
+                    bad = np.argwhere(a != b)
+                    raise AssertionError(f"seed {s}: {f} differs first at {bad[0]} ({len(bad)} entries)")
+
+
 def test_batched_full_size(oracle_mod, tmp_path):
     from paper_2606_28372_b300 import catune as ct
     dev = torch.device("cuda", 0)
