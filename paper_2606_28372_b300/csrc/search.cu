@@ -147,15 +147,46 @@ k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, con
     const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t dq = G / points, dj = G - dq * points;
+    // Subsets of at least 16 points on average: a warp's 32 consecutive points span few subsets,
+    // so lane 0 searches its subset and the other lanes step forward from it (the warp stays
+    // together: its lanes run the loop while lane 0 has a point).
+    const bool coop = points >= 16ull * (uint64_t)n_subsets;
+    const int lane = threadIdx.x & 31;
     uint64_t q = g0 / points, j = g0 - q * points;   // (g / points, g % points), stepped with g
-    for (uint64_t g = g0; g < total; g += G, q += dq, j += dj) {
+    for (uint64_t g = g0; coop ? g - lane < total : g < total; g += G, q += dq, j += dj) {
         if (j >= points) { j -= points; ++q; }
-        const uint64_t u = __ldg(cand + pend[q]);
-        int lo = 0, hi = n_subsets - 1;   // last subset with prefix <= j
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(prefix + mid) <= j) lo = mid; else hi = mid - 1;
+        const bool act = g < total;
+        int lo = 0;
+        if (coop) {
+            int hi = n_subsets - 1;   // lane 0: last subset with prefix <= j
+            if (lane == 0) {
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (__ldg(prefix + mid) <= j) lo = mid; else hi = mid - 1;
+                }
+            }
+            const int lo0 = __shfl_sync(0xffffffffu, lo, 0);
+            const uint64_t q0 = __shfl_sync(0xffffffffu, q, 0), j0 = __shfl_sync(0xffffffffu, j, 0);
+            if (act && q == q0 && j >= j0) {
+                lo = lo0;
+                while (lo + 1 < n_subsets && __ldg(prefix + lo + 1) <= j) ++lo;
+            } else if (act) {
+                lo = 0;
+                hi = n_subsets - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (__ldg(prefix + mid) <= j) lo = mid; else hi = mid - 1;
+                }
+            }
+            if (!act) continue;
+        } else {
+            int hi = n_subsets - 1;   // last subset with prefix <= j
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(prefix + mid) <= j) lo = mid; else hi = mid - 1;
+            }
         }
+        const uint64_t u = __ldg(cand + pend[q]);
         const uint32_t S = __ldg(masks + lo);
         if (fail && !fixes_possible(sp, __ldg(fail + pend[q]), S)) continue;
         uint32_t local = (uint32_t)(j - __ldg(prefix + lo));
