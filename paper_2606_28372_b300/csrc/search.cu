@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(256)
 k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, const uint32_t* __restrict__ masks,
        const uint64_t* __restrict__ prefix, int n_subsets, uint64_t points, const uint64_t* __restrict__ cand,
        const int32_t* __restrict__ pend, const uint32_t* __restrict__ count, unsigned long long* __restrict__ best,
-       const uint64_t* __restrict__ fail, const BallNext nx) {
+       const uint64_t* __restrict__ fail, const BallNext nx, uint32_t cmax) {
+    if (*count > cmax) return;   // this radius is k_ball_fs's (many pending candidates): no work, no resolve
     const uint64_t total = (uint64_t)(*count) * points;
     const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -213,6 +214,12 @@ k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, con
 // per (candidate, subset) pays for its plan only on large subsets; smaller ones keep a thread per
 // point).  On the large space that is radius 5 and above.
 constexpr uint64_t BALL_FS_MIN_AVG = 512;
+// Radii whose subsets average between BALL_DUAL_MIN_AVG and BALL_FS_MIN_AVG points take the
+// filtered search when at least BALL_DUAL_MIN_PENDING candidates are pending, the per-point search
+// otherwise (radius 4 of the large space: 256 uniform candidates, 157 pending, 1.19 -> 0.99 ms per
+// repair with the filtered search; 256 perturbed ones, 17 pending, 0.128 -> 0.156 ms).
+constexpr uint64_t BALL_DUAL_MIN_AVG = 128;
+constexpr uint32_t BALL_DUAL_MIN_PENDING = 64;
 
 // The ball search with single-parameter filtering: a warp per (pending candidate, subset); the
 // lanes take the subset's allowed points 32 at a time, test the constraints the masks do not
@@ -221,7 +228,8 @@ __global__ void __launch_bounds__(256)
 k_ball_fs(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, const uint32_t* __restrict__ masks,
           int n_subsets, const uint64_t* __restrict__ cand, const int32_t* __restrict__ pend,
           const uint32_t* __restrict__ count, unsigned long long* __restrict__ best, const uint64_t* __restrict__ fail,
-          const BallNext nx) {
+          const BallNext nx, uint32_t cmin) {
+    if (*count < cmin) return;   // this radius is k_ball's (few pending candidates): no work, no resolve
     const uint64_t total = (uint64_t)(*count) * (uint64_t)n_subsets;
     const int lane = threadIdx.x & 31;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -537,23 +545,33 @@ ct_status repair_launch(const ct_space* s, const RepairPtrs& p, int dmax, const 
     count_launch();
     uint64_t fs_min_avg = BALL_FS_MIN_AVG;   // CATUNE_BALL_FS_MIN_AVG overrides it (tests)
     if (const char* env = getenv("CATUNE_BALL_FS_MIN_AVG")) fs_min_avg = strtoull(env, nullptr, 10);
+    const uint64_t dual_min_avg = std::min<uint64_t>(fs_min_avg, BALL_DUAL_MIN_AVG);
     int cur = 0;
     for (int d = 1; d <= dmax; ++d) {
         const BallRadius& br = s->balls[d - 1];
         // the kernel's last CTA resolves this radius: settles, and queues the rest for the next
         const BallNext nx{p.done, d, d_out, d_dist, p.pend[cur ^ 1], p.cnt[cur ^ 1], p.best[cur ^ 1]};
+        const uint64_t fs_work = (uint64_t)n * br.masks.size() * 32;
+        const unsigned gfs = (unsigned)std::min<uint64_t>((fs_work + 255) / 256, (uint64_t)sms * 4);   // one wave
+        const uint64_t pt_work = (uint64_t)n * br.total;
+        const unsigned gpt = (unsigned)std::min<uint64_t>((pt_work + 255) / 256, (uint64_t)sms * 4);   // one wave
         if (br.total >= fs_min_avg * br.masks.size()) {
             // large subsets: a warp per (candidate, subset) over the filtered points
-            const uint64_t work = (uint64_t)n * br.masks.size() * 32;
-            const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 4);   // one wave
-            k_ball_fs<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, (int)br.masks.size(), d_cand, p.pend[cur],
-                                          p.cnt[cur], p.best[cur], p.fail, nx);
+            k_ball_fs<<<gfs, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, (int)br.masks.size(), d_cand, p.pend[cur],
+                                           p.cnt[cur], p.best[cur], p.fail, nx, 0u);
+        } else if (br.total >= dual_min_avg * br.masks.size()) {
+            // mid-sized subsets: a thread per point while few candidates are pending, the filtered
+            // search from BALL_DUAL_MIN_PENDING on; both are launched and the other one returns
+            k_ball<<<gpt, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
+                                        d_cand, p.pend[cur], p.cnt[cur], p.best[cur], p.fail, nx,
+                                        BALL_DUAL_MIN_PENDING - 1u);
+            k_ball_fs<<<gfs, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, (int)br.masks.size(), d_cand, p.pend[cur],
+                                           p.cnt[cur], p.best[cur], p.fail, nx, BALL_DUAL_MIN_PENDING);
+            count_launch();
         } else {
             // small subsets: a thread per point
-            const uint64_t work = (uint64_t)n * br.total;
-            const unsigned gb = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 4);   // one wave
-            k_ball<<<gb, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
-                                       d_cand, p.pend[cur], p.cnt[cur], p.best[cur], p.fail, nx);
+            k_ball<<<gpt, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, br.d_prefix.p, (int)br.masks.size(), br.total,
+                                        d_cand, p.pend[cur], p.cnt[cur], p.best[cur], p.fail, nx, ~0u);
         }
         count_launch();
         cur ^= 1;
