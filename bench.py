@@ -223,10 +223,14 @@ def job_throughput(units_per_rank_step, world, steps, ms):
     return world * units_per_rank_step * steps / (ms / 1000.0)
 
 
+REF_WINDOWS_PER_PROC, REF_WINDOW = 8, 31_250   # per process and step: 250,000 Cartesian indices
+
+
 def run_reference(args):
     """The reference arm: the oracle, as it stands, on every host core (a spawn-started process
-    pool, one 250,000-point window of the large space per process and step, the windows of a
-    step spread over the whole range), the same metric and workload as our arm."""
+    pool; per process and step, 8 windows of 31,250 Cartesian indices, the windows of a step
+    spread over the whole large space, so that every step meets some valid blocks), the same
+    metric and workload as our arm."""
     import multiprocessing as mp
     world, rank, _ = dist_env()
     if rank != 0:
@@ -235,30 +239,32 @@ def run_reference(args):
     O.build()
     cores = os.cpu_count() or 1
     n_steps = args.steps + args.warmup
-    wins = oracle_windows(cores * n_steps, 250_000, offset_seed=2)
-    step_wins = [wins[s::n_steps] for s in range(n_steps)]   # each step: cores windows over the range
+    per = REF_WINDOWS_PER_PROC
+    wins = oracle_windows(cores * per * n_steps, REF_WINDOW, offset_seed=2)
+    step_wins = [wins[s::n_steps] for s in range(n_steps)]   # each step: cores x per windows over the range
     ctx = mp.get_context("spawn")
     times, found = [], 0
     with ctx.Pool(cores) as pool:
         for s in range(n_steps):
+            shares = [step_wins[s][c::cores] for c in range(cores)]
             t0 = time.perf_counter()
-            res = pool.map(_oracle_window_worker, [[w] for w in step_wins[s]])
+            res = pool.map(_oracle_window_worker, shares)
             dt = time.perf_counter() - t0
             if s >= args.warmup:
                 times.append(dt)
                 found += sum(r[0] for r in res)
     total = sum(times)
     v = found / total
-    sample = (f"{args.steps} steps x {cores} windows x 250,000 Cartesian indices spread over the large space "
-              f"({found} valid found), brute-force oracle enumeration, one window per process on {cores} "
-              f"processes ({cpu_model()})")
+    sample = (f"{args.steps} steps x {cores} processes x {per} windows x {REF_WINDOW:,} Cartesian indices spread "
+              f"over the large space ({found} valid found), brute-force oracle enumeration on {cores} processes "
+              f"({cpu_model()})")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": dict(CONFIG, parallelism=f"replicas x{world}"),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
-        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
     return 0
 
 
