@@ -31,7 +31,9 @@ constexpr uint32_t SL_H32 = 0x80808080u;       // bit 7 of every lane
 constexpr uint32_t SL_B32 = 0x7F7F7F7Fu;       // lane state = 127 + best distance
 
 struct ScanLutPlan {
-    int ng;                            // groups; group g owns table entries [256 g, 256 g + 256)
+    int ng;                            // groups; group g owns table entries [goff[g], goff[g] + mask[g] + 1)
+    int n_entries;                     // entries of all groups
+    int goff[SL_MAX_GROUPS];
     int shift[SL_MAX_GROUPS];          // lowest key bit of the group
     uint32_t mask[SL_MAX_GROUPS];      // (1 << group width) - 1
     int k0[SL_MAX_GROUPS], k1[SL_MAX_GROUPS];   // parameters k0..k1 form the group
@@ -61,22 +63,28 @@ static bool scan_lut_plan(const ct_space* s, ScanLutPlan& pl) {
         pl.mask[g] = (1u << width) - 1u;
         while (k >= 0 && h.w[k] == 0) --k;
     }
+    pl.n_entries = 0;
+    for (int g = 0; g < pl.ng; ++g) {
+        pl.goff[g] = pl.n_entries;
+        pl.n_entries += (int)pl.mask[g] + 1;
+    }
     return pl.ng > 0;
 }
 
-// Tables of one chunk: entry 256 g + x, lane l of set s = number of group g's fields in which the
-// group value x differs from candidate 8 s + l (0 for lanes past the chunk).  One set: [entry].
-// Two or four sets: planes of 16-byte entries (sets 2p and 2p + 1 in plane p), so that the
-// 16-byte reads of one plane by a warp spread over all eight 16-byte bank groups.
-__device__ __forceinline__ size_t sl_index(int S, int ng, int e, int s) {
-    return S == 1 ? (size_t)e : (size_t)(s >> 1) * 512 * ng + (size_t)e * 2 + (s & 1);
+// Tables of one chunk: entry goff[g] + x, lane l of set s = number of group g's fields in which
+// the group value x differs from candidate 8 s + l (0 for lanes past the chunk); the groups'
+// entries are packed (a group of w bits has 2^w of them).  One set: [entry].  Two or four sets:
+// planes of 16-byte entries (sets 2p and 2p + 1 in plane p), so that the 16-byte reads of one
+// plane by a warp spread over all eight 16-byte bank groups.
+__device__ __forceinline__ size_t sl_index(int S, int ne, int e, int s) {
+    return S == 1 ? (size_t)e : (size_t)(s >> 1) * 2 * ne + (size_t)e * 2 + (s & 1);
 }
 __device__ void sl_tables(const DevSpace* __restrict__ sp, const ScanLutPlan& pl, const uint64_t* cq, int nq,
                           int S, unsigned long long* tab) {
-    for (int e = threadIdx.x; e < 256 * pl.ng; e += SL_THREADS) {
-        const int g = e >> 8;
-        const uint32_t x = (uint32_t)e & 255u;
-        if (x > pl.mask[g]) continue;   // never read
+    for (int e = threadIdx.x; e < pl.n_entries; e += SL_THREADS) {
+        int g = 0;
+        while (g + 1 < pl.ng && e >= pl.goff[g + 1]) ++g;
+        const uint32_t x = (uint32_t)(e - pl.goff[g]);
         const uint64_t local = (uint64_t)x << pl.shift[g];
         for (int s = 0; s < S; ++s) {
             unsigned long long word = 0;
@@ -88,22 +96,32 @@ __device__ void sl_tables(const DevSpace* __restrict__ sp, const ScanLutPlan& pl
                 for (int k = pl.k0[g]; k <= pl.k1[g]; ++k) nd += (d & sp->fmask[k]) != 0;
                 word |= (unsigned long long)nd << (8 * l);
             }
-            tab[sl_index(S, pl.ng, e, s)] = word;
+            tab[sl_index(S, pl.n_entries, e, s)] = word;
         }
     }
 }
+
+// Byte addressing of a key's table entries: entry of group g = ((key << 5) >> rs[g]) & mk[g],
+// plus the group's first byte gb[g]; planes `plane` bytes apart.
+template <int NG>
+struct SlAddr {
+    uint32_t rs[NG], mk[NG], gb[NG];
+    uint32_t plane;
+};
 
 // Adds the table entries of groups [G0, G1) of one key (shifted left by 5) to the sums of each
 // set of eight candidates, kept as two 32-bit halves: the lanes never carry or borrow into each
 // other, so the halves are summed and tested independently.
 template <int G0, int G1, int NG, int S>
-__device__ __forceinline__ void sl_add(uint64_t kx, const uint32_t (&rs)[NG], const uint32_t (&mk)[NG],
-                                       const char* __restrict__ tab, uint32_t (&dl)[S], uint32_t (&dh)[S]) {
-    constexpr int LGE = S == 1 ? 3 : 4;             // bytes per entry of a plane: 8 or 16
-    constexpr uint32_t PLANE = 256u * NG << LGE;    // bytes per plane
+__device__ __forceinline__ void sl_add(uint64_t kx, const SlAddr<NG>& ad, const char* __restrict__ tab,
+                                       uint32_t (&dl)[S], uint32_t (&dh)[S]) {
+    constexpr int LGE = S == 1 ? 3 : 4;
 #pragma unroll
     for (int g = G0; g < G1; ++g) {
-        const uint32_t a = ((uint32_t)(kx >> rs[g]) & mk[g]) | ((uint32_t)g << (8 + LGE));
+        // one or two sets: group g at entry 256 g (an OR, and constant plane strides); four sets:
+        // the packed groups (an add)
+        const uint32_t a = S == 4 ? ((uint32_t)(kx >> ad.rs[g]) & ad.mk[g]) + ad.gb[g]
+                                  : ((uint32_t)(kx >> ad.rs[g]) & ad.mk[g]) | ((uint32_t)g << (8 + LGE));
         if (S == 1) {
             const uint2 w = *reinterpret_cast<const uint2*>(tab + a);
             dl[0] += w.x;
@@ -111,7 +129,7 @@ __device__ __forceinline__ void sl_add(uint64_t kx, const uint32_t (&rs)[NG], co
         } else {
 #pragma unroll
             for (int p = 0; p < S / 2; ++p) {
-                const uint4 w = *reinterpret_cast<const uint4*>(tab + a + p * PLANE);
+                const uint4 w = *reinterpret_cast<const uint4*>(tab + a + p * (S == 4 ? ad.plane : 256u * NG << LGE));
                 dl[2 * p] += w.x;
                 dh[2 * p] += w.y;
                 dl[2 * p + 1] += w.z;
@@ -147,8 +165,8 @@ __device__ __forceinline__ void sl_test(uint32_t tag, const uint32_t (&dl)[S], c
 // bits changed; sorted keys keep them for runs of hundreds to thousands of keys) plus its NL low
 // groups' entries.
 template <int NL, int NG, int S>
-__device__ __forceinline__ void sl_dist(uint64_t key, int ushift, uint64_t& ucur, const uint32_t (&rs)[NG],
-                                        const uint32_t (&mk)[NG], const char* __restrict__ tab, uint32_t (&ul)[S],
+__device__ __forceinline__ void sl_dist(uint64_t key, int ushift, uint64_t& ucur, const SlAddr<NG>& ad,
+                                        const char* __restrict__ tab, uint32_t (&ul)[S],
                                         uint32_t (&uh)[S], uint32_t (&dl)[S], uint32_t (&dh)[S]) {
     if (NL < NG) {
         const uint64_t u = key >> ushift;
@@ -156,12 +174,12 @@ __device__ __forceinline__ void sl_dist(uint64_t key, int ushift, uint64_t& ucur
             ucur = u;
 #pragma unroll
             for (int s = 0; s < S; ++s) ul[s] = uh[s] = 0;
-            sl_add<NL, NG, NG, S>(key << 5, rs, mk, tab, ul, uh);
+            sl_add<NL, NG, NG, S>(key << 5, ad, tab, ul, uh);
         }
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) { dl[s] = ul[s]; dh[s] = uh[s]; }
-    sl_add<0, NL, NG, S>(key << 5, rs, mk, tab, dl, dh);
+    sl_add<0, NL, NG, S>(key << 5, ad, tab, dl, dh);
 }
 
 // The pass over the keys for one chunk.  Each warp takes contiguous segments of SL_SEG keys
@@ -182,12 +200,14 @@ __device__ void sl_pass(const uint64_t* __restrict__ keys, int64_t nv, const Sca
     constexpr int ROWS = SL_SEG / 32;
     constexpr int U = S == 4 ? 2 : 4;   // rows per step (their distances first, then their tests); the next
                                         // step's rows are loaded while this one is computed
-    uint32_t rs[NG], mk[NG];
+    SlAddr<NG> ad;
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
-        rs[g] = (uint32_t)(pl.shift[g] + 5 - LGE);
-        mk[g] = pl.mask[g] << LGE;
+        ad.rs[g] = (uint32_t)(pl.shift[g] + 5 - LGE);
+        ad.mk[g] = pl.mask[g] << LGE;
+        ad.gb[g] = (uint32_t)pl.goff[g] << LGE;
     }
+    ad.plane = (uint32_t)pl.n_entries << LGE;
     uint32_t vl[S], vh[S], ul[S], uh[S];
     uint32_t* tg = tags + threadIdx.x;
 #pragma unroll
@@ -225,7 +245,7 @@ __device__ void sl_pass(const uint64_t* __restrict__ keys, int64_t nv, const Sca
                 }
                 uint32_t dl[U][S], dh[U][S];
 #pragma unroll
-                for (int u = 0; u < U; ++u) sl_dist<NL, NG, S>(kk[u], ushift, ucur, rs, mk, tab, ul, uh, dl[u], dh[u]);
+                for (int u = 0; u < U; ++u) sl_dist<NL, NG, S>(kk[u], ushift, ucur, ad, tab, ul, uh, dl[u], dh[u]);
 #pragma unroll
                 for (int u = 0; u < U; ++u) sl_test<S>(m * ROWS + (uint32_t)(j + u), dl[u], dh[u], vl, vh, tg);
             }
@@ -234,7 +254,7 @@ __device__ void sl_pass(const uint64_t* __restrict__ keys, int64_t nv, const Sca
                 const int64_t i = base + (int64_t)j * 32;
                 if (i < nv) {
                     uint32_t dl[S], dh[S];
-                    sl_dist<NL, NG, S>(__ldg(keys + i), ushift, ucur, rs, mk, tab, ul, uh, dl, dh);
+                    sl_dist<NL, NG, S>(__ldg(keys + i), ushift, ucur, ad, tab, ul, uh, dl, dh);
                     sl_test<S>(m * ROWS + (uint32_t)j, dl, dh, vl, vh, tg);
                 }
             }
@@ -272,7 +292,7 @@ __device__ void sl_pass(const uint64_t* __restrict__ keys, int64_t nv, const Sca
 // S = 2 and S = 1 the last chunk when it holds 9..16 or at most 8.  One wave of CTAs, each scanning
 // its slice of the keys once per chunk; the per-S kernels keep the registers (and so the
 // occupancy) of the short candidate sets low.
-template <int S> struct SlBounds { static constexpr int ctas = 2; };
+template <int S> struct SlBounds { static constexpr int ctas = 3; };   // 32 candidates: 80 registers
 template <> struct SlBounds<1> { static constexpr int ctas = 4; };
 template <> struct SlBounds<2> { static constexpr int ctas = 3; };
 
@@ -294,15 +314,24 @@ k_scan_lut(const DevSpace* __restrict__ sp, const uint64_t* __restrict__ keys, i
         sl_tables(sp, pl, cq, nq, S, tab);
         __syncthreads();
         sl_pass<NG, S>(keys, nv, pl, reinterpret_cast<const char*>(tab),
-                       reinterpret_cast<uint32_t*>(tab + (size_t)256 * pl.ng * S), nq, best + q0, red);
+                       reinterpret_cast<uint32_t*>(tab + (size_t)pl.n_entries * S), nq, best + q0, red);
     }
 }
 
 template <int NG, int S>
-static ct_status launch_one(const ct_space* s, const ScanLutPlan& pl, const uint64_t* d_cand, const int32_t* pend,
+static ct_status launch_one(const ct_space* s, const ScanLutPlan& packed, const uint64_t* d_cand, const int32_t* pend,
                             const uint32_t* count, unsigned long long* best, cudaStream_t st, int sms) {
+    // Four sets: the groups' entries packed (the large space: 704 entries instead of 1,536), so
+    // that three CTAs fit an SM (2.38 -> 2.29 ms for 32 candidates).  One or two sets: each group
+    // at a multiple of 256 entries, which measured faster there (0.90 / 1.27 ms for 4 / 16
+    // candidates against 0.93 / 1.35 packed).
+    ScanLutPlan pl = packed;
+    if (S < 4) {
+        for (int g = 0; g < pl.ng; ++g) pl.goff[g] = 256 * g;
+        pl.n_entries = 256 * pl.ng;
+    }
     constexpr size_t TAGS = (size_t)8 * S * SL_THREADS * sizeof(uint32_t);
-    const size_t smem = (size_t)256 * pl.ng * S * sizeof(unsigned long long) + TAGS;
+    const size_t smem = (size_t)pl.n_entries * S * sizeof(unsigned long long) + TAGS;
     constexpr size_t SMEM_CAP = (size_t)SL_MAX_GROUPS * 256 * S * sizeof(unsigned long long) + TAGS;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
