@@ -117,7 +117,7 @@ __global__ void k_mlp_l1(const float* __restrict__ p, MlpOff o, int D, int H, in
 // EPI 0: z = acc + bias[n] -> out (z) and out2 (ReLU);  EPI 1: out = zmask > 0 ? acc : 0;
 // EPI 2: out = acc (and, with rowsum, rowsum[m] = sum_{k ascending} A(m,k), added from 0: the
 // bias gradients, by the threads of column 0);  EPI 3: out = acc + bias[n].
-constexpr int OG_T = 16, OG_K = 32, OG_THREADS = OG_T * OG_T, OG_PER = OG_T * OG_K / OG_THREADS;
+constexpr int OG_T = 16, OG_K = 64, OG_THREADS = OG_T * OG_T, OG_PER = OG_T * OG_K / OG_THREADS;
 
 template <int EPI, bool BF16>
 __global__ void __launch_bounds__(OG_THREADS)
