@@ -561,13 +561,18 @@ k_pcount(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parent
 
 __global__ void __launch_bounds__(PE_THREADS)
 k_pemit(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents, uint64_t F,
-        const unsigned long long* __restrict__ Fd, uint32_t pt, const unsigned long long* __restrict__ tile_base,
-        const unsigned long long* __restrict__ total, unsigned long long expect, uint64_t* __restrict__ out) {
+        const unsigned long long* __restrict__ Fd, uint32_t pt, uint32_t sub,
+        const unsigned long long* __restrict__ tile_base, const unsigned long long* __restrict__ total,
+        unsigned long long expect, uint64_t* __restrict__ out) {
     __shared__ uint32_t off_s[PE_THREADS], cnt_s[PE_THREADS], sig_s[PE_THREADS];
     __shared__ uint64_t par_s[PE_THREADS];
     __shared__ uint32_t wsum[PE_THREADS / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const uint64_t i0 = (uint64_t)blockIdx.x * pt;
+    // the CTA's scan tile of pt parents and its part of sub parents in it
+    const uint32_t parts = pt / sub;
+    const uint64_t tile = blockIdx.x / parts;
+    const uint32_t part = blockIdx.x - (uint32_t)(tile * parts);
+    const uint64_t i0 = tile * pt;
     if (Fd) {   // launched for an upper bound: the level's own size
         F = *Fd;
         if (i0 >= F) return;
@@ -594,34 +599,36 @@ k_pemit(const __grid_constant__ PatArgs pa, const uint64_t* __restrict__ parents
     sig_s[t] = sg;
     par_s[t] = parent;
     __syncthreads();
-    const uint64_t tb = tile_base[blockIdx.x];
+    const uint64_t tb = tile_base[tile];
     if (expect != ~0ull && *total != expect) return;   // launched for another level size: write nothing
-    const int np = (int)min((uint64_t)pt, F - i0);
-    for (int p = warp; p < np; p += PE_THREADS / 32) {
+    const int np = (int)min((uint64_t)(part + 1) * sub, min((uint64_t)pt, F - i0));
+    // wpp warps per parent (sub < 8) take its 32-key rows in turn
+    constexpr int NW = PE_THREADS / 32;
+    const int wpp = sub < NW ? NW / (int)sub : 1;
+    const uint32_t S = 32u * (uint32_t)wpp;
+    for (int p = (int)(part * sub) + warp / wpp; p < np; p += NW / wpp) {
         const uint32_t cp = cnt_s[p];
         const uint64_t par = par_s[p];
         const uint32_t* __restrict__ lst = pa.list + (uint64_t)sig_s[p] * pa.Bpad;
         uint64_t* __restrict__ o = out + tb + off_s[p];
-        uint32_t jj = lane;
-        for (; jj + 96 < cp; jj += 128) {   // four independent 32-key rows per iteration
-            const uint32_t a0 = __ldg(lst + jj), a1 = __ldg(lst + jj + 32), a2 = __ldg(lst + jj + 64),
-                           a3 = __ldg(lst + jj + 96);
+        uint32_t jj = (uint32_t)(warp % wpp) * 32u + lane;
+        for (; jj + 3 * S < cp; jj += 4 * S) {   // four independent 32-key rows per iteration
+            const uint32_t a0 = __ldg(lst + jj), a1 = __ldg(lst + jj + S), a2 = __ldg(lst + jj + 2 * S),
+                           a3 = __ldg(lst + jj + 3 * S);
             // streaming stores: the keys are written once per build, the pattern lists stay in L2
             __stcs(reinterpret_cast<unsigned long long*>(o + jj), par | ((uint64_t)a0 << pa.key_shift));
-            __stcs(reinterpret_cast<unsigned long long*>(o + jj + 32), par | ((uint64_t)a1 << pa.key_shift));
-            __stcs(reinterpret_cast<unsigned long long*>(o + jj + 64), par | ((uint64_t)a2 << pa.key_shift));
-            __stcs(reinterpret_cast<unsigned long long*>(o + jj + 96), par | ((uint64_t)a3 << pa.key_shift));
+            __stcs(reinterpret_cast<unsigned long long*>(o + jj + S), par | ((uint64_t)a1 << pa.key_shift));
+            __stcs(reinterpret_cast<unsigned long long*>(o + jj + 2 * S), par | ((uint64_t)a2 << pa.key_shift));
+            __stcs(reinterpret_cast<unsigned long long*>(o + jj + 3 * S), par | ((uint64_t)a3 << pa.key_shift));
         }
-        for (; jj < cp; jj += 32)
+        for (; jj < cp; jj += S)
             __stcs(reinterpret_cast<unsigned long long*>(o + jj), par | ((uint64_t)__ldg(lst + jj) << pa.key_shift));
     }
 }
 
-// Parents per CTA of the pattern count and emit kernels: halved from 256 (down to 8) until the
-// grid has about 64 CTAs per SM.  Short parent lists would otherwise leave SMs idle (with 256
-// per CTA a level of 6,032 parents ran on 24 CTAs), and on long ones many small CTAs even out
-// the uneven child counts of the parents: the large space's last level (1.14M parents) emits in
-// 0.864 ms with 64 per CTA, 0.895 with 128 and 0.930 with 256.
+// Parents per scan tile of the pattern count and emit kernels: halved from 256 (down to 8) until
+// the grid has about 64 tiles per SM, so that short parent lists still fill the SMs (with 256 per
+// tile a level of 6,032 parents ran on 24 CTAs).
 static uint64_t pattern_tile(uint64_t F) {
     int sms = 148, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -629,6 +636,15 @@ static uint64_t pattern_tile(uint64_t F) {
     while (pt > 8 && (F + pt - 1) / pt < (uint64_t)sms * 64) pt >>= 1;
     return pt;
 }
+
+// Parents per emit CTA: each emit CTA takes PE_SUB parents of its scan tile, one warp per parent,
+// after scanning the whole tile's counts for their offsets.  Small CTAs keep the output the SMs
+// write at one time short and even out the uneven child counts: the large space's last level
+// (1.14M parents, scan tiles of 64) emits in 0.778 ms with 8 parents per CTA against 0.877 ms
+// with 64 (8 per warp); 4 and 2 parents per CTA, with 2 and 4 warps sharing a parent's rows, took
+// 1.03 and 1.73 ms.
+constexpr uint64_t PE_SUB = 8;
+static uint64_t emit_sub(uint64_t pt) { return pt < PE_SUB ? pt : PE_SUB; }
 
 // ---------------------------------------------------------------------------
 // host: lowering
@@ -1247,7 +1263,8 @@ static ct_status build_levels(ct_space* s, cudaStream_t st, bool hinted, bool* o
         const uint64_t per_tile = bl.pattern ? pattern_tile(F) : EXP_TILE;
         const uint64_t tiles = (items + per_tile - 1) / per_tile;
         const uint64_t count_ctas = bl.pattern ? (F + PE_THREADS - 1) / PE_THREADS : tiles;
-        if (tiles > 0x7fffffffull || count_ctas > 0x7fffffffull) {
+        const uint64_t emit_ctas = bl.pattern ? tiles * (per_tile / emit_sub(per_tile)) : tiles;
+        if (emit_ctas > 0x7fffffffull || count_ctas > 0x7fffffffull) {
             set_error("level %d needs %llu tiles", j, (unsigned long long)tiles);
             return CT_ERR_LIMIT;
         }
@@ -1287,8 +1304,9 @@ static ct_status build_levels(ct_space* s, cudaStream_t st, bool hinted, bool* o
             const unsigned long long expect = hinted ? (unsigned long long)Fn : ~0ull;
             if (s->timing) CT_TRY_CUDA(cudaEventRecord(s->events[4 * j + 2], st));
             if (bl.pattern)
-                k_pemit<<<(unsigned)tiles, PE_THREADS, 0, st>>>(pa, parents, F, Fd, (uint32_t)per_tile, s->tile_base.p,
-                                                                total, expect, dst.p);
+                k_pemit<<<(unsigned)emit_ctas, PE_THREADS, 0, st>>>(
+                    pa, parents, F, Fd, (uint32_t)per_tile, (uint32_t)emit_sub(per_tile), s->tile_base.p, total, expect,
+                    dst.p);
             else
                 k_expand_emit<<<(unsigned)tiles, EXP_THREADS, EXP_THREADS * 32 * sizeof(uint64_t), st>>>(
                     s->d, s->tables.p, s->innerkey.p, j, parents, items, Fd, s->tile_base.p, total, expect, dst.p);
