@@ -885,8 +885,11 @@ def run_scan(args):
         gbs = 8 * nv / (ms / 1000.0) / 1e9
         res[f"q{q}"] = {"ms_per_call": ms, "key_stream_GBps": gbs, "frac_of_copy_peak": gbs / hbm,
                         "pairs_per_s": nv * q / (ms / 1000.0)}
+    smem = ct.measure_smem_peak()
     print(json.dumps({"mode": "scan", "workload": args.workload, "n_valid": nv, "peak_GBps": hbm,
-                      "peak_kind": kind, "results": res}))
+                      "peak_kind": kind, "smem_wavefront_peak_per_s": smem,
+                      "smem_peak_kind": "measured: ct_measure_smem_peak (16-byte shared loads, every SM)",
+                      "results": res}))
     return 0
 
 

@@ -507,6 +507,12 @@ ct_status ct_measure_int_peak(double *popc_per_s, ct_stream stream);
  * floating-point operations per second, two per fused multiply-add (synchronises). */
 ct_status ct_measure_fp32_peak(double *flop_per_s, ct_stream stream);
 
+/* Denominator of the distance-table scan (bound by shared-memory loads): runs a microbenchmark
+ * in which every warp reads 32 consecutive 16-byte entries of shared memory per load (four
+ * 128-byte wavefronts, no bank conflict), four independent loads per step, over every SM of the
+ * current device, and writes shared-memory wavefronts per second (synchronises). */
+ct_status ct_measure_smem_peak(double *wavefronts_per_s, ct_stream stream);
+
 /* Number of kernels this library has launched in this process (all devices). */
 uint64_t ct_launch_count(void);
 

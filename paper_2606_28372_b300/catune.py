@@ -133,6 +133,7 @@ _SIGS = {
     "ct_space_build_stats": [C.c_void_p, C.c_void_p],
     "ct_measure_int_peak": [C.POINTER(C.c_double), C.c_void_p],
     "ct_measure_fp32_peak": [C.POINTER(C.c_double), C.c_void_p],
+    "ct_measure_smem_peak": [C.POINTER(C.c_double), C.c_void_p],
     "ct_launch_count": [],
     "ct_alloc_count": [],
     "ct_trim_cache": [],
@@ -409,6 +410,14 @@ def measure_fp32_peak(stream=None):
     denominator of the surrogate's CUDA-core products)."""
     v = C.c_double()
     check(lib().ct_measure_fp32_peak(C.byref(v), _stream(stream)))
+    return float(v.value)
+
+
+def measure_smem_peak(stream=None):
+    """Shared-memory wavefronts per second of the library's 16-byte shared-load microbenchmark
+    (the denominator of the distance-table scan)."""
+    v = C.c_double()
+    check(lib().ct_measure_smem_peak(C.byref(v), _stream(stream)))
     return float(v.value)
 
 
