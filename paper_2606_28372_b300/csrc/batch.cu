@@ -110,8 +110,33 @@ struct RepairSmem {
     int32_t pend[BATCH_MAX_POP];
     unsigned long long best[BATCH_MAX_POP];
     uint64_t fail[BATCH_MAX_POP];   // per pending slot: the constraints the candidate fails
+    uint64_t pstart[BATCH_MAX_THREADS];   // first ball point of each thread's (candidate, subset) pair
+    uint64_t wsum[BATCH_MAX_THREADS / 32];
     int npend;
 };
+
+// Exclusive prefix sum of v over the CTA into start[threadIdx.x]; returns the total.  Every
+// thread calls it; blockDim.x is a multiple of 32.
+__device__ __forceinline__ uint64_t cta_exclusive_scan(uint64_t v, uint64_t* start, uint64_t* wsum) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = (int)(blockDim.x >> 5);
+    uint64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    uint64_t base = 0, total = 0;
+    for (int i = 0; i < nw; ++i) {
+        const uint64_t x = wsum[i];
+        if (i < w) base += x;
+        total += x;
+    }
+    start[t] = base + inc - v;
+    __syncthreads();
+    return total;
+}
 
 // The in-CTA exhaustive scan with per-candidate distance tables (as the repair's table scan):
 // for every group value, how many of the group's fields differ from each candidate, eight
@@ -249,33 +274,44 @@ __device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t*
         const uint32_t* masks = bs.masks[d - 1];
         const uint64_t* prefix = bs.prefix[d - 1];
         const int nsub = bs.n_subsets[d - 1];
-        const uint64_t total = (uint64_t)np * pts;
-        const uint64_t dq = (uint64_t)nt / pts, dj = (uint64_t)nt - dq * pts;
-        uint64_t q = (uint64_t)t / pts, j = (uint64_t)t - q * pts;   // (g / pts, g % pts), stepped with g
-        for (uint64_t g = t; g < total; g += nt, q += dq, j += dj) {
-            if (j >= pts) { j -= pts; ++q; }
-            const uint64_t u = cand[rs.pend[q]];
-            int lo = 0, hi = nsub - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(prefix + mid) <= j) lo = mid; else hi = mid - 1;
+        // The (pending candidate, subset) pairs, one per thread at a time: a subset that cannot
+        // fix every constraint the candidate fails holds no valid point, so only the points of
+        // the other pairs are generated, spread evenly over the threads.
+        const uint64_t npairs = (uint64_t)np * (uint64_t)nsub;
+        for (uint64_t p0 = 0; p0 < npairs; p0 += (uint64_t)nt) {
+            uint64_t size = 0;
+            if (p0 + t < npairs) {
+                const uint32_t q = (uint32_t)((p0 + t) / (uint64_t)nsub);
+                const int s = (int)(p0 + t - (uint64_t)q * nsub);
+                if (fixes_possible(sp, rs.fail[q], __ldg(masks + s)))
+                    size = (s + 1 < nsub ? __ldg(prefix + s + 1) : pts) - __ldg(prefix + s);
             }
-            const uint32_t S = __ldg(masks + lo);
-            if (!fixes_possible(sp, rs.fail[q], S)) continue;   // no point of S can be valid
-            uint32_t local = (uint32_t)(j - __ldg(prefix + lo));
-            uint32_t m = S;
-            uint64_t key = u;
-            while (m) {
-                const int k = 31 - __clz(m);
-                m &= ~(1u << k);
-                uint32_t a;
-                local = div_alt(sp, k, local, &a);
-                const uint32_t uk = (uint32_t)field(sp, u, k);
-                key = (key & ~sp->fmask[k]) | ((uint64_t)(a < uk ? a : a + 1u) << sp->off[k]);
+            const uint64_t T = cta_exclusive_scan(size, rs.pstart, rs.wsum);
+            for (uint64_t g = t; g < T; g += (uint64_t)nt) {
+                int lo = 0, hi = nt - 1;   // the pair holding point g: the last with start <= g
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (rs.pstart[mid] <= g) lo = mid; else hi = mid - 1;
+                }
+                const uint32_t q = (uint32_t)((p0 + lo) / (uint64_t)nsub);
+                const int s = (int)(p0 + lo - (uint64_t)q * nsub);
+                const uint64_t u = cand[rs.pend[q]];
+                const uint32_t S = __ldg(masks + s);
+                uint32_t local = (uint32_t)(g - rs.pstart[lo]);
+                uint32_t m = S;
+                uint64_t key = u;
+                while (m) {
+                    const int k = 31 - __clz(m);
+                    m &= ~(1u << k);
+                    uint32_t a;
+                    local = div_alt(sp, k, local, &a);
+                    const uint32_t uk = (uint32_t)field(sp, u, k);
+                    key = (key & ~sp->fmask[k]) | ((uint64_t)(a < uk ? a : a + 1u) << sp->off[k]);
+                }
+                // the atomic only when the key beats the candidate's current best
+                if (key < *(volatile unsigned long long*)&rs.best[q] && valid_changed(sp, bs.tables, key, S))
+                    atomicMin(&rs.best[q], (unsigned long long)key);
             }
-            // the atomic only when the key beats the candidate's current best
-            if (key < *(volatile unsigned long long*)&rs.best[q] && valid_changed(sp, bs.tables, key, S))
-                atomicMin(&rs.best[q], (unsigned long long)key);
         }
         __syncthreads();
         if (t == 0) {
