@@ -358,13 +358,17 @@ __device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t*
     }
 }
 
-__global__ void __launch_bounds__(BATCH_MAX_THREADS, 2) k_batch_gen(const __grid_constant__ BatchArgs ba) {
+__global__ void __launch_bounds__(BATCH_MAX_THREADS, 3) k_batch_gen(const __grid_constant__ BatchArgs ba) {
     extern __shared__ __align__(16) unsigned long long lut_tab[];   // the table scan's tables
     __shared__ uint64_t cand[BATCH_MAX_POP], rep[BATCH_MAX_POP];
     __shared__ float fit[BATCH_MAX_POP];
     __shared__ int order[BATCH_MAX_POP];
     __shared__ SelectSmemT<BATCH_MAX_THREADS, BATCH_MAX_POP> sel;
-    __shared__ RepairSmem rsm;
+    __shared__ union {   // the repair's scratch, then the GA mutation's
+        RepairSmem rs;
+        GaMutSmemT<BATCH_MAX_POP> gm;
+    } scr;
+    RepairSmem& rsm = scr.rs;
     __shared__ EventSmem evs;
     __shared__ int slot_s;
     const uint32_t gen = *ba.gen;
@@ -390,7 +394,7 @@ __global__ void __launch_bounds__(BATCH_MAX_THREADS, 2) k_batch_gen(const __grid
             cta_repair(bs, cand, rep, P, rsm, lut_tab, ba.scan_tags + (size_t)blockIdx.x * BATCH_LUT_CHUNK * blockDim.x);
         else for (int i = threadIdx.x; i < P; i += blockDim.x) rep[i] = cand[i];
         __syncthreads();
-        post_repair_dev(a, gen, rep);
+        post_repair_dev(a, gen, rep, scr.gm);
         __syncthreads();
         uint32_t* memo = ba.memo + run.off_memo;
         for (int i = threadIdx.x; i < P; i += blockDim.x) {

@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(OPT_THREADS) k_propose(OptArgs a, uint32_t gen
 }
 
 __global__ void __launch_bounds__(OPT_THREADS) k_post_repair(OptArgs a, uint32_t gen_arg, int use_dev, uint64_t* __restrict__ keys) {
-    post_repair_dev(a, gen_of(a, gen_arg, use_dev), keys);
+    __shared__ GaMutSmem gm;
+    post_repair_dev(a, gen_of(a, gen_arg, use_dev), keys, gm);
 }
 
 __global__ void __launch_bounds__(OPT_THREADS) k_select(OptArgs a, uint32_t gen_arg, int use_dev, const uint64_t* __restrict__ keys,

@@ -371,7 +371,20 @@ __device__ __forceinline__ uint64_t ga_neighbour(const DevSpace* __restrict__ sp
     return (u & ~sp->fmask[k]) | ((uint64_t)v << sp->off[k]);
 }
 
-static __device__ void post_repair_dev(const OptArgs& a, uint32_t gen, uint64_t* __restrict__ keys, int s = 0) {
+// Shared scratch of the GA mutation's flat form (populations of at most MAX_POP).
+constexpr int GA_MUT_WORDS = 4;   // at most 128 Hamming-1 neighbours per point
+template <int MAX_POP>
+struct GaMutSmemT {
+    uint32_t ok[MAX_POP][GA_MUT_WORDS];   // bit n: neighbour n of the slot's candidate is valid
+    int32_t idx[MAX_POP];                  // population index of each mutated candidate
+    uint32_t draw[MAX_POP];                // its draw for the choice among the valid neighbours
+    int n;
+};
+using GaMutSmem = GaMutSmemT<CT_MAX_POP>;
+
+template <class GM>
+static __device__ void post_repair_dev(const OptArgs& a, uint32_t gen, uint64_t* __restrict__ keys, GM& gm,
+                                       int s = 0) {
     if (a.kind != CT_GA || gen == 0) return;
     const DevSpace* sp = a.sp;
     if (!a.prm.constraint_aware) {   // baseline: one random parameter takes another value
@@ -389,6 +402,52 @@ static __device__ void post_repair_dev(const OptArgs& a, uint32_t gen, uint64_t*
     }
     uint32_t total = 0;   // Hamming-1 neighbours of any point
     for (int k = 0; k < a.N; ++k) total += (uint32_t)(sp->r[k] - 1);
+    if (total <= 32u * GA_MUT_WORDS) {
+        // Flat form: the mutated candidates into a list, every (candidate, neighbour) pair tested
+        // by one thread (a bit per valid neighbour), then per candidate the chosen valid
+        // neighbour, counted in neighbour order as below.
+        if (threadIdx.x == 0) gm.n = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < a.P; i += blockDim.x) {
+            uint32_t w[4];
+            rng_block(a.seed, (uint32_t)(i + s * a.P), gen, PU_GA_MUT, 0, w);
+            if (!(u01(w[0]) < a.prm.ga_pmut)) continue;
+            const int m = atomicAdd(&gm.n, 1);
+            gm.idx[m] = i;
+            gm.draw[m] = w[1];
+#pragma unroll
+            for (int q = 0; q < GA_MUT_WORDS; ++q) gm.ok[m][q] = 0u;
+        }
+        __syncthreads();
+        const uint32_t nm = (uint32_t)gm.n;
+        for (uint32_t f = threadIdx.x; f < nm * total; f += blockDim.x) {
+            const uint32_t m = f / total, nb = f - m * total;
+            int k;
+            const uint64_t kk = ga_neighbour(sp, keys[gm.idx[m]], a.N, nb, &k);
+            if (valid_changed(sp, a.tables, kk, 1u << k)) atomicOr(&gm.ok[m][nb >> 5], 1u << (nb & 31));
+        }
+        __syncthreads();
+        for (uint32_t m = threadIdx.x; m < nm; m += blockDim.x) {
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int q = 0; q < GA_MUT_WORDS; ++q) cnt += (uint32_t)__popc(gm.ok[m][q]);
+            if (!cnt) continue;
+            uint32_t pick = uint_below(gm.draw[m], cnt);
+            for (int q = 0; q < GA_MUT_WORDS; ++q) {
+                uint32_t bal = gm.ok[m][q];
+                const uint32_t c = (uint32_t)__popc(bal);
+                if (pick < c) {   // the pick-th valid neighbour lies in this word
+                    for (uint32_t t = 0; t < pick; ++t) bal &= bal - 1u;
+                    int k;
+                    const int i = gm.idx[m];
+                    keys[i] = ga_neighbour(sp, keys[i], a.N, 32u * (uint32_t)q + (uint32_t)(__ffs(bal) - 1), &k);
+                    break;
+                }
+                pick -= c;
+            }
+        }
+        return;
+    }
     const int lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
     for (int i = (int)(threadIdx.x >> 5); i < a.P; i += nw) {
         uint32_t w[4];

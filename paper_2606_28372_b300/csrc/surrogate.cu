@@ -536,7 +536,8 @@ __global__ void __launch_bounds__(256) k_propose_pool(OptArgs a, uint32_t gen, u
 }
 
 __global__ void __launch_bounds__(256) k_post_pool(OptArgs a, uint32_t gen, uint64_t* __restrict__ keys) {
-    post_repair_dev(a, gen, keys + (size_t)blockIdx.x * a.P, (int)blockIdx.x);
+    __shared__ GaMutSmem gm;
+    post_repair_dev(a, gen, keys + (size_t)blockIdx.x * a.P, gm, (int)blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_select_s(OptArgs a, uint32_t gen, const uint64_t* __restrict__ keys,
