@@ -253,9 +253,16 @@ __device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t*
     const int t = threadIdx.x, nt = blockDim.x;
     if (t == 0) rs.npend = 0;
     __syncthreads();
-    for (int i = t; i < P; i += nt) {
+    // the table test by groups of G lanes (as many as the population leaves room for), each lane
+    // testing every G-th constraint
+    int G = 1;
+    while (G < 32 && 2 * G * P <= nt) G <<= 1;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((t & 31) & ~(G - 1)));
+    for (int i = t / G; i < P; i += nt / G) {
         const uint64_t c = cand[i];
-        const uint64_t f = failing_mask(sp, bs.tables, c);
+        uint64_t f = failing_mask_part(sp, bs.tables, c, t & (G - 1), G);
+        for (int o = 1; o < G; o <<= 1) f |= __shfl_xor_sync(gmask, f, o);
+        if (t & (G - 1)) continue;
         if (!f) {
             rep[i] = c;
         } else {

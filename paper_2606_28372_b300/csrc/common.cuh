@@ -297,6 +297,25 @@ __device__ __forceinline__ uint64_t failing_mask(const DevSpace* __restrict__ sp
     return f;
 }
 
+// The constraints c = part (mod G) that an in-domain key fails (G a power of two): G lanes with
+// parts 0 .. G - 1 together give failing_mask.
+__device__ __forceinline__ uint64_t failing_mask_part(const DevSpace* __restrict__ sp,
+                                                      const uint32_t* __restrict__ tables, uint64_t key, int part,
+                                                      int G) {
+    uint64_t f = 0;
+    const int nb = sp->n_blocks;
+    for (int j = 0; j < nb; ++j) {
+        const DevBlock& bl = sp->blocks[j];
+        int c = bl.cons_begin + ((part - bl.cons_begin) & (G - 1));
+        if (c >= bl.cons_end) continue;
+        int32_t p = 0;
+        for (int k = bl.s; k < bl.e; ++k) p += field(sp, key, k) * bl.pstride[k - bl.s];
+        for (; c < bl.cons_end; c += G)
+            if (!cons_holds(sp, tables, key, bl, c, p)) f |= 1ull << c;
+    }
+    return f;
+}
+
 // Changing the parameters of S leaves every constraint that reads none of them as it was.  So
 // a point that differs from a candidate exactly in S can be valid only if each constraint the
 // candidate fails reads a parameter of S ...
@@ -309,13 +328,16 @@ __device__ __forceinline__ bool fixes_possible(const DevSpace* __restrict__ sp, 
     return true;
 }
 
-// ... and then it is valid iff the constraints reading a parameter of S hold at it.
+// ... and then it is valid iff the constraints reading a parameter of S hold at it (the union of
+// the parameters' constraint masks; only those constraints are visited).
 __device__ __forceinline__ bool valid_changed(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables,
                                               uint64_t key, uint32_t S) {
-    const int nc = sp->n_cons;
-    for (int c = 0; c < nc; ++c) {
+    uint64_t cm = 0;
+    for (uint32_t m = S; m; m &= m - 1u) cm |= sp->pcons[__ffs((int)m) - 1];
+    while (cm) {
+        const int c = __ffsll((long long)cm) - 1;
+        cm &= cm - 1;
         const DevCons& cs = sp->cons[c];
-        if (!(cs.scope & S)) continue;
         if (cs.cz_off != CZ_NONE) {
             if (!cons_holds_compact(sp, cs, key)) return false;
             continue;
