@@ -624,12 +624,13 @@ static void batch_lut_plan(const ct_space* s, BatchSpace& b) {
     b.lut_ng = ng;
 }
 
-// Ball radius of the in-CTA repair: the ball is cut where its cumulative size passes |V| / 8,
-// never below radius 1; an explicit ct_set_repair_mode on the space takes precedence.  With the
-// failing-constraint pruning a ball point is cheap, and on the 4096-run batched workload the
-// cut at |V| / 4 .. |V| / 16 is flat (2.84-2.88 ms per generation) against 3.19 at |V| / 32 and
-// 3.26 at |V| / 1.
-constexpr double BATCH_BALL_DIV = 8.0;   // |V| / 4 .. |V| / 8 measured flat, |V| / 32 5 % slower
+// Ball radius of the in-CTA repair: the ball is cut where its cumulative size passes 2 |V|,
+// never below radius 1; an explicit ct_set_repair_mode on the space takes precedence.  Only the
+// (candidate, subset) pairs that can fix the candidate's failing constraints generate points, so
+// a ball point is cheap against the scan of every key that a candidate past the cut needs: on the
+// 4096-run batched workload (100 generations, one launch) the cut at |V| / 8 took 97.0 ms, |V| / 2
+// 95.8, 2 |V| 87.8, 8 |V| and 32 |V| 89.3 (same results).
+constexpr double BATCH_BALL_DIV = 0.5;
 static int batch_radius(const ct_space* sp) {
     if (sp->repair_mode != 0) return wanted_radius(sp);
     return std::max(auto_radius(sp, BATCH_BALL_DIV), std::min(1, sp->ball_max));
