@@ -1,5 +1,6 @@
-"""GPU parity of the batched form: each run of one persistent launch per generation equals the
-same run done alone (and the oracle), for every optimizer, population and space size."""
+"""GPU parity of the batched form: each run of the persistent launches (one generation per
+launch, or many generations of each run per launch) equals the same run done alone (and the
+oracle), for every optimizer, population and space size."""
 import numpy as np
 import pytest
 import torch
@@ -37,7 +38,7 @@ def _single(pair, kind, pop, seed, target, gens):
     return from_dev_u64(k), f.cpu().numpy(), o.best()
 
 
-@pytest.mark.parametrize("mode", ["step", "graph"])
+@pytest.mark.parametrize("mode", ["step", "graph", "mixed"])
 def test_batch_equals_single_runs(spaces, mode):
     from paper_2606_28372_b300 import catune as ct
     runs = _runs(spaces, 24)
@@ -46,9 +47,15 @@ def test_batch_equals_single_runs(spaces, mode):
     if mode == "step":
         for _ in range(gens):
             b.step()
-    else:
+    elif mode == "graph":
         b.run_graph(1)
         b.run_graph(gens - 1)
+    else:   # launches of 1, 4 and 3 generations in turn
+        for _ in range(3):
+            b.step()
+        b.run_graph(4)
+        b.step()
+        b.run_graph(4)
     res = b.results()
     for r, (si, kind, pop, seed, tgt) in enumerate(runs):
         k = torch.empty(pop, dtype=torch.int64, device="cuda")
