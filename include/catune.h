@@ -406,9 +406,10 @@ ct_status ct_mlp_sgd(float *d_params, float *d_mom, const float *d_grad, int64_t
 /* batched runs                                                              */
 /* ------------------------------------------------------------------------- */
 /* Many independent runs of the optimizers above (Sections IV-B..IV-D) over
- * several built spaces, advanced together: one persistent kernel launch per
- * generation in which each CTA takes whole runs from a work list and performs
- * propose, repair, GA mutation, memoised evaluation and selection on chip.
+ * several built spaces, advanced together by one persistent kernel launch in
+ * which each CTA takes whole runs from a work list and carries each through the
+ * launch's generations (propose, repair, GA mutation, memoised evaluation and
+ * selection on chip) before it takes the next.
  * Every run gives exactly the trajectory ct_opt gives for the same space, kind,
  * population, seed and parameters.  Population per run: 3..256. */
 typedef struct {
@@ -429,7 +430,8 @@ ct_status ct_batch_create(ct_space *const *spaces, int32_t n_spaces, const ct_ba
 void ct_batch_destroy(ct_batch *batch);
 /* One generation for every run (generation 0 first). Asynchronous. */
 ct_status ct_batch_step(ct_batch *batch, ct_stream stream);
-/* `count` generations as one CUDA graph (captured once per count, replayed). */
+/* `count` generations of every run in one launch (captured once per count as a
+ * one-node CUDA graph, replayed). Asynchronous. */
 ct_status ct_batch_run_graph(ct_batch *batch, uint32_t count, ct_stream stream);
 /* Per-run summaries into host arrays of n_runs entries (each may be NULL). Synchronises. */
 ct_status ct_batch_results(ct_batch *batch, uint64_t *best_key, float *best_fit, uint64_t *n_unique,
