@@ -135,6 +135,8 @@ __device__ __forceinline__ void ball_resolve_last(const BallNext& nx, const int3
     if (threadIdx.x == 0) *nx.done = 0;   // for the next launch
 }
 
+constexpr int BALL_SMEM_SUBSETS = 2048;   // subsets whose table k_ball stages in shared memory
+
 // every point at Hamming distance exactly d of each pending candidate; with the candidates'
 // failing-constraint masks, subsets that cannot fix them are skipped and only the constraints
 // reading a changed parameter are tested
@@ -144,6 +146,20 @@ k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, con
        const int32_t* __restrict__ pend, const uint32_t* __restrict__ count, unsigned long long* __restrict__ best,
        const uint64_t* __restrict__ fail, const BallNext nx, uint32_t cmax) {
     if (*count > cmax) return;   // this radius is k_ball_fs's (many pending candidates): no work, no resolve
+    // the radius's subset table in shared memory when it fits: the per-point subset search then
+    // waits for shared memory instead of a chain of L1/L2 reads
+    __shared__ uint64_t pre_s[BALL_SMEM_SUBSETS];
+    __shared__ uint32_t msk_s[BALL_SMEM_SUBSETS];
+    const bool staged = n_subsets <= BALL_SMEM_SUBSETS;
+    if (staged) {
+        for (int e = threadIdx.x; e < n_subsets; e += blockDim.x) {
+            pre_s[e] = __ldg(prefix + e);
+            msk_s[e] = __ldg(masks + e);
+        }
+        __syncthreads();
+    }
+    const uint64_t* pre = staged ? pre_s : prefix;
+    const uint32_t* msk = staged ? msk_s : masks;
     const uint64_t total = (uint64_t)(*count) * points;
     const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -163,20 +179,20 @@ k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, con
             if (lane == 0) {
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (__ldg(prefix + mid) <= j) lo = mid; else hi = mid - 1;
+                    if (pre[mid] <= j) lo = mid; else hi = mid - 1;
                 }
             }
             const int lo0 = __shfl_sync(0xffffffffu, lo, 0);
             const uint64_t q0 = __shfl_sync(0xffffffffu, q, 0), j0 = __shfl_sync(0xffffffffu, j, 0);
             if (act && q == q0 && j >= j0) {
                 lo = lo0;
-                while (lo + 1 < n_subsets && __ldg(prefix + lo + 1) <= j) ++lo;
+                while (lo + 1 < n_subsets && pre[lo + 1] <= j) ++lo;
             } else if (act) {
                 lo = 0;
                 hi = n_subsets - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (__ldg(prefix + mid) <= j) lo = mid; else hi = mid - 1;
+                    if (pre[mid] <= j) lo = mid; else hi = mid - 1;
                 }
             }
             if (!act) continue;
@@ -184,13 +200,13 @@ k_ball(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, con
             int hi = n_subsets - 1;   // last subset with prefix <= j
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(prefix + mid) <= j) lo = mid; else hi = mid - 1;
+                if (pre[mid] <= j) lo = mid; else hi = mid - 1;
             }
         }
         const uint64_t u = __ldg(cand + pend[q]);
-        const uint32_t S = __ldg(masks + lo);
+        const uint32_t S = msk[lo];
         if (fail && !fixes_possible(sp, __ldg(fail + pend[q]), S)) continue;
-        uint32_t local = (uint32_t)(j - __ldg(prefix + lo));
+        uint32_t local = (uint32_t)(j - pre[lo]);
         uint32_t m = S;
         uint64_t key = u;
         while (m) {
