@@ -116,13 +116,18 @@ struct RepairSmem {
     unsigned long long best[BATCH_MAX_POP];
     uint64_t fail[BATCH_MAX_POP];   // per pending slot: the constraints the candidate fails
     uint64_t pstart[BATCH_MAX_THREADS];   // first ball point of each thread's (candidate, subset) pair
+    uint32_t pq[BATCH_MAX_THREADS];       // the pair's pending slot
+    uint32_t pS[BATCH_MAX_THREADS];       // the pair's subset (parameter mask)
     uint64_t wsum[BATCH_MAX_THREADS / 32];
     int npend;
 };
 
 // Exclusive prefix sum of v over the CTA into start[threadIdx.x]; returns the total.  Every
-// thread calls it; blockDim.x is a multiple of 32.
-__device__ __forceinline__ uint64_t cta_exclusive_scan(uint64_t v, uint64_t* start, uint64_t* wsum) {
+// thread calls it; blockDim.x is a multiple of 32.  `put` runs between the scan's two barriers:
+// after every thread has left the reads of the previous scan's results, before any reads this
+// one's.
+template <class Put>
+__device__ __forceinline__ uint64_t cta_exclusive_scan(uint64_t v, uint64_t* start, uint64_t* wsum, Put put) {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = (int)(blockDim.x >> 5);
     uint64_t inc = v;
 #pragma unroll
@@ -139,6 +144,7 @@ __device__ __forceinline__ uint64_t cta_exclusive_scan(uint64_t v, uint64_t* sta
         total += x;
     }
     start[t] = base + inc - v;
+    put();
     __syncthreads();
     return total;
 }
@@ -292,23 +298,27 @@ __device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t*
         const uint64_t npairs = (uint64_t)np * (uint64_t)nsub;
         for (uint64_t p0 = 0; p0 < npairs; p0 += (uint64_t)nt) {
             uint64_t size = 0;
+            uint32_t q = 0, S = 0;
             if (p0 + t < npairs) {
-                const uint32_t q = (uint32_t)((p0 + t) / (uint64_t)nsub);
+                q = (uint32_t)((p0 + t) / (uint64_t)nsub);
                 const int s = (int)(p0 + t - (uint64_t)q * nsub);
-                if (fixes_possible(sp, rs.fail[q], __ldg(masks + s)))
+                S = __ldg(masks + s);
+                if (fixes_possible(sp, rs.fail[q], S))
                     size = (s + 1 < nsub ? __ldg(prefix + s + 1) : pts) - __ldg(prefix + s);
             }
-            const uint64_t T = cta_exclusive_scan(size, rs.pstart, rs.wsum);
+            const uint64_t T = cta_exclusive_scan(size, rs.pstart, rs.wsum, [&] {
+                rs.pq[t] = q;
+                rs.pS[t] = S;
+            });
             for (uint64_t g = t; g < T; g += (uint64_t)nt) {
                 int lo = 0, hi = nt - 1;   // the pair holding point g: the last with start <= g
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
                     if (rs.pstart[mid] <= g) lo = mid; else hi = mid - 1;
                 }
-                const uint32_t q = (uint32_t)((p0 + lo) / (uint64_t)nsub);
-                const int s = (int)(p0 + lo - (uint64_t)q * nsub);
+                const uint32_t q = rs.pq[lo];
                 const uint64_t u = cand[rs.pend[q]];
-                const uint32_t S = __ldg(masks + s);
+                const uint32_t S = rs.pS[lo];
                 uint32_t local = (uint32_t)(g - rs.pstart[lo]);
                 uint32_t m = S;
                 uint64_t key = u;
