@@ -111,6 +111,11 @@ struct EventSmem {
     uint8_t fresh[BATCH_MAX_POP];
 };
 
+// Ball points per key of the scan at which the in-CTA repair switches to the scan (4096-run
+// workload, 100 generations: 75.5 ms without the switch, 69.0-69.7 ms at 0.5-0.75, 70.8 at 0.35,
+// 90.9 at 0.25).
+constexpr double BATCH_BALL_VS_SCAN = 0.5;
+
 struct RepairSmem {
     int32_t pend[BATCH_MAX_POP];
     unsigned long long best[BATCH_MAX_POP];
@@ -172,22 +177,51 @@ __device__ void cta_scan_pass(const BatchSpace& bs, const unsigned long long* __
         vh[s] = ih;
     }
     uint32_t* tg = tags + t;
-    for (int64_t i = t; i < bs.nv; i += nt) {
-        const uint64_t key = __ldg(bs.keys + i);
+    // the plan in registers (the tag stores below would otherwise make the compiler reload it
+    // from the space record for every key)
+    const uint64_t* __restrict__ keys = bs.keys;
+    const int64_t nv = bs.nv;
+    uint32_t sh[BATCH_LUT_GROUPS], mk[BATCH_LUT_GROUPS];
+#pragma unroll
+    for (int g = 0; g < BATCH_LUT_GROUPS; ++g) {
+        sh[g] = g < ng ? (uint32_t)bs.lut_shift[g] : 0u;
+        mk[g] = g < ng ? bs.lut_mask[g] : 0u;
+    }
+    auto add_group = [&](int g, uint64_t key, uint32_t (&al)[S], uint32_t (&ah)[S]) {
+        const uint32_t e = ((uint32_t)(key >> sh[g]) & mk[g]) + 256u * (uint32_t)g;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const unsigned long long w = tab[(size_t)e * S + s];
+            al[s] += (uint32_t)w;
+            ah[s] += (uint32_t)(w >> 32);
+        }
+    };
+    // Each warp scans one contiguous segment of the keys as rows of 32 consecutive keys, one per
+    // lane: a lane's keys are 32 apart, so the key bits above the two lowest groups change
+    // rarely, and the sum of those groups is kept per lane until they do.
+    const uint32_t ushift = ng > 2 ? sh[2] : 64u;
+    uint64_t ucur = ~0ull;
+    uint32_t ul[S], uh[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) ul[s] = uh[s] = 0;
+    const int nw = nt >> 5, warp = t >> 5, lane = t & 31;
+    const int64_t seg = ((nv + nw - 1) / nw + 31) & ~(int64_t)31;
+    const int64_t end = min(nv, (int64_t)(warp + 1) * seg);
+    for (int64_t i = (int64_t)warp * seg + lane; i < end; i += 32) {
+        const uint64_t key = __ldg(keys + i);
+        if (ushift < 64u && (key >> ushift) != ucur) {
+            ucur = key >> ushift;
+#pragma unroll
+            for (int s = 0; s < S; ++s) ul[s] = uh[s] = 0;
+#pragma unroll
+            for (int g = 2; g < BATCH_LUT_GROUPS; ++g)
+                if (g < ng) add_group(g, key, ul, uh);
+        }
         uint32_t dl[S], dh[S];
 #pragma unroll
-        for (int s = 0; s < S; ++s) dl[s] = dh[s] = 0;
-#pragma unroll
-        for (int g = 0; g < BATCH_LUT_GROUPS; ++g) {
-            if (g >= ng) break;
-            const uint32_t e = ((uint32_t)(key >> bs.lut_shift[g]) & bs.lut_mask[g]) + 256u * (uint32_t)g;
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const unsigned long long w = tab[(size_t)e * S + s];
-                dl[s] += (uint32_t)w;
-                dh[s] += (uint32_t)(w >> 32);
-            }
-        }
+        for (int s = 0; s < S; ++s) { dl[s] = ul[s]; dh[s] = uh[s]; }
+        add_group(0, key, dl, dh);
+        if (ng > 1) add_group(1, key, dl, dh);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const uint32_t ml = (vl[s] - dl[s]) & 0x80808080u, mh = (vh[s] - dh[s]) & 0x80808080u;
@@ -286,6 +320,12 @@ __device__ void cta_repair(const BatchSpace& bs, const uint64_t* cand, uint64_t*
     for (int d = 1; d <= bs.dmax; ++d) {
         const int np = rs.npend;
         if (np == 0) break;
+        // Past radius 1 the scan takes over once the pending candidates' balls at this radius hold
+        // more points than BATCH_BALL_VS_SCAN times the keys the scan's passes read (one pass per
+        // 32 candidates): a pass costs the same for 1 candidate as for 32, a ball per candidate.
+        if (d > 1 && (double)np * (double)bs.total[d - 1] >
+                         BATCH_BALL_VS_SCAN * (double)((np + BATCH_LUT_CHUNK - 1) / BATCH_LUT_CHUNK) * (double)bs.nv)
+            break;
         for (int q = t; q < np; q += nt) rs.best[q] = ~0ull;
         __syncthreads();
         const uint64_t pts = bs.total[d - 1];
