@@ -101,6 +101,123 @@ __global__ void k_repair_init(const DevSpace* __restrict__ sp, const uint32_t* _
     }
 }
 
+// The table test and the small radii in one launch: a CTA per candidate (in turn) tests its
+// constraints (a lane per constraint), then, while it is invalid, every point at distance
+// d = 1 .. nr of it, the CTA's threads taking the points in turn (the radii's subset tables and a
+// point -> subset map in shared memory).  A candidate settled at some radius gets the smallest
+// valid key of that radius; the others are queued, with their failing constraints, for the
+// launches of the larger radii.  It replaces the table-test launch and the first nr radius
+// launches when those balls are small (whose launches cost more than their points).
+constexpr int NEAR_MAX_R = 3;          // radii in one launch
+constexpr int NEAR_MAX_POINTS = 4096;  // points of those radii together
+constexpr int NEAR_MAX_SUBSETS = 512;  // subsets of those radii together
+struct NearArgs {
+    int nr;                                // radii 1 .. nr
+    uint32_t total[NEAR_MAX_R];            // points at each radius
+    int nsub[NEAR_MAX_R];
+    const uint32_t* masks[NEAR_MAX_R];
+    const uint64_t* prefix[NEAR_MAX_R];
+};
+
+__global__ void __launch_bounds__(256, 4)
+k_ball_near(const DevSpace* __restrict__ sp, const uint32_t* __restrict__ tables, const __grid_constant__ NearArgs na,
+            const uint64_t* __restrict__ cand, int64_t n, uint64_t* __restrict__ out, uint8_t* __restrict__ dist,
+            int32_t* __restrict__ pend, uint32_t* __restrict__ count, unsigned long long* __restrict__ best,
+            uint32_t* __restrict__ status, uint64_t* __restrict__ fail) {
+    __shared__ uint16_t sub_of[NEAR_MAX_POINTS];   // point (radius-major) -> subset within its radius
+    __shared__ uint32_t start_of[NEAR_MAX_SUBSETS], mask_of[NEAR_MAX_SUBSETS];
+    __shared__ unsigned long long best_s;
+    __shared__ uint64_t fail_s;
+    const int t = threadIdx.x, lane = t & 31, nt = blockDim.x;
+    {   // the radii's subset tables: per radius, subsets after point offsets pbase, subset offsets sbase
+        uint32_t pbase = 0;
+        int sbase = 0;
+        for (int r = 0; r < na.nr; ++r) {
+            for (int e = t; e < na.nsub[r]; e += nt) {
+                const uint32_t a = (uint32_t)__ldg(na.prefix[r] + e), b = (uint32_t)__ldg(na.prefix[r] + e + 1);
+                start_of[sbase + e] = a;
+                mask_of[sbase + e] = __ldg(na.masks[r] + e);
+                for (uint32_t j = a; j < b; ++j) sub_of[pbase + j] = (uint16_t)e;
+            }
+            pbase += na.total[r];
+            sbase += na.nsub[r];
+        }
+    }
+    __syncthreads();
+    const int nc = sp->n_cons;
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const uint64_t c = cand[i];
+        if (!in_domain(sp, c)) {   // the same for every thread
+            if (t == 0) {
+                out[i] = c;
+                if (dist) dist[i] = 255;
+                atomicOr(status, ST_BAD_CANDIDATE);
+            }
+            continue;
+        }
+        if (t < 32) {
+            const bool f0 = lane < nc && !cons_at(sp, tables, c, lane);
+            const bool f1 = lane + 32 < nc && !cons_at(sp, tables, c, lane + 32);
+            const uint64_t f = (uint64_t)__ballot_sync(0xffffffffu, f0) | ((uint64_t)__ballot_sync(0xffffffffu, f1) << 32);
+            if (lane == 0) {
+                fail_s = f;
+                best_s = NONE;
+            }
+        }
+        __syncthreads();
+        const uint64_t f = fail_s;
+        int found = 0;
+        if (!f) {
+            found = 1;
+            if (t == 0) {
+                out[i] = c;
+                if (dist) dist[i] = 0;
+            }
+        }
+        uint32_t pbase = 0;
+        int sbase = 0;
+        for (int r = 0; r < na.nr && !found; ++r) {
+            for (uint32_t j = t; j < na.total[r]; j += nt) {
+                const int sl = sub_of[pbase + j];
+                const uint32_t S = mask_of[sbase + sl];
+                if (!fixes_possible(sp, f, S)) continue;
+                uint32_t local = j - start_of[sbase + sl];
+                uint32_t m = S;
+                uint64_t key = c;
+                while (m) {
+                    const int k = 31 - __clz(m);
+                    m &= ~(1u << k);
+                    uint32_t a;
+                    local = div_alt(sp, k, local, &a);
+                    const uint32_t uk = (uint32_t)field(sp, c, k);
+                    key = (key & ~sp->fmask[k]) | ((uint64_t)(a < uk ? a : a + 1u) << sp->off[k]);
+                }
+                if (key < *(volatile unsigned long long*)&best_s && valid_changed(sp, tables, key, S))
+                    atomicMin(&best_s, (unsigned long long)key);
+            }
+            __syncthreads();
+            const unsigned long long b = best_s;
+            __syncthreads();   // read by every thread before the next radius can lower it
+            if (b != NONE) {
+                found = 1;
+                if (t == 0) {
+                    out[i] = b;
+                    if (dist) dist[i] = (uint8_t)(r + 1);
+                }
+            }
+            pbase += na.total[r];
+            sbase += na.nsub[r];
+        }
+        if (!found && t == 0) {   // for the larger radii
+            if (fail) fail[i] = f;
+            const uint32_t slot = atomicAdd(count, 1u);
+            pend[slot] = (int32_t)i;
+            best[slot] = NONE;
+        }
+        __syncthreads();   // fail_s and best_s are rewritten for the next candidate
+    }
+}
+
 // The resolve step of one radius, run by the last CTA of the ball kernel to finish (an atomic
 // ticket after a fence; nothing waits): candidates whose ball held a valid point are settled, the
 // others are queued for the next radius.
@@ -555,15 +672,40 @@ ct_status repair_launch(const ct_space* s, const RepairPtrs& p, int dmax, const 
                         uint64_t* d_out, uint8_t* d_dist, cudaStream_t st) {
     const int sms = sm_count();
     const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
-    const unsigned gi = (unsigned)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sms * 8);   // a warp per candidate
-    k_repair_init<<<gi, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, p.pend[0], p.cnt[0], p.best[0],
-                                      s->status.p, p.fail);
+    // the radii whose balls are small together go with the table test into one launch
+    NearArgs na{};
+    {
+        uint64_t pts = 0;
+        int subs = 0;
+        for (int d = 1; d <= std::min(dmax, NEAR_MAX_R) && d <= (int)s->balls.size(); ++d) {
+            const BallRadius& br = s->balls[d - 1];
+            if (!br.d_masks.p || !br.d_prefix.p || pts + br.total > (uint64_t)NEAR_MAX_POINTS ||
+                subs + (int)br.masks.size() > NEAR_MAX_SUBSETS)
+                break;
+            na.total[na.nr] = (uint32_t)br.total;
+            na.nsub[na.nr] = (int)br.masks.size();
+            na.masks[na.nr] = br.d_masks.p;
+            na.prefix[na.nr] = br.d_prefix.p;
+            ++na.nr;
+            pts += br.total;
+            subs += (int)br.masks.size();
+        }
+    }
+    if (na.nr > 0) {
+        const unsigned gn = (unsigned)std::min<int64_t>(n, (int64_t)sms * 8);   // a CTA per candidate in turn
+        k_ball_near<<<gn, 256, 0, st>>>(s->d, s->tables.p, na, d_cand, n, d_out, d_dist, p.pend[0], p.cnt[0],
+                                        p.best[0], s->status.p, p.fail);
+    } else {
+        const unsigned gi = (unsigned)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)sms * 8);   // a warp per candidate
+        k_repair_init<<<gi, 256, 0, st>>>(s->d, s->tables.p, d_cand, n, d_out, d_dist, p.pend[0], p.cnt[0], p.best[0],
+                                          s->status.p, p.fail);
+    }
     count_launch();
     uint64_t fs_min_avg = BALL_FS_MIN_AVG;   // CATUNE_BALL_FS_MIN_AVG overrides it (tests)
     if (const char* env = getenv("CATUNE_BALL_FS_MIN_AVG")) fs_min_avg = strtoull(env, nullptr, 10);
     const uint64_t dual_min_avg = std::min<uint64_t>(fs_min_avg, BALL_DUAL_MIN_AVG);
     int cur = 0;
-    for (int d = 1; d <= dmax; ++d) {
+    for (int d = na.nr + 1; d <= dmax; ++d) {
         const BallRadius& br = s->balls[d - 1];
         // the kernel's last CTA resolves this radius: settles, and queues the rest for the next
         const BallNext nx{p.done, d, d_out, d_dist, p.pend[cur ^ 1], p.cnt[cur ^ 1], p.best[cur ^ 1]};
