@@ -675,11 +675,14 @@ ct_status repair_launch(const ct_space* s, const RepairPtrs& p, int dmax, const 
     // the radii whose balls are small together go with the table test into one launch
     NearArgs na{};
     {
+        uint64_t near_points = NEAR_MAX_POINTS;   // CATUNE_BALL_NEAR_POINTS lowers it (0: off; tests)
+        if (const char* env = getenv("CATUNE_BALL_NEAR_POINTS"))
+            near_points = std::min<uint64_t>(near_points, strtoull(env, nullptr, 10));
         uint64_t pts = 0;
         int subs = 0;
         for (int d = 1; d <= std::min(dmax, NEAR_MAX_R) && d <= (int)s->balls.size(); ++d) {
             const BallRadius& br = s->balls[d - 1];
-            if (!br.d_masks.p || !br.d_prefix.p || pts + br.total > (uint64_t)NEAR_MAX_POINTS ||
+            if (!br.d_masks.p || !br.d_prefix.p || pts + br.total > near_points ||
                 subs + (int)br.masks.size() > NEAR_MAX_SUBSETS)
                 break;
             na.total[na.nr] = (uint32_t)br.total;

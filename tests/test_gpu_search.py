@@ -35,16 +35,23 @@ def test_lookup(pairs, name):
     assert np.array_equal(rank.cpu().numpy(), p.O.lookup(p.okeys, c))
 
 
-@pytest.mark.parametrize("filtered", [False, True])
+def _ball_path(path, monkeypatch):
+    """near: the default (table test and small radii in one launch); point: every radius by the
+    per-point kernel; filtered: every radius by the filtered warp-per-subset kernel."""
+    if path in ("point", "filtered"):
+        monkeypatch.setenv("CATUNE_BALL_NEAR_POINTS", "0")
+    if path == "filtered":
+        monkeypatch.setenv("CATUNE_BALL_FS_MIN_AVG", "0")
+
+
+@pytest.mark.parametrize("path", ["near", "point", "filtered"])
 @pytest.mark.parametrize("name", ["tiny", "medium"])
 @pytest.mark.parametrize("mode,radius", [(0, 0), (1, 0), (2, 1), (2, 2), (2, 3)])
-def test_repair(pairs, name, mode, radius, filtered, monkeypatch):
-    """Every repair mode against the oracle, with the ball search per point and with the filtered
-    warp-per-subset search forced on every radius."""
-    if filtered:
-        if mode == 1:
-            pytest.skip("no ball search")
-        monkeypatch.setenv("CATUNE_BALL_FS_MIN_AVG", "0")
+def test_repair(pairs, name, mode, radius, path, monkeypatch):
+    """Every repair mode against the oracle, by each path of the ball search."""
+    if path != "near" and mode == 1:
+        pytest.skip("no ball search")
+    _ball_path(path, monkeypatch)
     p = pairs[name]
     c = _cands(p, 5 + mode + radius)
     p.sp.set_repair_mode(mode, radius)
@@ -210,12 +217,11 @@ def test_large_repair_by_groups(oracle_mod, mode):   # mode 0 runs the filtered 
     assert np.array_equal(dist.cpu().numpy(), (da.astype(np.int64) + db).astype(np.uint8))
 
 
-@pytest.mark.parametrize("filtered", [False, True])
-def test_ball_search_spaces(oracle_mod, scan_spaces, filtered, monkeypatch):
+@pytest.mark.parametrize("path", ["near", "point", "filtered"])
+def test_ball_search_spaces(oracle_mod, scan_spaces, path, monkeypatch):
     """Ball search up to radius 3 on spaces with single-value parameters, keys wider than 32 bits
-    and a 300-value parameter (not filtered: more than 64 values), per point and filtered."""
-    if filtered:
-        monkeypatch.setenv("CATUNE_BALL_FS_MIN_AVG", "0")
+    and a 300-value parameter (not filtered: more than 64 values), by each path."""
+    _ball_path(path, monkeypatch)
     for sd, osp, okeys, sp in scan_spaces:
         cand = oracle_mod.pack(osp, W.uniform_tuples(sd, 96, seed=7))
         sp.set_repair_mode(2, 3)
