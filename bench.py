@@ -893,6 +893,42 @@ def run_scan(args):
     return 0
 
 
+def run_generation(args):
+    """One single-run generation at pop 256 on --workload, per optimizer: generations 0 to 4
+    untimed (the step graph is captured after the first eager steps), then --steps generations
+    timed with CUDA events on the launching stream."""
+    import torch
+    from paper_2606_28372_b300 import build as B
+    B.build()
+    from paper_2606_28372_b300 import catune as ct
+    from paper_2606_28372_b300 import workloads as W
+    dev = torch.device("cuda", 0)
+    sd = W.SPACES[args.workload]()
+    sp = ct.Space.from_def(sd)
+    nv = sp.build()
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234)
+    table = torch.exp(torch.randn(nv, generator=g, device=dev, dtype=torch.float32))
+    sp.set_fitness(table)
+    res = {}
+    for kind in ("de", "pso", "ga"):
+        o = ct.Opt(sp, kind, POP, 7)
+        for gen in range(5):
+            o.step(gen)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for gen in range(5, 5 + args.steps):
+            o.step(gen)
+        e1.record()
+        torch.cuda.synchronize()
+        res[kind] = {"ms_per_generation": e0.elapsed_time(e1) / max(1, args.steps)}
+        del o
+    print(json.dumps({"mode": "generation", "workload": args.workload, "pop": POP, "steps": args.steps,
+                      "results": res}))
+    return 0
+
+
 def run_repair(args):
     """Repair alone on --workload: calls of 256 uniform random tuples and 256 DE-like perturbations
     of valid keys, per radius cap of the ball search (--radius; the cost-model radius by default),
@@ -1212,7 +1248,7 @@ if __name__ == "__main__":
                          "numbers are never bench values)")
     ap.add_argument("--mode", default="step",
                     choices=["step", "scan", "repair", "aware", "variants", "batched", "rules", "surrogate",
-                             "surrogate_step", "onepct"],
+                             "surrogate_step", "onepct", "generation"],
                     help="scan: only the exhaustive repair scan (scan-only repair of 1 to 32 uniform candidates); "
                          "repair: only repair calls of 256 candidates on --workload (--kind, --radius); "
                          "aware: only the constraint-aware vs non-aware comparison over the density ladder; "
@@ -1220,7 +1256,8 @@ if __name__ == "__main__":
                          "comparison; rules: only the paper's repair rules on --workload; surrogate: only the "
                          "surrogate-vs-plain comparison on the large space; surrogate_step: milliseconds per "
                          "generation of plain, judged and forced-screening DE on --workload; onepct: the 1 %% "
-                         "criterion (table census, plain against surrogate-screened runs)")
+                         "criterion (table census, plain against surrogate-screened runs); generation: device "
+                         "milliseconds per single-run generation of DE, PSO and GA at pop 256 on --workload")
     ap.add_argument("--workload", default="large", choices=["large", "large_slice"],
                     help="large_slice: the same kernels on a 146M-key slice, for hardware-counter captures")
     ap.add_argument("--kind", default="both", choices=["both", "perturbed", "uniform"],
@@ -1247,4 +1284,6 @@ if __name__ == "__main__":
         sys.exit(run_rules(a))
     if a.mode == "repair":
         sys.exit(run_repair(a))
+    if a.mode == "generation":
+        sys.exit(run_generation(a))
     sys.exit(run_scan(a) if a.mode == "scan" else run_ours(a))
