@@ -641,8 +641,8 @@ static uint64_t pattern_tile(uint64_t F) {
 // after scanning the whole tile's counts for their offsets.  Small CTAs keep the output the SMs
 // write at one time short and even out the uneven child counts: the large space's last level
 // (1.14M parents, scan tiles of 64) emits in 0.778 ms with 8 parents per CTA against 0.877 ms
-// with 64 (8 per warp); 4 and 2 parents per CTA, with 2 and 4 warps sharing a parent's rows, took
-// 1.03 and 1.73 ms.
+// with 64 (8 per warp) and 0.810 ms with 16 (2 per warp); 4 and 2 parents per CTA, with 2 and 4
+// warps sharing a parent's rows, took 1.03 and 1.73 ms.
 constexpr uint64_t PE_SUB = 8;
 static uint64_t emit_sub(uint64_t pt) { return pt < PE_SUB ? pt : PE_SUB; }
 
