@@ -481,7 +481,8 @@ def run_ours(args):
     rr = repair_rates(sp, sd, torch, ct, dev, scan=args.full)
     also.update({k: rr[k] for k in ("repaired_candidates_per_s_perturbed", "repaired_candidates_per_s_uniform")})
     br = batched_runs(torch, ct, W, dev)
-    also.update({k: br[k] for k in ("batched_runs_per_s", "plain_runs_per_s_same_runs", "batched_vs_plain")})
+    also.update({k: br[k] for k in ("batched_runs_per_s", "batched_runs_per_s_launch_per_generation",
+                                  "plain_runs_per_s_same_runs", "batched_vs_plain")})
 
     sub = None
     if args.full:
@@ -690,6 +691,19 @@ def batched_runs(torch, ct, W, dev, n_runs=4096, gens=100, plain_sample=48):
     ms = e0.elapsed_time(e1)
     batched_launches = ct.launch_count() - l0
     res = b.results()
+    # the same runs with one persistent launch per generation (a graph of `gens` kernel nodes)
+    b.set_gens_per_launch(1)
+    b.reset()
+    b.run_graph(gens)                                  # capture + first replay (warm-up)
+    torch.cuda.synchronize()
+    b.reset()
+    e0.record()
+    b.run_graph(gens)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_per_gen_launch = e0.elapsed_time(e1)
+    same_per_gen = bool(np.array_equal(b.results()["best_key"], res["best_key"]))
+    b.set_gens_per_launch(0)
     hits = res["hit_evals"][res["hit_evals"] >= 0]
     # the same runs, one at a time (plain path: per-generation kernels, graph replay per run)
     torch.cuda.synchronize()
@@ -716,6 +730,8 @@ def batched_runs(torch, ct, W, dev, n_runs=4096, gens=100, plain_sample=48):
         m = float(np.median(h))
         return m if np.isfinite(m) else None
     return {"batched_runs_per_s": batched, "batched_ms_for_all_runs": ms, "batched_generations": gens,
+            "batched_runs_per_s_launch_per_generation": n_runs / (ms_per_gen_launch / 1000.0),
+            "batched_launch_per_generation_same_results": same_per_gen,
             "evals_to_1pct_same_runs": {"runs": plain_sample, "plain_median": med(plain_hits),
                                         "batched_median": med(same),
                                         "identical": bool(np.array_equal(np.asarray(plain_hits), np.asarray(same))),

@@ -461,6 +461,12 @@ ct_status ct_batch_trace(const ct_batch *batch, float *best_fit, uint64_t *cost,
 /* Launch shape of the persistent kernel: threads per CTA (64, 128 or 256) and
  * CTAs per SM (0 = 4). Results do not depend on it. */
 ct_status ct_batch_set_launch(ct_batch *batch, int32_t threads, int32_t ctas_per_sm);
+/* Generations per launch of ct_batch_run_graph: 0 (the default) advances every run through all
+ * `count` generations in one launch; k > 0 captures launches of k generations each (k = 1: one
+ * persistent launch per generation, `count` kernel nodes in the graph).  Results do not depend
+ * on it; with one launch per generation, every generation waits for its slowest run.  Drops
+ * captured graphs. */
+ct_status ct_batch_set_gens_per_launch(ct_batch *batch, int32_t gens);
 /* Autotuner: times `gens` generations for each launch shape from the reset state,
  * requires every shape to end in the same state, keeps the fastest and resets the
  * batch.  cache_path (nullable): a JSON-lines file; a stored result for the same

@@ -114,6 +114,7 @@ _SIGS = {
     "ct_batch_events": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_batch_trace": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "ct_batch_set_launch": [C.c_void_p, C.c_int32, C.c_int32],
+    "ct_batch_set_gens_per_launch": [C.c_void_p, C.c_int32],
     "ct_batch_autotune": [C.c_void_p, C.c_char_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                           C.POINTER(C.c_float), C.c_void_p],
     "ct_opt_last_generation": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -552,6 +553,9 @@ class Batch:
 
     def reset(self):
         check(lib().ct_batch_reset(self.h))
+
+    def set_gens_per_launch(self, gens):
+        check(lib().ct_batch_set_gens_per_launch(self.h, gens))
 
     def set_launch(self, threads, ctas_per_sm):
         check(lib().ct_batch_set_launch(self.h, threads, ctas_per_sm))

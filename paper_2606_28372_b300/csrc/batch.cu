@@ -575,6 +575,7 @@ struct ct_batch {
     std::vector<BatchRun> brun;
     uint64_t n_pop = 0, n_pn = 0, n_n = 0, n_memo = 0;
     int threads = 256, ctas_per_sm = 0, sms = 148;
+    uint32_t gens_per_launch = 0;   // run_graph: generations per launch (0: all of them in one)
     std::map<uint32_t, cudaGraphExec_t> graphs;
     uint32_t generation = 0;      // host mirror (generations launched)
     ~ct_batch() {
@@ -806,6 +807,14 @@ ct_status ct_batch_create(ct_space* const* spaces, int32_t n_spaces, const ct_ba
 
 void ct_batch_destroy(ct_batch* b) { delete b; }
 
+ct_status ct_batch_set_gens_per_launch(ct_batch* b, int32_t gens) {
+    if (!b || gens < 0) { set_error("bad argument"); return CT_ERR_INVALID_ARG; }
+    b->gens_per_launch = (uint32_t)gens;
+    for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
+    b->graphs.clear();
+    return CT_OK;
+}
+
 ct_status ct_batch_set_launch(ct_batch* b, int32_t threads, int32_t ctas_per_sm) {
     if (!b || (threads != 64 && threads != 128 && threads != 256) || ctas_per_sm < 0 || ctas_per_sm > 16) {
         set_error("threads must be 64, 128 or 256; ctas_per_sm in [0, 16]");
@@ -839,7 +848,8 @@ ct_status ct_batch_run_graph(ct_batch* b, uint32_t count, ct_stream stream) {
         }
         ct_status e = CT_OK;
         const uint64_t c0 = ct_launch_count();
-        e = batch_launch(b, cap, count);
+        const uint32_t per = b->gens_per_launch ? b->gens_per_launch : count;
+        for (uint32_t g0 = 0; g0 < count && e == CT_OK; g0 += per) e = batch_launch(b, cap, std::min(per, count - g0));
         count_launch(0 - (ct_launch_count() - c0));
         cudaGraph_t g;
         cudaError_t ce = cudaStreamEndCapture(cap, &g);
@@ -853,7 +863,7 @@ ct_status ct_batch_run_graph(ct_batch* b, uint32_t count, ct_stream stream) {
         it = b->graphs.emplace(count, ex).first;
     }
     CT_TRY_CUDA(cudaGraphLaunch(it->second, st));
-    count_launch(1);
+    count_launch(b->gens_per_launch ? (count + b->gens_per_launch - 1) / b->gens_per_launch : 1);
     b->generation += count;
     return CT_OK;
 }

@@ -38,7 +38,7 @@ def _single(pair, kind, pop, seed, target, gens):
     return from_dev_u64(k), f.cpu().numpy(), o.best()
 
 
-@pytest.mark.parametrize("mode", ["step", "graph", "mixed"])
+@pytest.mark.parametrize("mode", ["step", "graph", "mixed", "graph_per_generation"])
 def test_batch_equals_single_runs(spaces, mode):
     from paper_2606_28372_b300 import catune as ct
     runs = _runs(spaces, 24)
@@ -50,6 +50,11 @@ def test_batch_equals_single_runs(spaces, mode):
     elif mode == "graph":
         b.run_graph(1)
         b.run_graph(gens - 1)
+    elif mode == "graph_per_generation":   # one persistent launch per generation, captured
+        b.set_gens_per_launch(1)
+        b.run_graph(5)
+        b.set_gens_per_launch(3)
+        b.run_graph(gens - 5)
     else:   # launches of 1, 4 and 3 generations in turn
         for _ in range(3):
             b.step()
