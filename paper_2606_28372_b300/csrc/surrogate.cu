@@ -119,15 +119,37 @@ __global__ void k_mlp_l1(const float* __restrict__ p, MlpOff o, int D, int H, in
 // bias gradients, by the threads of column 0);  EPI 3: out = acc + bias[n].
 constexpr int OG_T = 16, OG_K = 64, OG_THREADS = OG_T * OG_T, OG_PER = OG_T * OG_K / OG_THREADS;
 
+// One product's arguments (see k_ogemm).
+struct OgArgs {
+    int M, Nn, K;
+    const float* A;
+    long sam, sak;
+    const float* Bm;
+    long sbn, sbk;
+    const float* bias;
+    const float* zmask;
+    float* out;
+    float* out2;
+    long ldc;
+    float* rowsum;
+};
+
+// The output tile (bx, by) of one ordered product.
 template <int EPI, bool BF16>
-__global__ void __launch_bounds__(OG_THREADS)
-k_ogemm(int M, int Nn, int K, const float* __restrict__ A, long sam, long sak, const float* __restrict__ Bm, long sbn,
-        long sbk, const float* __restrict__ bias, const float* __restrict__ zmask, float* __restrict__ out,
-        float* __restrict__ out2, long ldc, float* __restrict__ rowsum) {
+__device__ __forceinline__ void ogemm_tile(const OgArgs& g, int bx, int by) {
+    const int M = g.M, Nn = g.Nn, K = g.K;
+    const float* __restrict__ A = g.A;
+    const float* __restrict__ Bm = g.Bm;
+    const long sam = g.sam, sak = g.sak, sbn = g.sbn, sbk = g.sbk, ldc = g.ldc;
+    const float* __restrict__ bias = g.bias;
+    const float* __restrict__ zmask = g.zmask;
+    float* __restrict__ out = g.out;
+    float* __restrict__ out2 = g.out2;
+    float* __restrict__ rowsum = g.rowsum;
     __shared__ float As[OG_T][OG_K + 1], Bs[OG_T][OG_K + 1];
     const int tx = threadIdx.x % OG_T, ty = threadIdx.x / OG_T;
-    const int m0 = blockIdx.y * OG_T, n0 = blockIdx.x * OG_T;
-    const bool do_rs = EPI == 2 && rowsum && blockIdx.x == 0 && tx == 0;
+    const int m0 = by * OG_T, n0 = bx * OG_T;
+    const bool do_rs = EPI == 2 && rowsum && bx == 0 && tx == 0;
     // the elements this thread stages, e = threadIdx.x + q * OG_THREADS: consecutive threads run
     // along the operand's unit stride (k for a row-major operand, the row otherwise), so that the
     // loads are contiguous; the shared rows are padded, so either order stores without conflicts
@@ -186,6 +208,32 @@ k_ogemm(int M, int Nn, int K, const float* __restrict__ A, long sam, long sak, c
         out[idx] = acc;
     } else {
         out[idx] = __fadd_rn(acc, bias[n]);
+    }
+}
+
+
+template <int EPI, bool BF16>
+__global__ void __launch_bounds__(OG_THREADS)
+k_ogemm(int M, int Nn, int K, const float* __restrict__ A, long sam, long sak, const float* __restrict__ Bm, long sbn,
+        long sbk, const float* __restrict__ bias, const float* __restrict__ zmask, float* __restrict__ out,
+        float* __restrict__ out2, long ldc, float* __restrict__ rowsum) {
+    const OgArgs g{M, Nn, K, A, sam, sak, Bm, sbn, sbk, bias, zmask, out, out2, ldc, rowsum};
+    ogemm_tile<EPI, BF16>(g, blockIdx.x, blockIdx.y);
+}
+
+// The backward products that do not wait for one another, in one launch (blockIdx.z picks the
+// product; each keeps its own tiles): the delta through a layer's weights (EPI 1, bf16 weights)
+// beside the weight gradients (EPI 2) that need only the deltas already computed.  Each output
+// is computed exactly as by k_ogemm.
+__global__ void __launch_bounds__(OG_THREADS)
+k_ogemm_bwd(const OgArgs dl, const OgArgs gw0, const OgArgs gw1, int n_gw) {
+    const int z = blockIdx.z;
+    if (z == 0) {
+        if ((int)blockIdx.x * OG_T < dl.Nn && (int)blockIdx.y * OG_T < dl.M) ogemm_tile<1, true>(dl, blockIdx.x, blockIdx.y);
+    } else {
+        const OgArgs& g = z == 1 ? gw0 : gw1;
+        if (z <= n_gw && (int)blockIdx.x * OG_T < g.Nn && (int)blockIdx.y * OG_T < g.M)
+            ogemm_tile<2, false>(g, blockIdx.x, blockIdx.y);
     }
 }
 
@@ -462,31 +510,30 @@ static ct_status mlp_grad_impl(const float* p, int D, int H, int N, const int32_
     const float scale = 2.0f / (float)B;
     k_mlp_gout<<<(B + 255) / 256, 256, 0, st>>>(pred, y, B, scale, w.gout);
     k_mlp_d3<<<grid_for((size_t)B * H), 256, 0, st>>>(p, o, H, B, w.gout, w.z3, w.d3);
-    const dim3 gb = og_grid(B, H);
-    // deltas through W3 and W2 (transposed: B(n=i, k=j) = W[j*H + i])
-    k_ogemm<1, true><<<gb, OG_THREADS, 0, st>>>(B, H, H, w.d3, H, 1, p + o.W3, 1, H, nullptr, w.z2, w.d2, nullptr, H,
-                                                nullptr);
-    k_ogemm<1, true><<<gb, OG_THREADS, 0, st>>>(B, H, H, w.d2, H, 1, p + o.W2, 1, H, nullptr, w.z1, w.d1, nullptr, H,
-                                                nullptr);
-    // weight gradients: sums over samples, ascending; the bias gradients are the same sums of the
-    // deltas alone (the row sums of A)
-    const dim3 gw = og_grid(H, H);
-    k_ogemm<2, false><<<gw, OG_THREADS, 0, st>>>(H, H, B, w.d3, 1, H, w.h2, 1, H, nullptr, nullptr, grad + o.W3, nullptr,
-                                                 H, grad + o.b3);
-    k_ogemm<2, false><<<gw, OG_THREADS, 0, st>>>(H, H, B, w.d2, 1, H, w.h1, 1, H, nullptr, nullptr, grad + o.W2, nullptr,
-                                                 H, grad + o.b2);
-    k_ogemm<2, false><<<og_grid(1, H), OG_THREADS, 0, st>>>(1, H, B, w.gout, 0, 1, w.h3, 1, H, nullptr, nullptr,
-                                                            grad + o.W4, nullptr, H, grad + o.b4);
+    // Deltas through W3 and W2 (transposed: B(n=i, k=j) = W[j*H + i]) and the weight gradients
+    // (sums over samples, ascending; the bias gradients are the same sums of the deltas alone,
+    // the row sums of A).  Products that need only deltas already computed share a launch: the
+    // delta through W3 with the gradients of W3 and W4, then the delta through W2 with the
+    // gradient of W2.
+    const OgArgs d2a{B, H, H, w.d3, H, 1, p + o.W3, 1, H, nullptr, w.z2, w.d2, nullptr, H, nullptr};
+    const OgArgs gw3{H, H, B, w.d3, 1, H, w.h2, 1, H, nullptr, nullptr, grad + o.W3, nullptr, H, grad + o.b3};
+    const OgArgs gw4{1, H, B, w.gout, 0, 1, w.h3, 1, H, nullptr, nullptr, grad + o.W4, nullptr, H, grad + o.b4};
+    const OgArgs d1a{B, H, H, w.d2, H, 1, p + o.W2, 1, H, nullptr, w.z1, w.d1, nullptr, H, nullptr};
+    const OgArgs gw2{H, H, B, w.d2, 1, H, w.h1, 1, H, nullptr, nullptr, grad + o.W2, nullptr, H, grad + o.b2};
+    const dim3 gb = og_grid(B, H), gw = og_grid(H, H);
+    const dim3 gz(std::max(gb.x, gw.x), std::max(gb.y, gw.y), 1);
+    k_ogemm_bwd<<<dim3(gz.x, gz.y, 3), OG_THREADS, 0, st>>>(d2a, gw3, gw4, 2);
+    k_ogemm_bwd<<<dim3(gz.x, gz.y, 2), OG_THREADS, 0, st>>>(d1a, gw2, gw2, 1);
     int JB = 2;   // hidden units per CTA: few, so that the H / JB CTAs reach many SMs
     while (JB > 1 && (JB * N > 1024 || w1grad_smem(JB, D, N) > 48 * 1024)) JB >>= 1;
     if (JB * N <= 1024 && w1grad_smem(JB, D, N) <= 48 * 1024) {
         k_mlp_w1grad<<<(H + JB - 1) / JB, JB * N, w1grad_smem(JB, D, N), st>>>(w.d1, feats, B, N, D, H, JB, grad + o.W1,
                                                                            grad + o.b1);
-        count_launch(8);
+        count_launch(5);
     } else {
         k_mlp_w1grad_wide<<<grid_for((size_t)H * D, 64), 64, 0, st>>>(w.d1, feats, param_of, B, N, D, H, grad + o.W1);
         k_colsum<<<(H + 127) / 128, 128, 0, st>>>(w.d1, H, B, grad + o.b1);
-        count_launch(9);
+        count_launch(6);
     }
     CT_TRY_CUDA(cudaGetLastError());
     return CT_OK;
