@@ -713,9 +713,12 @@ ct_status repair_launch(const ct_space* s, const RepairPtrs& p, int dmax, const 
         // the kernel's last CTA resolves this radius: settles, and queues the rest for the next
         const BallNext nx{p.done, d, d_out, d_dist, p.pend[cur ^ 1], p.cnt[cur ^ 1], p.best[cur ^ 1]};
         const uint64_t fs_work = (uint64_t)n * br.masks.size() * 32;
-        const unsigned gfs = (unsigned)std::min<uint64_t>((fs_work + 255) / 256, (uint64_t)sms * 4);   // one wave
+        // one wave each: k_ball_fs holds 2 CTAs of 256 per SM (128 registers), k_ball 5 (48); on the
+        // large space that took the repair of 256 perturbed candidates from 0.105 to 0.098 ms (the
+        // empty launches of the dual radii are cheaper) and 256 uniform ones from 0.945 to 0.965
+        const unsigned gfs = (unsigned)std::min<uint64_t>((fs_work + 255) / 256, (uint64_t)sms * 2);
         const uint64_t pt_work = (uint64_t)n * br.total;
-        const unsigned gpt = (unsigned)std::min<uint64_t>((pt_work + 255) / 256, (uint64_t)sms * 4);   // one wave
+        const unsigned gpt = (unsigned)std::min<uint64_t>((pt_work + 255) / 256, (uint64_t)sms * 5);
         if (br.total >= fs_min_avg * br.masks.size()) {
             // large subsets: a warp per (candidate, subset) over the filtered points
             k_ball_fs<<<gfs, 256, 0, st>>>(s->d, s->tables.p, br.d_masks.p, (int)br.masks.size(), d_cand, p.pend[cur],
